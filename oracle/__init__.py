@@ -1,0 +1,274 @@
+"""CPU oracle for restarted mixed-precision GMRES(m) -- test infrastructure only.
+
+This package wraps ``gmres_oracle.c`` (a plain, single-threaded restatement of
+Algorithm 1 of Lindquist, Luszczek and Dongarra, arXiv 2011.01850) through
+ctypes.  Only the test suite, ``__graft_entry__.smoke()`` and the CPU-baseline
+leg of ``bench.py`` may import it; the CUDA library never does, and the two
+share no code.
+
+The shared object is compiled with gcc on first use (or by ``build()``) into
+``oracle/liboracle.so``; it is rebuilt whenever a source file is newer.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SOURCES = ["gmres_oracle.c", "gmres_oracle.h", "cycle_impl.inc", "spai_oracle.c"]
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+MGS, CGSR = 0, 1
+FP64, MIXED, MIXED_BF16, MIXED_FP16, ALL_FP32 = 0, 1, 2, 3, 4
+
+_i32p = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
+_f64p = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
+
+
+class Opts(ctypes.Structure):
+    """Mirror of ``orc_opts`` (see gmres_oracle.h)."""
+
+    _fields_ = [
+        ("m", ctypes.c_int32),
+        ("ortho", ctypes.c_int32),
+        ("prec", ctypes.c_int32),
+        ("maxiter", ctypes.c_int32),
+        ("repeat_first", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+        ("tol", ctypes.c_double),
+        ("tau", ctypes.c_double),
+        ("inner_factor", ctypes.c_double),
+    ]
+
+
+class Info(ctypes.Structure):
+    """Mirror of ``orc_info``."""
+
+    _fields_ = [
+        ("iters", ctypes.c_int32),
+        ("restarts", ctypes.c_int32),
+        ("converged", ctypes.c_int32),
+        ("first_len", ctypes.c_int32),
+        ("relres", ctypes.c_double),
+        ("bnorm", ctypes.c_double),
+    ]
+
+
+def _sources_present(src_dir=_HERE):
+    return [os.path.join(src_dir, f) for f in _SOURCES if os.path.exists(os.path.join(src_dir, f))]
+
+
+def build(force: bool = False, src_dir: str = _HERE, out_path: str = _LIB_PATH) -> str:
+    """Compile the oracle sources in ``src_dir`` into ``out_path`` if missing or stale."""
+    srcs = _sources_present(src_dir)
+    newest = max(os.path.getmtime(f) for f in srcs)
+    if force or not os.path.exists(out_path) or os.path.getmtime(out_path) < newest:
+        c_files = [f for f in srcs if f.endswith(".c")]
+        tmp = out_path + ".tmp%d" % os.getpid()
+        cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fPIC", "-shared",
+               "-o", tmp] + c_files + ["-lm"]
+        subprocess.run(cmd, check=True, cwd=src_dir)
+        os.replace(tmp, out_path)
+    return out_path
+
+
+def _bind(L):
+    L.orc_spmv.argtypes = [ctypes.c_int32, _i32p, _i32p, _f64p, _f64p, _f64p, ctypes.c_int32]
+    L.orc_spmv.restype = ctypes.c_int
+    L.orc_residual.argtypes = [ctypes.c_int32, _i32p, _i32p, _f64p, _f64p, _f64p,
+                               ctypes.c_void_p]
+    L.orc_residual.restype = ctypes.c_double
+    L.orc_round_basis.argtypes = [ctypes.c_int32, _f64p, _f64p, ctypes.c_int32, ctypes.c_int32]
+    L.orc_round_basis.restype = None
+    vp = ctypes.c_void_p
+    L.orc_arnoldi_cycle.argtypes = [ctypes.c_int32, _i32p, _i32p, _f64p, _f64p,
+                                    ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                    ctypes.c_int32, ctypes.c_double, ctypes.c_double,
+                                    vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp,
+                                    ctypes.POINTER(ctypes.c_int32),
+                                    ctypes.POINTER(ctypes.c_int32)]
+    L.orc_arnoldi_cycle.restype = ctypes.c_int
+    L.orc_gmres.argtypes = [ctypes.c_int32, _i32p, _i32p, _f64p, _f64p, _f64p,
+                            ctypes.POINTER(Opts), vp, vp, vp, ctypes.POINTER(Info), vp, vp]
+    L.orc_gmres.restype = ctypes.c_int
+    if hasattr(L, "orc_spai_features"):
+        _bind_spai(L)
+    return L
+
+
+def load_path(path):
+    """Open an oracle build at ``path`` (used by the planted-mistake tests)."""
+    return _bind(ctypes.CDLL(path))
+
+
+def lib():
+    """The loaded oracle library (built on first use)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            _lib = _bind(ctypes.CDLL(_LIB_PATH))
+        return _lib
+
+
+_active = None  # when set, the wrappers below call this library instead of lib()
+
+
+def _L():
+    return _active if _active is not None else lib()
+
+
+class use:
+    """Context manager: route the module-level wrappers to another build."""
+
+    def __init__(self, L):
+        self.L = L
+
+    def __enter__(self):
+        global _active
+        self.prev = _active
+        _active = self.L
+        return self.L
+
+    def __exit__(self, *exc):
+        global _active
+        _active = self.prev
+        return False
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _csr(A):
+    rowptr, colind, vals = A
+    return (np.ascontiguousarray(rowptr, dtype=np.int32),
+            np.ascontiguousarray(colind, dtype=np.int32),
+            np.ascontiguousarray(vals, dtype=np.float64))
+
+
+def spmv(A, x, prec=FP64):
+    """y = A x (binary64, or binary32 values/sum for any other precision)."""
+    rp, ci, va = _csr(A)
+    n = len(rp) - 1
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.empty(n, dtype=np.float64)
+    rc = _L().orc_spmv(n, rp, ci, va, x, y, prec)
+    if rc:
+        raise ValueError("orc_spmv failed: %d" % rc)
+    return y
+
+
+def residual(A, b, x):
+    """(z, ||z||) with z = b - A x in binary64."""
+    rp, ci, va = _csr(A)
+    n = len(rp) - 1
+    z = np.empty(n, dtype=np.float64)
+    nrm = _L().orc_residual(n, rp, ci, va, np.ascontiguousarray(b, np.float64),
+                             np.ascontiguousarray(x, np.float64), _ptr(z))
+    return z, nrm
+
+
+def residual_norm(A, b, x):
+    """||b - A x||_2 in binary64."""
+    rp, ci, va = _csr(A)
+    n = len(rp) - 1
+    return _L().orc_residual(n, rp, ci, va, np.ascontiguousarray(b, np.float64),
+                              np.ascontiguousarray(x, np.float64), None)
+
+
+def round_basis(v, prec, n):
+    """Values a Krylov basis of precision ``prec`` stores for ``v`` (length-n system)."""
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    out = np.empty_like(v)
+    _L().orc_round_basis(v.size, v.ravel(), out.ravel(), prec, n)
+    return out
+
+
+def arnoldi_cycle(A, r0, m, ortho=CGSR, prec=FP64, kmax=None, tau=0.0, inner_abs=0.0, M=None):
+    """One restart cycle from residual r0; returns a dict of its quantities.
+
+    V is (m+1, n) (row i = basis vector i), Hbar/H are (m+1, m), the first ``j``
+    columns valid."""
+    rp, ci, va = _csr(A)
+    n = len(rp) - 1
+    kmax = m if kmax is None else kmax
+    V = np.zeros((m + 1, n))
+    Hb = np.zeros((m, m + 1))
+    H = np.zeros((m, m + 1))
+    s = np.zeros(m + 1)
+    cs = np.zeros(m)
+    sn = np.zeros(m)
+    y = np.zeros(m)
+    u = np.zeros(n)
+    arn = np.zeros(m)
+    j = ctypes.c_int32(0)
+    bd = ctypes.c_int32(0)
+    if M is not None:
+        mp, mc, mv = _csr(M)
+        keep = (mp, mc, mv)
+        margs = (_ptr(mp), _ptr(mc), _ptr(mv))
+    else:
+        keep = None
+        margs = (None, None, None)
+    rc = _L().orc_arnoldi_cycle(n, rp, ci, va, np.ascontiguousarray(r0, np.float64), m, kmax,
+                                 ortho, prec, tau, inner_abs, *margs, _ptr(V), _ptr(Hb), _ptr(H),
+                                 _ptr(s), _ptr(cs), _ptr(sn), _ptr(y), _ptr(u), _ptr(arn),
+                                 ctypes.byref(j), ctypes.byref(bd))
+    del keep
+    if rc:
+        raise ValueError("orc_arnoldi_cycle failed: %d" % rc)
+    jj = j.value
+    return dict(V=V, Hbar=Hb.T.copy(), H=H.T.copy(), s=s, cs=cs, sn=sn, y=y, u=u, arn=arn, j=jj,
+                breakdown=bool(bd.value))
+
+
+def default_tau(prec):
+    """Restart threshold on the Arnoldi-residual gain per precision (Sec. 3,
+    second strategy; the performance study's 1e-6 for binary32, scaled to the
+    unit roundoff for the 16-bit bases)."""
+    return {FP64: 0.0, MIXED: 1e-6, MIXED_BF16: 1e-2, MIXED_FP16: 1e-3, ALL_FP32: 1e-6}[prec]
+
+
+def gmres(A, b, x0=None, m=30, tol=1e-10, ortho=CGSR, prec=FP64, maxiter=10000, tau=None,
+          repeat_first=None, inner_factor=0.5, M=None, history=False):
+    """Restarted GMRES(m) (Algorithm 1).  Returns (x, info dict)."""
+    rp, ci, va = _csr(A)
+    n = len(rp) - 1
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    x = np.zeros(n) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
+    o = Opts()
+    o.m, o.ortho, o.prec, o.maxiter = m, ortho, prec, maxiter
+    o.repeat_first = int(prec != FP64) if repeat_first is None else int(repeat_first)
+    o.tol = tol
+    o.tau = default_tau(prec) if tau is None else tau
+    o.inner_factor = inner_factor
+    info = Info()
+    arn = np.zeros(max(maxiter, 1)) if history else None
+    cyc = np.zeros(maxiter + 2) if history else None
+    if M is not None:
+        mp, mc, mv = _csr(M)
+        margs = (_ptr(mp), _ptr(mc), _ptr(mv))
+    else:
+        mp = mc = mv = None
+        margs = (None, None, None)
+    rc = _L().orc_gmres(n, rp, ci, va, b, x, ctypes.byref(o), *margs, ctypes.byref(info),
+                         _ptr(arn), _ptr(cyc))
+    if rc:
+        raise ValueError("orc_gmres failed: %d" % rc)
+    out = dict(iters=info.iters, restarts=info.restarts, converged=bool(info.converged),
+               first_len=info.first_len, relres=info.relres, bnorm=info.bnorm)
+    if history:
+        out["arnoldi"] = arn[: info.iters].copy()
+        out["cycle_relres"] = cyc[: info.restarts + 1].copy()
+    return x, out
+
+
+def _bind_spai(L):  # pragma: no cover - filled in with the preconditioner oracle
+    pass

@@ -1,0 +1,123 @@
+/*
+ * gmres_oracle.h -- CPU oracle for restarted mixed-precision GMRES(m).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This header and gmres_oracle.c form a plain,
+ * slow, single-threaded restatement of Algorithm 1 of Lindquist, Luszczek and
+ * Dongarra, "Improving the Performance of the GMRES Method using
+ * Mixed-Precision Techniques" (arXiv 2011.01850).  Only the test suite, the
+ * smoke check and the CPU-baseline leg of the benchmark may load it.  It
+ * shares no code, header, table or helper with the CUDA library under
+ * paper_2011_01850_gb300/.
+ *
+ * Conventions
+ *   - CSR matrices: rowptr[n+1], colind[nnz] (int32, 0-based), vals[nnz].
+ *   - Basis V is column-major: vector i occupies V[i*n .. i*n+n-1].
+ *   - Hessenberg matrices are column-major with leading dimension m+1:
+ *     entry (row i, column j), both 0-based, lives at H[j*(m+1) + i].
+ *   - Every sum is sequential in index order, in the working precision.
+ *   - Return value 0 = success, negative = argument error.
+ */
+#ifndef GMRES_ORACLE_H
+#define GMRES_ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Orthogonalisation schemes (Algorithm 1, procedures MGS and CGSR). */
+enum { ORC_MGS = 0, ORC_CGSR = 1 };
+
+/* Precision assignments.
+ *   ORC_FP64       every variable in binary64 (the double-precision baseline).
+ *   ORC_MIXED      the paper's "fully mixed" solver (Sec. 4, 4.1): the residual
+ *                  z = b - A x, its norm and the update x += u in binary64; the
+ *                  whole restart cycle (Alg. 1 from the convergence test to the
+ *                  correction) in binary32.
+ *   ORC_MIXED_BF16 as ORC_MIXED, but each Krylov vector is stored rounded to
+ *                  bfloat16 (round-to-nearest-even); arithmetic stays binary32.
+ *   ORC_MIXED_FP16 as ORC_MIXED, with each Krylov vector stored as binary16
+ *                  after scaling by the power of two 2^floor(log2(n)/2).
+ *   ORC_ALL_FP32   negative control: residual and update in binary32 as well,
+ *                  which Sec. 2 predicts cannot pass single-precision accuracy. */
+enum { ORC_FP64 = 0, ORC_MIXED = 1, ORC_MIXED_BF16 = 2, ORC_MIXED_FP16 = 3, ORC_ALL_FP32 = 4 };
+
+typedef struct {
+    int32_t m;            /* maximum inner iterations per restart cycle         */
+    int32_t ortho;        /* ORC_MGS or ORC_CGSR                                 */
+    int32_t prec;         /* ORC_FP64 ... ORC_ALL_FP32                           */
+    int32_t maxiter;      /* cap on the total number of inner iterations         */
+    int32_t repeat_first; /* 1: after the first cycle, every cycle is limited to
+                             the first cycle's length (Sec. 3, first strategy)  */
+    int32_t reserved;
+    double tol;           /* stop when ||b - A x||_2 <= tol * ||b||_2 (binary64) */
+    double tau;           /* restart when |s_{j+1}| <= tau * beta (Sec. 3,
+                             second strategy); 0 disables                       */
+    double inner_factor;  /* end a cycle once |s_{j+1}| <= inner_factor*tol*||b||*/
+} orc_opts;
+
+typedef struct {
+    int32_t iters;        /* total inner iterations                              */
+    int32_t restarts;     /* number of restart cycles that ran                   */
+    int32_t converged;    /* 1 if the binary64 residual met tol                  */
+    int32_t first_len;    /* length of the first cycle                           */
+    double relres;        /* final ||b - A x|| / ||b||, binary64                 */
+    double bnorm;         /* ||b||_2                                             */
+} orc_info;
+
+/* y = A x.  prec = ORC_FP64: binary64 arithmetic.  Any other prec: the values,
+ * x and the running sum are binary32 (the copy of A used by the Arnoldi loop,
+ * Sec. 4). */
+int orc_spmv(int32_t n, const int32_t *rowptr, const int32_t *colind, const double *vals,
+             const double *x, double *y, int32_t prec);
+
+/* z = b - A x in binary64 (Alg. 1, first line of the outer loop); returns ||z||_2. */
+double orc_residual(int32_t n, const int32_t *rowptr, const int32_t *colind, const double *vals,
+                    const double *b, const double *x, double *z);
+
+/* Round each of count binary64 values as stored in a Krylov basis of the given
+ * precision (ORC_FP64: unchanged; ORC_MIXED: binary32; ORC_MIXED_BF16: bfloat16
+ * via binary32; ORC_MIXED_FP16: binary16 with scale 2^floor(log2(n)/2)). */
+void orc_round_basis(int32_t count, const double *in, double *out, int32_t prec, int32_t n);
+
+/* One restart cycle (Alg. 1, from "r_k <- M^-1 z_k" to the correction u_k),
+ * starting from the residual r0 (length n, already in the caller's precision;
+ * it is rounded to the working precision here).
+ *
+ *   kmax        maximum number of inner iterations (<= m)
+ *   tau, inner_abs  restart when |s_{j+1}| <= tau*beta or |s_{j+1}| <= inner_abs
+ *   pm_*        right preconditioner M on its own CSR pattern, or NULL for M = I;
+ *               with M the loop uses w = A M v_j and u = M V_j y
+ * Outputs (any may be NULL):
+ *   V     (m+1)*n  basis, logical values after storage rounding
+ *   Hbar  (m+1)*m  unrotated Hessenberg matrix
+ *   Hrot  (m+1)*m  Hessenberg matrix after the Givens rotations (upper triangle)
+ *   s     m+1      rotated right-hand side
+ *   cs,sn m        rotations (alpha_i, beta_i)
+ *   y     m        least-squares solution
+ *   u     n        correction
+ *   arn   m        |s_{j+1}| after each inner iteration
+ *   jout           number of inner iterations done
+ *   breakdown      1 if the cycle ended on h_{j+1,j} ~ 0
+ */
+int orc_arnoldi_cycle(int32_t n, const int32_t *rowptr, const int32_t *colind, const double *vals,
+                      const double *r0, int32_t m, int32_t kmax, int32_t ortho, int32_t prec,
+                      double tau, double inner_abs,
+                      const int32_t *pm_rowptr, const int32_t *pm_colind, const double *pm_vals,
+                      double *V, double *Hbar, double *Hrot, double *s, double *cs, double *sn,
+                      double *y, double *u, double *arn, int32_t *jout, int32_t *breakdown);
+
+/* Restarted GMRES(m) (Alg. 1).  x holds x_0 on entry and the result on exit.
+ * arn_hist (length maxiter) receives |s_{j+1}| of every inner iteration;
+ * cyc_hist (length maxiter+1) receives ||b - A x_k|| / ||b|| at the top of every
+ * cycle k and after the last one.  Either may be NULL. */
+int orc_gmres(int32_t n, const int32_t *rowptr, const int32_t *colind, const double *vals,
+              const double *b, double *x, const orc_opts *o,
+              const int32_t *pm_rowptr, const int32_t *pm_colind, const double *pm_vals,
+              orc_info *info, double *arn_hist, double *cyc_hist);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,381 @@
+"""Pins for the CPU oracle: facts fixed by the paper and by the mathematics.
+
+Every ``pin_*`` function checks the oracle against something other than itself
+-- a library routine (LAPACK solve/lstsq through numpy, torch's bfloat16 and
+numpy's binary16 conversions), a closed form, a hand-worked example, an
+invariant of exact arithmetic, or brute force on a tiny input.  They are run
+once against the real oracle (test_oracle_pins.py) and again against builds
+with planted mistakes, each of which at least one pin must reject.
+"""
+from __future__ import annotations
+
+import math
+import os
+
+import numpy as np
+
+import oracle as O
+from paper_2011_01850_gb300 import inputs as I
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def _dense(A):
+    return I.csr_to_dense(A)
+
+
+# ---------------------------------------------------------------------------
+# whole solver
+# ---------------------------------------------------------------------------
+
+def pin_lu_fp64():
+    """Binary64 GMRES equals a dense LU solve (numpy/LAPACK) up to kappa*1e-13
+    on random diagonally dominant non-symmetric systems (MGS and CGSR)."""
+    for seed in range(3):
+        A = I.random_dd(40, density=0.3, dom=0.6, seed=seed)
+        D = _dense(A)
+        b = np.random.default_rng(100 + seed).standard_normal(40)
+        xl = np.linalg.solve(D, b)
+        kappa = np.linalg.cond(D)
+        for ortho in (O.MGS, O.CGSR):
+            x, info = O.gmres(A, b, m=15, tol=1e-13, ortho=ortho, prec=O.FP64, maxiter=2000)
+            err = np.linalg.norm(x - xl) / np.linalg.norm(xl)
+            assert info["converged"], info
+            assert err <= kappa * 1e-13, (seed, ortho, err, kappa)
+
+
+def pin_exact_convergence():
+    """Without restarts (m >= n) GMRES solves an n x n system in at most n steps."""
+    n = 24
+    rng = np.random.default_rng(7)
+    D = rng.standard_normal((n, n)) + 6.0 * np.eye(n)
+    A = I.dense_to_csr(D)
+    b = rng.standard_normal(n)
+    for ortho in (O.MGS, O.CGSR):
+        x, info = O.gmres(A, b, m=n, tol=1e-12, ortho=ortho, prec=O.FP64, maxiter=n,
+                          inner_factor=0.5)
+        assert info["iters"] <= n and info["restarts"] == 1, info
+        assert np.linalg.norm(b - D @ x) <= 1e-12 * np.linalg.norm(b), info
+
+
+def pin_identity():
+    """A = I: every cycle takes one inner iteration (w = v_1 breaks down at
+    once); in binary64 one cycle gives x = b, while the binary32 correction of
+    the mixed solver leaves an O(u32) error that the next one-step cycles
+    remove."""
+    n = 17
+    A = I.dense_to_csr(np.eye(n))
+    b = np.arange(1.0, n + 1)
+    for ortho in (O.MGS, O.CGSR):
+        x, info = O.gmres(A, b, m=10, tol=1e-10, ortho=ortho, prec=O.FP64, maxiter=50)
+        assert info["iters"] == 1 and info["restarts"] == 1, info
+        assert np.allclose(x, b, rtol=1e-14, atol=0), x
+        x, info = O.gmres(A, b, m=10, tol=1e-10, ortho=ortho, prec=O.MIXED, maxiter=50)
+        assert info["converged"] and info["iters"] == info["restarts"] <= 3, info
+        assert np.allclose(x, b, rtol=1e-10, atol=0), x
+
+
+def pin_diag_distinct():
+    """A diagonal matrix with k distinct eigenvalues: the Krylov space of any b
+    has dimension <= k, so GMRES ends (breakdown) after k steps with the exact
+    solution."""
+    k = 5
+    vals = np.array([1.0, 2.0, 3.5, 7.0, 11.0])
+    d = np.repeat(vals, 8)
+    n = d.size
+    A = I.dense_to_csr(np.diag(d))
+    b = np.random.default_rng(3).uniform(0.5, 1.5, n)
+    for ortho in (O.MGS, O.CGSR):
+        x, info = O.gmres(A, b, m=20, tol=1e-12, ortho=ortho, prec=O.FP64, maxiter=100)
+        assert info["iters"] == k, info
+        assert np.allclose(x, b / d, rtol=1e-12, atol=0)
+
+
+def pin_cyclic_shift():
+    """Cyclic shift P e_i = e_{i+1}, b = e_1, x0 = 0: the Krylov vectors are
+    e_1, e_2, ..., so the residual stays 1 for n-1 steps (complete stagnation)
+    and the exact solution x = e_n appears at step n."""
+    n = 12
+    P = np.zeros((n, n))
+    for i in range(n):
+        P[(i + 1) % n, i] = 1.0
+    A = I.dense_to_csr(P)
+    b = np.zeros(n)
+    b[0] = 1.0
+    for ortho in (O.MGS, O.CGSR):
+        cyc = O.arnoldi_cycle(A, b, m=n, ortho=ortho, prec=O.FP64)
+        assert cyc["j"] == n, cyc["j"]
+        assert np.allclose(cyc["arn"][: n - 1], 1.0, atol=1e-14)
+        assert abs(cyc["arn"][n - 1]) <= 1e-14
+        e_n = np.zeros(n)
+        e_n[-1] = 1.0
+        assert np.allclose(cyc["u"], e_n, atol=1e-13)
+
+
+def pin_hand_2x2():
+    """Every quantity of the hand-worked 2x2 cycle in tests/golden."""
+    g = {}
+    with open(os.path.join(HERE, "golden", "gmres_2x2_by_hand.txt")) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            k, v = line.split(None, 1)
+            g[k] = float(eval(v, {"sqrt": math.sqrt}))
+    A = I.dense_to_csr(np.array([[2.0, 1.0], [0.0, 1.0]]))
+    b = np.array([1.0, 1.0])
+    c = O.arnoldi_cycle(A, b, m=2, ortho=O.MGS, prec=O.FP64)
+    tol = 1e-14
+    assert c["j"] == g["iterations"]
+    Hb = c["Hbar"]
+    assert abs(Hb[0, 0] - g["hbar_1_1"]) < tol and abs(Hb[1, 0] - g["hbar_2_1"]) < tol
+    assert abs(Hb[0, 1] - g["hbar_1_2"]) < tol and abs(Hb[1, 1] - g["hbar_2_2"]) < tol
+    assert abs(Hb[2, 1] - g["hbar_3_2"]) < tol
+    assert abs(c["cs"][0] - g["alpha_1"]) < tol and abs(c["sn"][0] - g["beta_1"]) < tol
+    assert abs(c["cs"][1] - g["alpha_2"]) < tol and abs(c["sn"][1] - g["beta_2"]) < tol
+    assert abs(c["s"][0] - g["s_1"]) < tol
+    assert abs(c["s"][1] - g["s_2_after_step1"]) < tol
+    assert abs(c["arn"][0] - g["arnoldi_res_1"]) < tol and abs(c["arn"][1]) < tol
+    R = c["H"]
+    assert abs(R[0, 0] - g["r_1_1"]) < tol and abs(R[0, 1] - g["r_1_2"]) < tol
+    assert abs(R[1, 1] - g["r_2_2"]) < tol
+    assert abs(c["y"][0] - g["y_1"]) < tol and abs(c["y"][1] - g["y_2"]) < tol
+    assert abs(c["u"][0] - g["x_1"]) < tol and abs(c["u"][1] - g["x_2"]) < tol
+
+
+# ---------------------------------------------------------------------------
+# Arnoldi process and least-squares problem
+# ---------------------------------------------------------------------------
+
+def _cd_small():
+    A = I.convdiff2d(8, pe=10.0)
+    b = I.rhs_ones_noise(A, 1e-3, 5)
+    return A, b
+
+
+def pin_arnoldi_relation():
+    """A V_k = V_{k+1} Hbar_k to 1e-12 (Frobenius, relative to ||A||_F) in
+    binary64, for MGS and CGSR."""
+    A, b = _cd_small()
+    D = _dense(A)
+    k = 20
+    for ortho in (O.MGS, O.CGSR):
+        c = O.arnoldi_cycle(A, b, m=k, ortho=ortho, prec=O.FP64)
+        j = c["j"]
+        V = c["V"][: j + 1].T
+        Hb = c["Hbar"][: j + 1, :j]
+        err = np.linalg.norm(D @ V[:, :j] - V @ Hb) / np.linalg.norm(D)
+        assert err <= 1e-12, (ortho, err)
+
+
+def pin_orthonormality():
+    """||I - V^T V||_F <= 1e-12 in binary64 for CGSR over the whole cycle and
+    <= 1e-4 for a binary32 CGSR basis.  MGS keeps orthogonality only until the
+    Arnoldi residual nears working accuracy (Sec. 3): its loss grows like
+    u * kappa(A) / (|s_{j+1}| / beta), so the pin checks that product, and the
+    1e-12 bound while the relative Arnoldi residual is above 1e-2."""
+    A, b = _cd_small()
+    beta = np.linalg.norm(b)
+    kappa = np.linalg.cond(_dense(A))
+    k = 20
+    for ortho, prec, tol in ((O.CGSR, O.FP64, 1e-12), (O.CGSR, O.MIXED, 1e-4)):
+        c = O.arnoldi_cycle(A, b, m=k, ortho=ortho, prec=prec)
+        V = c["V"][: c["j"] + 1]
+        err = np.linalg.norm(np.eye(V.shape[0]) - V @ V.T)
+        assert err <= tol, (ortho, prec, err)
+    c = O.arnoldi_cycle(A, b, m=k, ortho=O.MGS, prec=O.FP64)
+    u = 2.0 ** -53
+    for j in range(1, c["j"] + 1):
+        V = c["V"][: j + 1]
+        err = np.linalg.norm(np.eye(j + 1) - V @ V.T)
+        rel = c["arn"][j - 1] / beta
+        assert err * rel <= 100 * kappa * u, (j, err, rel)
+        if rel > 1e-2:
+            assert err <= 1e-12, (j, err)
+
+
+def pin_mgs_equals_cgsr():
+    """In exact arithmetic MGS and CGSR give the same Hessenberg matrix; in
+    binary64 on a well-conditioned system they agree to 1e-10."""
+    A, b = _cd_small()
+    c1 = O.arnoldi_cycle(A, b, m=15, ortho=O.MGS, prec=O.FP64)
+    c2 = O.arnoldi_cycle(A, b, m=15, ortho=O.CGSR, prec=O.FP64)
+    assert c1["j"] == c2["j"]
+    d = np.abs(c1["Hbar"] - c2["Hbar"]).max() / np.abs(c1["Hbar"]).max()
+    assert d <= 1e-10, d
+
+
+def pin_givens_least_squares():
+    """The rotated problem solves min ||beta e1 - Hbar y|| (checked against
+    numpy lstsq), |s_{j+1}| equals that minimum, and it never increases."""
+    A, b = _cd_small()
+    beta = np.linalg.norm(b)
+    for ortho in (O.MGS, O.CGSR):
+        c = O.arnoldi_cycle(A, b, m=18, ortho=ortho, prec=O.FP64)
+        j = c["j"]
+        Hb = c["Hbar"][: j + 1, :j]
+        rhs = np.zeros(j + 1)
+        rhs[0] = beta
+        y, *_ = np.linalg.lstsq(Hb, rhs, rcond=None)
+        assert np.allclose(c["y"][:j], y, rtol=1e-11, atol=1e-12 * np.abs(y).max())
+        res = np.linalg.norm(rhs - Hb @ y)
+        assert abs(c["arn"][j - 1] - res) <= 1e-12 * beta
+        arn = c["arn"][:j]
+        assert np.all(np.diff(arn) <= 1e-14 * beta)
+        # the rotations are orthogonal
+        assert np.allclose(c["cs"][:j] ** 2 + c["sn"][:j] ** 2, 1.0, atol=1e-15)
+
+
+def pin_arnoldi_residual_is_true_residual():
+    """Before stagnation, in binary64, |s_{j+1}| = ||r0 - A V_j y_j|| (Saad,
+    Prop. 6.9; Sec. 3), checked for every j by brute force."""
+    A, b = _cd_small()
+    D = _dense(A)
+    full = O.arnoldi_cycle(A, b, m=12, ortho=O.CGSR, prec=O.FP64)
+    for j in range(1, full["j"] + 1):
+        c = O.arnoldi_cycle(A, b, m=12, kmax=j, ortho=O.CGSR, prec=O.FP64)
+        true = np.linalg.norm(b - D @ c["u"])
+        assert abs(true - full["arn"][j - 1]) <= 1e-10 * max(true, 1e-300) + 1e-14, (j, true)
+
+
+def pin_tau_restart():
+    """Restart strategy 2 (Sec. 3): the cycle ends at the first j with
+    |s_{j+1}| <= tau * beta, where the LS residuals come from numpy lstsq."""
+    A, b = _cd_small()
+    beta = np.linalg.norm(b)
+    ref = O.arnoldi_cycle(A, b, m=30, ortho=O.CGSR, prec=O.FP64)
+    Hb = ref["Hbar"]
+    ls = []
+    for j in range(1, ref["j"] + 1):
+        rhs = np.zeros(j + 1)
+        rhs[0] = beta
+        H = Hb[: j + 1, :j]
+        y, *_ = np.linalg.lstsq(H, rhs, rcond=None)
+        ls.append(np.linalg.norm(rhs - H @ y))
+    tau = 1e-3
+    expect = next(i + 1 for i, r in enumerate(ls) if r <= tau * beta)
+    c = O.arnoldi_cycle(A, b, m=30, ortho=O.CGSR, prec=O.FP64, tau=tau)
+    assert c["j"] == expect, (c["j"], expect)
+
+
+# ---------------------------------------------------------------------------
+# precision behaviour (Sec. 2, Sec. 4.1)
+# ---------------------------------------------------------------------------
+
+def pin_mixed_reaches_double():
+    """With a binary64 residual and update, every mixed form reaches a binary64
+    relative residual <= 1e-10 (Sec. 4.1) and the solution matches LAPACK."""
+    A = I.convdiff2d(16, pe=10.0)
+    b = I.rhs_ones_noise(A, 1e-3, 9)
+    xl = np.linalg.solve(_dense(A), b)
+    for prec in (O.MIXED, O.MIXED_BF16, O.MIXED_FP16):
+        for ortho in (O.MGS, O.CGSR):
+            x, info = O.gmres(A, b, m=30, tol=1e-10, ortho=ortho, prec=prec, maxiter=3000)
+            assert info["converged"] and info["relres"] <= 1e-10, (prec, ortho, info)
+            assert np.linalg.norm(b - _dense(A) @ x) <= 1e-10 * np.linalg.norm(b)
+            assert np.linalg.norm(x - xl) / np.linalg.norm(xl) <= 1e-8
+
+
+def pin_negative_control():
+    """A residual and update in binary32 cannot pass single-precision accuracy
+    (Sec. 2, Sec. 4.1): the all-binary32 solver stalls above 1e-8."""
+    A = I.convdiff2d(16, pe=10.0)
+    b = I.rhs_ones_noise(A, 1e-3, 9)
+    for ortho in (O.MGS, O.CGSR):
+        x, info = O.gmres(A, b, m=30, tol=1e-10, ortho=ortho, prec=O.ALL_FP32, maxiter=600)
+        assert not info["converged"] and info["relres"] >= 1e-8, info
+
+
+def pin_monotone_restarts():
+    """Each restart cycle minimises the residual over a space that contains the
+    zero correction, so the binary64 true residual does not grow from cycle to
+    cycle (Sec. 2: ||r_i|| <= delta ||r_{i-1}||)."""
+    A = I.convdiff2d(16, pe=10.0)
+    b = I.rhs_ones_noise(A, 1e-3, 9)
+    for prec in (O.FP64, O.MIXED):
+        x, info = O.gmres(A, b, m=8, tol=1e-10, ortho=O.CGSR, prec=prec, maxiter=3000,
+                          history=True)
+        r = info["cycle_relres"]
+        assert len(r) >= 4
+        assert np.all(r[1:] <= r[:-1] * (1 + 1e-12)), r
+
+
+def pin_repeat_first():
+    """Restart strategy 1 with the gain-threshold first restart (Sec. 3,
+    Sec. 4.2): the first cycle ends on |s_{j+1}| <= tau beta, every later cycle
+    runs exactly as long as the first (the last may end early on
+    convergence)."""
+    A = I.convdiff2d(16, pe=10.0)
+    b = I.rhs_ones_noise(A, 1e-3, 9)
+    x, info = O.gmres(A, b, m=30, tol=1e-10, ortho=O.CGSR, prec=O.MIXED, maxiter=3000,
+                      tau=1e-2, repeat_first=True, history=True)
+    k1 = info["first_len"]
+    assert k1 < 30
+    assert info["iters"] <= k1 * info["restarts"]
+    assert info["iters"] > k1 * (info["restarts"] - 1)
+
+
+# ---------------------------------------------------------------------------
+# kernels: SpMV, residual, basis rounding
+# ---------------------------------------------------------------------------
+
+def pin_spmv_and_residual():
+    """SpMV and residual against dense numpy products: binary64 to 1e-14
+    relative; the binary32 SpMV within the sequential-sum bound
+    gamma_k u32 sum|a||x| per row, k the row length."""
+    A = I.powerlaw_random(300, seed=4)
+    D = _dense(A)
+    x = np.random.default_rng(1).standard_normal(300)
+    y = O.spmv(A, x)
+    assert np.allclose(y, D @ x, rtol=1e-14, atol=1e-14 * np.abs(D).sum(1).max())
+    y32 = O.spmv(A, x, prec=O.MIXED)
+    a32 = D.astype(np.float32).astype(np.float64)
+    x32 = x.astype(np.float32).astype(np.float64)
+    exact = a32 @ x32
+    k = np.diff(A[0])
+    u = 2.0 ** -24
+    bound = (k * u / (1 - k * u)) * (np.abs(a32) @ np.abs(x32))
+    assert np.all(np.abs(y32 - exact) <= bound + 1e-300)
+    b = np.random.default_rng(2).standard_normal(300)
+    z, nrm = O.residual(A, b, x)
+    assert np.allclose(z, b - D @ x, rtol=1e-13, atol=1e-13)
+    assert abs(nrm - np.linalg.norm(b - D @ x)) <= 1e-13 * nrm
+
+
+def _bf16_ref(v):
+    import torch
+    t = torch.tensor(np.asarray(v, np.float32), dtype=torch.float32)
+    return t.to(torch.bfloat16).to(torch.float32).numpy().astype(np.float64)
+
+
+def pin_basis_rounding():
+    """bfloat16 storage equals torch's float32 -> bfloat16 conversion
+    (round-to-nearest-even, ties included); binary16 storage equals numpy's
+    float32 -> float16 conversion of the value scaled by 2^floor(log2(n)/2)."""
+    rng = np.random.default_rng(11)
+    v = rng.standard_normal(4000) * np.exp(rng.uniform(-20, 5, 4000))
+    v = v.astype(np.float32).astype(np.float64)
+    # exact ties between bfloat16 neighbours (odd and even kept parts)
+    ties = np.array([1.0 + 2.0 ** -8, 1.0 + 3 * 2.0 ** -8, -(1.0 + 2.0 ** -8), 3.0 + 2.0 ** -7],
+                    dtype=np.float64)
+    v = np.concatenate([v, ties])
+    got = O.round_basis(v, O.MIXED_BF16, 1000)
+    assert np.array_equal(got, _bf16_ref(v))
+    for n in (1000, 4096, 2_000_000):
+        sc = 2.0 ** (int(math.floor(math.log2(n))) // 2)
+        w = (rng.standard_normal(3000) / math.sqrt(n)).astype(np.float32)
+        w = np.concatenate([w, np.float32([1.0, -1.0, 2.0 ** -30, 5e-8])])
+        ref = (w * np.float32(sc)).astype(np.float16).astype(np.float64) / sc
+        got = O.round_basis(w.astype(np.float64), O.MIXED_FP16, n)
+        assert np.array_equal(got, ref), n
+    f32 = O.round_basis(np.array([1.0 + 2.0 ** -30, 0.1]), O.MIXED, 10)
+    assert np.array_equal(f32, np.float32([1.0 + 2.0 ** -30, 0.1]).astype(np.float64))
+
+
+ALL_PINS = [
+    pin_lu_fp64, pin_exact_convergence, pin_identity, pin_diag_distinct, pin_cyclic_shift,
+    pin_hand_2x2, pin_arnoldi_relation, pin_orthonormality, pin_mgs_equals_cgsr,
+    pin_givens_least_squares, pin_arnoldi_residual_is_true_residual, pin_tau_restart,
+    pin_mixed_reaches_double, pin_negative_control, pin_monotone_restarts, pin_repeat_first,
+    pin_spmv_and_residual, pin_basis_rounding,
+]

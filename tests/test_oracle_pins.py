@@ -1,0 +1,88 @@
+"""The CPU oracle against its pins, and planted mistakes against the pins.
+
+Runs on any CPU host (marker: not gpu).  The planted-mistake tests copy the
+oracle sources to a temporary directory, apply one textual mistake of the kind
+a restatement of Algorithm 1 could plausibly contain (a flipped sign, a wrong
+index, a dropped term, a transposed operand), compile that copy with gcc and
+check that at least one pin rejects it.
+"""
+from __future__ import annotations
+
+import os
+import shutil
+import warnings
+
+import pytest
+
+import oracle as O
+import oracle_pins as P
+
+ORACLE_DIR = os.path.dirname(os.path.abspath(O.__file__))
+
+
+@pytest.mark.parametrize("pin", P.ALL_PINS, ids=lambda f: f.__name__)
+def test_pin(pin):
+    pin()
+
+
+# (file, exact text, replacement, what the mistake is)
+MUTATIONS = [
+    ("cycle_impl.inc", "s[c + 1] = -be * sj;", "s[c + 1] = be * sj;",
+     "sign of the new s_{j+1}"),
+    ("cycle_impl.inc", "col[i + 1] = -sn[i] * hi + cs[i] * hi1;",
+     "col[i + 1] = sn[i] * hi + cs[i] * hi1;", "sign in applying an old rotation"),
+    ("cycle_impl.inc", "col[i] = cs[i] * hi + sn[i] * hi1;",
+     "col[i] = cs[i] * hi + sn[i + 1] * hi1;", "wrong rotation index"),
+    ("cycle_impl.inc", "be = hj1 / rho;", "be = hjj / rho;", "rotation formed from wrong entry"),
+    ("cycle_impl.inc", "s[c] = al * sj;", "s[c] = sj;", "dropped rotation of s_j"),
+    ("cycle_impl.inc", "acc -= H[(size_t)l * ld + i] * y[l];",
+     "acc -= H[(size_t)i * ld + l] * y[l];", "transposed triangle in back substitution"),
+    ("cycle_impl.inc", "for (int32_t l = i + 1; l < j; ++l)",
+     "for (int32_t l = i + 2; l < j; ++l)", "dropped term in back substitution"),
+    ("cycle_impl.inc", "V[(size_t)(c + 1) * n + r] = (R)orc_store(w[r] / hnext, prec, n);",
+     "V[(size_t)(c + 1) * n + r] = (R)orc_store(w[r], prec, n);", "v_{j+1} not normalised"),
+    ("cycle_impl.inc", "V[r] = (R)orc_store(r0[r] / beta, prec, n);",
+     "V[r] = (R)orc_store(r0[r], prec, n);", "v_1 not normalised"),
+    ("cycle_impl.inc", "for (int32_t i = 0; i < j; ++i) {\n        const R *v = V + (size_t)i * n;",
+     "for (int32_t i = 0; i + 1 < j; ++i) {\n        const R *v = V + (size_t)i * n;",
+     "MGS skips the last projection"),
+    ("cycle_impl.inc", "FN(cgs_pass)(n, j, V, w, g2);\n", "",
+     "CGSR without its second pass"),
+    ("cycle_impl.inc", "Hb[(size_t)c * ld + c + 1] = hnext;", "Hb[(size_t)c * ld + c + 1] = wnorm0;",
+     "subdiagonal from the wrong norm"),
+    ("cycle_impl.inc", "acc += a[k] * x[colind[k]];\n        y[i] = acc;",
+     "acc += a[k] * x[i];\n        y[i] = acc;", "SpMV gathers the wrong operand"),
+    ("gmres_oracle.c", "double zi = b[i] - acc;", "double zi = b[i] + acc;",
+     "residual sign"),
+    ("gmres_oracle.c", "x[i] = x[i] + u[i];", "x[i] = x[i] - u[i];", "update sign"),
+    ("gmres_oracle.c", "bits += 0x7fffu + lsb;", "bits += 0x8000u;",
+     "bfloat16 ties away from even"),
+    ("gmres_oracle.c", "return ldexp(1.0, lg / 2);", "return ldexp(1.0, lg);",
+     "binary16 scale"),
+    ("gmres_oracle.c", "return (double)(float)v;\n", "return v;\n",
+     "binary32 basis not rounded"),
+]
+
+
+@pytest.mark.parametrize("mut", MUTATIONS, ids=[m[3] for m in MUTATIONS])
+def test_planted_mistake_is_caught(mut, tmp_path):
+    fname, old, new, what = mut
+    src = tmp_path / "src"
+    src.mkdir()
+    for f in os.listdir(ORACLE_DIR):
+        if f.endswith((".c", ".h", ".inc")):
+            shutil.copy(os.path.join(ORACLE_DIR, f), src / f)
+    text = (src / fname).read_text()
+    assert text.count(old) >= 1, "mutation anchor missing: " + what
+    (src / fname).write_text(text.replace(old, new, 1))
+    so = O.build(force=True, src_dir=str(src), out_path=str(tmp_path / "mutant.so"))
+    L = O.load_path(so)
+    caught = []
+    with O.use(L), warnings.catch_warnings():
+        warnings.simplefilter("ignore")
+        for pin in P.ALL_PINS:
+            try:
+                pin()
+            except Exception:  # any failure of the pin rejects the mutant
+                caught.append(pin.__name__)
+    assert caught, "planted mistake not caught by any pin: " + what
