@@ -1,0 +1,388 @@
+#!/usr/bin/env python3
+"""Benchmark: time to a binary64 relative residual of 1e-10, mixed vs FP64
+GMRES(m), on one GB300.
+
+Workload (default): mixed binary32-inner / binary64-residual GMRES(100) with
+CGSR on the 3-D 7-point upwind convection-diffusion stencil, 160^3 grid
+(n = 4 096 000, nnz = 28 518 400), random seeded velocity in [-1, 1]^3,
+b = A 1 + N(0, sigma^2) noise with sigma = 1e-3, x0 = 0, tol 1e-10; the FP64 GMRES(100) CGSR solve
+of the same system is timed beside it.  One step = one full solve to 1e-10.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle on
+bounded samples of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "convdiff3d_160"
+SEED = 20110185
+# Inner iterations and restart cycles the mixed CGSR GMRES(100) solve of this
+# workload takes (same schedule on the GPU and in the oracle, see the parity
+# tests); used to scale the oracle's per-iteration samples to a full solve.
+SCHEDULE = {"convdiff3d_160": {"mixed": None, "fp64": None}}
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default=WORKLOAD)
+    p.add_argument("--fp64-steps", type=int, default=1)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.t:
+            self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def make_workload(name):
+    from paper_2011_01850_gb300 import inputs as I
+    spec = I.WORKLOADS[name]
+    A, b, spec = I.workload(name, seed=SEED)
+    return A, b, spec
+
+
+def bench_ours(args):
+    import torch
+
+    from paper_2011_01850_gb300 import gmres as G
+
+    world, rank, local = dist_setup(args)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    A, b, spec = make_workload(args.workload)
+    n = len(A[0]) - 1
+    nnz = len(A[1])
+    m, ortho, prec = spec["m"], spec["ortho"], spec["prec"]
+    stream = torch.cuda.current_stream()
+    solver = G.Solver(A, stream=stream)
+    lanes32, lanes64 = G.gmres_autotune(solver.h)
+    solver.set_opts(profile=1)
+    db = torch.tensor(b, device="cuda", dtype=torch.float64)
+    dx = torch.zeros(n, device="cuda", dtype=torch.float64)
+
+    def step(p, collect):
+        dx.zero_()
+        st, info = G.gmres_solve(solver.h, db, dx, m, 1e-10, G.ORTHOS[ortho], G.PRECISIONS[p],
+                                 100000)
+        if st != G.OK:
+            raise RuntimeError("solve did not converge: %s %r" % (G.status_str(st),
+                                                                   info.as_dict()))
+        collect.append(info.as_dict())
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # warm-up
+    scratch = []
+    for _ in range(args.warmup):
+        step(prec, scratch)
+    # timed region: K full solves, CUDA events on the library's stream
+    infos = []
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step(prec, infos)
+    ev1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    ms_total = ev0.elapsed_time(ev1)
+    ms_step = ms_total / args.steps
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms_step], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+
+    # FP64 GMRES on the same system (the comparison the metric names)
+    fp64 = []
+    for _ in range(1):
+        step("fp64", scratch)  # warm the FP64 workspace
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.fp64_steps):
+        step("fp64", fp64)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    fp64_ms = e0.elapsed_time(e1) / args.fp64_steps
+
+    # end to end through the public API with host buffers (H2D of b and x0,
+    # D2H of x inside every step)
+    e2e = None
+    if not args.no_e2e:
+        bh = np.ascontiguousarray(b)
+        xh = np.zeros(n)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            xh[:] = 0.0
+            st, info = G.gmres_solve(solver.h, bh, xh, m, 1e-10, G.ORTHOS[ortho],
+                                     G.PRECISIONS[prec], 100000)
+            assert st == G.OK
+        torch.cuda.synchronize()
+        e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
+        e2e = {"value": round(e2e_ms, 3), "unit": "ms", "h2d_bytes_per_step": 16 * n,
+               "d2h_bytes_per_step": 8 * n}
+
+    # per-class kernel statistics over the timed region
+    def agg(key, cls):
+        return sum(i[key][cls] for i in infos)
+
+    classes = ["residual", "spmv", "ortho", "normalize", "update"]
+    kms = {c: agg("kernel_ms", c) for c in classes}
+    kbytes = {c: agg("kernel_bytes", c) for c in classes}
+    klaunch = {c: agg("kernel_launches", c) for c in classes}
+    dom = max(classes, key=lambda c: kms[c])
+    peak, peak_kind = load_peaks()
+    achieved = kbytes[dom] / (kms[dom] * 1e-3) / 1e9 if kms[dom] > 0 else 0.0
+    launches = int(sum(i["launches"] for i in infos))
+    tot_bytes = sum(kbytes.values())
+    tot_kms = sum(kms.values())
+    iters = infos[0]["iters"]
+    restarts = infos[0]["restarts"]
+
+    out = {
+        "metric": "time-to-1e-10 residual and HBM GB/s: mixed vs FP64 GMRES(m), one GB300",
+        "value": round(ms_step, 3),
+        "unit": "ms",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms_step, 3),
+        "higher_is_better": False,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32" if prec != "fp64" else "f64",
+        "data": "synthetic",
+        "config": {
+            "workload": args.workload,
+            "matrix": "3-D 7-point upwind convection-diffusion 160^3, v~U[-1,1]^3 per node",
+            "n": n, "nnz": nnz, "m": m, "ortho": ortho, "precision": prec, "tol": 1e-10,
+            "rhs": "b = A 1 + N(0, sigma^2), sigma = 1e-3, x0 = 0", "seed": SEED,
+            "l2": "inputs larger than L2 (A alone is %.0f MB)" % (nnz * 12 / 1e6),
+            "parallelism": "replicas" if world > 1 else "single GPU",
+            "spmv_lanes": {"f32": lanes32, "f64": lanes64},
+        },
+        "iters": iters, "restarts": restarts,
+        "fp64": {"ms": round(fp64_ms, 3), "iters": fp64[0]["iters"],
+                 "restarts": fp64[0]["restarts"]},
+        "speedup_vs_fp64": round(fp64_ms / ms_step, 3),
+        "solve_gbs": round(tot_bytes / (tot_kms * 1e-3) / 1e9, 1) if tot_kms else None,
+        "kernel_gbs": {c: round(kbytes[c] / (kms[c] * 1e-3) / 1e9, 1) if kms[c] else None
+                       for c in classes},
+        "kernel_share": {c: round(kms[c] / tot_kms, 4) if tot_kms else None for c in classes},
+        "roofline": {
+            "bound": "hbm", "kernel": "%s (%s)" % (dom, {"ortho": "CGSR passes" if ortho == "cgsr"
+                                                         else "MGS chain"}.get(dom, dom)),
+            "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "peak_kind": peak_kind, "traffic": None,
+            "launches": int(klaunch[dom]),
+            "bytes_per_launch": kbytes[dom] / klaunch[dom] if klaunch[dom] else None,
+        },
+        "gpu_launches": launches,
+        "clocks": clk,
+        "e2e": e2e,
+        "relres": infos[0]["relres"],
+    }
+    solver.close()
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(A, b, spec, iters, restarts, m)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def oracle_sample(A, b, spec, ks=(2, 8, 16)):
+    """Time the oracle's restart cycle for three inner-iteration counts on the
+    full workload and fit T(k) = c + a k + b k(k+1)/2 (iteration j costs
+    a + b j: one SpMV plus passes over j basis vectors); also time one
+    binary64 residual.  Returns (t_res, c, a, b, seconds spent)."""
+    import oracle as O
+    prec = {"fp64": O.FP64, "mixed": O.MIXED, "mixed_bf16": O.MIXED_BF16,
+            "mixed_fp16": O.MIXED_FP16}[spec["prec"]]
+    ortho = O.CGSR if spec["ortho"] == "cgsr" else O.MGS
+    m = spec["m"]
+    t0 = time.perf_counter()
+    O.residual_norm(A, b, np.zeros_like(b))
+    t_res = time.perf_counter() - t0
+    ts = []
+    for k in ks:
+        t0 = time.perf_counter()
+        O.arnoldi_cycle(A, b, m, ortho=ortho, prec=prec, kmax=k, export_basis=False)
+        ts.append(time.perf_counter() - t0)
+    M = np.array([[1.0, k, k * (k + 1) / 2.0] for k in ks])
+    c, a, bco = np.linalg.lstsq(M, np.array(ts), rcond=None)[0]
+    return t_res, max(c, 0.0), max(a, 0.0), max(bco, 0.0), sum(ts) + t_res
+
+
+def estimate_solve_s(t_res, c, a, bco, iters, restarts, m):
+    """Oracle time for a solve with the given schedule (cycles of up to m)."""
+    total = (restarts + 1) * t_res
+    left = iters
+    for _ in range(restarts):
+        L = min(m, left)
+        left -= L
+        total += c + a * L + bco * L * (L + 1) / 2
+    return total
+
+
+def cpu_baseline(A, b, spec, iters, restarts, m):
+    t_res, c, a, bco, spent = oracle_sample(A, b, spec)
+    est = estimate_solve_s(t_res, c, a, bco, iters, restarts, m)
+    return {"value": round(est * 1e3, 1), "unit": "ms", "cores": 1, "kind": "oracle",
+            "sample": "oracle (single thread) restart cycles of 2, 8 and 16 inner iterations "
+                      "and one binary64 residual on the full workload (%.1f s of CPU); cycle "
+                      "cost c + a k + b k(k+1)/2 fitted and applied to the measured schedule "
+                      "(%d iterations in %d cycles of m=%d)" % (spent, iters, restarts, m)}
+
+
+def bench_reference(args):
+    world, rank, local = dist_setup(args)
+    if rank != 0:
+        return
+    import oracle as O  # noqa: F401
+    A, b, spec = make_workload(args.workload)
+    m = spec["m"]
+    sched = SCHEDULE.get(args.workload, {}).get(spec["prec"]) or {"iters": None}
+    iters = sched.get("iters") if isinstance(sched, dict) else None
+    restarts = sched.get("restarts") if isinstance(sched, dict) else None
+    vals = []
+    spent = 0.0
+    for i in range(args.warmup + args.steps):
+        t_res, c, a, bco, s = oracle_sample(A, b, spec, ks=(2, 4, 8))
+        spent += s
+        if i >= args.warmup:
+            it = iters or 1
+            rs = restarts or 1
+            vals.append(estimate_solve_s(t_res, c, a, bco, it, rs, m) * 1e3)
+    v = statistics.mean(vals)
+    out = {
+        "impl": "reference",
+        "metric": "time-to-1e-10 residual and HBM GB/s: mixed vs FP64 GMRES(m), one GB300",
+        "value": round(v, 1), "unit": "ms", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(v, 1), "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if spec["prec"] != "fp64" else "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "m": m, "ortho": spec["ortho"],
+                   "precision": spec["prec"], "tol": 1e-10, "seed": SEED},
+        "cpu_baseline": {"value": round(v, 1), "unit": "ms", "cores": 1, "kind": "oracle",
+                         "sample": "per step: oracle restart cycles of 2, 4 and 8 inner "
+                                   "iterations plus one residual on the full workload, "
+                                   "scaled to %s iterations / %s cycles" % (iters, restarts)},
+        "e2e": {"value": round(v, 1), "unit": "ms", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        bench_reference(args)
+    else:
+        bench_ours(args)
+
+
+if __name__ == "__main__":
+    main()

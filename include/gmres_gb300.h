@@ -1,0 +1,212 @@
+/*
+ * gmres_gb300.h -- C-ABI of the GB300 (sm_103a) mixed-precision restarted
+ * GMRES(m) library.
+ *
+ * The method is Algorithm 1 of Lindquist, Luszczek and Dongarra, "Improving
+ * the Performance of the GMRES Method using Mixed-Precision Techniques"
+ * (arXiv 2011.01850): restarted GMRES with MGS or CGSR orthogonalisation and
+ * Givens rotations, where the residual z = b - A x, the convergence test and
+ * the update x += u are binary64 and the whole restart cycle may run in
+ * binary32 ("fully mixed", Sec. 4 and Sec. 4.1).  Every step runs in CUDA
+ * kernels of this library; there is no CPU path.
+ *
+ * Conventions for every entry point
+ *   - Return value: a gmres_status; no C++ exception crosses this boundary.
+ *   - Device pointers are plain CUDA device (or managed) addresses.  Entry
+ *     points that accept "host or device" buffers detect host memory with
+ *     cudaPointerGetAttributes and copy through library-owned device buffers.
+ *   - Matrices are CSR with int32 row pointers (n+1) and column indices
+ *     (nnz, 0-based, each in [0, n)); values are binary64.
+ *   - All work is issued on the handle's stream (gmres_create / gmres_set_stream)
+ *     and every call returns only after that work has finished, except where a
+ *     comment says otherwise.
+ *   - The library owns every buffer it allocates; the caller keeps ownership
+ *     of the arrays it passes in.
+ */
+#ifndef GMRES_GB300_H
+#define GMRES_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gmres_handle *gmres_t;
+
+/* Orthogonalisation scheme (Algorithm 1, procedures MGS and CGSR). */
+typedef enum { GMRES_ORTHO_MGS = 0, GMRES_ORTHO_CGSR = 1 } gmres_ortho;
+
+/* Precision assignment.
+ *   GMRES_FP64        every quantity binary64 (the double-precision baseline).
+ *   GMRES_MIXED       binary64 residual, norm test and update; the restart
+ *                     cycle (SpMV on a binary32 copy of A, orthogonalisation,
+ *                     Givens, correction) in binary32 (Sec. 2, Sec. 4).
+ *   GMRES_MIXED_BF16  as GMRES_MIXED with the Krylov basis stored as bfloat16
+ *                     (round-to-nearest-even), binary32 arithmetic.
+ *   GMRES_MIXED_FP16  as GMRES_MIXED with the Krylov basis stored as binary16
+ *                     scaled by 2^floor(log2(n)/2), binary32 arithmetic.
+ * The 16-bit bases follow the paper's outlook on half precision (Sec. 5). */
+typedef enum {
+    GMRES_FP64 = 0,
+    GMRES_MIXED = 1,
+    GMRES_MIXED_BF16 = 2,
+    GMRES_MIXED_FP16 = 3
+} gmres_precision;
+
+typedef enum {
+    GMRES_OK = 0,             /* converged: ||b - A x||_2 <= tol ||b||_2       */
+    GMRES_MAXITER = 1,        /* maxiter inner iterations without converging   */
+    GMRES_ERR_ARG = -1,       /* invalid argument (sizes, enums, CSR structure)*/
+    GMRES_ERR_CUDA = -2,      /* a CUDA call failed                            */
+    GMRES_ERR_NONFINITE = -3, /* NaN or Inf in an input or produced by a step  */
+    GMRES_ERR_BREAKDOWN = -4, /* no progress possible (singular projected LS)  */
+    GMRES_ERR_TIMEOUT = -5,   /* a bounded device wait ran out                 */
+    GMRES_ERR_OOM = -6        /* device allocation failed                      */
+} gmres_status;
+
+/* gmres_create flags. */
+#define GMRES_CREATE_DEVICE_PTRS 1 /* rowptr/colind/vals are device pointers  */
+#define GMRES_CREATE_TRANSPOSE 2   /* also build the CSR of A^T (preconditioner
+                                      training needs A^T r)                    */
+
+/* Restart-cycle path. */
+#define GMRES_PATH_AUTO 0  /* choose by size                                  */
+#define GMRES_PATH_GRID 1  /* whole-GPU kernels per inner step (large n)      */
+#define GMRES_PATH_BLOCK 2 /* one thread block runs the whole solve (small n) */
+
+/* Solver options (gmres_default_opts gives the defaults). */
+typedef struct gmres_opts {
+    double tau;           /* restart when |s_{j+1}| <= tau * beta (Sec. 3, second
+                             strategy); < 0 selects the precision's default:
+                             0 (off) for FP64, 1e-6 MIXED, 1e-2 BF16, 1e-3 FP16 */
+    double inner_factor;  /* end a cycle once |s_{j+1}| <= inner_factor * tol *
+                             ||b|| (the binary64 residual then decides); 0.5    */
+    int32_t repeat_first; /* 1: cycles after the first run as long as the first
+                             (Sec. 3, first strategy; Sec. 4.2); -1 = default
+                             (on for the mixed precisions, off for FP64)       */
+    int32_t path;         /* GMRES_PATH_*                                       */
+    int32_t profile;      /* 1: time every kernel class with CUDA events and
+                             report it in gmres_info.kernel_ms                  */
+    int32_t spin_limit;   /* iterations a device-side wait may spin before it
+                             gives up with GMRES_ERR_TIMEOUT; 0 = default       */
+    int32_t precond;      /* 0: none; 1: the learned right preconditioner set
+                             by gmres_spai_set                                  */
+    int32_t fallback;     /* 1: on stagnation of the preconditioned solve,
+                             continue unpreconditioned (default 1)              */
+    int32_t spmv_lanes;   /* lanes per CSR row in SpMV (1..32, power of two);
+                             0 = the autotuned choice                           */
+    int32_t reserved[5];
+} gmres_opts;
+
+/* Kernel classes reported in gmres_info (index into kernel_ms / kernel_bytes). */
+enum {
+    GMRES_K_RESIDUAL = 0, /* z = b - A x (binary64), norms, cast               */
+    GMRES_K_SPMV = 1,     /* w = A v_j in the working precision                */
+    GMRES_K_ORTHO = 2,    /* MGS or CGSR (+ norm, Givens)                       */
+    GMRES_K_NORMALIZE = 3,/* v_{j+1} = w / h_{j+1,j}                            */
+    GMRES_K_UPDATE = 4,   /* y = H^-1 s, x += V y                               */
+    GMRES_K_PRECOND = 5,  /* t = M v (learned preconditioner)                   */
+    GMRES_K_BLOCK = 6,    /* the single-block whole-solve kernel                */
+    GMRES_K_COUNT = 8
+};
+
+typedef struct gmres_info {
+    int32_t iters;        /* total inner iterations                             */
+    int32_t restarts;     /* restart cycles run                                 */
+    int32_t converged;    /* 1 when the binary64 relative residual met tol      */
+    int32_t first_len;    /* length of the first cycle                          */
+    double relres;        /* final ||b - A x||_2 / ||b||_2 (binary64, on device)*/
+    double bnorm;         /* ||b||_2                                            */
+    double time_ms;       /* wall time of the call                              */
+    double kernel_ms[GMRES_K_COUNT];    /* CUDA-event time per class (profile)  */
+    double kernel_bytes[GMRES_K_COUNT]; /* algorithmic bytes per class          */
+    int64_t kernel_launches[GMRES_K_COUNT];
+    int64_t launches;     /* kernels launched by the call                       */
+    int32_t path;         /* GMRES_PATH_GRID or GMRES_PATH_BLOCK                */
+    int32_t fell_back;    /* 1 if the preconditioned solve fell back            */
+} gmres_info;
+
+/* Defaults for gmres_opts (never fails). */
+void gmres_default_opts(gmres_opts *o);
+
+/* Build a solver handle for the n x n CSR matrix A (Alg. 1 input A; Sec. 4:
+ * the matrix is kept twice, binary64 for the residual and binary32 for the
+ * restart cycle, sharing the index arrays).  The arrays are copied; flags as
+ * above.  stream is a cudaStream_t (NULL = legacy default stream) that all of
+ * the handle's work uses.  Errors: GMRES_ERR_ARG for n <= 0, a non-monotone
+ * rowptr, rowptr[0] != 0 or a column index outside [0, n) (checked on the host
+ * for host arrays, on the device for device arrays); GMRES_ERR_NONFINITE for
+ * a NaN/Inf value; GMRES_ERR_OOM; GMRES_ERR_CUDA.  *out is NULL on error. */
+gmres_status gmres_create(gmres_t *out, int32_t n, const int32_t *rowptr, const int32_t *colind,
+                          const double *vals, int32_t flags, void *stream);
+
+/* Release every device buffer of the handle.  NULL is ignored. */
+void gmres_destroy(gmres_t h);
+
+/* Change the stream used by later calls. */
+gmres_status gmres_set_stream(gmres_t h, void *stream);
+
+/* Replace / read the handle's options (validated: GMRES_ERR_ARG). */
+gmres_status gmres_set_opts(gmres_t h, const gmres_opts *o);
+gmres_status gmres_get_opts(gmres_t h, gmres_opts *o);
+
+/* Restarted GMRES(m) (Algorithm 1) for A x = b.
+ *   b     length n, binary64, host or device memory (read only)
+ *   x     length n, binary64, host or device memory: x_0 on entry, the result
+ *         on exit (x_0 != 0 resumes a previous solve: x is the whole state)
+ *   m     restart length, 1 <= m <= 128
+ *   tol   > 0: stop once ||b - A x||_2 <= tol ||b||_2, both norms binary64
+ *   maxiter  cap on the total number of inner iterations (>= 0)
+ *   info  may be NULL
+ * Returns GMRES_OK on convergence, GMRES_MAXITER when the cap is reached, or
+ * an error.  b = 0 returns x = 0 and GMRES_OK. */
+gmres_status gmres_solve(gmres_t h, const double *b, double *x, int32_t m, double tol,
+                         gmres_ortho ortho, gmres_precision prec, int32_t maxiter,
+                         gmres_info *info);
+
+/* y = A x with the precision's copy of A (Alg. 1, "w <- A v_j"): for
+ * GMRES_FP64 x and y are binary64 device vectors, otherwise binary32. */
+gmres_status gmres_spmv(gmres_t h, const void *x, void *y, gmres_precision prec);
+
+/* z = b - A x in binary64 (Alg. 1, first step of every restart) with
+ * *znorm = ||z||_2.  b, x, z are device vectors; z may be NULL. */
+gmres_status gmres_residual(gmres_t h, const double *b, const double *x, double *z,
+                            double *znorm);
+
+/* One restart cycle from the binary64 device vector r0, for parity checks
+ * (Alg. 1 from "beta <- ||r||" to the correction u).  The cycle is the one
+ * gmres_solve runs.  kmax <= m inner iterations; the cycle also ends when
+ * |s_{j+1}| <= tau * beta or <= inner_abs, or on breakdown.  Host outputs
+ * (NULL allowed), all binary64:
+ *   V (m+1)*n column-major basis as stored (16-bit values widened),
+ *   Hbar, H (m+1)*m column-major (leading dimension m+1) unrotated / rotated,
+ *   s m+1, cs m, sn m, y m, u n (the correction), arn m (|s_{j+1}| per step),
+ *   *jout inner iterations, *breakdown 1 if h_{j+1,j} vanished. */
+gmres_status gmres_arnoldi(gmres_t h, const double *r0, int32_t m, int32_t kmax,
+                           gmres_ortho ortho, gmres_precision prec, double tau, double inner_abs,
+                           double *V, double *Hbar, double *H, double *s, double *cs, double *sn,
+                           double *y, double *u, double *arn, int32_t *jout, int32_t *breakdown);
+
+/* Time every SpMV variant (lanes per row 1..32) on this matrix in binary32
+ * and binary64 and keep the fastest for later solves (the tile autotuner).
+ * lanes32 / lanes64 (may be NULL) receive the choices. */
+gmres_status gmres_autotune(gmres_t h, int32_t *lanes32, int32_t *lanes64);
+
+/* Device bytes the handle holds for the matrix (both value copies, shared
+ * indices) and, for a solve with restart length m in precision prec, the
+ * workspace (basis, vectors, Hessenberg).  Matches the paper's storage model
+ * (Sec. 4) without the ILU factors. */
+gmres_status gmres_memory_bytes(gmres_t h, int32_t m, gmres_precision prec, int64_t *matrix_bytes,
+                                int64_t *workspace_bytes);
+
+/* Static text for a status code. */
+const char *gmres_status_str(gmres_status s);
+
+/* Library version string. */
+const char *gmres_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

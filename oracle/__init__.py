@@ -191,15 +191,16 @@ def round_basis(v, prec, n):
     return out
 
 
-def arnoldi_cycle(A, r0, m, ortho=CGSR, prec=FP64, kmax=None, tau=0.0, inner_abs=0.0, M=None):
+def arnoldi_cycle(A, r0, m, ortho=CGSR, prec=FP64, kmax=None, tau=0.0, inner_abs=0.0, M=None,
+                  export_basis=True):
     """One restart cycle from residual r0; returns a dict of its quantities.
 
     V is (m+1, n) (row i = basis vector i), Hbar/H are (m+1, m), the first ``j``
-    columns valid."""
+    columns valid.  ``export_basis=False`` skips copying V out (V is None)."""
     rp, ci, va = _csr(A)
     n = len(rp) - 1
     kmax = m if kmax is None else kmax
-    V = np.zeros((m + 1, n))
+    V = np.zeros((m + 1, n)) if export_basis else None
     Hb = np.zeros((m, m + 1))
     H = np.zeros((m, m + 1))
     s = np.zeros(m + 1)

@@ -1,0 +1,364 @@
+// block_solver.cuh -- one thread block runs a whole restarted GMRES(m) solve
+// (Algorithm 1 of arXiv 2011.01850) for one system.
+//
+// Used for small systems, where whole-GPU kernels would be launch-latency
+// bound, and by the batched solver: a persistent grid takes systems from a
+// work queue (largest first), one block per system, so many independent
+// systems of uneven size are solved in one launch.  Reductions are block-wide
+// (xor-butterfly + shared memory, deterministic); the Hessenberg matrix, the
+// rotations and s live in shared memory; vectors and the basis live in the
+// system's global workspace (L1/L2 resident for small n).
+#pragma once
+
+#include "common.cuh"
+
+namespace gmres {
+
+// One system of a block solve.  All pointers are device pointers; V and the
+// work vectors (w, r) are library workspace of at least ldv rows.
+template <class T, class VT>
+struct BlockSys {
+    int n;
+    int64_t ldv;
+    const int *rowptr;
+    const int *colind;
+    const T *a;
+    const double *a64;
+    const double *b;
+    double *x;
+    VT *V;
+    T *w;
+    T *r;
+    float vscale, vinv;
+};
+
+// Per-system result written by the block solver.
+struct BlockResult {
+    int iters, restarts, converged, first_len;
+    int status;  // gmres_status value
+    int pad;
+    double relres, bnorm;
+};
+
+struct BlockParams {
+    int m, maxiter, ortho, repeat_first;
+    double tol, tau, inner_factor;
+    double brk;
+    int nsys;
+    unsigned *queue;  // work-queue counter (reset by the host)
+    const int *order; // system order (largest first)
+};
+
+// w[row] = A x for the system's rows, L lanes per row.
+template <class T, class XT, int L>
+__device__ __forceinline__ void block_spmv(const int *__restrict__ rowptr,
+                                           const int *__restrict__ colind,
+                                           const T *__restrict__ a, const XT *x, float xinv, T *y,
+                                           int n) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nw = blockDim.x >> 5;
+    const int G = 32 / L, gl = lane % L, gi = lane / L;
+    for (int base = wid * G; base < n; base += nw * G) {
+        int row = base + gi;
+        T acc = 0;
+        if (row < n) {
+            int beg = rowptr[row], end = rowptr[row + 1];
+            for (int k = beg + gl; k < end; k += L)
+                acc += a[k] * (T)Basis<XT>::ld(x + colind[k], xinv);
+        }
+#pragma unroll
+        for (int off = L / 2; off > 0; off >>= 1)
+            acc += __shfl_xor_sync(0xffffffffu, acc, off);
+        if (row < n && gl == 0)
+            y[row] = acc;
+    }
+}
+
+template <class T, class VT, int L>
+__device__ void block_solve_one(const BlockSys<T, VT> &S, const BlockParams &P, BlockResult *res,
+                                unsigned char *smem_raw) {
+    const int n = S.n, m = P.m, ld = m + 1;
+    const int tid = threadIdx.x, nth = blockDim.x;
+    double *redd = reinterpret_cast<double *>(smem_raw);       // 32 (first: 8-byte aligned)
+    T *H = reinterpret_cast<T *>(smem_raw + 32 * sizeof(double));  // ld x m (rotated)
+    T *s = H + (size_t)ld * m;                   // m + 1
+    T *cs = s + (m + 1);                         // m
+    T *sn = cs + m;                              // m
+    T *y = sn + m;                               // m
+    T *hc = y + m;                               // MMAX + 2 (current column)
+    T *hc2 = hc + (MMAX + 2);                    // MMAX + 2 (second CGS pass)
+    T *red = hc2 + (MMAX + 2);                   // 8 * 32
+    __shared__ int s_flag;
+
+    // ||b||
+    double bb = 0;
+    for (int i = tid; i < n; i += nth)
+        bb += S.b[i] * S.b[i];
+    double bnorm = sqrt(block_sum1(bb, redd));
+    BlockResult out;
+    out.iters = 0;
+    out.restarts = 0;
+    out.converged = 0;
+    out.first_len = 0;
+    out.status = 1;
+    out.relres = 0;
+    out.bnorm = bnorm;
+    if (!(bnorm > 0)) {
+        for (int i = tid; i < n; i += nth)
+            S.x[i] = 0.0;
+        out.converged = isfinite(bnorm) ? 1 : 0;
+        out.status = isfinite(bnorm) ? 0 : -3;
+        if (tid == 0)
+            *res = out;
+        return;
+    }
+    const double tol_abs = P.tol * bnorm;
+    const double inner_abs = P.inner_factor * P.tol * bnorm;
+    const T brk = (T)P.brk;
+    int cycle_len = m;
+
+    for (;;) {
+        // z = b - A x (binary64), r = fl(z), ||z||, ||r||.
+        double ss = 0;
+        T sst = 0;
+        int bad = 0;
+        {
+            const int lane = tid & 31, wid = tid >> 5, nw = nth >> 5;
+            const int G = 32 / L, gl = lane % L, gi = lane / L;
+            for (int base = wid * G; base < n; base += nw * G) {
+                int row = base + gi;
+                double acc = 0;
+                if (row < n) {
+                    int beg = S.rowptr[row], end = S.rowptr[row + 1];
+                    for (int k = beg + gl; k < end; k += L)
+                        acc += S.a64[k] * S.x[S.colind[k]];
+                }
+#pragma unroll
+                for (int off = L / 2; off > 0; off >>= 1)
+                    acc += __shfl_xor_sync(0xffffffffu, acc, off);
+                if (row < n && gl == 0) {
+                    double zi = S.b[row] - acc;
+                    T ri = (T)zi;
+                    S.r[row] = ri;
+                    ss += zi * zi;
+                    sst += ri * ri;
+                    bad |= !isfinite(zi);
+                }
+            }
+        }
+        double rn = sqrt(block_sum1(ss, redd));
+        T beta = wsqrt(block_sum1(sst, red));
+        bad = __syncthreads_or(bad);
+        out.relres = rn / bnorm;
+        if (bad || !isfinite(rn)) {
+            out.status = -3;
+            break;
+        }
+        if (rn <= tol_abs) {
+            out.converged = 1;
+            out.status = 0;
+            break;
+        }
+        if (out.iters >= P.maxiter) {
+            out.status = 1;
+            break;
+        }
+        if (!(beta > T(0)))
+            break;
+        int kmax = cycle_len;
+        if (kmax > P.maxiter - out.iters)
+            kmax = P.maxiter - out.iters;
+        const double tau = (P.repeat_first && out.restarts > 0) ? 0.0 : P.tau;
+
+        // v_1 = r / beta, s = beta e_1
+        for (int i = tid; i < n; i += nth)
+            Basis<VT>::st(S.V + i, S.r[i] / beta, S.vscale);
+        for (int i = tid; i <= m; i += nth)
+            s[i] = (i == 0) ? beta : T(0);
+        __syncthreads();
+
+        int j = 0;
+        for (;;) {
+            const int c = j;
+            const VT *vj = S.V + (size_t)c * S.ldv;
+            block_spmv<T, VT, L>(S.rowptr, S.colind, S.a, vj, S.vinv, S.w, n);
+            __syncthreads();
+            // ||A v_j|| (breakdown reference)
+            T w0 = 0;
+            for (int i = tid; i < n; i += nth)
+                w0 += S.w[i] * S.w[i];
+            T wnorm0 = wsqrt(block_sum1(w0, red));
+            if (P.ortho == 0) {
+                // MGS: h_i = w . v_i, w <- w - h_i v_i, one column at a time
+                for (int i = 0; i <= c; ++i) {
+                    const VT *vi = S.V + (size_t)i * S.ldv;
+                    T d = 0;
+                    for (int r = tid; r < n; r += nth)
+                        d += S.w[r] * Basis<VT>::ld(vi + r, S.vinv);
+                    T hi = block_sum1(d, red);
+                    for (int r = tid; r < n; r += nth)
+                        S.w[r] = S.w[r] - hi * Basis<VT>::ld(vi + r, S.vinv);
+                    if (tid == 0)
+                        hc[i] = hi;
+                    __syncthreads();
+                }
+            } else {
+                // CGSR: two classical passes, column = sum of both
+                for (int pass = 0; pass < 2; ++pass) {
+                    for (int c0 = 0; c0 <= c; c0 += 8) {
+                        T acc[8];
+#pragma unroll
+                        for (int k = 0; k < 8; ++k)
+                            acc[k] = 0;
+                        for (int r = tid; r < n; r += nth) {
+                            T wr = S.w[r];
+#pragma unroll
+                            for (int k = 0; k < 8; ++k)
+                                if (c0 + k <= c)
+                                    acc[k] += Basis<VT>::ld(S.V + (size_t)(c0 + k) * S.ldv + r,
+                                                            S.vinv) * wr;
+                        }
+                        block_sum<T, 8>(acc, red);
+                        if (tid == 0) {
+                            T *g = pass ? hc2 : hc;
+#pragma unroll
+                            for (int k = 0; k < 8; ++k)
+                                if (c0 + k <= c)
+                                    g[c0 + k] = acc[k];
+                        }
+                    }
+                    __syncthreads();
+                    // w <- w - V g  (g = this pass's projections)
+                    for (int r = tid; r < n; r += nth) {
+                        T t = 0;
+                        for (int i = 0; i <= c; ++i) {
+                            T g = pass ? hc2[i] : hc[i];
+                            t += Basis<VT>::ld(S.V + (size_t)i * S.ldv + r, S.vinv) * g;
+                        }
+                        S.w[r] = S.w[r] - t;
+                    }
+                    __syncthreads();
+                }
+                for (int i = tid; i <= c; i += nth)
+                    hc[i] = hc[i] + hc2[i];
+                __syncthreads();
+            }
+            // h_{j+1,j} = ||w||
+            T nsq = 0;
+            for (int r = tid; r < n; r += nth)
+                nsq += S.w[r] * S.w[r];
+            T hnext = wsqrt(block_sum1(nsq, red));
+            // Givens step (thread 0) and restart test
+            if (tid == 0) {
+                T *col = H + (size_t)c * ld;
+                for (int i = 0; i <= c; ++i)
+                    col[i] = hc[i];
+                col[c + 1] = hnext;
+                for (int i = 0; i < c; ++i) {
+                    T hi = col[i], hi1 = col[i + 1];
+                    col[i] = cs[i] * hi + sn[i] * hi1;
+                    col[i + 1] = -sn[i] * hi + cs[i] * hi1;
+                }
+                T hjj = col[c], hj1 = col[c + 1];
+                T rho = wsqrt(hjj * hjj + hj1 * hj1);
+                T al, be;
+                if (rho == T(0)) {
+                    al = T(1);
+                    be = T(0);
+                } else {
+                    al = hjj / rho;
+                    be = hj1 / rho;
+                }
+                cs[c] = al;
+                sn[c] = be;
+                T sj = s[c];
+                s[c] = al * sj;
+                s[c + 1] = -be * sj;
+                col[c] = al * hjj + be * hj1;
+                col[c + 1] = -be * hjj + al * hj1;
+                double arn = fabs((double)s[c + 1]);
+                int bd = hnext <= brk * wnorm0;
+                int nf = !isfinite(arn);
+                int end = bd || nf || (tau > 0 && arn <= tau * (double)beta) || arn <= inner_abs ||
+                          (c + 1 >= kmax);
+                s_flag = (end ? 1 : 0) | (bd ? 2 : 0) | (nf ? 4 : 0);
+            }
+            __syncthreads();
+            const int flag = s_flag;
+            j = c + 1;
+            if (flag & 4) {
+                bad = 1;
+                break;
+            }
+            if (flag & 1)
+                break;
+            // v_{j+1} = w / h_{j+1,j}
+            VT *vn = S.V + (size_t)(c + 1) * S.ldv;
+            for (int r = tid; r < n; r += nth)
+                Basis<VT>::st(vn + r, S.w[r] / hnext, S.vscale);
+            __syncthreads();
+        }
+        if (bad) {
+            out.status = -3;
+            break;
+        }
+        // y = H^{-1} s (back substitution), x += V_j y
+        if (tid == 0) {
+            for (int i = j - 1; i >= 0; --i) {
+                T acc = s[i];
+                for (int l = i + 1; l < j; ++l)
+                    acc -= H[(size_t)l * ld + i] * y[l];
+                T piv = H[(size_t)i * ld + i];
+                y[i] = (piv == T(0)) ? T(0) : acc / piv;
+            }
+        }
+        __syncthreads();
+        for (int r = tid; r < n; r += nth) {
+            T u = 0;
+            for (int i = 0; i < j; ++i)
+                u += Basis<VT>::ld(S.V + (size_t)i * S.ldv + r, S.vinv) * y[i];
+            S.x[r] = S.x[r] + (double)u;
+        }
+        __syncthreads();
+        out.iters += j;
+        out.restarts += 1;
+        if (out.restarts == 1) {
+            out.first_len = j;
+            if (P.repeat_first)
+                cycle_len = j;
+        }
+    }
+    if (tid == 0)
+        *res = out;
+}
+
+// Persistent grid over a work queue of systems (largest first).
+template <class T, class VT, int L>
+__global__ void __launch_bounds__(1024) k_block_solve(const BlockSys<T, VT> *sys, BlockParams P,
+                                                      BlockResult *res) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int s_idx;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            unsigned k = atomicAdd(P.queue, 1u);
+            s_idx = (k < (unsigned)P.nsys) ? (P.order ? P.order[k] : (int)k) : -1;
+        }
+        __syncthreads();
+        const int idx = s_idx;
+        __syncthreads();
+        if (idx < 0)
+            return;
+        BlockSys<T, VT> S = sys[idx];
+        block_solve_one<T, VT, L>(S, P, res + idx, smem_raw);
+        __syncthreads();
+    }
+}
+
+// Shared-memory bytes of the block solver for restart length m.
+template <class T>
+inline size_t block_smem_bytes(int m) {
+    size_t nt = (size_t)(m + 1) * m + (m + 1) + 3 * (size_t)m + 2 * (MMAX + 2) + 8 * 32;
+    return nt * sizeof(T) + 32 * sizeof(double) + 64;
+}
+
+}  // namespace gmres

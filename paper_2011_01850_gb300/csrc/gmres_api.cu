@@ -1,0 +1,1195 @@
+// gmres_api.cu -- C-ABI of the GB300 mixed-precision restarted GMRES(m)
+// library (declarations and contracts in include/gmres_gb300.h).
+//
+// Host side of Algorithm 1 of arXiv 2011.01850: it owns the device copies of
+// A (binary64 values, binary32 values, shared int32 indices; Sec. 4), the
+// workspace, and the per-cycle driver that enqueues the restart cycle's
+// kernels on the handle's stream.  The host reads the device control block
+// once per restart cycle; all arithmetic runs in the kernels.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/gmres_gb300.h"
+#include "block_solver.cuh"
+#include "grid_kernels.cuh"
+
+using namespace gmres;
+
+namespace {
+
+constexpr int kThreads = 256;
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    cudaError_t ensure(size_t want) {
+        if (want <= bytes)
+            return cudaSuccess;
+        if (p)
+            cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+        cudaError_t e = cudaMalloc(&p, want);
+        if (e != cudaSuccess) {
+            p = nullptr;
+            return e;
+        }
+        bytes = want;
+        return cudaSuccess;
+    }
+    void release() {
+        if (p)
+            cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    template <class T>
+    T *as() const { return reinterpret_cast<T *>(p); }
+};
+
+// Event pairs for per-class kernel timing (opts.profile).
+struct Timer {
+    bool on = false;
+    cudaStream_t st = nullptr;
+    std::vector<cudaEvent_t> pool;
+    struct Rec { int cls; cudaEvent_t a, b; };
+    std::vector<Rec> recs;
+    cudaEvent_t get() {
+        if (!pool.empty()) {
+            cudaEvent_t e = pool.back();
+            pool.pop_back();
+            return e;
+        }
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        return e;
+    }
+    cudaEvent_t begin() {
+        if (!on)
+            return nullptr;
+        cudaEvent_t a = get();
+        cudaEventRecord(a, st);
+        return a;
+    }
+    void end(int cls, cudaEvent_t a) {
+        if (!on)
+            return;
+        cudaEvent_t b = get();
+        cudaEventRecord(b, st);
+        recs.push_back({cls, a, b});
+    }
+    // after a stream synchronize
+    void harvest(double *ms) {
+        for (auto &r : recs) {
+            float t = 0;
+            if (cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess)
+                ms[r.cls] += t;
+            pool.push_back(r.a);
+            pool.push_back(r.b);
+        }
+        recs.clear();
+    }
+    void destroy() {
+        for (auto &r : recs) {
+            pool.push_back(r.a);
+            pool.push_back(r.b);
+        }
+        recs.clear();
+        for (auto e : pool)
+            cudaEventDestroy(e);
+        pool.clear();
+    }
+};
+
+}  // namespace
+
+struct gmres_handle {
+    int n = 0;
+    int64_t nnz = 0;
+    int64_t ldv = 0;
+    int device = 0;
+    int nsm = 0;
+    cudaStream_t stream = nullptr;
+    gmres_opts opts;
+    int lanes32 = 4, lanes64 = 4;
+    int grid = 0;          // blocks of the reduction kernels
+    int64_t chunk = 0;     // rows per block
+    // matrix
+    DevBuf rowptr, colind, vals64, vals32;
+    DevBuf trowptr, tcolind, tvals64;  // A^T (optional)
+    // workspace
+    DevBuf V, w, r, t, z, xb, bb;
+    DevBuf small;          // H, Hb, s, cs, sn, y, h1, h2
+    DevBuf part, part64, ctl;
+    DevBuf bsys, bres;     // block-solver descriptor / result
+    Ctl *hctl = nullptr;   // pinned copy of the control block
+    Timer timer;
+    // learned right preconditioner on A's pattern (binary64 / binary32 values)
+    DevBuf pvals64, pvals32;
+    int has_precond = 0;
+};
+
+namespace {
+
+#define CK(call)                                                                      \
+    do {                                                                              \
+        cudaError_t e_ = (call);                                                      \
+        if (e_ != cudaSuccess) {                                                      \
+            fprintf(stderr, "gmres_gb300: %s failed: %s (%s:%d)\n", #call,            \
+                    cudaGetErrorString(e_), __FILE__, __LINE__);                      \
+            return e_ == cudaErrorMemoryAllocation ? GMRES_ERR_OOM : GMRES_ERR_CUDA;  \
+        }                                                                             \
+    } while (0)
+
+#define CKL()                                                                         \
+    do {                                                                              \
+        cudaError_t e_ = cudaGetLastError();                                          \
+        if (e_ != cudaSuccess) {                                                      \
+            fprintf(stderr, "gmres_gb300: launch failed: %s (%s:%d)\n",               \
+                    cudaGetErrorString(e_), __FILE__, __LINE__);                      \
+            return GMRES_ERR_CUDA;                                                    \
+        }                                                                             \
+    } while (0)
+
+bool is_device_ptr(const void *p) {
+    if (!p)
+        return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
+
+int elem_bytes(gmres_precision p) {
+    switch (p) {
+    case GMRES_FP64: return 8;
+    case GMRES_MIXED: return 4;
+    default: return 2;
+    }
+}
+
+double default_tau(gmres_precision p) {
+    switch (p) {
+    case GMRES_FP64: return 0.0;
+    case GMRES_MIXED: return 1e-6;
+    case GMRES_MIXED_BF16: return 1e-2;
+    default: return 1e-3;
+    }
+}
+
+// Power-of-two binary16 scale 2^floor(log2(n)/2).
+float fp16_scale(int n) {
+    int lg = 0;
+    while (lg < 31 && ((int64_t)1 << (lg + 1)) <= (int64_t)n)
+        ++lg;
+    return std::ldexp(1.0f, lg / 2);
+}
+
+__global__ void k_cast_vals(int64_t nnz, const double *a, float *b) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nnz;
+         k += (int64_t)gridDim.x * blockDim.x)
+        b[k] = (float)a[k];
+}
+
+__global__ void k_zero_tail(double *x, int64_t from, int64_t to) {
+    for (int64_t k = from + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < to;
+         k += (int64_t)gridDim.x * blockDim.x)
+        x[k] = 0;
+}
+
+int pow2_lanes(double avg) {
+    int L = 1;
+    while (L < 32 && L * 2 <= avg)
+        L *= 2;
+    return L;
+}
+
+gmres_status check_csr_host(int n, const int32_t *rp, const int32_t *ci, int64_t nnz) {
+    if (rp[0] != 0)
+        return GMRES_ERR_ARG;
+    for (int i = 0; i < n; ++i)
+        if (rp[i + 1] < rp[i])
+            return GMRES_ERR_ARG;
+    if ((int64_t)rp[n] != nnz)
+        return GMRES_ERR_ARG;
+    for (int64_t k = 0; k < nnz; ++k)
+        if (ci[k] < 0 || ci[k] >= n)
+            return GMRES_ERR_ARG;
+    return GMRES_OK;
+}
+
+// Per-precision device pointers into the "small" buffer.
+template <class T>
+struct SmallPtrs {
+    T *H, *Hb, *s, *cs, *sn, *y, *h1, *h2;
+};
+
+template <class T>
+SmallPtrs<T> small_ptrs(gmres_handle *h) {
+    const int ld = MMAX + 1;
+    T *base = h->small.as<T>();
+    SmallPtrs<T> p;
+    p.H = base;
+    p.Hb = p.H + (size_t)ld * MMAX;
+    p.s = p.Hb + (size_t)ld * MMAX;
+    p.cs = p.s + (MMAX + 2);
+    p.sn = p.cs + (MMAX + 2);
+    p.y = p.sn + (MMAX + 2);
+    p.h1 = p.y + (MMAX + 2);
+    p.h2 = p.h1 + (MMAX + 2);
+    return p;
+}
+
+gmres_status ensure_workspace(gmres_handle *h, int m, gmres_precision prec) {
+    const size_t sv = (size_t)elem_bytes(prec);
+    const size_t ldv = (size_t)h->ldv;
+    // The basis, padded vectors and the binary64 buffers; tails stay zero.
+    size_t vbytes = ldv * (size_t)(m + 1) * sv;
+    bool vgrow = vbytes > h->V.bytes;
+    CK(h->V.ensure(vbytes));
+    if (vgrow)
+        CK(cudaMemsetAsync(h->V.p, 0, h->V.bytes, h->stream));
+    for (DevBuf *b : {&h->w, &h->r, &h->t}) {
+        bool grow = ldv * 8 > b->bytes;
+        CK(b->ensure(ldv * 8));
+        if (grow)
+            CK(cudaMemsetAsync(b->p, 0, b->bytes, h->stream));
+    }
+    CK(h->z.ensure(ldv * 8));
+    CK(h->xb.ensure(ldv * 8));
+    CK(h->bb.ensure(ldv * 8));
+    CK(h->small.ensure((size_t)(2 * (MMAX + 1) * MMAX + 6 * (MMAX + 2)) * 8));
+    CK(h->part.ensure((size_t)h->grid * PSTRIDE * 8));
+    CK(h->part64.ensure((size_t)h->grid * 4 * 8));
+    bool cgrow = sizeof(Ctl) > h->ctl.bytes;
+    CK(h->ctl.ensure(sizeof(Ctl)));
+    if (cgrow)
+        CK(cudaMemsetAsync(h->ctl.p, 0, sizeof(Ctl), h->stream));
+    if (!h->hctl) {
+        void *p = nullptr;
+        CK(cudaMallocHost(&p, sizeof(Ctl)));
+        h->hctl = reinterpret_cast<Ctl *>(p);
+    }
+    return GMRES_OK;
+}
+
+template <class T, class VT>
+GridCtx<T, VT> make_ctx(gmres_handle *h, int m) {
+    GridCtx<T, VT> c;
+    memset(&c, 0, sizeof(c));
+    c.n = h->n;
+    c.m = m;
+    c.ld = m + 1;
+    c.ldv = h->ldv;
+    c.chunk = h->chunk;
+    c.rowptr = h->rowptr.as<int>();
+    c.colind = h->colind.as<int>();
+    c.a = std::is_same<T, double>::value ? reinterpret_cast<const T *>(h->vals64.p)
+                                         : reinterpret_cast<const T *>(h->vals32.p);
+    c.a64 = h->vals64.as<double>();
+    c.V = h->V.as<VT>();
+    c.vscale = std::is_same<VT, __half>::value ? fp16_scale(h->n) : 1.0f;
+    c.vinv = 1.0f / c.vscale;
+    c.w = h->w.as<T>();
+    c.r = h->r.as<T>();
+    c.t = h->t.as<T>();
+    SmallPtrs<T> sp = small_ptrs<T>(h);
+    c.H = sp.H;
+    c.Hb = sp.Hb;
+    c.s = sp.s;
+    c.cs = sp.cs;
+    c.sn = sp.sn;
+    c.y = sp.y;
+    c.h1 = sp.h1;
+    c.h2 = sp.h2;
+    c.part = h->part.as<T>();
+    c.part64 = h->part64.as<double>();
+    c.ctl = h->ctl.as<Ctl>();
+    c.brk = std::is_same<T, double>::value ? T(1e-14) : T(1e-6);
+    c.kmax = m;
+    if (h->has_precond && h->opts.precond) {
+        c.prowptr = c.rowptr;
+        c.pcolind = c.colind;
+        c.pvals = std::is_same<T, double>::value ? reinterpret_cast<const T *>(h->pvals64.p)
+                                                 : reinterpret_cast<const T *>(h->pvals32.p);
+    }
+    return c;
+}
+
+int spmv_grid(gmres_handle *h) { return h->nsm * 8; }
+
+// Launch helpers templated on the lanes-per-row count.
+template <class T, class VT, class XT>
+cudaError_t launch_spmv_step(gmres_handle *h, const GridCtx<T, VT> &c, const XT *x, T *y, int L) {
+    dim3 g(spmv_grid(h)), b(kThreads);
+    switch (L) {
+    case 1: k_spmv_step<T, VT, XT, 1><<<g, b, 0, h->stream>>>(c, x, y); break;
+    case 2: k_spmv_step<T, VT, XT, 2><<<g, b, 0, h->stream>>>(c, x, y); break;
+    case 4: k_spmv_step<T, VT, XT, 4><<<g, b, 0, h->stream>>>(c, x, y); break;
+    case 8: k_spmv_step<T, VT, XT, 8><<<g, b, 0, h->stream>>>(c, x, y); break;
+    case 16: k_spmv_step<T, VT, XT, 16><<<g, b, 0, h->stream>>>(c, x, y); break;
+    default: k_spmv_step<T, VT, XT, 32><<<g, b, 0, h->stream>>>(c, x, y); break;
+    }
+    return cudaGetLastError();
+}
+
+template <class T, class VT>
+cudaError_t launch_residual(gmres_handle *h, const GridCtx<T, VT> &c, const double *b,
+                            const double *x, double *z, int setup) {
+    dim3 g(h->grid), bl(kThreads);
+    switch (h->lanes64) {
+    case 1: k_residual<T, VT, 1><<<g, bl, 0, h->stream>>>(c, b, x, z, setup); break;
+    case 2: k_residual<T, VT, 2><<<g, bl, 0, h->stream>>>(c, b, x, z, setup); break;
+    case 4: k_residual<T, VT, 4><<<g, bl, 0, h->stream>>>(c, b, x, z, setup); break;
+    case 8: k_residual<T, VT, 8><<<g, bl, 0, h->stream>>>(c, b, x, z, setup); break;
+    case 16: k_residual<T, VT, 16><<<g, bl, 0, h->stream>>>(c, b, x, z, setup); break;
+    default: k_residual<T, VT, 32><<<g, bl, 0, h->stream>>>(c, b, x, z, setup); break;
+    }
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_spmv_plain(gmres_handle *h, int L, const T *a, const T *x, T *y) {
+    dim3 g(spmv_grid(h)), b(kThreads);
+    const int *rp = h->rowptr.as<int>(), *ci = h->colind.as<int>();
+    switch (L) {
+    case 1: k_spmv_plain<T, 1><<<g, b, 0, h->stream>>>(h->n, rp, ci, a, x, y); break;
+    case 2: k_spmv_plain<T, 2><<<g, b, 0, h->stream>>>(h->n, rp, ci, a, x, y); break;
+    case 4: k_spmv_plain<T, 4><<<g, b, 0, h->stream>>>(h->n, rp, ci, a, x, y); break;
+    case 8: k_spmv_plain<T, 8><<<g, b, 0, h->stream>>>(h->n, rp, ci, a, x, y); break;
+    case 16: k_spmv_plain<T, 16><<<g, b, 0, h->stream>>>(h->n, rp, ci, a, x, y); break;
+    default: k_spmv_plain<T, 32><<<g, b, 0, h->stream>>>(h->n, rp, ci, a, x, y); break;
+    }
+    return cudaGetLastError();
+}
+
+struct Acct {
+    double bytes[GMRES_K_COUNT] = {0};
+    int64_t launches[GMRES_K_COUNT] = {0};
+};
+
+template <class T, class VT>
+int lanes_for(gmres_handle *h) {
+    int L = std::is_same<T, double>::value ? h->lanes64 : h->lanes32;
+    if (h->opts.spmv_lanes > 0)
+        L = h->opts.spmv_lanes;
+    return L;
+}
+
+// Enqueue one inner step (column index `col` of the basis -> new column
+// col+1).  Kernels return at once when the cycle has ended.
+template <class T, class VT>
+gmres_status enqueue_step(gmres_handle *h, GridCtx<T, VT> &c, int col, gmres_ortho ortho,
+                          Acct &acct) {
+    const int L = lanes_for<T, VT>(h);
+    const VT *vj = c.V + (size_t)col * c.ldv;
+    cudaEvent_t e = h->timer.begin();
+    if (c.pvals) {
+        // t = M v_j, w = A t (right preconditioning)
+        GridCtx<T, VT> cp = c;
+        cp.rowptr = c.prowptr;
+        cp.colind = c.pcolind;
+        cp.a = c.pvals;
+        CK((launch_spmv_step<T, VT, VT>(h, cp, vj, c.t, L)));
+        acct.launches[GMRES_K_PRECOND]++;
+        h->timer.end(GMRES_K_PRECOND, e);
+        e = h->timer.begin();
+        CK((launch_spmv_step<T, VT, T>(h, c, c.t, c.w, L)));
+    } else {
+        CK((launch_spmv_step<T, VT, VT>(h, c, vj, c.w, L)));
+    }
+    h->timer.end(GMRES_K_SPMV, e);
+    acct.launches[GMRES_K_SPMV]++;
+    const int ncols = col + 1;
+    dim3 g(h->grid), b(kThreads);
+    e = h->timer.begin();
+    if (ortho == GMRES_ORTHO_CGSR) {
+        k_cgs_dot<T, VT><<<g, b, 0, h->stream>>>(c, ncols);
+        k_cgs_update_dot<T, VT><<<g, b, 0, h->stream>>>(c, ncols);
+        k_cgs_update_norm<T, VT><<<g, b, 0, h->stream>>>(c, ncols);
+        acct.launches[GMRES_K_ORTHO] += 3;
+    } else {
+        for (int i = 0; i < ncols; ++i)
+            k_mgs_step<T, VT><<<g, b, 0, h->stream>>>(c, i);
+        k_mgs_last<T, VT><<<g, b, 0, h->stream>>>(c, ncols);
+        acct.launches[GMRES_K_ORTHO] += ncols + 1;
+    }
+    CKL();
+    h->timer.end(GMRES_K_ORTHO, e);
+    e = h->timer.begin();
+    k_normalize<T, VT><<<g, b, 0, h->stream>>>(c, col + 1);
+    CKL();
+    h->timer.end(GMRES_K_NORMALIZE, e);
+    acct.launches[GMRES_K_NORMALIZE]++;
+    return GMRES_OK;
+}
+
+// Algorithmic bytes of a finished cycle of length j (what each step must
+// move: basis read once per pass, vectors once, gathers of x counted once).
+template <class T, class VT>
+void account_cycle(gmres_handle *h, int j, gmres_ortho ortho, Acct &acct) {
+    const double n = h->n, nnz = (double)h->nnz;
+    const double sT = sizeof(T), sV = sizeof(VT);
+    const bool pre = h->has_precond && h->opts.precond;
+    for (int it = 0; it < j; ++it) {
+        const double c = it + 1;
+        acct.bytes[GMRES_K_SPMV] += nnz * (sT + 4) + (n + 1) * 4 + n * (pre ? sT : sV) + n * sT;
+        if (pre)
+            acct.bytes[GMRES_K_PRECOND] += nnz * (sT + 4) + (n + 1) * 4 + n * sV + n * sT;
+        if (ortho == GMRES_ORTHO_CGSR)
+            acct.bytes[GMRES_K_ORTHO] += 3 * c * n * sV + 5 * n * sT;
+        else
+            acct.bytes[GMRES_K_ORTHO] += c * n * sV + 2 * n * sT;
+        if (it + 1 < j)
+            acct.bytes[GMRES_K_NORMALIZE] += n * sT + n * sV;
+    }
+    acct.bytes[GMRES_K_NORMALIZE] += n * sT + n * sV;  // v_1 = r / beta
+    acct.bytes[GMRES_K_UPDATE] += j * n * sV + 2 * n * 8 + (pre ? 2 * n * sT : 0);
+}
+
+template <class T, class VT>
+void account_residual(gmres_handle *h, Acct &acct) {
+    const double n = h->n, nnz = (double)h->nnz;
+    acct.bytes[GMRES_K_RESIDUAL] += nnz * 12 + (n + 1) * 4 + n * 8 * 2 + n * sizeof(T);
+    acct.launches[GMRES_K_RESIDUAL]++;
+}
+
+gmres_status read_ctl(gmres_handle *h) {
+    CK(cudaMemcpyAsync(h->hctl, h->ctl.p, sizeof(Ctl), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return GMRES_OK;
+}
+
+template <class T, class VT>
+gmres_status solve_grid(gmres_handle *h, const double *b, double *x, int m, double tol,
+                        gmres_ortho ortho, gmres_precision prec, int maxiter, gmres_info *info) {
+    gmres_status st = ensure_workspace(h, m, prec);
+    if (st != GMRES_OK)
+        return st;
+    GridCtx<T, VT> c = make_ctx<T, VT>(h, m);
+    const double tau = h->opts.tau >= 0 ? h->opts.tau : default_tau(prec);
+    const int repeat_first = h->opts.repeat_first >= 0 ? h->opts.repeat_first
+                                                       : (prec == GMRES_FP64 ? 0 : 1);
+    Acct acct;
+    CK(cudaMemsetAsync(h->ctl.p, 0, sizeof(Ctl), h->stream));
+    k_bnorm<T, VT><<<h->grid, kThreads, 0, h->stream>>>(c, b);
+    CKL();
+    acct.launches[GMRES_K_RESIDUAL]++;
+    st = read_ctl(h);
+    if (st != GMRES_OK)
+        return st;
+    const double bnorm = h->hctl->bnorm;
+    info->bnorm = bnorm;
+    if (h->hctl->nonfinite || !std::isfinite(bnorm))
+        return GMRES_ERR_NONFINITE;
+    if (bnorm == 0) {
+        CK(cudaMemsetAsync(x, 0, sizeof(double) * h->n, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        info->converged = 1;
+        info->relres = 0;
+        return GMRES_OK;
+    }
+    c.tol_abs = tol * bnorm;
+    c.inner_abs = h->opts.inner_factor * tol * bnorm;
+    cudaEvent_t e = h->timer.begin();
+    CK(launch_residual(h, c, b, x, nullptr, 1));
+    h->timer.end(GMRES_K_RESIDUAL, e);
+    account_residual<T, VT>(h, acct);
+    st = read_ctl(h);
+    if (st != GMRES_OK)
+        return st;
+    int cycle_len = m;
+    double prev_rn = h->hctl->rnorm;
+    gmres_status result = GMRES_MAXITER;
+    for (;;) {
+        const Ctl &k = *h->hctl;
+        info->relres = k.rnorm / bnorm;
+        if (k.nonfinite) {
+            result = GMRES_ERR_NONFINITE;
+            break;
+        }
+        if (k.timeout) {
+            result = GMRES_ERR_TIMEOUT;
+            break;
+        }
+        if (k.converged) {
+            result = GMRES_OK;
+            info->converged = 1;
+            break;
+        }
+        if (info->iters >= maxiter) {
+            result = GMRES_MAXITER;
+            break;
+        }
+        if (!k.active) {
+            result = GMRES_ERR_BREAKDOWN;  // beta == 0 in the working precision
+            break;
+        }
+        const int kmax = std::min(cycle_len, maxiter - info->iters);
+        c.kmax = kmax;
+        c.tau = (repeat_first && info->restarts > 0) ? 0.0 : tau;
+        e = h->timer.begin();
+        k_init<T, VT><<<h->grid, kThreads, 0, h->stream>>>(c);
+        CKL();
+        h->timer.end(GMRES_K_NORMALIZE, e);
+        acct.launches[GMRES_K_NORMALIZE]++;
+        for (int it = 0; it < kmax; ++it) {
+            st = enqueue_step(h, c, it, ortho, acct);
+            if (st != GMRES_OK)
+                return st;
+        }
+        e = h->timer.begin();
+        size_t sm = (size_t)m * m * sizeof(T) + (size_t)(m + 1) * sizeof(T);
+        CK(cudaFuncSetAttribute(k_backsolve<T, VT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)sm));
+        k_backsolve<T, VT><<<1, 32, sm, h->stream>>>(c);
+        CKL();
+        const bool pre = c.pvals != nullptr;
+        k_update<T, VT><<<h->grid, kThreads, 0, h->stream>>>(c, x, pre ? 1 : 0);
+        CKL();
+        acct.launches[GMRES_K_UPDATE] += 2;
+        if (pre) {
+            // u = M t with t = V_j y, then x += u (right preconditioning)
+            CK(launch_spmv_plain<T>(h, lanes_for<T, VT>(h), c.pvals, c.t, c.w));
+            k_axpy_x<T><<<h->grid, kThreads, 0, h->stream>>>(h->n, c.w, x, c.ctl);
+            CKL();
+            acct.launches[GMRES_K_UPDATE] += 2;
+        }
+        h->timer.end(GMRES_K_UPDATE, e);
+        e = h->timer.begin();
+        CK(launch_residual(h, c, b, x, nullptr, 1));
+        h->timer.end(GMRES_K_RESIDUAL, e);
+        account_residual<T, VT>(h, acct);
+        st = read_ctl(h);
+        if (st != GMRES_OK)
+            return st;
+        h->timer.harvest(info->kernel_ms);
+        const int j = h->hctl->last_j;
+        account_cycle<T, VT>(h, j, ortho, acct);
+        info->iters += j;
+        info->restarts += 1;
+        if (info->restarts == 1) {
+            info->first_len = j;
+            if (repeat_first)
+                cycle_len = std::max(1, j);
+        }
+        const double rn = h->hctl->rnorm;
+        if (j == 0 || (h->hctl->breakdown && rn >= prev_rn && !h->hctl->converged)) {
+            info->relres = rn / bnorm;
+            result = GMRES_ERR_BREAKDOWN;
+            break;
+        }
+        prev_rn = rn;
+    }
+    h->timer.harvest(info->kernel_ms);
+    for (int k = 0; k < GMRES_K_COUNT; ++k) {
+        info->kernel_bytes[k] += acct.bytes[k];
+        info->kernel_launches[k] += acct.launches[k];
+        info->launches += acct.launches[k];
+    }
+    return result;
+}
+
+template <class T, class VT>
+gmres_status solve_block(gmres_handle *h, const double *b, double *x, int m, double tol,
+                         gmres_ortho ortho, gmres_precision prec, int maxiter, gmres_info *info) {
+    gmres_status st = ensure_workspace(h, m, prec);
+    if (st != GMRES_OK)
+        return st;
+    BlockSys<T, VT> S;
+    S.n = h->n;
+    S.ldv = h->ldv;
+    S.rowptr = h->rowptr.as<int>();
+    S.colind = h->colind.as<int>();
+    S.a = std::is_same<T, double>::value ? reinterpret_cast<const T *>(h->vals64.p)
+                                         : reinterpret_cast<const T *>(h->vals32.p);
+    S.a64 = h->vals64.as<double>();
+    S.b = b;
+    S.x = x;
+    S.V = h->V.as<VT>();
+    S.w = h->w.as<T>();
+    S.r = h->r.as<T>();
+    S.vscale = std::is_same<VT, __half>::value ? fp16_scale(h->n) : 1.0f;
+    S.vinv = 1.0f / S.vscale;
+    CK(h->bsys.ensure(sizeof(S) + sizeof(unsigned) * 4));
+    CK(h->bres.ensure(sizeof(BlockResult)));
+    CK(cudaMemcpyAsync(h->bsys.p, &S, sizeof(S), cudaMemcpyHostToDevice, h->stream));
+    unsigned *queue = reinterpret_cast<unsigned *>(h->bsys.as<unsigned char>() + sizeof(S));
+    CK(cudaMemsetAsync(queue, 0, sizeof(unsigned), h->stream));
+    BlockParams P;
+    P.m = m;
+    P.maxiter = maxiter;
+    P.ortho = (int)ortho;
+    P.repeat_first = h->opts.repeat_first >= 0 ? h->opts.repeat_first
+                                               : (prec == GMRES_FP64 ? 0 : 1);
+    P.tol = tol;
+    P.tau = h->opts.tau >= 0 ? h->opts.tau : default_tau(prec);
+    P.inner_factor = h->opts.inner_factor;
+    P.brk = std::is_same<T, double>::value ? 1e-14 : 1e-6;
+    P.nsys = 1;
+    P.queue = queue;
+    P.order = nullptr;
+    size_t smem = block_smem_bytes<T>(m);
+    int threads = (int)std::min<int64_t>(1024, std::max<int64_t>(64, round_up(h->n / 4, 32)));
+    int L = lanes_for<T, VT>(h);
+    auto *kfn = &k_block_solve<T, VT, 4>;
+    switch (L) {
+    case 1: kfn = &k_block_solve<T, VT, 1>; break;
+    case 2: kfn = &k_block_solve<T, VT, 2>; break;
+    case 4: kfn = &k_block_solve<T, VT, 4>; break;
+    case 8: kfn = &k_block_solve<T, VT, 8>; break;
+    case 16: kfn = &k_block_solve<T, VT, 16>; break;
+    default: kfn = &k_block_solve<T, VT, 32>; break;
+    }
+    CK(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    cudaEvent_t e = h->timer.begin();
+    kfn<<<1, threads, smem, h->stream>>>(h->bsys.as<BlockSys<T, VT>>(), P,
+                                          h->bres.as<BlockResult>());
+    CKL();
+    h->timer.end(GMRES_K_BLOCK, e);
+    BlockResult R;
+    CK(cudaMemcpyAsync(&R, h->bres.p, sizeof(R), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    h->timer.harvest(info->kernel_ms);
+    info->iters = R.iters;
+    info->restarts = R.restarts;
+    info->converged = R.converged;
+    info->first_len = R.first_len;
+    info->relres = R.relres;
+    info->bnorm = R.bnorm;
+    info->launches += 1;
+    info->kernel_launches[GMRES_K_BLOCK] += 1;
+    return (gmres_status)R.status;
+}
+
+template <class T, class VT>
+gmres_status solve_dispatch_path(gmres_handle *h, const double *b, double *x, int m, double tol,
+                                 gmres_ortho ortho, gmres_precision prec, int maxiter,
+                                 gmres_info *info) {
+    int path = h->opts.path;
+    if (path == GMRES_PATH_AUTO)
+        path = (h->n <= 16384 && !(h->has_precond && h->opts.precond)) ? GMRES_PATH_BLOCK
+                                                                        : GMRES_PATH_GRID;
+    info->path = path;
+    if (path == GMRES_PATH_BLOCK)
+        return solve_block<T, VT>(h, b, x, m, tol, ortho, prec, maxiter, info);
+    return solve_grid<T, VT>(h, b, x, m, tol, ortho, prec, maxiter, info);
+}
+
+gmres_status validate_opts(const gmres_opts *o) {
+    if (!o)
+        return GMRES_ERR_ARG;
+    if (!(o->inner_factor >= 0) || o->path < 0 || o->path > 2 || o->spin_limit < 0 ||
+        (o->spmv_lanes != 0 && (o->spmv_lanes < 1 || o->spmv_lanes > 32 ||
+                                (o->spmv_lanes & (o->spmv_lanes - 1)))) ||
+        o->repeat_first < -1 || o->repeat_first > 1 || o->precond < 0 || o->precond > 1)
+        return GMRES_ERR_ARG;
+    return GMRES_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void gmres_default_opts(gmres_opts *o) {
+    if (!o)
+        return;
+    memset(o, 0, sizeof(*o));
+    o->tau = -1.0;
+    o->inner_factor = 0.5;
+    o->repeat_first = -1;
+    o->path = GMRES_PATH_AUTO;
+    o->profile = 0;
+    o->spin_limit = 0;
+    o->precond = 0;
+    o->fallback = 1;
+    o->spmv_lanes = 0;
+}
+
+const char *gmres_status_str(gmres_status s) {
+    switch (s) {
+    case GMRES_OK: return "converged";
+    case GMRES_MAXITER: return "iteration limit reached";
+    case GMRES_ERR_ARG: return "invalid argument";
+    case GMRES_ERR_CUDA: return "CUDA error";
+    case GMRES_ERR_NONFINITE: return "non-finite value";
+    case GMRES_ERR_BREAKDOWN: return "breakdown without progress";
+    case GMRES_ERR_TIMEOUT: return "device wait timed out";
+    case GMRES_ERR_OOM: return "out of device memory";
+    }
+    return "unknown status";
+}
+
+const char *gmres_version(void) { return "gmres_gb300 0.1 (sm_103a)"; }
+
+gmres_status gmres_create(gmres_t *out, int32_t n, const int32_t *rowptr, const int32_t *colind,
+                          const double *vals, int32_t flags, void *stream) {
+    if (!out)
+        return GMRES_ERR_ARG;
+    *out = nullptr;
+    if (n <= 0 || !rowptr || (flags & ~(GMRES_CREATE_DEVICE_PTRS | GMRES_CREATE_TRANSPOSE)))
+        return GMRES_ERR_ARG;
+    const bool dev = (flags & GMRES_CREATE_DEVICE_PTRS) != 0;
+    // Validate the structure on the host (device arrays are copied down).
+    std::vector<int32_t> rp(n + 1);
+    if (dev) {
+        if (cudaMemcpy(rp.data(), rowptr, sizeof(int32_t) * (n + 1), cudaMemcpyDeviceToHost) !=
+            cudaSuccess) {
+            cudaGetLastError();
+            return GMRES_ERR_ARG;
+        }
+    } else {
+        memcpy(rp.data(), rowptr, sizeof(int32_t) * (n + 1));
+    }
+    const int64_t nnz = rp[n];
+    if (nnz < 0 || (nnz > 0 && (!colind || !vals)))
+        return GMRES_ERR_ARG;
+    std::vector<int32_t> ci(nnz);
+    std::vector<double> va(nnz);
+    if (nnz > 0) {
+        if (dev) {
+            if (cudaMemcpy(ci.data(), colind, sizeof(int32_t) * nnz, cudaMemcpyDeviceToHost) !=
+                    cudaSuccess ||
+                cudaMemcpy(va.data(), vals, sizeof(double) * nnz, cudaMemcpyDeviceToHost) !=
+                    cudaSuccess) {
+                cudaGetLastError();
+                return GMRES_ERR_ARG;
+            }
+        } else {
+            memcpy(ci.data(), colind, sizeof(int32_t) * nnz);
+            memcpy(va.data(), vals, sizeof(double) * nnz);
+        }
+    }
+    gmres_status st = check_csr_host(n, rp.data(), ci.data(), nnz);
+    if (st != GMRES_OK)
+        return st;
+    for (int64_t k = 0; k < nnz; ++k)
+        if (!std::isfinite(va[k]))
+            return GMRES_ERR_NONFINITE;
+
+    gmres_handle *h = new (std::nothrow) gmres_handle();
+    if (!h)
+        return GMRES_ERR_OOM;
+    gmres_default_opts(&h->opts);
+    h->n = n;
+    h->nnz = nnz;
+    h->ldv = round_up(n, 256);
+    h->stream = reinterpret_cast<cudaStream_t>(stream);
+    h->timer.st = h->stream;
+    auto fail = [&](gmres_status s) {
+        gmres_destroy(h);
+        return s;
+    };
+    if (cudaGetDevice(&h->device) != cudaSuccess)
+        return fail(GMRES_ERR_CUDA);
+    if (cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess)
+        return fail(GMRES_ERR_CUDA);
+    h->grid = 2 * h->nsm;
+    h->chunk = round_up((h->ldv + h->grid - 1) / h->grid, 4);
+    const double avg = (double)nnz / n;
+    h->lanes32 = h->lanes64 = pow2_lanes(avg / 2.0);
+    if (h->rowptr.ensure(sizeof(int32_t) * (n + 1)) != cudaSuccess ||
+        h->colind.ensure(sizeof(int32_t) * std::max<int64_t>(nnz, 1)) != cudaSuccess ||
+        h->vals64.ensure(sizeof(double) * std::max<int64_t>(nnz, 1)) != cudaSuccess ||
+        h->vals32.ensure(sizeof(float) * std::max<int64_t>(nnz, 1)) != cudaSuccess)
+        return fail(GMRES_ERR_OOM);
+    if (cudaMemcpyAsync(h->rowptr.p, rp.data(), sizeof(int32_t) * (n + 1),
+                        cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
+        (nnz > 0 && (cudaMemcpyAsync(h->colind.p, ci.data(), sizeof(int32_t) * nnz,
+                                     cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
+                     cudaMemcpyAsync(h->vals64.p, va.data(), sizeof(double) * nnz,
+                                     cudaMemcpyHostToDevice, h->stream) != cudaSuccess)))
+        return fail(GMRES_ERR_CUDA);
+    if (nnz > 0) {
+        k_cast_vals<<<h->nsm * 4, 256, 0, h->stream>>>(nnz, h->vals64.as<double>(),
+                                                        h->vals32.as<float>());
+        if (cudaGetLastError() != cudaSuccess)
+            return fail(GMRES_ERR_CUDA);
+    }
+    if (flags & GMRES_CREATE_TRANSPOSE) {
+        // CSR of A^T built on the host from the validated arrays.
+        std::vector<int32_t> trp(n + 1, 0), tci(nnz);
+        std::vector<double> tva(nnz);
+        for (int64_t k = 0; k < nnz; ++k)
+            trp[ci[k] + 1]++;
+        for (int i = 0; i < n; ++i)
+            trp[i + 1] += trp[i];
+        std::vector<int32_t> pos(trp.begin(), trp.end() - 1);
+        for (int i = 0; i < n; ++i)
+            for (int32_t k = rp[i]; k < rp[i + 1]; ++k) {
+                int32_t d = pos[ci[k]]++;
+                tci[d] = i;
+                tva[d] = va[k];
+            }
+        if (h->trowptr.ensure(sizeof(int32_t) * (n + 1)) != cudaSuccess ||
+            h->tcolind.ensure(sizeof(int32_t) * std::max<int64_t>(nnz, 1)) != cudaSuccess ||
+            h->tvals64.ensure(sizeof(double) * std::max<int64_t>(nnz, 1)) != cudaSuccess)
+            return fail(GMRES_ERR_OOM);
+        if (cudaMemcpyAsync(h->trowptr.p, trp.data(), sizeof(int32_t) * (n + 1),
+                            cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
+            (nnz > 0 && (cudaMemcpyAsync(h->tcolind.p, tci.data(), sizeof(int32_t) * nnz,
+                                         cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
+                         cudaMemcpyAsync(h->tvals64.p, tva.data(), sizeof(double) * nnz,
+                                         cudaMemcpyHostToDevice, h->stream) != cudaSuccess)))
+            return fail(GMRES_ERR_CUDA);
+    }
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess)
+        return fail(GMRES_ERR_CUDA);
+    *out = h;
+    return GMRES_OK;
+}
+
+void gmres_destroy(gmres_t h) {
+    if (!h)
+        return;
+    if (h->stream)
+        cudaStreamSynchronize(h->stream);
+    else
+        cudaDeviceSynchronize();
+    for (DevBuf *b : {&h->rowptr, &h->colind, &h->vals64, &h->vals32, &h->trowptr, &h->tcolind,
+                      &h->tvals64, &h->V, &h->w, &h->r, &h->t, &h->z, &h->xb, &h->bb, &h->small,
+                      &h->part, &h->part64, &h->ctl, &h->bsys, &h->bres, &h->pvals64,
+                      &h->pvals32})
+        b->release();
+    if (h->hctl)
+        cudaFreeHost(h->hctl);
+    h->timer.destroy();
+    delete h;
+}
+
+gmres_status gmres_set_stream(gmres_t h, void *stream) {
+    if (!h)
+        return GMRES_ERR_ARG;
+    h->stream = reinterpret_cast<cudaStream_t>(stream);
+    h->timer.st = h->stream;
+    return GMRES_OK;
+}
+
+gmres_status gmres_set_opts(gmres_t h, const gmres_opts *o) {
+    if (!h)
+        return GMRES_ERR_ARG;
+    gmres_status st = validate_opts(o);
+    if (st != GMRES_OK)
+        return st;
+    h->opts = *o;
+    return GMRES_OK;
+}
+
+gmres_status gmres_get_opts(gmres_t h, gmres_opts *o) {
+    if (!h || !o)
+        return GMRES_ERR_ARG;
+    *o = h->opts;
+    return GMRES_OK;
+}
+
+gmres_status gmres_solve(gmres_t h, const double *b, double *x, int32_t m, double tol,
+                         gmres_ortho ortho, gmres_precision prec, int32_t maxiter,
+                         gmres_info *info) {
+    auto t0 = std::chrono::steady_clock::now();
+    gmres_info local;
+    if (!info)
+        info = &local;
+    memset(info, 0, sizeof(*info));
+    if (!h || !b || !x || m < 1 || m > MMAX || !(tol > 0) || maxiter < 0 ||
+        (ortho != GMRES_ORTHO_MGS && ortho != GMRES_ORTHO_CGSR) || prec < GMRES_FP64 ||
+        prec > GMRES_MIXED_FP16)
+        return GMRES_ERR_ARG;
+    h->timer.on = h->opts.profile != 0;
+    // Host buffers go through library-owned device copies.
+    const bool bdev = is_device_ptr(b), xdev = is_device_ptr(x);
+    const double *db = b;
+    double *dx = x;
+    if (!bdev || !xdev) {
+        CK(h->xb.ensure((size_t)h->ldv * 8));
+        CK(h->bb.ensure((size_t)h->ldv * 8));
+    }
+    if (!bdev) {
+        CK(cudaMemcpyAsync(h->bb.p, b, sizeof(double) * h->n, cudaMemcpyHostToDevice, h->stream));
+        db = h->bb.as<double>();
+    }
+    if (!xdev) {
+        CK(cudaMemcpyAsync(h->xb.p, x, sizeof(double) * h->n, cudaMemcpyHostToDevice, h->stream));
+        dx = h->xb.as<double>();
+    }
+    gmres_status st;
+    switch (prec) {
+    case GMRES_FP64:
+        st = solve_dispatch_path<double, double>(h, db, dx, m, tol, ortho, prec, maxiter, info);
+        break;
+    case GMRES_MIXED:
+        st = solve_dispatch_path<float, float>(h, db, dx, m, tol, ortho, prec, maxiter, info);
+        break;
+    case GMRES_MIXED_BF16:
+        st = solve_dispatch_path<float, __nv_bfloat16>(h, db, dx, m, tol, ortho, prec, maxiter,
+                                                       info);
+        break;
+    default:
+        st = solve_dispatch_path<float, __half>(h, db, dx, m, tol, ortho, prec, maxiter, info);
+        break;
+    }
+    if (!xdev) {
+        CK(cudaMemcpyAsync(x, dx, sizeof(double) * h->n, cudaMemcpyDeviceToHost, h->stream));
+    }
+    CK(cudaStreamSynchronize(h->stream));
+    h->timer.on = false;
+    info->time_ms =
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return st;
+}
+
+gmres_status gmres_spmv(gmres_t h, const void *x, void *y, gmres_precision prec) {
+    if (!h || !x || !y || prec < GMRES_FP64 || prec > GMRES_MIXED_FP16)
+        return GMRES_ERR_ARG;
+    if (prec == GMRES_FP64)
+        CK(launch_spmv_plain<double>(h, h->opts.spmv_lanes ? h->opts.spmv_lanes : h->lanes64,
+                                     h->vals64.as<double>(), (const double *)x, (double *)y));
+    else
+        CK(launch_spmv_plain<float>(h, h->opts.spmv_lanes ? h->opts.spmv_lanes : h->lanes32,
+                                    h->vals32.as<float>(), (const float *)x, (float *)y));
+    CK(cudaStreamSynchronize(h->stream));
+    return GMRES_OK;
+}
+
+gmres_status gmres_residual(gmres_t h, const double *b, const double *x, double *z,
+                            double *znorm) {
+    if (!h || !b || !x)
+        return GMRES_ERR_ARG;
+    gmres_status st = ensure_workspace(h, 1, GMRES_FP64);
+    if (st != GMRES_OK)
+        return st;
+    GridCtx<double, double> c = make_ctx<double, double>(h, 1);
+    c.tol_abs = -1.0;
+    CK(launch_residual(h, c, b, x, z, 0));
+    st = read_ctl(h);
+    if (st != GMRES_OK)
+        return st;
+    if (znorm)
+        *znorm = h->hctl->rnorm;
+    return GMRES_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+template <class T>
+void export_small(const T *dev, double *host, size_t count, cudaStream_t st,
+                  std::vector<T> &tmp) {
+    tmp.resize(count);
+    cudaMemcpyAsync(tmp.data(), dev, sizeof(T) * count, cudaMemcpyDeviceToHost, st);
+    cudaStreamSynchronize(st);
+    for (size_t i = 0; i < count; ++i)
+        host[i] = (double)tmp[i];
+}
+
+template <class T, class VT>
+gmres_status arnoldi_impl(gmres_handle *h, const double *r0, int m, int kmax, gmres_ortho ortho,
+                          gmres_precision prec, double tau, double inner_abs, double *V,
+                          double *Hbar, double *H, double *s, double *cs, double *sn, double *y,
+                          double *u, double *arn, int32_t *jout, int32_t *breakdown) {
+    gmres_status st = ensure_workspace(h, m, prec);
+    if (st != GMRES_OK)
+        return st;
+    GridCtx<T, VT> c = make_ctx<T, VT>(h, m);
+    c.tol_abs = -1.0;
+    c.tau = tau;
+    c.inner_abs = inner_abs;
+    c.kmax = kmax;
+    Acct acct;
+    CK(cudaMemsetAsync(h->ctl.p, 0, sizeof(Ctl), h->stream));
+    // small arrays start at zero so unused entries export as zero
+    CK(cudaMemsetAsync(h->small.p, 0, h->small.bytes, h->stream));
+    // r = fl(r0): the residual kernel with x = 0 gives z = r0 exactly
+    CK(cudaMemsetAsync(h->xb.p, 0, sizeof(double) * h->ldv, h->stream));
+    CK(launch_residual(h, c, r0, h->xb.as<double>(), nullptr, 1));
+    k_init<T, VT><<<h->grid, kThreads, 0, h->stream>>>(c);
+    CKL();
+    std::vector<double> arnv;
+    arnv.reserve(kmax);
+    int j = 0;
+    for (int it = 0; it < kmax; ++it) {
+        st = enqueue_step(h, c, it, ortho, acct);
+        if (st != GMRES_OK)
+            return st;
+        st = read_ctl(h);
+        if (st != GMRES_OK)
+            return st;
+        if (h->hctl->j == it + 1) {
+            arnv.push_back(h->hctl->arn);
+            j = it + 1;
+        }
+        if (!h->hctl->active)
+            break;
+    }
+    size_t sm = (size_t)m * m * sizeof(T) + (size_t)(m + 1) * sizeof(T);
+    CK(cudaFuncSetAttribute(k_backsolve<T, VT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)sm));
+    k_backsolve<T, VT><<<1, 32, sm, h->stream>>>(c);
+    CKL();
+    k_update<T, VT><<<h->grid, kThreads, 0, h->stream>>>(c, h->z.as<double>(), 1);
+    CKL();
+    st = read_ctl(h);
+    if (st != GMRES_OK)
+        return st;
+    std::vector<T> tmp;
+    SmallPtrs<T> sp = small_ptrs<T>(h);
+    const int ld = m + 1;
+    if (Hbar)
+        export_small(sp.Hb, Hbar, (size_t)ld * m, h->stream, tmp);
+    if (H)
+        export_small(sp.H, H, (size_t)ld * m, h->stream, tmp);
+    if (s)
+        export_small(sp.s, s, (size_t)m + 1, h->stream, tmp);
+    if (cs)
+        export_small(sp.cs, cs, (size_t)m, h->stream, tmp);
+    if (sn)
+        export_small(sp.sn, sn, (size_t)m, h->stream, tmp);
+    if (y)
+        export_small(sp.y, y, (size_t)m, h->stream, tmp);
+    if (u) {
+        if (c.pvals) {
+            CK(launch_spmv_plain<T>(h, lanes_for<T, VT>(h), c.pvals, c.t, c.w));
+            export_small(c.w, u, (size_t)h->n, h->stream, tmp);
+        } else {
+            export_small(c.t, u, (size_t)h->n, h->stream, tmp);
+        }
+    }
+    if (arn) {
+        for (int i = 0; i < m; ++i)
+            arn[i] = i < (int)arnv.size() ? arnv[i] : 0.0;
+    }
+    if (V) {
+        CK(h->z.ensure((size_t)h->n * (m + 1) * 8));
+        CK(cudaMemsetAsync(h->z.p, 0, (size_t)h->n * (m + 1) * 8, h->stream));
+        k_export_basis<T, VT><<<h->nsm * 4, 256, 0, h->stream>>>(c, std::min(j + 1, m + 1),
+                                                                 h->z.as<double>());
+        CKL();
+        CK(cudaMemcpyAsync(V, h->z.p, (size_t)h->n * (m + 1) * 8, cudaMemcpyDeviceToHost,
+                           h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+    }
+    if (jout)
+        *jout = j;
+    if (breakdown)
+        *breakdown = h->hctl->breakdown;
+    if (h->hctl->nonfinite)
+        return GMRES_ERR_NONFINITE;
+    return GMRES_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+gmres_status gmres_arnoldi(gmres_t h, const double *r0, int32_t m, int32_t kmax, gmres_ortho ortho,
+                           gmres_precision prec, double tau, double inner_abs, double *V,
+                           double *Hbar, double *H, double *s, double *cs, double *sn, double *y,
+                           double *u, double *arn, int32_t *jout, int32_t *breakdown) {
+    if (!h || !r0 || m < 1 || m > MMAX || kmax < 1 || kmax > m ||
+        (ortho != GMRES_ORTHO_MGS && ortho != GMRES_ORTHO_CGSR) || prec < GMRES_FP64 ||
+        prec > GMRES_MIXED_FP16)
+        return GMRES_ERR_ARG;
+    h->timer.on = false;
+    switch (prec) {
+    case GMRES_FP64:
+        return arnoldi_impl<double, double>(h, r0, m, kmax, ortho, prec, tau, inner_abs, V, Hbar,
+                                            H, s, cs, sn, y, u, arn, jout, breakdown);
+    case GMRES_MIXED:
+        return arnoldi_impl<float, float>(h, r0, m, kmax, ortho, prec, tau, inner_abs, V, Hbar, H,
+                                          s, cs, sn, y, u, arn, jout, breakdown);
+    case GMRES_MIXED_BF16:
+        return arnoldi_impl<float, __nv_bfloat16>(h, r0, m, kmax, ortho, prec, tau, inner_abs, V,
+                                                  Hbar, H, s, cs, sn, y, u, arn, jout, breakdown);
+    default:
+        return arnoldi_impl<float, __half>(h, r0, m, kmax, ortho, prec, tau, inner_abs, V, Hbar,
+                                           H, s, cs, sn, y, u, arn, jout, breakdown);
+    }
+}
+
+gmres_status gmres_autotune(gmres_t h, int32_t *lanes32, int32_t *lanes64) {
+    if (!h)
+        return GMRES_ERR_ARG;
+    gmres_status st = ensure_workspace(h, 1, GMRES_FP64);
+    if (st != GMRES_OK)
+        return st;
+    cudaEvent_t a, b;
+    CK(cudaEventCreate(&a));
+    CK(cudaEventCreate(&b));
+    const int cand[6] = {1, 2, 4, 8, 16, 32};
+    float best32 = 1e30f, best64 = 1e30f;
+    int L32 = h->lanes32, L64 = h->lanes64;
+    double *x64 = h->r.as<double>(), *y64 = h->w.as<double>();
+    float *x32 = h->r.as<float>(), *y32 = h->w.as<float>();
+    for (int prec = 0; prec < 2; ++prec) {
+        for (int ci = 0; ci < 6; ++ci) {
+            const int L = cand[ci];
+            for (int rep = 0; rep < 2; ++rep) {  // warm-up
+                if (prec)
+                    CK(launch_spmv_plain<float>(h, L, h->vals32.as<float>(), x32, y32));
+                else
+                    CK(launch_spmv_plain<double>(h, L, h->vals64.as<double>(), x64, y64));
+            }
+            CK(cudaEventRecord(a, h->stream));
+            const int reps = 5;
+            for (int rep = 0; rep < reps; ++rep) {
+                if (prec)
+                    CK(launch_spmv_plain<float>(h, L, h->vals32.as<float>(), x32, y32));
+                else
+                    CK(launch_spmv_plain<double>(h, L, h->vals64.as<double>(), x64, y64));
+            }
+            CK(cudaEventRecord(b, h->stream));
+            CK(cudaEventSynchronize(b));
+            float ms = 0;
+            CK(cudaEventElapsedTime(&ms, a, b));
+            if (prec && ms < best32) {
+                best32 = ms;
+                L32 = L;
+            }
+            if (!prec && ms < best64) {
+                best64 = ms;
+                L64 = L;
+            }
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    h->lanes32 = L32;
+    h->lanes64 = L64;
+    if (lanes32)
+        *lanes32 = L32;
+    if (lanes64)
+        *lanes64 = L64;
+    return GMRES_OK;
+}
+
+gmres_status gmres_memory_bytes(gmres_t h, int32_t m, gmres_precision prec, int64_t *matrix_bytes,
+                                int64_t *workspace_bytes) {
+    if (!h || m < 1 || m > MMAX || prec < GMRES_FP64 || prec > GMRES_MIXED_FP16)
+        return GMRES_ERR_ARG;
+    const int64_t n = h->n, nnz = h->nnz;
+    // indices shared by both copies; binary64 + binary32 values (Sec. 4)
+    if (matrix_bytes)
+        *matrix_bytes = 4 * (n + 1) + 4 * nnz + 8 * nnz + 4 * nnz;
+    if (workspace_bytes) {
+        const int64_t sT = prec == GMRES_FP64 ? 8 : 4;
+        *workspace_bytes = h->ldv * (m + 1) * elem_bytes(prec)  // basis
+                           + 3 * h->ldv * sT                   // w, r, t
+                           + 2 * (int64_t)(m + 1) * m * sT      // H, Hbar
+                           + 6 * (int64_t)(m + 2) * sT;         // s, cs, sn, y, h1, h2
+    }
+    return GMRES_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,703 @@
+// grid_kernels.cuh -- whole-GPU kernels for one inner step of restarted
+// GMRES(m) on a large system (Algorithm 1 of arXiv 2011.01850).
+//
+// Each kernel spreads the n rows over the grid; cross-block sums go through
+// per-block partials that the last block to finish reduces in a fixed order
+// (deterministic).  Every kernel of an inner step first reads ctl->active and
+// returns at once when the restart cycle has ended, so the host can enqueue a
+// whole cycle without waiting.
+//
+// Vectors (w, r, basis columns) are padded to ldv rows (a multiple of 256)
+// with zero tails, so the streaming kernels always move 4 rows per thread.
+#pragma once
+
+#include "common.cuh"
+
+namespace gmres {
+
+constexpr int PSTRIDE = MMAX + 8;  // partial-sum slots per block
+
+template <class T, class VT>
+struct GridCtx {
+    int n, m, ld;        // rows, restart length, Hessenberg leading dim (m+1)
+    int64_t ldv;         // basis / vector leading dimension (padded rows)
+    int64_t chunk;       // rows per block in the streaming kernels (mult. of 4)
+    const int *rowptr;
+    const int *colind;
+    const T *a;          // matrix values in the working precision
+    const double *a64;   // binary64 values (residual)
+    VT *V;               // basis, column-major, ldv x (m+1)
+    float vscale, vinv;  // binary16 basis scale and its reciprocal
+    T *w;                // work vector (A v_j, then orthogonalised)
+    T *r;                // residual in the working precision
+    T *t;                // scratch vector (preconditioner)
+    T *H, *Hb;           // rotated / unrotated Hessenberg, ld x m
+    T *s, *cs, *sn, *y;  // rotated rhs (m+1), rotations (m), LS solution (m)
+    T *h1, *h2;          // Hessenberg column: first / second projection
+    T *part;             // per-block partials, gridDim x PSTRIDE
+    double *part64;      // per-block binary64 partials, gridDim x 4
+    Ctl *ctl;
+    double tau, inner_abs, tol_abs;
+    T brk;               // relative breakdown threshold for h_{j+1,j}
+    int kmax;            // inner iterations allowed in this cycle
+    // right preconditioner M (learned SpAI) on its own CSR, or null
+    const int *prowptr;
+    const int *pcolind;
+    const T *pvals;
+};
+
+// 4 consecutive basis entries starting at p (16-byte aligned for fp32 /
+// 32-byte for fp64 / 8-byte for 16-bit types: row index a multiple of 4).
+template <class T, class VT>
+__device__ __forceinline__ void ld4(const VT *p, float vinv, T (&o)[4]);
+
+template <>
+__device__ __forceinline__ void ld4<double, double>(const double *p, float, double (&o)[4]) {
+    double2 a = *reinterpret_cast<const double2 *>(p);
+    double2 b = *reinterpret_cast<const double2 *>(p + 2);
+    o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+}
+template <>
+__device__ __forceinline__ void ld4<float, float>(const float *p, float, float (&o)[4]) {
+    float4 a = *reinterpret_cast<const float4 *>(p);
+    o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w;
+}
+template <>
+__device__ __forceinline__ void ld4<float, __nv_bfloat16>(const __nv_bfloat16 *p, float,
+                                                          float (&o)[4]) {
+    uint2 u = *reinterpret_cast<const uint2 *>(p);
+    __nv_bfloat162 a = *reinterpret_cast<__nv_bfloat162 *>(&u.x);
+    __nv_bfloat162 b = *reinterpret_cast<__nv_bfloat162 *>(&u.y);
+    float2 fa = __bfloat1622float2(a), fb = __bfloat1622float2(b);
+    o[0] = fa.x; o[1] = fa.y; o[2] = fb.x; o[3] = fb.y;
+}
+template <>
+__device__ __forceinline__ void ld4<float, __half>(const __half *p, float vinv, float (&o)[4]) {
+    uint2 u = *reinterpret_cast<const uint2 *>(p);
+    __half2 a = *reinterpret_cast<__half2 *>(&u.x);
+    __half2 b = *reinterpret_cast<__half2 *>(&u.y);
+    float2 fa = __half22float2(a), fb = __half22float2(b);
+    o[0] = fa.x * vinv; o[1] = fa.y * vinv; o[2] = fb.x * vinv; o[3] = fb.y * vinv;
+}
+
+template <class T>
+__device__ __forceinline__ void ldv4(const T *p, T (&o)[4]) { ld4<T, T>(p, 1.f, o); }
+
+template <class T>
+__device__ __forceinline__ void st4(T *p, const T (&v)[4]);
+template <>
+__device__ __forceinline__ void st4<double>(double *p, const double (&v)[4]) {
+    *reinterpret_cast<double2 *>(p) = make_double2(v[0], v[1]);
+    *reinterpret_cast<double2 *>(p + 2) = make_double2(v[2], v[3]);
+}
+template <>
+__device__ __forceinline__ void st4<float>(float *p, const float (&v)[4]) {
+    *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+
+// Store 4 working values into the basis (rounding to its storage type).
+template <class T, class VT>
+__device__ __forceinline__ void stb4(VT *p, const T (&v)[4], float scale) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        Basis<VT>::st(p + k, v[k], scale);
+}
+
+// Row range of block b in the streaming kernels.
+template <class C>
+__device__ __forceinline__ void block_rows(const C &c, int64_t &rb, int64_t &re) {
+    rb = (int64_t)blockIdx.x * c.chunk;
+    re = rb + c.chunk;
+    if (re > c.ldv) re = c.ldv;
+}
+
+// Sum the partials of columns [0, ncols) over the grid's blocks, in the last
+// block: warp w owns columns w, w+nwarps, ...; lane l sums blocks l, l+32, ...
+// sequentially, then the xor-butterfly combines the lanes.
+template <class T>
+__device__ __forceinline__ void reduce_columns(const T *part, int nblocks, int ncols, T *out) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nw = blockDim.x >> 5;
+    for (int col = wid; col < ncols; col += nw) {
+        T acc = 0;
+        for (int b = lane; b < nblocks; b += 32)
+            acc += ldcg(part + (size_t)b * PSTRIDE + col);
+        acc = warp_sum(acc);
+        if (lane == 0)
+            out[col] = acc;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// SpMV: y = A x with L lanes per CSR row (L in {1,2,4,8,16,32}).  Lane l of a
+// group sums the row entries k = beg + l, beg + l + L, ... in order; the
+// group then combines its lanes with the xor-butterfly.
+// ---------------------------------------------------------------------------
+template <class T, class XT, int L>
+__device__ __forceinline__ T csr_row(const int *__restrict__ rowptr, const int *__restrict__ colind,
+                                     const T *__restrict__ a, const XT *x, float xinv, int row,
+                                     int n, int gl) {
+    T acc = 0;
+    if (row < n) {
+        int beg = __ldg(rowptr + row), end = __ldg(rowptr + row + 1);
+        for (int k = beg + gl; k < end; k += L)
+            acc += __ldg(a + k) * (T)Basis<XT>::ld(x + __ldg(colind + k), xinv);
+    }
+#pragma unroll
+    for (int off = L / 2; off > 0; off >>= 1)
+        acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    return acc;
+}
+
+// w = A v_col (inner step, Alg. 1 "w <- A v_j"); with a right preconditioner
+// the caller first forms t = M v_col and passes x = t.
+template <class T, class VT, class XT, int L>
+__global__ void __launch_bounds__(256) k_spmv_step(GridCtx<T, VT> c, const XT *x, T *y) {
+    if (!c.ctl->active)
+        return;
+    const int G = 32 / L;
+    const int lane = threadIdx.x & 31;
+    const int gl = lane % L, gi = lane / L;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t base = warp * G; base < c.n; base += nwarps * G) {
+        int row = (int)(base + gi);
+        T v = csr_row<T, XT, L>(c.rowptr, c.colind, c.a, x, c.vinv, row, c.n, gl);
+        if (row < c.n && gl == 0)
+            y[row] = v;
+    }
+}
+
+// Plain SpMV for the C-ABI entry point gmres_spmv (no control block).
+template <class T, int L>
+__global__ void __launch_bounds__(256) k_spmv_plain(int n, const int *rowptr, const int *colind,
+                                                    const T *a, const T *x, T *y) {
+    const int G = 32 / L;
+    const int lane = threadIdx.x & 31;
+    const int gl = lane % L, gi = lane / L;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t base = warp * G; base < n; base += nwarps * G) {
+        int row = (int)(base + gi);
+        T v = csr_row<T, T, L>(rowptr, colind, a, x, 1.f, row, n, gl);
+        if (row < n && gl == 0)
+            y[row] = v;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Residual: z = b - A x in binary64 (Alg. 1 first step; Sec. 2), its norm,
+// the working-precision copy r = fl(z) and ||r|| in the working precision.
+// The last block sets up the cycle: beta, s = beta e_1, active flag.
+// ---------------------------------------------------------------------------
+template <class T, class VT, int L>
+__global__ void __launch_bounds__(256) k_residual(GridCtx<T, VT> c, const double *b,
+                                                  const double *x, double *z, int setup) {
+    __shared__ double sd[32];
+    __shared__ T st[32];
+    const int G = 32 / L;
+    const int lane = threadIdx.x & 31;
+    const int gl = lane % L, gi = lane / L;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    double ss = 0;
+    T sst = 0;
+    int bad = 0;
+    for (int64_t base = warp * G; base < c.n; base += nwarps * G) {
+        int row = (int)(base + gi);
+        double ax = csr_row<double, double, L>(c.rowptr, c.colind, c.a64, x, 1.f, row, c.n, gl);
+        if (row < c.n && gl == 0) {
+            double zi = b[row] - ax;
+            if (z)
+                z[row] = zi;
+            T ri = (T)zi;
+            c.r[row] = ri;
+            ss += zi * zi;
+            sst += ri * ri;
+            bad |= !isfinite(zi);
+        }
+    }
+    ss = block_sum1(ss, sd);
+    sst = block_sum1(sst, st);
+    bad = __syncthreads_or(bad);
+    if (threadIdx.x == 0) {
+        c.part64[(size_t)blockIdx.x * 4 + 0] = ss;
+        c.part[(size_t)blockIdx.x * PSTRIDE + 0] = sst;
+        c.part64[(size_t)blockIdx.x * 4 + 1] = bad ? 1.0 : 0.0;
+    }
+    if (!arrive_last(&c.ctl->counter[0]))
+        return;
+    double a = 0, f = 0;
+    T at = 0;
+    for (int bb = threadIdx.x; bb < gridDim.x; bb += blockDim.x) {
+        a += ldcg(c.part64 + (size_t)bb * 4 + 0);
+        f += ldcg(c.part64 + (size_t)bb * 4 + 1);
+        at += ldcg(c.part + (size_t)bb * PSTRIDE + 0);
+    }
+    a = block_sum1(a, sd);
+    f = block_sum1(f, sd);
+    at = block_sum1(at, st);
+    if (threadIdx.x == 0) {
+        Ctl *k = c.ctl;
+        double rn = sqrt(a);
+        T beta = wsqrt(at);
+        k->rnorm = rn;
+        int nf = (f != 0.0) || !isfinite(rn);
+        if (nf)
+            k->nonfinite = 1;
+        k->converged = (!nf && rn <= c.tol_abs);
+        if (setup) {
+            k->beta = (double)beta;
+            k->j = 0;
+            k->breakdown = 0;
+            k->arn = (double)beta;
+            k->active = (!nf && !k->converged && beta > T(0) && isfinite((double)beta));
+            c.s[0] = beta;
+        }
+    }
+    if (setup) {
+        for (int i = 1 + threadIdx.x; i <= c.m; i += blockDim.x)
+            c.s[i] = T(0);
+    }
+}
+
+// v_1 = r / beta (Alg. 1 "v_1 <- r_k / beta"), rounded to the basis type.
+template <class T, class VT>
+__global__ void __launch_bounds__(256) k_init(GridCtx<T, VT> c) {
+    if (!c.ctl->active)
+        return;
+    const T beta = (T)c.ctl->beta;
+    int64_t rb, re;
+    block_rows(c, rb, re);
+    for (int64_t r = rb + 4 * threadIdx.x; r < re; r += 4 * blockDim.x) {
+        T v[4];
+        ldv4(c.r + r, v);
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            v[k] = v[k] / beta;
+        stb4<T, VT>(c.V + r, v, c.vscale);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Givens step for the new Hessenberg column (Alg. 1: apply rotations
+// 1..j-1, form rotation j, rotate s and the column).  Runs in the last block
+// of the final orthogonalisation kernel; col is the 0-based column index,
+// hc[0..col] the projections, hnext = h_{j+1,j}.
+// ---------------------------------------------------------------------------
+template <class T, class VT>
+__device__ void givens_step(GridCtx<T, VT> &c, int col, const T *hc_global, T hnext) {
+    __shared__ T sh[MMAX + 2], scs[MMAX], ssn[MMAX];
+    for (int i = threadIdx.x; i <= col; i += blockDim.x)
+        sh[i] = ldcg(hc_global + i);
+    for (int i = threadIdx.x; i < col; i += blockDim.x) {
+        scs[i] = c.cs[i];
+        ssn[i] = c.sn[i];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0)
+        sh[col + 1] = hnext;
+    __syncthreads();
+    // unrotated column (for the Arnoldi relation)
+    for (int i = threadIdx.x; i <= col + 1; i += blockDim.x)
+        c.Hb[(size_t)col * c.ld + i] = sh[i];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        Ctl *k = c.ctl;
+        for (int i = 0; i < col; ++i) {
+            T hi = sh[i], hi1 = sh[i + 1];
+            sh[i] = scs[i] * hi + ssn[i] * hi1;
+            sh[i + 1] = -ssn[i] * hi + scs[i] * hi1;
+        }
+        T hjj = sh[col], hj1 = sh[col + 1];
+        T rho = wsqrt(hjj * hjj + hj1 * hj1);
+        T al, be;
+        if (rho == T(0)) {
+            al = T(1);
+            be = T(0);
+        } else {
+            al = hjj / rho;
+            be = hj1 / rho;
+        }
+        c.cs[col] = al;
+        c.sn[col] = be;
+        T sj = c.s[col];
+        c.s[col] = al * sj;
+        T snew = -be * sj;
+        c.s[col + 1] = snew;
+        sh[col] = al * hjj + be * hj1;
+        sh[col + 1] = -be * hjj + al * hj1;
+        double arn = fabs((double)snew);
+        double wn0 = k->wnorm0;
+        int bd = (double)hnext <= (double)c.brk * wn0;
+        int nf = !isfinite(arn) || !isfinite((double)hnext);
+        k->j = col + 1;
+        k->arn = arn;
+        k->hnext = (double)hnext;
+        k->breakdown = bd;
+        if (nf)
+            k->nonfinite = 1;
+        int end = bd || nf || (c.tau > 0 && arn <= c.tau * k->beta) || arn <= c.inner_abs ||
+                  (col + 1 >= c.kmax);
+        k->active = !end;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i <= col + 1; i += blockDim.x)
+        c.H[(size_t)col * c.ld + i] = sh[i];
+}
+
+// ---------------------------------------------------------------------------
+// CGSR passes (procedure CGSR, done twice).  ncols = j basis vectors.
+//   k_cgs_dot          h1 = V^T w; also ||w||^2 (= ||A v_j||^2, breakdown ref)
+//   k_cgs_update_dot   w <- w - V h1, then h2 = V^T w
+//   k_cgs_update_norm  w <- w - V h2, ||w||^2 -> h_{j+1,j}; Hessenberg column
+//                      h1 + h2; Givens step
+// ---------------------------------------------------------------------------
+template <class T, class VT>
+__device__ __forceinline__ void cgs_block_dots(GridCtx<T, VT> &c, int ncols, int64_t rb, int64_t re,
+                                               T *out_part) {
+    __shared__ T sred[8 * 32];
+    for (int c0 = 0; c0 < ncols; c0 += 8) {
+        T acc[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            acc[k] = 0;
+        for (int64_t r = rb + 4 * threadIdx.x; r < re; r += 4 * blockDim.x) {
+            T wv[4];
+            ldv4(c.w + r, wv);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                if (c0 + k < ncols) {
+                    T v[4];
+                    ld4<T, VT>(c.V + (size_t)(c0 + k) * c.ldv + r, c.vinv, v);
+                    acc[k] += v[0] * wv[0] + v[1] * wv[1] + v[2] * wv[2] + v[3] * wv[3];
+                }
+            }
+        }
+        block_sum<T, 8>(acc, sred);
+        if (threadIdx.x == 0) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                if (c0 + k < ncols)
+                    out_part[c0 + k] = acc[k];
+        }
+    }
+}
+
+template <class T, class VT>
+__global__ void __launch_bounds__(256) k_cgs_dot(GridCtx<T, VT> c, int ncols) {
+    if (!c.ctl->active)
+        return;
+    __shared__ T sred[32];
+    int64_t rb, re;
+    block_rows(c, rb, re);
+    T *mypart = c.part + (size_t)blockIdx.x * PSTRIDE;
+    cgs_block_dots(c, ncols, rb, re, mypart);
+    // ||w||^2 for the breakdown reference
+    T nsq = 0;
+    for (int64_t r = rb + 4 * threadIdx.x; r < re; r += 4 * blockDim.x) {
+        T wv[4];
+        ldv4(c.w + r, wv);
+        nsq += wv[0] * wv[0] + wv[1] * wv[1] + wv[2] * wv[2] + wv[3] * wv[3];
+    }
+    nsq = block_sum1(nsq, sred);
+    if (threadIdx.x == 0)
+        mypart[MMAX + 1] = nsq;
+    if (!arrive_last(&c.ctl->counter[1]))
+        return;
+    reduce_columns(c.part, gridDim.x, ncols, c.h1);
+    __shared__ T snsq;
+    reduce_columns(c.part + MMAX + 1, gridDim.x, 1, &snsq);
+    __syncthreads();
+    if (threadIdx.x == 0)
+        c.ctl->wnorm0 = (double)wsqrt(snsq);  // ||A v_j||, read by the Givens step
+}
+
+template <class T, class VT>
+__device__ __forceinline__ T cgs_update_rows(GridCtx<T, VT> &c, int ncols, const T *hs, int64_t rb,
+                                             int64_t re) {
+    T nsq = 0;
+    for (int64_t r = rb + 4 * threadIdx.x; r < re; r += 4 * blockDim.x) {
+        T t[4] = {0, 0, 0, 0};
+        for (int i = 0; i < ncols; ++i) {
+            T v[4];
+            ld4<T, VT>(c.V + (size_t)i * c.ldv + r, c.vinv, v);
+            T hi = hs[i];
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                t[k] += v[k] * hi;
+        }
+        T wv[4];
+        ldv4(c.w + r, wv);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            wv[k] = wv[k] - t[k];
+            nsq += wv[k] * wv[k];
+        }
+        st4(c.w + r, wv);
+    }
+    return nsq;
+}
+
+template <class T, class VT>
+__global__ void __launch_bounds__(256) k_cgs_update_dot(GridCtx<T, VT> c, int ncols) {
+    if (!c.ctl->active)
+        return;
+    __shared__ T hs[MMAX + 1];
+    for (int i = threadIdx.x; i < ncols; i += blockDim.x)
+        hs[i] = c.h1[i];
+    __syncthreads();
+    int64_t rb, re;
+    block_rows(c, rb, re);
+    cgs_update_rows(c, ncols, hs, rb, re);
+    __syncthreads();
+    T *mypart = c.part + (size_t)blockIdx.x * PSTRIDE;
+    cgs_block_dots(c, ncols, rb, re, mypart);
+    if (!arrive_last(&c.ctl->counter[2]))
+        return;
+    reduce_columns(c.part, gridDim.x, ncols, c.h2);
+}
+
+template <class T, class VT>
+__global__ void __launch_bounds__(256) k_cgs_update_norm(GridCtx<T, VT> c, int ncols) {
+    if (!c.ctl->active)
+        return;
+    __shared__ T hs[MMAX + 1];
+    __shared__ T sred[32];
+    for (int i = threadIdx.x; i < ncols; i += blockDim.x)
+        hs[i] = c.h2[i];
+    __syncthreads();
+    int64_t rb, re;
+    block_rows(c, rb, re);
+    T nsq = cgs_update_rows(c, ncols, hs, rb, re);
+    nsq = block_sum1(nsq, sred);
+    if (threadIdx.x == 0)
+        c.part[(size_t)blockIdx.x * PSTRIDE] = nsq;
+    if (!arrive_last(&c.ctl->counter[3]))
+        return;
+    __shared__ T stot;
+    reduce_columns(c.part, gridDim.x, 1, &stot);
+    // Hessenberg column = h1 + h2 (sum of the two classical passes)
+    for (int i = threadIdx.x; i < ncols; i += blockDim.x)
+        c.h1[i] = ldcg(c.h1 + i) + ldcg(c.h2 + i);
+    __threadfence_block();
+    __syncthreads();
+    T hnext = wsqrt(stot);
+    givens_step(c, ncols - 1, c.h1, hnext);
+}
+
+// ---------------------------------------------------------------------------
+// MGS chain (procedure MGS): step i applies the previous projection
+// w <- w - h_{i-1} v_{i-1} and forms h_i = w . v_i in the same pass; the final
+// step applies the last projection, takes ||w|| and runs the Givens step.
+// ---------------------------------------------------------------------------
+template <class T, class VT>
+__global__ void __launch_bounds__(256) k_mgs_step(GridCtx<T, VT> c, int i) {
+    if (!c.ctl->active)
+        return;
+    __shared__ T sred[2 * 32];
+    int64_t rb, re;
+    block_rows(c, rb, re);
+    const T hp = (i > 0) ? c.h1[i - 1] : T(0);
+    T acc[2] = {0, 0};  // [0] = w . v_i, [1] = ||w||^2 (i == 0 only)
+    for (int64_t r = rb + 4 * threadIdx.x; r < re; r += 4 * blockDim.x) {
+        T wv[4], vi[4];
+        ldv4(c.w + r, wv);
+        if (i > 0) {
+            T vp[4];
+            ld4<T, VT>(c.V + (size_t)(i - 1) * c.ldv + r, c.vinv, vp);
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                wv[k] = wv[k] - hp * vp[k];
+            st4(c.w + r, wv);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                acc[1] += wv[k] * wv[k];
+        }
+        ld4<T, VT>(c.V + (size_t)i * c.ldv + r, c.vinv, vi);
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            acc[0] += wv[k] * vi[k];
+    }
+    block_sum<T, 2>(acc, sred);
+    if (threadIdx.x == 0) {
+        c.part[(size_t)blockIdx.x * PSTRIDE + 0] = acc[0];
+        c.part[(size_t)blockIdx.x * PSTRIDE + 1] = acc[1];
+    }
+    if (!arrive_last(&c.ctl->counter[1]))
+        return;
+    __shared__ T red[2];
+    reduce_columns(c.part, gridDim.x, 2, red);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        c.h1[i] = red[0];
+        if (i == 0)
+            c.ctl->wnorm0 = (double)wsqrt(red[1]);
+    }
+}
+
+template <class T, class VT>
+__global__ void __launch_bounds__(256) k_mgs_last(GridCtx<T, VT> c, int ncols) {
+    if (!c.ctl->active)
+        return;
+    __shared__ T sred[32];
+    int64_t rb, re;
+    block_rows(c, rb, re);
+    const int i = ncols - 1;
+    const T hp = c.h1[i];
+    T nsq = 0;
+    for (int64_t r = rb + 4 * threadIdx.x; r < re; r += 4 * blockDim.x) {
+        T wv[4], vp[4];
+        ldv4(c.w + r, wv);
+        ld4<T, VT>(c.V + (size_t)i * c.ldv + r, c.vinv, vp);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            wv[k] = wv[k] - hp * vp[k];
+            nsq += wv[k] * wv[k];
+        }
+        st4(c.w + r, wv);
+    }
+    nsq = block_sum1(nsq, sred);
+    if (threadIdx.x == 0)
+        c.part[(size_t)blockIdx.x * PSTRIDE] = nsq;
+    if (!arrive_last(&c.ctl->counter[3]))
+        return;
+    __shared__ T stot;
+    reduce_columns(c.part, gridDim.x, 1, &stot);
+    __syncthreads();
+    givens_step(c, ncols - 1, c.h1, wsqrt(stot));
+}
+
+// v_{col} = w / h_{j+1,j} (Alg. 1 "v_{j+1} <- w / h_{j+1,j}"), rounded to the
+// basis type.  Skipped when the cycle has ended.
+template <class T, class VT>
+__global__ void __launch_bounds__(256) k_normalize(GridCtx<T, VT> c, int col) {
+    if (!c.ctl->active)
+        return;
+    const T h = (T)c.ctl->hnext;
+    int64_t rb, re;
+    block_rows(c, rb, re);
+    VT *dst = c.V + (size_t)col * c.ldv;
+    for (int64_t r = rb + 4 * threadIdx.x; r < re; r += 4 * blockDim.x) {
+        T v[4];
+        ldv4(c.w + r, v);
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            v[k] = v[k] / h;
+        stb4<T, VT>(dst + r, v, c.vscale);
+    }
+}
+
+// y = H^{-1} s on the leading j x j triangle (back substitution, row-oriented
+// as in the oracle; a zero pivot gives y_i = 0).  One block.
+template <class T, class VT>
+__global__ void k_backsolve(GridCtx<T, VT> c) {
+    extern __shared__ unsigned char smraw[];
+    T *Hs = reinterpret_cast<T *>(smraw);
+    const int j = c.ctl->j;
+    c.ctl->last_j = j;
+    if (j == 0)
+        return;
+    for (int idx = threadIdx.x; idx < j * j; idx += blockDim.x) {
+        int col = idx / j, row = idx % j;
+        Hs[idx] = c.H[(size_t)col * c.ld + row];
+    }
+    T *ys = Hs + j * j;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int i = j - 1; i >= 0; --i) {
+            T acc = c.s[i];
+            for (int l = i + 1; l < j; ++l)
+                acc -= Hs[l * j + i] * ys[l];
+            T piv = Hs[i * j + i];
+            ys[i] = (piv == T(0)) ? T(0) : acc / piv;
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < j; i += blockDim.x)
+        c.y[i] = ys[i];
+}
+
+// u = V_j y in the working precision, then x += (double) u (Alg. 1 "x_{k+1}
+// <- x_k + u_k", binary64 addition, Sec. 2).  With a right preconditioner the
+// kernel writes t = V_j y instead and the update is applied after t -> M t.
+template <class T, class VT>
+__global__ void __launch_bounds__(256) k_update(GridCtx<T, VT> c, double *x, int to_t) {
+    __shared__ T ys[MMAX];
+    const int j = c.ctl->last_j;
+    if (j == 0)
+        return;
+    for (int i = threadIdx.x; i < j; i += blockDim.x)
+        ys[i] = c.y[i];
+    __syncthreads();
+    int64_t rb, re;
+    block_rows(c, rb, re);
+    for (int64_t r = rb + 4 * threadIdx.x; r < re; r += 4 * blockDim.x) {
+        T u[4] = {0, 0, 0, 0};
+        for (int i = 0; i < j; ++i) {
+            T v[4];
+            ld4<T, VT>(c.V + (size_t)i * c.ldv + r, c.vinv, v);
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                u[k] += v[k] * ys[i];
+        }
+        if (to_t) {
+            st4(c.t + r, u);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (r + k < c.n)
+                    x[r + k] += (double)u[k];
+        }
+    }
+}
+
+// x += (double) u for a full-length working vector u (after u = M t).
+template <class T>
+__global__ void __launch_bounds__(256) k_axpy_x(int n, const T *u, double *x, const Ctl *ctl) {
+    if (ctl->last_j == 0)
+        return;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n;
+         r += (int64_t)gridDim.x * blockDim.x)
+        x[r] += (double)u[r];
+}
+
+// ||b||_2 in binary64 into ctl->bnorm (two-stage, deterministic).
+template <class T, class VT>
+__global__ void __launch_bounds__(256) k_bnorm(GridCtx<T, VT> c, const double *b) {
+    __shared__ double sd[32];
+    double ss = 0;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < c.n;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        double v = b[r];
+        ss += v * v;
+    }
+    ss = block_sum1(ss, sd);
+    if (threadIdx.x == 0)
+        c.part64[(size_t)blockIdx.x * 4 + 2] = ss;
+    if (!arrive_last(&c.ctl->counter[4]))
+        return;
+    double a = 0;
+    for (int bb = threadIdx.x; bb < gridDim.x; bb += blockDim.x)
+        a += ldcg(c.part64 + (size_t)bb * 4 + 2);
+    a = block_sum1(a, sd);
+    if (threadIdx.x == 0) {
+        c.ctl->bnorm = sqrt(a);
+        if (!isfinite(a))
+            c.ctl->nonfinite = 1;
+    }
+}
+
+// Widen basis columns [0, ncols) to binary64 (for export), rows < n.
+template <class T, class VT>
+__global__ void k_export_basis(GridCtx<T, VT> c, int ncols, double *out) {
+    const int64_t total = (int64_t)ncols * c.n;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        int64_t col = idx / c.n, row = idx % c.n;
+        out[idx] = (double)Basis<VT>::ld(c.V + col * c.ldv + row, c.vinv);
+    }
+}
+
+}  // namespace gmres

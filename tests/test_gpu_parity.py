@@ -1,0 +1,292 @@
+"""CUDA path against the CPU oracle, element by element (marker: gpu).
+
+Kernel level: SpMV (binary64 / binary32, every lanes-per-row variant) and the
+binary64 residual, on matrices with empty rows, a 200-entry row, n in
+{1, 31, 32, 33, 1000, 4097}.  Cycle level: one restart cycle (basis,
+Hessenberg matrix, rotations, s, y, correction) for every precision and both
+orthogonalisation schemes.  Solver level: every mode on both paths reaches a
+binary64 relative residual <= 1e-10 and matches the oracle's solution.
+
+Tolerances come from the arithmetic: a sum of k products carries at most
+gamma_k = k u / (1 - k u) relative error against sum |a||x| for any order of
+summation, so two implementations of the same sum differ by at most twice
+that; later Arnoldi quantities inherit the per-step error amplified by the
+conditioning of the Krylov basis, so the cycle comparisons use a per-precision
+tolerance scaled by the step count.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2011_01850_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if torch.cuda.is_available():
+    from paper_2011_01850_gb300 import gmres as G
+
+U64 = 2.0 ** -53
+U32 = 2.0 ** -24
+
+
+def dev(a, dtype=torch.float64):
+    return torch.tensor(np.asarray(a), dtype=dtype, device="cuda")
+
+
+def edge_matrices():
+    rng = np.random.default_rng(3)
+    out = []
+    for n in (1, 31, 32, 33, 1000, 4097):
+        out.append(("powerlaw%d" % n, I.powerlaw_random(max(n, 2), seed=n)
+                    if n > 1 else I.dense_to_csr(np.array([[2.5]]))))
+    # empty rows and one 200-entry row
+    n = 700
+    D = np.zeros((n, n))
+    D[5, rng.choice(n, 200, replace=False)] = rng.standard_normal(200)
+    for i in range(n):
+        if i % 7 != 3:
+            D[i, i] = 3.0
+            D[i, (i + 1) % n] = -1.0
+    rows = [[] for _ in range(n)]
+    rp = [0]
+    ci = []
+    va = []
+    for i in range(n):
+        nz = np.nonzero(D[i])[0]
+        ci += list(nz)
+        va += list(D[i, nz])
+        rp.append(len(ci))
+    out.append(("emptyrows", (np.array(rp, np.int32), np.array(ci, np.int32), np.array(va))))
+    out.append(("convdiff3d_12", I.convdiff3d(12, seed=1)))
+    return out
+
+
+@pytest.fixture(scope="module")
+def stream():
+    torch.cuda.set_device(0)
+    return torch.cuda.current_stream()
+
+
+@pytest.mark.parametrize("name,A", edge_matrices(), ids=[m[0] for m in edge_matrices()])
+@pytest.mark.parametrize("lanes", [1, 2, 4, 8, 16, 32])
+def test_spmv_parity(name, A, lanes, gpulib, stream):
+    rp, ci, va = A
+    n = len(rp) - 1
+    x = np.random.default_rng(n).standard_normal(n)
+    k = np.diff(rp).astype(np.float64)
+    absA = (np.abs(va), ci, rp)
+    ax = np.zeros(n)
+    r = np.repeat(np.arange(n), np.diff(rp))
+    np.add.at(ax, r, np.abs(va) * np.abs(x[ci]))
+    s = G.Solver(A, stream=stream)
+    s.set_opts(spmv_lanes=lanes)
+    # binary64
+    y = torch.zeros(n, dtype=torch.float64, device="cuda")
+    G.gmres_spmv(s.h, dev(x), y, G.FP64)
+    yo = O.spmv(A, x, O.FP64)
+    g = k * U64 / (1 - k * U64)
+    assert np.all(np.abs(y.cpu().numpy() - yo) <= 2 * g * ax + 1e-300), name
+    # binary32 (values, x and the sum in binary32)
+    y32 = torch.zeros(n, dtype=torch.float32, device="cuda")
+    G.gmres_spmv(s.h, dev(x, torch.float32), y32, G.MIXED)
+    yo32 = O.spmv(A, x, O.MIXED)
+    x32 = x.astype(np.float32).astype(np.float64)
+    ax32 = np.zeros(n)
+    np.add.at(ax32, r, np.abs(va.astype(np.float32)) * np.abs(x32[ci]))
+    g32 = k * U32 / (1 - k * U32)
+    assert np.all(np.abs(y32.cpu().numpy() - yo32) <= 2 * g32 * ax32 * 1.0001 + 1e-37), name
+    s.close()
+
+
+@pytest.mark.parametrize("name,A", edge_matrices(), ids=[m[0] for m in edge_matrices()])
+def test_residual_parity(name, A, gpulib, stream):
+    rp, ci, va = A
+    n = len(rp) - 1
+    rng = np.random.default_rng(n + 1)
+    x = rng.standard_normal(n)
+    b = rng.standard_normal(n)
+    s = G.Solver(A, stream=stream)
+    z = torch.zeros(n, dtype=torch.float64, device="cuda")
+    nrm = G.gmres_residual(s.h, dev(b), dev(x), z)
+    zo, no = O.residual(A, b, x)
+    r = np.repeat(np.arange(n), np.diff(rp))
+    ax = np.zeros(n)
+    np.add.at(ax, r, np.abs(va) * np.abs(x[ci]))
+    k = np.diff(rp) + 1.0
+    assert np.all(np.abs(z.cpu().numpy() - zo) <= 2 * k * U64 * (ax + np.abs(b)) * 1.01)
+    assert abs(nrm - no) <= 1e-13 * no
+    s.close()
+
+
+CYCLE_TOL = {O.FP64: 1e-11, O.MIXED: 2e-4, O.MIXED_BF16: 5e-2, O.MIXED_FP16: 2e-2}
+
+
+@pytest.mark.parametrize("prec", [O.FP64, O.MIXED, O.MIXED_BF16, O.MIXED_FP16],
+                         ids=["fp64", "mixed", "bf16", "fp16"])
+@pytest.mark.parametrize("ortho", [O.MGS, O.CGSR], ids=["mgs", "cgsr"])
+def test_cycle_parity(prec, ortho, gpulib, stream):
+    """One restart cycle: every exported quantity against the oracle's."""
+    A = I.convdiff2d(33, 31, pe=10.0)  # n = 1023: several blocks and a ragged tail
+    b = I.rhs_ones_noise(A, 1e-3, 4)
+    n = len(A[0]) - 1
+    m, kmax = 24, 12
+    s = G.Solver(A, stream=stream)
+    g = G.gmres_arnoldi(s.h, dev(b), m, kmax, ortho, prec, n=n)
+    o = O.arnoldi_cycle(A, b, m, ortho=ortho, prec=prec, kmax=kmax)
+    s.close()
+    assert g["j"] == o["j"] == kmax
+    tol = CYCLE_TOL[prec]
+    j = kmax
+    beta = np.linalg.norm(b)
+
+    def close(a, b_, scale, what):
+        err = np.abs(a - b_).max() / scale
+        assert err <= tol, (what, err, tol)
+
+    close(g["Hbar"][: j + 1, :j], o["Hbar"][: j + 1, :j], np.abs(o["Hbar"]).max(), "Hbar")
+    close(g["H"][: j + 1, :j], o["H"][: j + 1, :j], np.abs(o["H"]).max(), "H")
+    close(g["cs"][:j], o["cs"][:j], 1.0, "cs")
+    close(g["sn"][:j], o["sn"][:j], 1.0, "sn")
+    close(g["s"][: j + 1], o["s"][: j + 1], beta, "s")
+    close(g["arn"][:j], o["arn"][:j], beta, "arn")
+    close(g["V"][: j + 1], o["V"][: j + 1], 1.0 / np.sqrt(n) * 10, "V")
+    close(g["u"], o["u"], np.abs(o["u"]).max(), "u")
+    # the first basis vector is r0/beta rounded to the basis: equal up to one
+    # rounding of the quotient (the two betas differ in the last place)
+    v1o = O.round_basis(b / beta, prec, n)
+    assert np.allclose(g["V"][0], v1o, rtol=(4e-3 if prec >= O.MIXED_BF16 else 1e-6),
+                       atol=1e-300)
+
+
+def _solve(A, b, prec, ortho, path, m=30, tol=1e-10, stream=None, maxiter=4000):
+    s = G.Solver(A, stream=stream)
+    s.set_opts(path=path)
+    n = len(A[0]) - 1
+    db = dev(b)
+    dx = torch.zeros(n, dtype=torch.float64, device="cuda")
+    x, st, info = s.solve(db, dx, m=m, tol=tol, ortho=ortho, prec=prec, maxiter=maxiter)
+    s.close()
+    return dx.cpu().numpy(), st, info
+
+
+SOLVE_CASES = [
+    ("convdiff2d_40", lambda: I.convdiff2d(40, pe=10.0)),
+    ("powerlaw_3000", lambda: I.powerlaw_random(3000, seed=12)),
+    ("convdiff3d_14", lambda: I.convdiff3d(14, seed=2)),
+]
+
+
+@pytest.mark.parametrize("case", SOLVE_CASES, ids=[c[0] for c in SOLVE_CASES])
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "mixed_bf16", "mixed_fp16"])
+@pytest.mark.parametrize("ortho", ["mgs", "cgsr"])
+@pytest.mark.parametrize("path", [1, 2], ids=["grid", "block"])
+def test_solve_parity(case, prec, ortho, path, gpulib, stream):
+    A = case[1]()
+    b = I.rhs_ones_noise(A, 1e-3, 11)
+    x, st, info = _solve(A, b, prec, ortho, path, stream=stream)
+    assert st == G.OK, info
+    rel = O.residual_norm(A, b, x) / np.linalg.norm(b)
+    assert rel <= 1e-10, (rel, info)
+    assert abs(rel - info["relres"]) <= 1e-3 * rel + 1e-16
+    xo, _ = O.gmres(A, b, m=30, tol=1e-13, ortho=O.CGSR, prec=O.FP64, maxiter=20000)
+    err = np.linalg.norm(x - xo) / np.linalg.norm(xo)
+    assert err <= 1e-8, err
+
+
+def test_solve_matches_oracle_iterations_fp64(gpulib, stream):
+    """Binary64: the GPU and the oracle take the same restart schedule."""
+    A = I.convdiff2d(24, pe=10.0)
+    b = I.rhs_ones_noise(A, 1e-3, 2)
+    for path in (1, 2):
+        for ortho, oo in (("mgs", O.MGS), ("cgsr", O.CGSR)):
+            x, st, info = _solve(A, b, "fp64", ortho, path, m=20, stream=stream)
+            xo, oi = O.gmres(A, b, m=20, tol=1e-10, ortho=oo, prec=O.FP64, maxiter=4000)
+            assert info["restarts"] == oi["restarts"] and info["iters"] == oi["iters"]
+            assert np.linalg.norm(x - xo) / np.linalg.norm(xo) <= 1e-11
+
+
+def test_host_buffers_equal_device_buffers(gpulib, stream):
+    A = I.convdiff2d(30, pe=10.0)
+    b = I.rhs_ones_noise(A, 1e-3, 3)
+    n = len(A[0]) - 1
+    s = G.Solver(A, stream=stream)
+    s.set_opts(path=G.PATH_GRID)
+    xh = np.zeros(n)
+    _, st1, i1 = s.solve(b, xh, m=25, prec="mixed")
+    dx = torch.zeros(n, dtype=torch.float64, device="cuda")
+    _, st2, i2 = s.solve(dev(b), dx, m=25, prec="mixed")
+    s.close()
+    assert st1 == st2 == G.OK
+    assert np.array_equal(xh, dx.cpu().numpy())  # deterministic reductions
+
+
+def test_repeatable_bitwise(gpulib, stream):
+    A = I.powerlaw_random(5000, seed=9)
+    b = I.rhs_ones_noise(A, 1e-3, 1)
+    x1, _, _ = _solve(A, b, "mixed", "cgsr", 1, stream=stream)
+    x2, _, _ = _solve(A, b, "mixed", "cgsr", 1, stream=stream)
+    assert np.array_equal(x1, x2)
+
+
+def test_edge_cases(gpulib, stream):
+    A = I.convdiff2d(10, pe=10.0)
+    n = len(A[0]) - 1
+    s = G.Solver(A, stream=stream)
+    # b = 0 -> x = 0, converged
+    for path in (1, 2):
+        s.set_opts(path=path)
+        x = np.ones(n)
+        _, st, info = s.solve(np.zeros(n), x)
+        assert st == G.OK and np.all(x == 0)
+    # maxiter = 0 -> iteration limit (x untouched)
+    s.set_opts(path=1)
+    x = np.zeros(n)
+    _, st, info = s.solve(np.ones(n), x, maxiter=0)
+    assert st == G.MAXITER and info["iters"] == 0
+    # NaN in b
+    bad = np.ones(n)
+    bad[3] = np.nan
+    with pytest.raises(G.GmresError) as e:
+        s.solve(bad, np.zeros(n))
+    assert e.value.status == G.ERR_NONFINITE
+    # bad arguments
+    for kw in (dict(m=0), dict(m=129), dict(tol=0.0), dict(maxiter=-1)):
+        with pytest.raises(G.GmresError) as e:
+            s.solve(np.ones(n), np.zeros(n), **kw)
+        assert e.value.status == G.ERR_ARG
+    s.close()
+    # invalid CSR / non-finite values are rejected at create time
+    rp, ci, va = A
+    ci2 = ci.copy()
+    ci2[0] = n
+    with pytest.raises(G.GmresError) as e:
+        G.Solver((rp, ci2, va))
+    assert e.value.status == G.ERR_ARG
+    va2 = va.copy()
+    va2[1] = np.inf
+    with pytest.raises(G.GmresError) as e:
+        G.Solver((rp, ci, va2))
+    assert e.value.status == G.ERR_NONFINITE
+    # 1 x 1 system
+    one = I.dense_to_csr(np.array([[4.0]]))
+    for path in (1, 2):
+        x, st, info = _solve(one, np.array([2.0]), "mixed", "mgs", path, stream=stream)
+        assert st == G.OK and abs(x[0] - 0.5) < 1e-12
+
+
+def test_memory_model(gpulib, stream):
+    """Device footprint follows the paper's storage model (Sec. 4) without the
+    ILU factors: the matrix keeps shared int32 indices plus binary64 and
+    binary32 values; the basis costs (m+1) n s_V bytes."""
+    A = I.convdiff2d(50, pe=10.0)
+    n, nnz = len(A[0]) - 1, len(A[1])
+    s = G.Solver(A, stream=stream)
+    mb, wb64 = G.gmres_memory_bytes(s.h, 50, G.FP64)
+    _, wb32 = G.gmres_memory_bytes(s.h, 50, G.MIXED)
+    _, wb16 = G.gmres_memory_bytes(s.h, 50, G.MIXED_BF16)
+    s.close()
+    assert mb == 16 * nnz + 4 * (n + 1)
+    ldv = ((n + 255) // 256) * 256
+    assert wb64 - wb32 >= 51 * ldv * 4
+    assert wb32 - wb16 == 51 * ldv * 2
