@@ -132,6 +132,8 @@ def powerlaw_random(n, lmin=3, lmax=200, alpha=1.734, dom=1.2, seed=0):
     uniform over [0, n) without the diagonal, with N(0, 1) values; the
     diagonal is ``dom`` times the row's off-diagonal absolute sum."""
     rng = np.random.default_rng(seed)
+    lmax = min(lmax, n)
+    lmin = min(lmin, lmax)
     L = _powerlaw_lengths(rng, n, lmin, lmax, alpha)
     k = L - 1
     rows = np.repeat(np.arange(n, dtype=np.int64), k)
@@ -139,7 +141,7 @@ def powerlaw_random(n, lmin=3, lmax=200, alpha=1.734, dom=1.2, seed=0):
     cols = rng.integers(0, n - 1, size=tot, dtype=np.int64)
     cols += cols >= rows  # skip the diagonal
     # make the columns of every row distinct: redraw duplicates until none remain
-    for _ in range(64):
+    for _ in range(256):
         order = np.lexsort((cols, rows))
         rows, cols = rows[order], cols[order]
         dup = np.zeros(tot, dtype=bool)
