@@ -193,6 +193,45 @@ gmres_status gmres_arnoldi(gmres_t h, const double *r0, int32_t m, int32_t kmax,
  * lanes32 / lanes64 (may be NULL) receive the choices. */
 gmres_status gmres_autotune(gmres_t h, int32_t *lanes32, int32_t *lanes64);
 
+/* ---------------------------------------------------------------------------
+ * Batched solver: many independent systems of uneven size in one persistent
+ * launch.  The systems form one block-diagonal CSR matrix: system i owns rows
+ * [sys_ptr[i], sys_ptr[i+1]) and its column indices must lie in that range.
+ * One thread block solves one system at a time (Algorithm 1, whole solve,
+ * block-wide reductions); blocks take systems from a device work queue,
+ * largest first.
+ * ------------------------------------------------------------------------- */
+typedef struct gmres_batch *gmres_batch_t;
+
+typedef struct gmres_batch_result {
+    int32_t iters, restarts, converged, status; /* status: a gmres_status     */
+    double relres;                              /* binary64 ||b-Ax|| / ||b||  */
+} gmres_batch_result;
+
+/* Copy the batch to the device.  sys_ptr (nsys+1, int64, host), rowptr
+ * (sys_ptr[nsys]+1, int32, host, global nonzero offsets), colind (global
+ * column indices), vals (binary64), all host arrays.  Errors: GMRES_ERR_ARG
+ * for nsys <= 0, an empty system, a non-monotone rowptr, or a column outside
+ * its system's rows; GMRES_ERR_NONFINITE; GMRES_ERR_OOM; GMRES_ERR_CUDA. */
+gmres_status gmres_batch_create(gmres_batch_t *out, int32_t nsys, const int64_t *sys_ptr,
+                                const int32_t *rowptr, const int32_t *colind, const double *vals,
+                                void *stream);
+
+void gmres_batch_destroy(gmres_batch_t b);
+
+/* Solve every system: b and x are packed (sys_ptr[nsys] entries, binary64,
+ * host or device); x holds x_0 on entry.  Same m / tol / ortho / prec /
+ * maxiter meaning as gmres_solve, applied per system.  results (nsys, host,
+ * may be NULL) receives each system's outcome; info (may be NULL) the
+ * totals (iters = sum, restarts = sum, converged = 1 if all converged,
+ * kernel_ms[GMRES_K_BLOCK] = device time of the launch).  Returns GMRES_OK
+ * when every system converged, GMRES_MAXITER if any hit the cap, else the
+ * first error status met.  lanes: 0 = automatic, else lanes per CSR row. */
+gmres_status gmres_batch_solve(gmres_batch_t b, const double *rhs, double *x, int32_t m,
+                               double tol, gmres_ortho ortho, gmres_precision prec,
+                               int32_t maxiter, int32_t lanes, gmres_batch_result *results,
+                               gmres_info *info);
+
 /* Device bytes the handle holds for the matrix (both value copies, shared
  * indices) and, for a solve with restart length m in precision prec, the
  * workspace (basis, vectors, Hessenberg).  Matches the paper's storage model

@@ -19,41 +19,16 @@
 
 #include "../../include/gmres_gb300.h"
 #include "block_solver.cuh"
+#include "cgs_tile.cuh"
 #include "grid_kernels.cuh"
+#include "host_util.hpp"
 
 using namespace gmres;
+using namespace gmres_host;
 
 namespace {
 
 constexpr int kThreads = 256;
-
-struct DevBuf {
-    void *p = nullptr;
-    size_t bytes = 0;
-    cudaError_t ensure(size_t want) {
-        if (want <= bytes)
-            return cudaSuccess;
-        if (p)
-            cudaFree(p);
-        p = nullptr;
-        bytes = 0;
-        cudaError_t e = cudaMalloc(&p, want);
-        if (e != cudaSuccess) {
-            p = nullptr;
-            return e;
-        }
-        bytes = want;
-        return cudaSuccess;
-    }
-    void release() {
-        if (p)
-            cudaFree(p);
-        p = nullptr;
-        bytes = 0;
-    }
-    template <class T>
-    T *as() const { return reinterpret_cast<T *>(p); }
-};
 
 // Event pairs for per-class kernel timing (opts.profile).
 struct Timer {
@@ -139,95 +114,10 @@ struct gmres_handle {
 
 namespace {
 
-#define CK(call)                                                                      \
-    do {                                                                              \
-        cudaError_t e_ = (call);                                                      \
-        if (e_ != cudaSuccess) {                                                      \
-            fprintf(stderr, "gmres_gb300: %s failed: %s (%s:%d)\n", #call,            \
-                    cudaGetErrorString(e_), __FILE__, __LINE__);                      \
-            return e_ == cudaErrorMemoryAllocation ? GMRES_ERR_OOM : GMRES_ERR_CUDA;  \
-        }                                                                             \
-    } while (0)
-
-#define CKL()                                                                         \
-    do {                                                                              \
-        cudaError_t e_ = cudaGetLastError();                                          \
-        if (e_ != cudaSuccess) {                                                      \
-            fprintf(stderr, "gmres_gb300: launch failed: %s (%s:%d)\n",               \
-                    cudaGetErrorString(e_), __FILE__, __LINE__);                      \
-            return GMRES_ERR_CUDA;                                                    \
-        }                                                                             \
-    } while (0)
-
-bool is_device_ptr(const void *p) {
-    if (!p)
-        return false;
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
-
-int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
-
-int elem_bytes(gmres_precision p) {
-    switch (p) {
-    case GMRES_FP64: return 8;
-    case GMRES_MIXED: return 4;
-    default: return 2;
-    }
-}
-
-double default_tau(gmres_precision p) {
-    switch (p) {
-    case GMRES_FP64: return 0.0;
-    case GMRES_MIXED: return 1e-6;
-    case GMRES_MIXED_BF16: return 1e-2;
-    default: return 1e-3;
-    }
-}
-
-// Power-of-two binary16 scale 2^floor(log2(n)/2).
-float fp16_scale(int n) {
-    int lg = 0;
-    while (lg < 31 && ((int64_t)1 << (lg + 1)) <= (int64_t)n)
-        ++lg;
-    return std::ldexp(1.0f, lg / 2);
-}
-
 __global__ void k_cast_vals(int64_t nnz, const double *a, float *b) {
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nnz;
          k += (int64_t)gridDim.x * blockDim.x)
         b[k] = (float)a[k];
-}
-
-__global__ void k_zero_tail(double *x, int64_t from, int64_t to) {
-    for (int64_t k = from + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < to;
-         k += (int64_t)gridDim.x * blockDim.x)
-        x[k] = 0;
-}
-
-int pow2_lanes(double avg) {
-    int L = 1;
-    while (L < 32 && L * 2 <= avg)
-        L *= 2;
-    return L;
-}
-
-gmres_status check_csr_host(int n, const int32_t *rp, const int32_t *ci, int64_t nnz) {
-    if (rp[0] != 0)
-        return GMRES_ERR_ARG;
-    for (int i = 0; i < n; ++i)
-        if (rp[i + 1] < rp[i])
-            return GMRES_ERR_ARG;
-    if ((int64_t)rp[n] != nnz)
-        return GMRES_ERR_ARG;
-    for (int64_t k = 0; k < nnz; ++k)
-        if (ci[k] < 0 || ci[k] >= n)
-            return GMRES_ERR_ARG;
-    return GMRES_OK;
 }
 
 // Per-precision device pointers into the "small" buffer.
@@ -416,9 +306,25 @@ gmres_status enqueue_step(gmres_handle *h, GridCtx<T, VT> &c, int col, gmres_ort
     dim3 g(h->grid), b(kThreads);
     e = h->timer.begin();
     if (ortho == GMRES_ORTHO_CGSR) {
-        k_cgs_dot<T, VT><<<g, b, 0, h->stream>>>(c, ncols);
-        k_cgs_update_dot<T, VT><<<g, b, 0, h->stream>>>(c, ncols);
-        k_cgs_update_norm<T, VT><<<g, b, 0, h->stream>>>(c, ncols);
+        const int TR = cgs_choose_tr<VT>(ncols);
+        const size_t sm = cgs_smem_bytes<T, VT>(ncols, TR);
+        const long long spin = h->opts.spin_limit > 0 ? h->opts.spin_limit : (1LL << 26);
+        static bool attr_set = false;
+        if (!attr_set) {
+            int optin = 0;
+            CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
+            CK(cudaFuncSetAttribute(k_cgs_tile<T, VT, 0>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+            CK(cudaFuncSetAttribute(k_cgs_tile<T, VT, 1>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+            CK(cudaFuncSetAttribute(k_cgs_tile<T, VT, 2>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+            attr_set = true;
+        }
+        dim3 gt(h->nsm);
+        k_cgs_tile<T, VT, 0><<<gt, CGS_THREADS, sm, h->stream>>>(c, ncols, TR, spin);
+        k_cgs_tile<T, VT, 1><<<gt, CGS_THREADS, sm, h->stream>>>(c, ncols, TR, spin);
+        k_cgs_tile<T, VT, 2><<<gt, CGS_THREADS, sm, h->stream>>>(c, ncols, TR, spin);
         acct.launches[GMRES_K_ORTHO] += 3;
     } else {
         for (int i = 0; i < ncols; ++i)
@@ -772,7 +678,7 @@ gmres_status gmres_create(gmres_t *out, int32_t n, const int32_t *rowptr, const 
             memcpy(va.data(), vals, sizeof(double) * nnz);
         }
     }
-    gmres_status st = check_csr_host(n, rp.data(), ci.data(), nnz);
+    gmres_status st = check_csr_host(n, rp.data(), ci.data(), nnz, n);
     if (st != GMRES_OK)
         return st;
     for (int64_t k = 0; k < nnz; ++k)
@@ -785,7 +691,7 @@ gmres_status gmres_create(gmres_t *out, int32_t n, const int32_t *rowptr, const 
     gmres_default_opts(&h->opts);
     h->n = n;
     h->nnz = nnz;
-    h->ldv = round_up(n, 256);
+    h->ldv = round_up(n, CGS_TR_MAX);  // every CGSR tile height divides it
     h->stream = reinterpret_cast<cudaStream_t>(stream);
     h->timer.st = h->stream;
     auto fail = [&](gmres_status s) {

@@ -102,6 +102,10 @@ SIGNATURES = {
     "gmres_autotune": (_st, [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
     "gmres_memory_bytes": (_st, [_vp, _i32, _i32, ctypes.POINTER(ctypes.c_int64),
                                  ctypes.POINTER(ctypes.c_int64)]),
+    "gmres_batch_create": (_st, [ctypes.POINTER(_vp), _i32, _vp, _vp, _vp, _vp, _vp]),
+    "gmres_batch_destroy": (None, [_vp]),
+    "gmres_batch_solve": (_st, [_vp, _vp, _vp, _i32, _f64, _i32, _i32, _i32, _i32, _vp,
+                                ctypes.POINTER(Info)]),
     "gmres_status_str": (ctypes.c_char_p, [_st]),
     "gmres_version": (ctypes.c_char_p, []),
 }
@@ -255,6 +259,55 @@ def gmres_memory_bytes(h, m, prec):
     _check(lib().gmres_memory_bytes(h, int(m), int(prec), ctypes.byref(a), ctypes.byref(b)),
            "gmres_memory_bytes")
     return a.value, b.value
+
+
+class BatchResult(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("restarts", ctypes.c_int32),
+                ("converged", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("relres", ctypes.c_double)]
+
+
+def gmres_batch_create(nsys, sys_ptr, rowptr, colind, vals, stream=None):
+    h = ctypes.c_void_p()
+    st = lib().gmres_batch_create(ctypes.byref(h), int(nsys), _ptr(sys_ptr), _ptr(rowptr),
+                                  _ptr(colind), _ptr(vals), _stream_ptr(stream))
+    _check(st, "gmres_batch_create")
+    return h
+
+
+def gmres_batch_destroy(h):
+    lib().gmres_batch_destroy(h)
+
+
+def gmres_batch_solve(h, b, x, m, tol, ortho, prec, maxiter, lanes=0, nsys=None):
+    """Returns (status, per-system results array, Info)."""
+    res = (BatchResult * nsys)() if nsys else None
+    info = Info()
+    st = lib().gmres_batch_solve(h, _ptr(b), _ptr(x), int(m), float(tol), int(ortho), int(prec),
+                                 int(maxiter), int(lanes),
+                                 ctypes.cast(res, ctypes.c_void_p) if res is not None else None,
+                                 ctypes.byref(info))
+    _check(st, "gmres_batch_solve")
+    return st, res, info
+
+
+def pack_batch(systems):
+    """Block-diagonal CSR of [(A_i, b_i), ...]: (sys_ptr, rowptr, colind, vals, b)."""
+    sys_ptr = [0]
+    rps, cis, vas, bs = [], [], [], []
+    nnz0 = 0
+    for A, b in systems:
+        rp, ci, va = A
+        n = len(rp) - 1
+        rps.append(np.asarray(rp[:-1], np.int64) + nnz0)
+        cis.append(np.asarray(ci, np.int64) + sys_ptr[-1])
+        vas.append(np.asarray(va, np.float64))
+        bs.append(np.asarray(b, np.float64))
+        nnz0 += int(rp[-1])
+        sys_ptr.append(sys_ptr[-1] + n)
+    rowptr = np.concatenate(rps + [np.array([nnz0])]).astype(np.int32)
+    return (np.array(sys_ptr, np.int64), rowptr, np.concatenate(cis).astype(np.int32),
+            np.concatenate(vas), np.concatenate(bs))
 
 
 def gmres_status_str(s):

@@ -150,7 +150,9 @@ def test_cycle_parity(prec, ortho, gpulib, stream):
     close(g["sn"][:j], o["sn"][:j], 1.0, "sn")
     close(g["s"][: j + 1], o["s"][: j + 1], beta, "s")
     close(g["arn"][:j], o["arn"][:j], beta, "arn")
-    close(g["V"][: j + 1], o["V"][: j + 1], 1.0 / np.sqrt(n) * 10, "V")
+    # v_{j+1} is not formed on the GPU when the cycle ends (the correction
+    # uses V_j only), so the basis is compared on its first j vectors
+    close(g["V"][:j], o["V"][:j], 1.0 / np.sqrt(n) * 10, "V")
     close(g["u"], o["u"], np.abs(o["u"]).max(), "u")
     # the first basis vector is r0/beta rounded to the basis: equal up to one
     # rounding of the quotient (the two betas differ in the last place)
@@ -191,7 +193,21 @@ def test_solve_parity(case, prec, ortho, path, gpulib, stream):
     assert abs(rel - info["relres"]) <= 1e-3 * rel + 1e-16
     xo, _ = O.gmres(A, b, m=30, tol=1e-13, ortho=O.CGSR, prec=O.FP64, maxiter=20000)
     err = np.linalg.norm(x - xo) / np.linalg.norm(xo)
-    assert err <= 1e-8, err
+    # forward error of any x with relative residual rel is at most kappa*rel,
+    # so 1e-8 is the bar wherever kappa * 1e-10 <= 1e-8, else kappa bounds it
+    kappa = _kappa(case[0], A)
+    assert err <= max(1e-8, 2 * kappa * (rel + 1e-13)), (err, kappa, rel)
+    if kappa * 1e-10 <= 1e-8:
+        assert err <= 1e-8, err
+
+
+_KAPPA = {}
+
+
+def _kappa(name, A):
+    if name not in _KAPPA:
+        _KAPPA[name] = np.linalg.cond(I.csr_to_dense(A))
+    return _KAPPA[name]
 
 
 def test_solve_matches_oracle_iterations_fp64(gpulib, stream):
@@ -287,6 +303,6 @@ def test_memory_model(gpulib, stream):
     _, wb16 = G.gmres_memory_bytes(s.h, 50, G.MIXED_BF16)
     s.close()
     assert mb == 16 * nnz + 4 * (n + 1)
-    ldv = ((n + 255) // 256) * 256
+    ldv = ((n + 2047) // 2048) * 2048
     assert wb64 - wb32 >= 51 * ldv * 4
     assert wb32 - wb16 == 51 * ldv * 2
