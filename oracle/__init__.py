@@ -271,5 +271,91 @@ def gmres(A, b, x0=None, m=30, tol=1e-10, ortho=CGSR, prec=FP64, maxiter=10000, 
     return x, out
 
 
-def _bind_spai(L):  # pragma: no cover - filled in with the preconditioner oracle
-    pass
+def _bind_spai(L):
+    i64 = ctypes.c_int64
+    vp = ctypes.c_void_p
+    L.orc_spai_nparam.argtypes = []
+    L.orc_spai_nparam.restype = ctypes.c_int
+    L.orc_spai_features.argtypes = [ctypes.c_int32, _i32p, _i32p, _f64p, _f64p]
+    L.orc_spai_features.restype = ctypes.c_int
+    L.orc_spai_forward.argtypes = [i64, _f64p, _f64p, _f64p]
+    L.orc_spai_forward.restype = ctypes.c_int
+    L.orc_spai_values.argtypes = [ctypes.c_int32, _i32p, _i32p, _f64p, _f64p, _f64p]
+    L.orc_spai_values.restype = ctypes.c_int
+    L.orc_spai_loss_grad_m.argtypes = [ctypes.c_int32, _i32p, _i32p, _f64p, _f64p,
+                                       ctypes.c_int32, _f64p, vp]
+    L.orc_spai_loss_grad_m.restype = ctypes.c_double
+    L.orc_spai_loss_grad.argtypes = [ctypes.c_int32, _i32p, _i32p, _f64p, _f64p, ctypes.c_int32,
+                                     _f64p, vp, vp]
+    L.orc_spai_loss_grad.restype = ctypes.c_double
+
+
+SPAI_NF, SPAI_NH = 8, 64
+SPAI_NPARAM = SPAI_NH * SPAI_NF + SPAI_NH + SPAI_NH * SPAI_NH + SPAI_NH + SPAI_NH + 1
+
+
+def spai_unpack(params):
+    """(W1[64,8], b1[64], W2[64,64], b2[64], w3[64], b3) views of a parameter vector."""
+    p = np.asarray(params)
+    o = 0
+    W1 = p[o:o + 512].reshape(64, 8); o += 512
+    b1 = p[o:o + 64]; o += 64
+    W2 = p[o:o + 4096].reshape(64, 64); o += 4096
+    b2 = p[o:o + 64]; o += 64
+    w3 = p[o:o + 64]; o += 64
+    return W1, b1, W2, b2, w3, p[o]
+
+
+def spai_jacobi_params():
+    """Parameters whose network outputs g = [p == q] exactly, i.e. M = D^-1."""
+    p = np.zeros(SPAI_NPARAM)
+    W1, b1, W2, b2, w3, _ = spai_unpack(p)
+    W1[0, 2] = 1.0
+    W2[0, 0] = 1.0
+    w3[0] = 1.0
+    return p
+
+
+def spai_features(A):
+    rp, ci, va = _csr(A)
+    n = len(rp) - 1
+    f = np.zeros((len(ci), 8))
+    _L().orc_spai_features(n, rp, ci, va, f)
+    return f
+
+
+def spai_forward(feat, params):
+    feat = np.ascontiguousarray(feat, np.float64)
+    g = np.zeros(feat.shape[0])
+    _L().orc_spai_forward(feat.shape[0], feat, np.ascontiguousarray(params, np.float64), g)
+    return g
+
+
+def spai_values(A, params):
+    rp, ci, va = _csr(A)
+    m = np.zeros(len(ci))
+    _L().orc_spai_values(len(rp) - 1, rp, ci, va, np.ascontiguousarray(params, np.float64), m)
+    return m
+
+
+def spai_loss_grad_m(A, mvals, Z, grad=True):
+    """(loss, dL/dm) for M's values on A's pattern; Z is (P, n)."""
+    rp, ci, va = _csr(A)
+    n = len(rp) - 1
+    Z = np.ascontiguousarray(Z, np.float64).reshape(-1, n)
+    g = np.zeros(len(ci)) if grad else None
+    loss = _L().orc_spai_loss_grad_m(n, rp, ci, va, np.ascontiguousarray(mvals, np.float64),
+                                     Z.shape[0], Z, _ptr(g))
+    return loss, g
+
+
+def spai_loss_grad(A, params, Z, grad=True):
+    """(loss, dL/dparams, dL/dm) of the learned preconditioner; Z is (P, n)."""
+    rp, ci, va = _csr(A)
+    n = len(rp) - 1
+    Z = np.ascontiguousarray(Z, np.float64).reshape(-1, n)
+    gp = np.zeros(SPAI_NPARAM) if grad else None
+    gm = np.zeros(len(ci)) if grad else None
+    loss = _L().orc_spai_loss_grad(n, rp, ci, va, np.ascontiguousarray(params, np.float64),
+                                   Z.shape[0], Z, _ptr(gp), _ptr(gm))
+    return loss, gp, gm

@@ -309,18 +309,26 @@ gmres_status enqueue_step(gmres_handle *h, GridCtx<T, VT> &c, int col, gmres_ort
         const int TR = cgs_choose_tr<VT>(ncols);
         const size_t sm = cgs_smem_bytes<T, VT>(ncols, TR);
         const long long spin = h->opts.spin_limit > 0 ? h->opts.spin_limit : (1LL << 26);
-        static bool attr_set = false;
-        if (!attr_set) {
+        // dynamic shared memory may use the opt-in limit minus the kernel's
+        // static shared memory
+        static int dyn_max = 0;
+        if (dyn_max == 0) {
             int optin = 0;
             CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
-            CK(cudaFuncSetAttribute(k_cgs_tile<T, VT, 0>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
-            CK(cudaFuncSetAttribute(k_cgs_tile<T, VT, 1>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
-            CK(cudaFuncSetAttribute(k_cgs_tile<T, VT, 2>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
-            attr_set = true;
+            void (*fns[3])(GridCtx<T, VT>, int, int, long long) = {
+                k_cgs_tile<T, VT, 0>, k_cgs_tile<T, VT, 1>, k_cgs_tile<T, VT, 2>};
+            int lim = optin;
+            for (auto fn : fns) {
+                cudaFuncAttributes fa;
+                CK(cudaFuncGetAttributes(&fa, fn));
+                lim = std::min(lim, optin - (int)fa.sharedSizeBytes);
+            }
+            for (auto fn : fns)
+                CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+            dyn_max = lim;
         }
+        if ((int64_t)sm > dyn_max)
+            return GMRES_ERR_ARG;
         dim3 gt(h->nsm);
         k_cgs_tile<T, VT, 0><<<gt, CGS_THREADS, sm, h->stream>>>(c, ncols, TR, spin);
         k_cgs_tile<T, VT, 1><<<gt, CGS_THREADS, sm, h->stream>>>(c, ncols, TR, spin);

@@ -238,6 +238,8 @@ WORKLOADS = {
                            prec="mixed"),
     "convdiff3d_24": dict(kind="3d", N=24, eps=(0.1, 0.1, 0.1), m=100, ortho="cgsr",
                           prec="mixed"),
+    "convdiff3d_96": dict(kind="3d", N=96, eps=(0.1, 0.1, 0.1), m=100, ortho="cgsr",
+                          prec="mixed"),
     "powerlaw_2m": dict(kind="powerlaw", n=2_000_000, m=50, ortho="mgs", prec="mixed_bf16"),
     "powerlaw_20k": dict(kind="powerlaw", n=20_000, m=50, ortho="mgs", prec="mixed_bf16"),
     "aniso3d_128": dict(kind="3d", N=128, eps=(0.1, 1.0, 10.0), m=50, ortho="cgsr",

@@ -372,10 +372,132 @@ def pin_basis_rounding():
     assert np.array_equal(f32, np.float32([1.0 + 2.0 ** -30, 0.1]).astype(np.float64))
 
 
+# ---------------------------------------------------------------------------
+# learned SpAI preconditioner (loss, gradients, special cases)
+# ---------------------------------------------------------------------------
+
+def _spai_case(seed=0, P=3):
+    A = I.convdiff3d(3, eps=(0.1, 1.0, 10.0), seed=seed)  # n = 27, anisotropic
+    n = len(A[0]) - 1
+    rng = np.random.default_rng(seed)
+    Z = rng.standard_normal((P, n))
+    params = rng.standard_normal(O.SPAI_NPARAM) * 0.3
+    return A, n, Z, params
+
+
+def pin_spai_grad_m_fd():
+    """dL/dm against central finite differences (L is quadratic in m, so the
+    differences are exact up to rounding)."""
+    A, n, Z, params = _spai_case(1)
+    m = O.spai_values(A, params)
+    _, g = O.spai_loss_grad_m(A, m, Z)
+    rng = np.random.default_rng(2)
+    for k in rng.choice(len(m), 25, replace=False):
+        h = 1e-4
+        mp = m.copy(); mp[k] += h
+        mm = m.copy(); mm[k] -= h
+        fd = (O.spai_loss_grad_m(A, mp, Z, grad=False)[0]
+              - O.spai_loss_grad_m(A, mm, Z, grad=False)[0]) / (2 * h)
+        assert abs(fd - g[k]) <= 1e-7 * max(1.0, abs(g[k])) * 10, (k, fd, g[k])
+
+
+def pin_spai_grad_params_fd():
+    """dL/dparams (chain rule through the MLP and m = g / a_pp) against
+    central finite differences, relative 1e-6, on entries of every layer."""
+    A, n, Z, params = _spai_case(3)
+    _, gp, _ = O.spai_loss_grad(A, params, Z)
+    rng = np.random.default_rng(4)
+    idx = list(rng.choice(512, 8, replace=False)) + list(512 + rng.choice(64, 4, replace=False))
+    idx += list(576 + rng.choice(4096, 10, replace=False)) + list(4672 + rng.choice(64, 4, replace=False))
+    idx += list(4736 + rng.choice(64, 6, replace=False)) + [4800]
+    for k in idx:
+        h = 1e-6 * max(1.0, abs(params[k]))
+        pp = params.copy(); pp[k] += h
+        pm = params.copy(); pm[k] -= h
+        fd = (O.spai_loss_grad(A, pp, Z, grad=False)[0]
+              - O.spai_loss_grad(A, pm, Z, grad=False)[0]) / (2 * h)
+        assert abs(fd - gp[k]) <= 1e-6 * max(abs(gp[k]), 1e-3 * np.abs(gp).max()), (k, fd, gp[k])
+
+
+def pin_spai_special_cases():
+    """Jacobi parameters give M = D^-1 exactly; zero parameters give M = 0
+    and L = ||Z||^2 / (2 P n); the loss scales with the square of the probes."""
+    A, n, Z, params = _spai_case(5)
+    rp, ci, va = A
+    m = O.spai_values(A, O.spai_jacobi_params())
+    rows = np.repeat(np.arange(n), np.diff(rp))
+    diag = va[rows == ci]
+    assert np.array_equal(m[rows == ci], 1.0 / diag)
+    assert np.all(m[rows != ci] == 0.0)
+    l0, _, _ = O.spai_loss_grad(A, np.zeros(O.SPAI_NPARAM), Z)
+    assert abs(l0 - 0.5 * np.sum(Z * Z) / (Z.shape[0] * n)) <= 1e-15 * l0
+    l1, _, _ = O.spai_loss_grad(A, params, Z, grad=False)
+    l3, _, _ = O.spai_loss_grad(A, params, 3.0 * Z, grad=False)
+    assert abs(l3 - 9.0 * l1) <= 1e-12 * l3
+
+
+def pin_spai_optimum():
+    """With the identity as probes, L = ||A M - I||_F^2 / (2 n^2).  The exact
+    on-pattern optimum (column-wise least squares, numpy lstsq) is a lower
+    bound for every parameter vector, and dL/dm vanishes there."""
+    A, n, _, params = _spai_case(6)
+    rp, ci, va = A
+    D = I.csr_to_dense(A)
+    Z = np.eye(n)
+    mstar = np.zeros(len(ci))
+    rows = np.repeat(np.arange(n), np.diff(rp))
+    for q in range(n):
+        ks = np.nonzero(ci == q)[0]          # entries of column q of M on A's pattern
+        pr = rows[ks]                        # their row indices
+        e = np.zeros(n); e[q] = 1.0
+        sol, *_ = np.linalg.lstsq(D[:, pr], e, rcond=None)
+        mstar[ks] = sol
+    lstar, g = O.spai_loss_grad_m(A, mstar, Z)
+    fstar = np.sum((D @ I.csr_to_dense((rp, ci, mstar)) - np.eye(n)) ** 2)
+    assert abs(lstar - fstar / (2 * n * n)) <= 1e-12 * fstar
+    assert np.abs(g).max() <= 1e-12
+    for prm in (params, O.spai_jacobi_params(), np.zeros(O.SPAI_NPARAM)):
+        l, _, _ = O.spai_loss_grad(A, prm, Z, grad=False)
+        assert l >= lstar * (1 - 1e-12)
+
+
+def pin_spai_feature_invariants():
+    """Feature invariants: on the diagonal f0 = f1 = f2 = 1 and f7 = 0; off
+    it f2 = 0 and f7 = sign(q - p); f3, f4 >= 1 with the diagonal part of the
+    row/column weight; f6 = sign(a)."""
+    A = I.powerlaw_random(60, seed=8)
+    rp, ci, va = A
+    n = len(rp) - 1
+    F = O.spai_features(A)
+    rows = np.repeat(np.arange(n), np.diff(rp))
+    d = rows == ci
+    assert np.all(F[d, 0] == 1) and np.all(F[d, 1] == 1) and np.all(F[d, 2] == 1)
+    assert np.all(F[d, 7] == 0) and np.all(F[~d, 2] == 0)
+    assert np.array_equal(F[~d, 7], np.sign(ci[~d] - rows[~d]))
+    assert np.all(F[:, 3] >= 1 - 1e-15) and np.all(F[:, 4] >= 1 - 1e-15)
+    assert np.array_equal(F[:, 6], np.sign(va))
+    assert np.allclose(F[:, 5], np.diff(rp)[rows] / 8.0)
+    # transpose relations: entry (q, p) of A^T sees the column weight of
+    # (p, q) as its row weight, the inverse diagonal ratio and the flipped
+    # direction
+    AT = I.dense_to_csr(I.csr_to_dense(A).T)
+    FT = O.spai_features(AT)
+    trp, tci, _ = AT
+    trows = np.repeat(np.arange(n), np.diff(trp))
+    pos = {(int(r), int(c)): k for k, (r, c) in enumerate(zip(trows, tci))}
+    for k in range(len(ci)):
+        kt = pos[(int(ci[k]), int(rows[k]))]
+        assert abs(FT[kt, 3] - F[k, 4]) <= 1e-14 * F[k, 4]
+        assert abs(FT[kt, 1] * F[k, 1] - 1.0) <= 1e-14
+        assert FT[kt, 7] == -F[k, 7]
+
+
 ALL_PINS = [
     pin_lu_fp64, pin_exact_convergence, pin_identity, pin_diag_distinct, pin_cyclic_shift,
     pin_hand_2x2, pin_arnoldi_relation, pin_orthonormality, pin_mgs_equals_cgsr,
     pin_givens_least_squares, pin_arnoldi_residual_is_true_residual, pin_tau_restart,
     pin_mixed_reaches_double, pin_negative_control, pin_monotone_restarts, pin_repeat_first,
     pin_spmv_and_residual, pin_basis_rounding,
+    pin_spai_grad_m_fd, pin_spai_grad_params_fd, pin_spai_special_cases, pin_spai_optimum,
+    pin_spai_feature_invariants,
 ]

@@ -61,6 +61,14 @@ MUTATIONS = [
      "binary16 scale"),
     ("gmres_oracle.c", "return (double)(float)v;\n", "return v;\n",
      "binary32 basis not rounded"),
+    ("spai_oracle.c", "atr[colind[k]] += vals[k] * r[i];", "atr[i] += vals[k] * r[colind[k]];",
+     "A instead of A^T in the preconditioner gradient"),
+    ("spai_oracle.c", "d2[o] = z2[o] > 0 ? dgk * params[P_W3 + o] : 0;",
+     "d2[o] = dgk * params[P_W3 + o];", "missing ReLU derivative"),
+    ("spai_oracle.c", "const double dgk = gm[k] / dg[p];", "const double dgk = gm[k];",
+     "chain rule through m = g / a_pp dropped"),
+    ("spai_oracle.c", "f[4] = cs[q] / fabs(d[q]);", "f[4] = rs[q] / fabs(d[q]);",
+     "row weight used as column weight"),
 ]
 
 
