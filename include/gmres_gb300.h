@@ -144,6 +144,11 @@ gmres_status gmres_create(gmres_t *out, int32_t n, const int32_t *rowptr, const 
 /* Release every device buffer of the handle.  NULL is ignored. */
 void gmres_destroy(gmres_t h);
 
+/* Replace A's values (same pattern; nnz binary64 values, host or device).
+ * Drops the learned preconditioner and cached derived data of the old values.
+ * Errors: GMRES_ERR_ARG, GMRES_ERR_NONFINITE (host values), GMRES_ERR_CUDA. */
+gmres_status gmres_set_values(gmres_t h, const double *vals);
+
 /* Change the stream used by later calls. */
 gmres_status gmres_set_stream(gmres_t h, void *stream);
 
@@ -192,6 +197,52 @@ gmres_status gmres_arnoldi(gmres_t h, const double *r0, int32_t m, int32_t kmax,
  * and binary64 and keep the fastest for later solves (the tile autotuner).
  * lanes32 / lanes64 (may be NULL) receive the choices. */
 gmres_status gmres_autotune(gmres_t h, int32_t *lanes32, int32_t *lanes64);
+
+/* ---------------------------------------------------------------------------
+ * Learned sparse-approximate-inverse right preconditioner (the paper has no
+ * counterpart; it preconditions with ILU(0) on the left, Sec. 4).  M has A's
+ * sparsity pattern; m_pq = g_pq / a_pp where g = MLP(features of (p, q)), an
+ * 8 -> 64 -> 64 -> 1 ReLU network with binary32 parameters laid out as
+ * W1[64][8], b1[64], W2[64][64], b2[64], w3[64], b3 (GMRES_SPAI_NPARAM values).
+ * Features (a zero diagonal counts as 1): a_pq/a_pp, a_qq/a_pp, [p==q],
+ * sum_k|a_pk|/|a_pp|, sum_k|a_kq|/|a_qq|, nnz(row p)/8, sign(a_pq), sign(q-p).
+ * Training minimises L = 1/(2 P n) sum_p ||A M z_p - z_p||^2 over probes z_p.
+ * ------------------------------------------------------------------------- */
+#define GMRES_SPAI_NPARAM 4801
+
+/* The 8 features per nonzero, feature-major (feat[f * nnz + k]); host or
+ * device buffer of 8 * nnz binary32 values (NULL only computes and caches). */
+gmres_status gmres_spai_features(gmres_t h, float *feat);
+
+/* Loss and gradients for the parameters `params` (host or device) and the P
+ * probe vectors Z (device, n x P column-major, binary32): *loss (host, may be
+ * NULL), grad_params (device, GMRES_SPAI_NPARAM, may be NULL) and dL/dm on
+ * A's pattern (device, nnz, may be NULL). */
+gmres_status gmres_spai_loss_grad(gmres_t h, const float *params, int32_t nprobe, const float *Z,
+                                  double *loss, float *grad_params, float *grad_m);
+
+/* One Adam step (Kingma & Ba; beta1 0.9, beta2 0.999, eps 1e-8) on device
+ * arrays params, adam_m, adam_v (GMRES_SPAI_NPARAM each) with gradient grad;
+ * step >= 1 is the 1-based step count for the bias corrections. */
+gmres_status gmres_spai_adam(gmres_t h, float *params, float *adam_m, float *adam_v,
+                             const float *grad, int32_t step, float lr);
+
+/* One training step on this handle's matrix: nprobe Rademacher probes drawn
+ * on the device from `seed` (a counter-based mix of seed, probe and row), plus
+ * nzx extra probes Zx (device, n x nzx, e.g. residuals a solve produced), then
+ * loss, gradient and one Adam step on the device arrays.  *loss (host, may be
+ * NULL) is the loss before the step. */
+gmres_status gmres_spai_train_step(gmres_t h, float *params, float *adam_m, float *adam_v,
+                                   int32_t step, int32_t nprobe, uint64_t seed, const float *Zx,
+                                   int32_t nzx, float lr, double *loss);
+
+/* Inference: M's values from `params` (host or device) on A's pattern; the
+ * solver uses them as right preconditioner when opts.precond = 1 (grid path;
+ * w = A M v_j, x += M V_j y).  gmres_spai_values copies them out (nnz
+ * binary64, host or device); gmres_spai_clear drops them. */
+gmres_status gmres_spai_set(gmres_t h, const float *params);
+gmres_status gmres_spai_values(gmres_t h, double *mvals);
+gmres_status gmres_spai_clear(gmres_t h);
 
 /* ---------------------------------------------------------------------------
  * Batched solver: many independent systems of uneven size in one persistent

@@ -288,6 +288,10 @@ def _bind_spai(L):
     L.orc_spai_loss_grad.argtypes = [ctypes.c_int32, _i32p, _i32p, _f64p, _f64p, ctypes.c_int32,
                                      _f64p, vp, vp]
     L.orc_spai_loss_grad.restype = ctypes.c_double
+    L.orc_adam_step.argtypes = [ctypes.c_int32, _f64p, _f64p, _f64p, _f64p, ctypes.c_int32,
+                                ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                ctypes.c_double]
+    L.orc_adam_step.restype = None
 
 
 SPAI_NF, SPAI_NH = 8, 64
@@ -359,3 +363,12 @@ def spai_loss_grad(A, params, Z, grad=True):
     loss = _L().orc_spai_loss_grad(n, rp, ci, va, np.ascontiguousarray(params, np.float64),
                                    Z.shape[0], Z, _ptr(gp), _ptr(gm))
     return loss, gp, gm
+
+
+def adam_step(p, m, v, g, t, lr, b1=0.9, b2=0.999, eps=1e-8):
+    """One Adam step in binary64 on copies; returns (p, m, v)."""
+    p = np.array(p, dtype=np.float64)
+    m = np.array(m, dtype=np.float64)
+    v = np.array(v, dtype=np.float64)
+    _L().orc_adam_step(p.size, p, m, v, np.ascontiguousarray(g, np.float64), t, lr, b1, b2, eps)
+    return p, m, v

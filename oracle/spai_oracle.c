@@ -249,3 +249,17 @@ double orc_spai_loss_grad(int32_t n, const int32_t *rowptr, const int32_t *colin
     free(feat); free(m); free(gm); free(dg);
     return loss;
 }
+
+/* One Adam step (Kingma and Ba, 2015) in binary64:
+ * m = b1 m + (1 - b1) g, v = b2 v + (1 - b2) g^2,
+ * p -= lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps). */
+void orc_adam_step(int32_t np, double *p, double *m, double *v, const double *g, int32_t t,
+                   double lr, double b1, double b2, double eps)
+{
+    double c1 = 1.0 - pow(b1, t), c2 = 1.0 - pow(b2, t);
+    for (int32_t i = 0; i < np; ++i) {
+        m[i] = b1 * m[i] + (1.0 - b1) * g[i];
+        v[i] = b2 * v[i] + (1.0 - b2) * g[i] * g[i];
+        p[i] -= lr * (m[i] / c1) / (sqrt(v[i] / c2) + eps);
+    }
+}

@@ -21,96 +21,15 @@
 #include "block_solver.cuh"
 #include "cgs_tile.cuh"
 #include "grid_kernels.cuh"
+#include "handle.hpp"
 #include "host_util.hpp"
 
 using namespace gmres;
 using namespace gmres_host;
 
 namespace {
-
 constexpr int kThreads = 256;
-
-// Event pairs for per-class kernel timing (opts.profile).
-struct Timer {
-    bool on = false;
-    cudaStream_t st = nullptr;
-    std::vector<cudaEvent_t> pool;
-    struct Rec { int cls; cudaEvent_t a, b; };
-    std::vector<Rec> recs;
-    cudaEvent_t get() {
-        if (!pool.empty()) {
-            cudaEvent_t e = pool.back();
-            pool.pop_back();
-            return e;
-        }
-        cudaEvent_t e;
-        cudaEventCreate(&e);
-        return e;
-    }
-    cudaEvent_t begin() {
-        if (!on)
-            return nullptr;
-        cudaEvent_t a = get();
-        cudaEventRecord(a, st);
-        return a;
-    }
-    void end(int cls, cudaEvent_t a) {
-        if (!on)
-            return;
-        cudaEvent_t b = get();
-        cudaEventRecord(b, st);
-        recs.push_back({cls, a, b});
-    }
-    // after a stream synchronize
-    void harvest(double *ms) {
-        for (auto &r : recs) {
-            float t = 0;
-            if (cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess)
-                ms[r.cls] += t;
-            pool.push_back(r.a);
-            pool.push_back(r.b);
-        }
-        recs.clear();
-    }
-    void destroy() {
-        for (auto &r : recs) {
-            pool.push_back(r.a);
-            pool.push_back(r.b);
-        }
-        recs.clear();
-        for (auto e : pool)
-            cudaEventDestroy(e);
-        pool.clear();
-    }
-};
-
 }  // namespace
-
-struct gmres_handle {
-    int n = 0;
-    int64_t nnz = 0;
-    int64_t ldv = 0;
-    int device = 0;
-    int nsm = 0;
-    cudaStream_t stream = nullptr;
-    gmres_opts opts;
-    int lanes32 = 4, lanes64 = 4;
-    int grid = 0;          // blocks of the reduction kernels
-    int64_t chunk = 0;     // rows per block
-    // matrix
-    DevBuf rowptr, colind, vals64, vals32;
-    DevBuf trowptr, tcolind, tvals64;  // A^T (optional)
-    // workspace
-    DevBuf V, w, r, t, z, xb, bb;
-    DevBuf small;          // H, Hb, s, cs, sn, y, h1, h2
-    DevBuf part, part64, ctl;
-    DevBuf bsys, bres;     // block-solver descriptor / result
-    Ctl *hctl = nullptr;   // pinned copy of the control block
-    Timer timer;
-    // learned right preconditioner on A's pattern (binary64 / binary32 values)
-    DevBuf pvals64, pvals32;
-    int has_precond = 0;
-};
 
 namespace {
 
@@ -425,6 +344,7 @@ gmres_status solve_grid(gmres_handle *h, const double *b, double *x, int m, doub
     if (st != GMRES_OK)
         return st;
     int cycle_len = m;
+    int stall = 0;
     double prev_rn = h->hctl->rnorm;
     gmres_status result = GMRES_MAXITER;
     for (;;) {
@@ -500,7 +420,30 @@ gmres_status solve_grid(gmres_handle *h, const double *b, double *x, int m, doub
                 cycle_len = std::max(1, j);
         }
         const double rn = h->hctl->rnorm;
-        if (j == 0 || (h->hctl->breakdown && rn >= prev_rn && !h->hctl->converged)) {
+        const bool no_progress =
+            j == 0 || (h->hctl->breakdown && rn >= prev_rn && !h->hctl->converged);
+        if (c.pvals) {
+            // Stagnation fallback for the learned preconditioner: a cycle that
+            // produced non-finite values, made no progress, or two cycles in a
+            // row that cut the binary64 residual by less than 10 % switch the
+            // solve to unpreconditioned mixed GMRES (the residual decides).
+            stall = (rn > 0.9 * prev_rn) ? stall + 1 : 0;
+            if (h->opts.fallback && (h->hctl->nonfinite || no_progress || stall >= 2)) {
+                c.pvals = nullptr;
+                info->fell_back = 1;
+                stall = 0;
+                if (h->hctl->nonfinite) {
+                    CK(cudaMemsetAsync(h->ctl.p, 0, sizeof(Ctl), h->stream));
+                    CK(launch_residual(h, c, b, x, nullptr, 1));
+                    st = read_ctl(h);
+                    if (st != GMRES_OK)
+                        return st;
+                }
+                prev_rn = h->hctl->rnorm;
+                continue;
+            }
+        }
+        if (no_progress) {
             info->relres = rn / bnorm;
             result = GMRES_ERR_BREAKDOWN;
             break;
@@ -775,12 +718,40 @@ void gmres_destroy(gmres_t h) {
     for (DevBuf *b : {&h->rowptr, &h->colind, &h->vals64, &h->vals32, &h->trowptr, &h->tcolind,
                       &h->tvals64, &h->V, &h->w, &h->r, &h->t, &h->z, &h->xb, &h->bb, &h->small,
                       &h->part, &h->part64, &h->ctl, &h->bsys, &h->bres, &h->pvals64,
-                      &h->pvals32})
+                      &h->pvals32, &h->spai_feat, &h->spai_rowv, &h->tvals32, &h->spai_params,
+                      &h->spai_m, &h->spai_gm, &h->spai_H, &h->spai_vec, &h->spai_part,
+                      &h->spai_Z, &h->spai_grad})
         b->release();
     if (h->hctl)
         cudaFreeHost(h->hctl);
     h->timer.destroy();
     delete h;
+}
+
+gmres_status gmres_set_values(gmres_t h, const double *vals) {
+    if (!h || (h->nnz > 0 && !vals))
+        return GMRES_ERR_ARG;
+    if (h->nnz == 0)
+        return GMRES_OK;
+    const bool dev = is_device_ptr(vals);
+    if (!dev) {
+        for (int64_t k = 0; k < h->nnz; ++k)
+            if (!std::isfinite(vals[k]))
+                return GMRES_ERR_NONFINITE;
+    }
+    CK(cudaMemcpyAsync(h->vals64.p, vals, sizeof(double) * h->nnz,
+                       dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
+    k_cast_vals<<<h->nsm * 4, 256, 0, h->stream>>>(h->nnz, h->vals64.as<double>(),
+                                                    h->vals32.as<float>());
+    CKL();
+    CK(cudaStreamSynchronize(h->stream));
+    // derived data of the old values is stale
+    h->trowptr.release();
+    h->tcolind.release();
+    h->tvals64.release();
+    h->spai_feat_ok = 0;
+    h->has_precond = 0;
+    return GMRES_OK;
 }
 
 gmres_status gmres_set_stream(gmres_t h, void *stream) {

@@ -626,7 +626,7 @@ template <class T, class VT>
 __global__ void __launch_bounds__(256) k_update(GridCtx<T, VT> c, double *x, int to_t) {
     __shared__ T ys[MMAX];
     const int j = c.ctl->last_j;
-    if (j == 0)
+    if (j == 0 || c.ctl->nonfinite)
         return;
     for (int i = threadIdx.x; i < j; i += blockDim.x)
         ys[i] = c.y[i];
@@ -656,7 +656,7 @@ __global__ void __launch_bounds__(256) k_update(GridCtx<T, VT> c, double *x, int
 // x += (double) u for a full-length working vector u (after u = M t).
 template <class T>
 __global__ void __launch_bounds__(256) k_axpy_x(int n, const T *u, double *x, const Ctl *ctl) {
-    if (ctl->last_j == 0)
+    if (ctl->last_j == 0 || ctl->nonfinite)
         return;
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n;
          r += (int64_t)gridDim.x * blockDim.x)

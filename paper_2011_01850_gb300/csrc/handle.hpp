@@ -1,0 +1,103 @@
+// handle.hpp -- the gmres_handle structure shared by the library's
+// translation units (solver driver, learned preconditioner): device copies of
+// A, the workspace, the control block and the per-class event timer.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "common.cuh"
+#include "host_util.hpp"
+
+namespace gmres_host {
+
+// Event pairs for per-class kernel timing (opts.profile).
+struct Timer {
+    bool on = false;
+    cudaStream_t st = nullptr;
+    std::vector<cudaEvent_t> pool;
+    struct Rec { int cls; cudaEvent_t a, b; };
+    std::vector<Rec> recs;
+    cudaEvent_t get() {
+        if (!pool.empty()) {
+            cudaEvent_t e = pool.back();
+            pool.pop_back();
+            return e;
+        }
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        return e;
+    }
+    cudaEvent_t begin() {
+        if (!on)
+            return nullptr;
+        cudaEvent_t a = get();
+        cudaEventRecord(a, st);
+        return a;
+    }
+    void end(int cls, cudaEvent_t a) {
+        if (!on)
+            return;
+        cudaEvent_t b = get();
+        cudaEventRecord(b, st);
+        recs.push_back({cls, a, b});
+    }
+    // after a stream synchronize
+    void harvest(double *ms) {
+        for (auto &r : recs) {
+            float t = 0;
+            if (cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess)
+                ms[r.cls] += t;
+            pool.push_back(r.a);
+            pool.push_back(r.b);
+        }
+        recs.clear();
+    }
+    void destroy() {
+        for (auto &r : recs) {
+            pool.push_back(r.a);
+            pool.push_back(r.b);
+        }
+        recs.clear();
+        for (auto e : pool)
+            cudaEventDestroy(e);
+        pool.clear();
+    }
+};
+
+}  // namespace gmres_host
+
+struct gmres_handle {
+    using DevBuf = gmres_host::DevBuf;
+    using Timer = gmres_host::Timer;
+    int n = 0;
+    int64_t nnz = 0;
+    int64_t ldv = 0;
+    int device = 0;
+    int nsm = 0;
+    cudaStream_t stream = nullptr;
+    gmres_opts opts;
+    int lanes32 = 4, lanes64 = 4;
+    int grid = 0;          // blocks of the reduction kernels
+    int64_t chunk = 0;     // rows per block
+    // matrix
+    DevBuf rowptr, colind, vals64, vals32;
+    DevBuf trowptr, tcolind, tvals64;  // A^T (optional)
+    // workspace
+    DevBuf V, w, r, t, z, xb, bb;
+    DevBuf small;          // H, Hb, s, cs, sn, y, h1, h2
+    DevBuf part, part64, ctl;
+    DevBuf bsys, bres;     // block-solver descriptor / result
+    gmres::Ctl *hctl = nullptr;   // pinned copy of the control block
+    Timer timer;
+    // learned right preconditioner on A's pattern (binary64 / binary32 values)
+    DevBuf pvals64, pvals32;
+    int has_precond = 0;
+    // learned-preconditioner workspace: features (9 x nnz), per-row stats,
+    // binary32 A^T values, parameters, M, dL/dm, activations, vectors,
+    // partial sums, probes, gradient
+    DevBuf spai_feat, spai_rowv, tvals32, spai_params, spai_m, spai_gm, spai_H, spai_vec,
+        spai_part, spai_Z, spai_grad;
+    int spai_feat_ok = 0;
+};

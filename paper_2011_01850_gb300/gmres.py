@@ -106,6 +106,15 @@ SIGNATURES = {
     "gmres_batch_destroy": (None, [_vp]),
     "gmres_batch_solve": (_st, [_vp, _vp, _vp, _i32, _f64, _i32, _i32, _i32, _i32, _vp,
                                 ctypes.POINTER(Info)]),
+    "gmres_set_values": (_st, [_vp, _vp]),
+    "gmres_spai_features": (_st, [_vp, _vp]),
+    "gmres_spai_loss_grad": (_st, [_vp, _vp, _i32, _vp, ctypes.POINTER(_f64), _vp, _vp]),
+    "gmres_spai_adam": (_st, [_vp, _vp, _vp, _vp, _vp, _i32, ctypes.c_float]),
+    "gmres_spai_train_step": (_st, [_vp, _vp, _vp, _vp, _i32, _i32, ctypes.c_uint64, _vp, _i32,
+                                    ctypes.c_float, ctypes.POINTER(_f64)]),
+    "gmres_spai_set": (_st, [_vp, _vp]),
+    "gmres_spai_values": (_st, [_vp, _vp]),
+    "gmres_spai_clear": (_st, [_vp]),
     "gmres_status_str": (ctypes.c_char_p, [_st]),
     "gmres_version": (ctypes.c_char_p, []),
 }
@@ -259,6 +268,50 @@ def gmres_memory_bytes(h, m, prec):
     _check(lib().gmres_memory_bytes(h, int(m), int(prec), ctypes.byref(a), ctypes.byref(b)),
            "gmres_memory_bytes")
     return a.value, b.value
+
+
+SPAI_NPARAM = 4801
+
+
+def gmres_set_values(h, vals):
+    return _check(lib().gmres_set_values(h, _ptr(vals)), "gmres_set_values")
+
+
+def gmres_spai_features(h, feat=None):
+    return _check(lib().gmres_spai_features(h, _ptr(feat)), "gmres_spai_features")
+
+
+def gmres_spai_loss_grad(h, params, nprobe, Z, grad_params=None, grad_m=None):
+    loss = ctypes.c_double()
+    _check(lib().gmres_spai_loss_grad(h, _ptr(params), int(nprobe), _ptr(Z), ctypes.byref(loss),
+                                      _ptr(grad_params), _ptr(grad_m)), "gmres_spai_loss_grad")
+    return loss.value
+
+
+def gmres_spai_adam(h, params, adam_m, adam_v, grad, step, lr):
+    return _check(lib().gmres_spai_adam(h, _ptr(params), _ptr(adam_m), _ptr(adam_v), _ptr(grad),
+                                        int(step), float(lr)), "gmres_spai_adam")
+
+
+def gmres_spai_train_step(h, params, adam_m, adam_v, step, nprobe, seed, Zx=None, nzx=0, lr=1e-3):
+    loss = ctypes.c_double()
+    _check(lib().gmres_spai_train_step(h, _ptr(params), _ptr(adam_m), _ptr(adam_v), int(step),
+                                       int(nprobe), int(seed) & ((1 << 64) - 1), _ptr(Zx),
+                                       int(nzx), float(lr), ctypes.byref(loss)),
+           "gmres_spai_train_step")
+    return loss.value
+
+
+def gmres_spai_set(h, params):
+    return _check(lib().gmres_spai_set(h, _ptr(params)), "gmres_spai_set")
+
+
+def gmres_spai_values(h, mvals):
+    return _check(lib().gmres_spai_values(h, _ptr(mvals)), "gmres_spai_values")
+
+
+def gmres_spai_clear(h):
+    return _check(lib().gmres_spai_clear(h), "gmres_spai_clear")
 
 
 class BatchResult(ctypes.Structure):

@@ -492,6 +492,17 @@ def pin_spai_feature_invariants():
         assert FT[kt, 7] == -F[k, 7]
 
 
+def pin_adam_first_step():
+    """The first Adam step moves every parameter with a nonzero gradient by
+    lr * sign(g) (m/(1-b1) = g and sqrt(v/(1-b2)) = |g|, up to eps), and leaves
+    a zero-gradient parameter unchanged."""
+    p = np.array([1.0, 1.0, 1.0, -2.0])
+    g = np.array([1.0, -2.0, 0.0, 3e-3])
+    p1, m1, v1 = O.adam_step(p, np.zeros(4), np.zeros(4), g, 1, 0.1)
+    assert np.allclose(p1, [0.9, 1.1, 1.0, -2.1], rtol=0, atol=1e-6)
+    assert np.allclose(m1, 0.1 * g) and np.allclose(v1, 0.001 * g * g)
+
+
 ALL_PINS = [
     pin_lu_fp64, pin_exact_convergence, pin_identity, pin_diag_distinct, pin_cyclic_shift,
     pin_hand_2x2, pin_arnoldi_relation, pin_orthonormality, pin_mgs_equals_cgsr,
@@ -499,5 +510,5 @@ ALL_PINS = [
     pin_mixed_reaches_double, pin_negative_control, pin_monotone_restarts, pin_repeat_first,
     pin_spmv_and_residual, pin_basis_rounding,
     pin_spai_grad_m_fd, pin_spai_grad_params_fd, pin_spai_special_cases, pin_spai_optimum,
-    pin_spai_feature_invariants,
+    pin_spai_feature_invariants, pin_adam_first_step,
 ]
