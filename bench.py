@@ -42,7 +42,8 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default=WORKLOAD)
-    p.add_argument("--fp64-steps", type=int, default=1)
+    p.add_argument("--compare-steps", "--fp64-steps", dest="compare_steps", type=int, default=1)
+    p.add_argument("--spai-params", default=None)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     return p.parse_args()
@@ -130,6 +131,20 @@ def make_workload(name):
     return A, b, spec
 
 
+# Comparisons timed beside the headline mode of each workload:
+# (label, precision, ortho, preconditioner)
+COMPARE = {
+    "convdiff3d_160": [("fp64", "fp64", "cgsr", None)],
+    "convdiff3d_96": [("fp64", "fp64", "cgsr", None)],
+    "convdiff2d_64": [("mixed_mgs", "mixed", "mgs", None), ("fp64_grid", "fp64", "mgs", "grid")],
+    "powerlaw_2m": [("mixed_fp16", "mixed_fp16", "mgs", None), ("mixed_fp32", "mixed", "mgs", None),
+                    ("fp64", "fp64", "mgs", None)],
+    "aniso3d_128": [("unpreconditioned", "mixed", "cgsr", "none"),
+                    ("jacobi", "mixed", "cgsr", "jacobi"), ("fp64", "fp64", "cgsr", "none")],
+}
+SPAI_PARAMS = os.path.join(ROOT, "paper_2011_01850_gb300", "data", "spai_aniso64.npy")
+
+
 def bench_ours(args):
     import torch
 
@@ -140,6 +155,8 @@ def bench_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
+    if args.workload == "batched2048":
+        return bench_batched(args, world, rank, local)
     A, b, spec = make_workload(args.workload)
     n = len(A[0]) - 1
     nnz = len(A[1])
@@ -148,12 +165,31 @@ def bench_ours(args):
     solver = G.Solver(A, stream=stream)
     lanes32, lanes64 = G.gmres_autotune(solver.h)
     solver.set_opts(profile=1)
+    learned = spec.get("precond") == "learned"
+    spai_params = None
+    if learned:
+        from paper_2011_01850_gb300 import spai as S
+        spai_params = np.load(args.spai_params).astype(np.float32)
+        jac = S.jacobi_params()
     db = torch.tensor(b, device="cuda", dtype=torch.float64)
     dx = torch.zeros(n, device="cuda", dtype=torch.float64)
 
-    def step(p, collect):
+    def set_pre(kind):
+        o = G.gmres_get_opts(solver.h)
+        o.path = G.PATH_AUTO
+        if kind in (None, "none"):
+            o.precond = 0
+        elif kind == "grid":
+            o.precond = 0
+            o.path = G.PATH_GRID
+        else:
+            G.gmres_spai_set(solver.h, spai_params if kind == "learned" else jac)
+            o.precond = 1
+        G.gmres_set_opts(solver.h, o)
+
+    def step(p, o_, collect):
         dx.zero_()
-        st, info = G.gmres_solve(solver.h, db, dx, m, 1e-10, G.ORTHOS[ortho], G.PRECISIONS[p],
+        st, info = G.gmres_solve(solver.h, db, dx, m, 1e-10, G.ORTHOS[o_], G.PRECISIONS[p],
                                  100000)
         if st != G.OK:
             raise RuntimeError("solve did not converge: %s %r" % (G.status_str(st),
@@ -166,11 +202,11 @@ def bench_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    # warm-up
+    main_pre = "learned" if learned else None
+    set_pre(main_pre)
     scratch = []
     for _ in range(args.warmup):
-        step(prec, scratch)
-    # timed region: K full solves, CUDA events on the library's stream
+        step(prec, ortho, scratch)
     infos = []
     clocks = ClockSampler(local)
     clocks.start()
@@ -179,32 +215,16 @@ def bench_ours(args):
     ev1 = torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
     for _ in range(args.steps):
-        step(prec, infos)
+        step(prec, ortho, infos)
     ev1.record(stream)
     barrier()
     clk = clocks.stop()
-    ms_total = ev0.elapsed_time(ev1)
-    ms_step = ms_total / args.steps
+    ms_step = ev0.elapsed_time(ev1) / args.steps
     if world > 1:
         import torch.distributed as dist
         t = torch.tensor([ms_step], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms_step = float(t.item())
-
-    # FP64 GMRES on the same system (the comparison the metric names)
-    fp64 = []
-    fp64_ms = None
-    if args.fp64_steps > 0:
-        step("fp64", scratch)  # warm the FP64 workspace
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(args.fp64_steps):
-            step("fp64", fp64)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        fp64_ms = e0.elapsed_time(e1) / args.fp64_steps
 
     # end to end through the public API with host buffers (H2D of b and x0,
     # D2H of x inside every step)
@@ -224,11 +244,31 @@ def bench_ours(args):
         e2e = {"value": round(e2e_ms, 3), "unit": "ms", "h2d_bytes_per_step": 16 * n,
                "d2h_bytes_per_step": 8 * n}
 
-    # per-class kernel statistics over the timed region
+    # comparisons on the same system
+    compare = {}
+    if args.compare_steps > 0:
+        for label, p_, o_, pre in COMPARE.get(args.workload, []):
+            set_pre(pre)
+            step(p_, o_, scratch)
+            torch.cuda.synchronize()
+            got = []
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(args.compare_steps):
+                step(p_, o_, got)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            cms = e0.elapsed_time(e1) / args.compare_steps
+            compare[label] = {"ms": round(cms, 3), "iters": got[0]["iters"],
+                              "restarts": got[0]["restarts"],
+                              "speedup_of_headline": round(cms / ms_step, 3)}
+        set_pre(main_pre)
+
     def agg(key, cls):
         return sum(i[key][cls] for i in infos)
 
-    classes = ["residual", "spmv", "ortho", "normalize", "update"]
+    classes = ["residual", "spmv", "ortho", "normalize", "update", "precond", "block"]
     kms = {c: agg("kernel_ms", c) for c in classes}
     kbytes = {c: agg("kernel_bytes", c) for c in classes}
     klaunch = {c: agg("kernel_launches", c) for c in classes}
@@ -240,7 +280,10 @@ def bench_ours(args):
     tot_kms = sum(kms.values())
     iters = infos[0]["iters"]
     restarts = infos[0]["restarts"]
-
+    kernel_names = {"ortho": "CGSR passes (k_cgs_tile x3)" if ortho == "cgsr"
+                    else "MGS chain (k_mgs_step x j, k_mgs_last)",
+                    "block": "single-block solver (k_block_solve)",
+                    "spmv": "SpMV (k_spmv_step)", "residual": "binary64 residual (k_residual)"}
     out = {
         "metric": "time-to-1e-10 residual and HBM GB/s: mixed vs FP64 GMRES(m), one GB300",
         "value": round(ms_step, 3),
@@ -255,25 +298,23 @@ def bench_ours(args):
         "dtype": "f32" if prec != "fp64" else "f64",
         "data": "synthetic",
         "config": {
-            "workload": args.workload,
-            "matrix": "3-D 7-point upwind convection-diffusion 160^3, v~U[-1,1]^3 per node",
+            "workload": args.workload, "description": spec.get("desc"),
             "n": n, "nnz": nnz, "m": m, "ortho": ortho, "precision": prec, "tol": 1e-10,
+            "precond": "learned SpAI" if learned else None,
             "rhs": "b = A 1 + N(0, sigma^2), sigma = 1e-3, x0 = 0", "seed": SEED,
-            "l2": "inputs larger than L2 (A alone is %.0f MB)" % (nnz * 12 / 1e6),
+            "l2": "inputs larger than L2" if nnz * 12 > 129e6
+                  else "inputs L2-resident (no flush; small-system workload)",
             "parallelism": "replicas" if world > 1 else "single GPU",
             "spmv_lanes": {"f32": lanes32, "f64": lanes64},
         },
         "iters": iters, "restarts": restarts,
-        "fp64": ({"ms": round(fp64_ms, 3), "iters": fp64[0]["iters"],
-                  "restarts": fp64[0]["restarts"]} if fp64 else None),
-        "speedup_vs_fp64": round(fp64_ms / ms_step, 3) if fp64 else None,
+        "compare": compare,
         "solve_gbs": round(tot_bytes / (tot_kms * 1e-3) / 1e9, 1) if tot_kms else None,
         "kernel_gbs": {c: round(kbytes[c] / (kms[c] * 1e-3) / 1e9, 1) if kms[c] else None
-                       for c in classes},
-        "kernel_share": {c: round(kms[c] / tot_kms, 4) if tot_kms else None for c in classes},
+                       for c in classes if kms[c] > 0},
+        "kernel_share": {c: round(kms[c] / tot_kms, 4) for c in classes if kms[c] > 0},
         "roofline": {
-            "bound": "hbm", "kernel": "%s (%s)" % (dom, {"ortho": "CGSR passes" if ortho == "cgsr"
-                                                         else "MGS chain"}.get(dom, dom)),
+            "bound": "hbm", "kernel": kernel_names.get(dom, dom),
             "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "peak_kind": peak_kind, "traffic": None,
             "launches": int(klaunch[dom]),
@@ -284,6 +325,8 @@ def bench_ours(args):
         "e2e": e2e,
         "relres": infos[0]["relres"],
     }
+    if "fp64" in compare:
+        out["speedup_vs_fp64"] = compare["fp64"]["speedup_of_headline"]
     solver.close()
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(A, b, spec, iters, restarts, m)
@@ -292,6 +335,101 @@ def bench_ours(args):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def bench_batched(args, world, rank, local):
+    """2048 independent 2-D systems (n log-uniform in [500, 50000]) solved by
+    one persistent launch; a step is one batched solve of all systems."""
+    import torch
+
+    from paper_2011_01850_gb300 import gmres as G
+    from paper_2011_01850_gb300 import inputs as I
+
+    systems = I.batched_convdiff2d(count=2048, nmin=500, nmax=50000, seed=SEED)
+    sys_ptr, rp, ci, va, b = G.pack_batch(systems)
+    nsys = len(systems)
+    stream = torch.cuda.current_stream()
+    h = G.gmres_batch_create(nsys, sys_ptr, rp, ci, va, stream=stream)
+    db = torch.tensor(b, device="cuda", dtype=torch.float64)
+    dx = torch.zeros(len(b), device="cuda", dtype=torch.float64)
+    m = 30
+
+    def step(prec, collect):
+        dx.zero_()
+        st, res, info = G.gmres_batch_solve(h, db, dx, m, 1e-10, G.ORTHO_MGS,
+                                            G.PRECISIONS[prec], 100000, nsys=nsys)
+        if st != G.OK:
+            raise RuntimeError("batched solve did not converge: %d" % st)
+        collect.append((info.kernel_ms[G.K_BLOCK], info.kernel_bytes[G.K_BLOCK], info.iters,
+                        info.restarts, res))
+
+    scratch = []
+    for _ in range(args.warmup):
+        step("mixed", scratch)
+    infos = []
+    clocks = ClockSampler(local)
+    clocks.start()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step("mixed", infos)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms_step = ev0.elapsed_time(ev1) / args.steps
+    compare = {}
+    if args.compare_steps > 0:
+        got = []
+        step("fp64", scratch)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.compare_steps):
+            step("fp64", got)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        cms = e0.elapsed_time(e1) / args.compare_steps
+        compare["fp64"] = {"ms": round(cms, 3), "iters": got[0][2],
+                           "speedup_of_headline": round(cms / ms_step, 3)}
+    e2e = None
+    if not args.no_e2e:
+        xh = np.zeros(len(b))
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            xh[:] = 0
+            st, res, info = G.gmres_batch_solve(h, b, xh, m, 1e-10, G.ORTHO_MGS, G.MIXED,
+                                                100000, nsys=nsys)
+            assert st == G.OK
+        e2e = {"value": round((time.perf_counter() - t0) * 1e3 / args.steps, 3), "unit": "ms",
+               "h2d_bytes_per_step": 16 * len(b), "d2h_bytes_per_step": 8 * len(b)}
+    G.gmres_batch_destroy(h)
+    kms = sum(i[0] for i in infos)
+    kb = sum(i[1] for i in infos)
+    peak, peak_kind = load_peaks()
+    ach = kb / (kms * 1e-3) / 1e9
+    out = {
+        "metric": "time-to-1e-10 residual and HBM GB/s: mixed vs FP64 GMRES(m), one GB300",
+        "value": round(ms_step, 3), "unit": "ms", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_step, 3), "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "batched2048", "systems": nsys, "rows": int(len(b)),
+                   "nnz": int(len(ci)), "m": m, "ortho": "mgs", "precision": "mixed",
+                   "tol": 1e-10, "launch": "one persistent launch per batched solve",
+                   "l2": "inputs larger than L2"},
+        "systems_per_s": round(nsys / (ms_step * 1e-3), 1),
+        "iters_total": infos[0][2], "restarts_total": infos[0][3],
+        "compare": compare,
+        "roofline": {"bound": "hbm", "kernel": "batched single-block solver (k_block_solve)",
+                     "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(ach / peak, 4), "peak_kind": peak_kind, "traffic": None,
+                     "launches": args.steps, "bytes_per_launch": kb / args.steps},
+        "gpu_launches": args.steps, "clocks": clk, "e2e": e2e,
+    }
+    if rank == 0:
+        print(json.dumps(out), flush=True)
 
 
 def oracle_sample(A, b, spec, ks=(2, 8, 16)):
@@ -308,9 +446,14 @@ def oracle_sample(A, b, spec, ks=(2, 8, 16)):
     O.residual_norm(A, b, np.zeros_like(b))
     t_res = time.perf_counter() - t0
     ts = []
+    # a preconditioned workload costs one more SpMV per step: time the oracle
+    # with an M on A's pattern computed by the oracle itself (Jacobi values)
+    M = None
+    if spec.get("precond"):
+        M = (A[0], A[1], O.spai_values(A, O.spai_jacobi_params()))
     for k in ks:
         t0 = time.perf_counter()
-        O.arnoldi_cycle(A, b, m, ortho=ortho, prec=prec, kmax=k, export_basis=False)
+        O.arnoldi_cycle(A, b, m, ortho=ortho, prec=prec, kmax=k, export_basis=False, M=M)
         ts.append(time.perf_counter() - t0)
     M = np.array([[1.0, k, k * (k + 1) / 2.0] for k in ks])
     c, a, bco = np.linalg.lstsq(M, np.array(ts), rcond=None)[0]
@@ -379,6 +522,8 @@ def bench_reference(args):
 
 def main():
     args = parse()
+    if args.spai_params is None:
+        args.spai_params = SPAI_PARAMS
     if args.impl == "reference":
         bench_reference(args)
     else:

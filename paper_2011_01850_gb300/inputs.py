@@ -233,18 +233,23 @@ def batched_convdiff2d(count=2048, nmin=500, nmax=50000, pe_range=(1.0, 50.0), s
 # Named workloads.  "full" entries are the benchmarked sizes, "small" entries
 # are the same families at sizes the CPU oracle finishes in seconds.
 WORKLOADS = {
-    "convdiff2d_64": dict(kind="2d", N=64, pe=10.0, m=50, ortho="mgs", prec="fp64"),
+    "convdiff2d_64": dict(kind="2d", N=64, pe=10.0, m=50, ortho="mgs", prec="fp64",
+                          desc="2-D 5-point upwind convection-diffusion 64^2, Pe 10"),
     "convdiff3d_160": dict(kind="3d", N=160, eps=(0.1, 0.1, 0.1), m=100, ortho="cgsr",
-                           prec="mixed"),
+                           prec="mixed",
+                           desc="3-D 7-point upwind convection-diffusion 160^3, v~U[-1,1]^3"),
     "convdiff3d_24": dict(kind="3d", N=24, eps=(0.1, 0.1, 0.1), m=100, ortho="cgsr",
                           prec="mixed"),
     "convdiff3d_96": dict(kind="3d", N=96, eps=(0.1, 0.1, 0.1), m=100, ortho="cgsr",
                           prec="mixed"),
-    "powerlaw_2m": dict(kind="powerlaw", n=2_000_000, m=50, ortho="mgs", prec="mixed_bf16"),
+    "powerlaw_2m": dict(kind="powerlaw", n=2_000_000, m=50, ortho="mgs", prec="mixed_bf16",
+                        desc="random power-law rows 3-200 (mean 16), diagonal 1.2 x row sum"),
     "powerlaw_20k": dict(kind="powerlaw", n=20_000, m=50, ortho="mgs", prec="mixed_bf16"),
     "aniso3d_128": dict(kind="3d", N=128, eps=(0.1, 1.0, 10.0), m=50, ortho="cgsr",
-                        prec="mixed"),
-    "aniso3d_24": dict(kind="3d", N=24, eps=(0.1, 1.0, 10.0), m=50, ortho="cgsr", prec="mixed"),
+                        prec="mixed", precond="learned",
+                        desc="3-D convection-diffusion 128^3, anisotropy 1:10:100, learned SpAI"),
+    "aniso3d_24": dict(kind="3d", N=24, eps=(0.1, 1.0, 10.0), m=50, ortho="cgsr", prec="mixed",
+                       precond="learned"),
 }
 
 

@@ -108,8 +108,7 @@ def test_preconditioned_solve_parity(gpulib):
     b = I.rhs_ones_noise(A, 1e-3, 2)
     s = G.Solver(A)
     G.gmres_spai_set(s.h, p)
-    mvals = np.zeros(len(A[1]))
-    G.gmres_spai_values(s.h, mvals)
+    mvals = O.spai_values(A, p.astype(np.float64))  # the oracle's own M
     s.set_opts(precond=1, path=G.PATH_GRID)
     x, st, info = s.solve(b, np.zeros(n), m=30, prec="mixed")
     s.close()
