@@ -44,6 +44,8 @@ def parse():
     p.add_argument("--workload", default=WORKLOAD)
     p.add_argument("--compare-steps", "--fp64-steps", dest="compare_steps", type=int, default=1)
     p.add_argument("--spai-params", default=None)
+    p.add_argument("--cgs-kernel", type=int, default=0,
+                   help="CGSR kernel family: 0 register-streaming rows, 1 TMA tiles")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     return p.parse_args()
@@ -164,7 +166,7 @@ def bench_ours(args):
     stream = torch.cuda.current_stream()
     solver = G.Solver(A, stream=stream)
     lanes32, lanes64 = G.gmres_autotune(solver.h)
-    solver.set_opts(profile=1)
+    solver.set_opts(profile=1, cgs_kernel=args.cgs_kernel)
     learned = spec.get("precond") == "learned"
     spai_params = None
     if learned:
@@ -306,6 +308,7 @@ def bench_ours(args):
                   else "inputs L2-resident (no flush; small-system workload)",
             "parallelism": "replicas" if world > 1 else "single GPU",
             "spmv_lanes": {"f32": lanes32, "f64": lanes64},
+            "cgs_kernel": ["register-streaming rows", "TMA tiles"][args.cgs_kernel],
         },
         "iters": iters, "restarts": restarts,
         "compare": compare,

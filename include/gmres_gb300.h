@@ -96,7 +96,9 @@ typedef struct gmres_opts {
                              continue unpreconditioned (default 1)              */
     int32_t spmv_lanes;   /* lanes per CSR row in SpMV (1..32, power of two);
                              0 = the autotuned choice                           */
-    int32_t reserved[5];
+    int32_t cgs_kernel;   /* CGSR kernel family: 0 = register-streaming rows
+                             (default), 1 = TMA-fed shared-memory tiles         */
+    int32_t reserved[4];
 } gmres_opts;
 
 /* Kernel classes reported in gmres_info (index into kernel_ms / kernel_bytes). */

@@ -19,6 +19,7 @@
 
 #include "../../include/gmres_gb300.h"
 #include "block_solver.cuh"
+#include "cgs_rows.cuh"
 #include "cgs_tile.cuh"
 #include "grid_kernels.cuh"
 #include "handle.hpp"
@@ -80,7 +81,7 @@ gmres_status ensure_workspace(gmres_handle *h, int m, gmres_precision prec) {
     CK(h->xb.ensure(ldv * 8));
     CK(h->bb.ensure(ldv * 8));
     CK(h->small.ensure((size_t)(2 * (MMAX + 1) * MMAX + 6 * (MMAX + 2)) * 8));
-    CK(h->part.ensure((size_t)h->grid * PSTRIDE * 8));
+    CK(h->part.ensure((size_t)std::max(h->grid, h->nsm * h->rows_blocks_per_sm) * PSTRIDE * 8));
     CK(h->part64.ensure((size_t)h->grid * 4 * 8));
     bool cgrow = sizeof(Ctl) > h->ctl.bytes;
     CK(h->ctl.ensure(sizeof(Ctl)));
@@ -224,7 +225,23 @@ gmres_status enqueue_step(gmres_handle *h, GridCtx<T, VT> &c, int col, gmres_ort
     const int ncols = col + 1;
     dim3 g(h->grid), b(kThreads);
     e = h->timer.begin();
-    if (ortho == GMRES_ORTHO_CGSR) {
+    if (ortho == GMRES_ORTHO_CGSR && h->opts.cgs_kernel == 0) {
+        // one resident wave per kernel: grid = SMs x resident blocks per SM
+        static int per_sm[3] = {0, 0, 0};
+        if (per_sm[0] == 0) {
+            void (*fns[3])(GridCtx<T, VT>, int) = {k_cgs_rows<T, VT, 0>, k_cgs_rows<T, VT, 1>,
+                                                   k_cgs_rows<T, VT, 2>};
+            for (int k = 0; k < 3; ++k) {
+                int b = 0;
+                CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fns[k], ROWS_THREADS, 0));
+                per_sm[k] = std::max(1, std::min(b, h->rows_blocks_per_sm));
+            }
+        }
+        k_cgs_rows<T, VT, 0><<<h->nsm * per_sm[0], ROWS_THREADS, 0, h->stream>>>(c, ncols);
+        k_cgs_rows<T, VT, 1><<<h->nsm * per_sm[1], ROWS_THREADS, 0, h->stream>>>(c, ncols);
+        k_cgs_rows<T, VT, 2><<<h->nsm * per_sm[2], ROWS_THREADS, 0, h->stream>>>(c, ncols);
+        acct.launches[GMRES_K_ORTHO] += 3;
+    } else if (ortho == GMRES_ORTHO_CGSR) {
         const int TR = cgs_choose_tr<VT>(ncols);
         const size_t sm = cgs_smem_bytes<T, VT>(ncols, TR);
         const long long spin = h->opts.spin_limit > 0 ? h->opts.spin_limit : (1LL << 26);
@@ -551,6 +568,7 @@ gmres_status validate_opts(const gmres_opts *o) {
     if (!(o->inner_factor >= 0) || o->path < 0 || o->path > 2 || o->spin_limit < 0 ||
         (o->spmv_lanes != 0 && (o->spmv_lanes < 1 || o->spmv_lanes > 32 ||
                                 (o->spmv_lanes & (o->spmv_lanes - 1)))) ||
+        o->cgs_kernel < 0 || o->cgs_kernel > 1 ||
         o->repeat_first < -1 || o->repeat_first > 1 || o->precond < 0 || o->precond > 1)
         return GMRES_ERR_ARG;
     return GMRES_OK;
@@ -654,6 +672,7 @@ gmres_status gmres_create(gmres_t *out, int32_t n, const int32_t *rowptr, const 
     if (cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess)
         return fail(GMRES_ERR_CUDA);
     h->grid = 2 * h->nsm;
+    h->rows_blocks_per_sm = 8;
     h->chunk = round_up((h->ldv + h->grid - 1) / h->grid, 4);
     const double avg = (double)nnz / n;
     h->lanes32 = h->lanes64 = pow2_lanes(avg / 2.0);

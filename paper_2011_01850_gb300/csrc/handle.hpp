@@ -80,6 +80,7 @@ struct gmres_handle {
     gmres_opts opts;
     int lanes32 = 4, lanes64 = 4;
     int grid = 0;          // blocks of the reduction kernels
+    int rows_blocks_per_sm = 4;  // blocks per SM of the register-streaming CGSR kernels
     int64_t chunk = 0;     // rows per block
     // matrix
     DevBuf rowptr, colind, vals64, vals32;

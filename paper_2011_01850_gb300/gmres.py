@@ -49,7 +49,8 @@ class Opts(ctypes.Structure):
         ("precond", ctypes.c_int32),
         ("fallback", ctypes.c_int32),
         ("spmv_lanes", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 5),
+        ("cgs_kernel", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 4),
     ]
 
 
