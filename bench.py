@@ -282,8 +282,9 @@ def bench_ours(args):
     tot_kms = sum(kms.values())
     iters = infos[0]["iters"]
     restarts = infos[0]["restarts"]
-    kernel_names = {"ortho": "CGSR passes (k_cgs_tile x3)" if ortho == "cgsr"
-                    else "MGS chain (k_mgs_step x j, k_mgs_last)",
+    kernel_names = {"ortho": ("CGSR passes (k_cgs_rows x3 + k_reduce_cols x2)"
+                              if args.cgs_kernel == 0 else "CGSR passes (k_cgs_tile x3)")
+                    if ortho == "cgsr" else "MGS step (k_mgs_persist, cooperative)",
                     "block": "single-block solver (k_block_solve)",
                     "spmv": "SpMV (k_spmv_step)", "residual": "binary64 residual (k_residual)"}
     out = {

@@ -98,7 +98,10 @@ typedef struct gmres_opts {
                              0 = the autotuned choice                           */
     int32_t cgs_kernel;   /* CGSR kernel family: 0 = register-streaming rows
                              (default), 1 = TMA-fed shared-memory tiles         */
-    int32_t reserved[4];
+    int32_t mgs_kernel;   /* MGS: 0 = one cooperative kernel per inner step with
+                             w in shared memory (default; used when w's row
+                             chunk fits), 1 = one kernel per basis vector       */
+    int32_t reserved[3];
 } gmres_opts;
 
 /* Kernel classes reported in gmres_info (index into kernel_ms / kernel_bytes). */

@@ -1,44 +1,32 @@
 // cgs_rows.cuh -- the three passes of CGSR (procedure CGSR of Algorithm 1,
 // done twice; arXiv 2011.01850) as register-streaming kernels.
 //
-//   MODE 0  h1 = V^T w (+ ||w||, the breakdown reference)
-//   MODE 1  w <- w - V h1, then h2 = V^T w
-//   MODE 2  w <- w - V h2, ||w||^2 -> h_{j+1,j}, column h1 + h2, Givens step
+//   MODE 0  partial h1 = V^T w per block            (+ ||w||^2)
+//   MODE 1  w <- w - V h1, then partial h2 = V^T w per block
+//   MODE 2  w <- w - V h2, ||w||^2 -> h_{j+1,j}; column h1 + h2; Givens step
+// k_reduce_cols sums the per-block partials of MODE 0 / 1 (one block per
+// basis vector, fixed order) between the passes.
 //
-// Every warp walks its own row slices (warp-steps) in grid-stride order.  In
-// a warp-step each lane holds RPL consecutive rows of w and, for every basis
-// vector, loads the same RPL rows with one 16-byte vector load, so a warp
-// moves 512 contiguous bytes of each column per load instruction and keeps
-// many of them in flight without staging.  The dot products accumulate in
-// one register per column per lane across all of the warp's slices and are
-// reduced once at the end (warp butterfly, then block, then grid through the
-// last block, all in a fixed order).  Pass B's second step reloads the slice
-// it has just read: those lines are still in L2, so the basis crosses HBM
-// once per pass.  binary64 bases split the columns over lane pairs so the
-// per-column accumulators fit in registers.
+// A block walks slices of SR = 4 RW rows (RW = rows of one warp-step: 32
+// lanes x RPL rows, RPL rows = one 16-byte vector of the basis type).  For
+// the dot products the four warps split the basis vectors (warp w takes
+// vectors w, w+4, ...), so a lane keeps at most 33 accumulators, and load the
+// four row groups of the slice; for the update each warp takes one row group
+// and all vectors.  Loads are issued in batches of CB vectors before their
+// values are used, so a warp keeps CB x 512 contiguous bytes in flight.  In
+// pass B the updated w of the slice goes through shared memory from the
+// update step to the dot step (two block barriers per slice), and the basis
+// slice the dot step reloads is still in L2: the basis crosses HBM once per
+// pass.
 #pragma once
 
 #include "grid_kernels.cuh"
 
 namespace gmres {
 
-template <class T, class VT>
-struct RowsCfg;
-template <>
-struct RowsCfg<float, float> {
-    static constexpr int RPL = 4, LPR = 1;
-};
-template <>
-struct RowsCfg<double, double> {
-    static constexpr int RPL = 2, LPR = 2;
-};
-template <>
-struct RowsCfg<float, __nv_bfloat16> {
-    static constexpr int RPL = 8, LPR = 1;
-};
-template <>
-struct RowsCfg<float, __half> {
-    static constexpr int RPL = 8, LPR = 1;
+template <class VT>
+struct RowsCfg {
+    static constexpr int RPL = 16 / (int)sizeof(VT);  // rows per 16-byte vector
 };
 
 // RPL consecutive basis entries (16 bytes) widened to the working type.
@@ -81,11 +69,13 @@ __device__ __forceinline__ void ld_rows<float, __half, 8>(const __half *p, float
     }
 }
 
-// RPL working-precision entries of w (plain loads: w is written by pass B/C).
+// RPL working-precision entries of w (plain loads and stores: pass B and C
+// write w).  RPL * sizeof(T) is 16 or 32 bytes.
 template <class T, int RPL>
 __device__ __forceinline__ void ld_w(const T *p, T (&o)[RPL]) {
+    constexpr int PER = 16 / (int)sizeof(T);
 #pragma unroll
-    for (int q = 0; q < RPL; q += 16 / (int)sizeof(T) < RPL ? 16 / (int)sizeof(T) : RPL) {
+    for (int q = 0; q < RPL; q += PER) {
         if (sizeof(T) == 4) {
             float4 a = *reinterpret_cast<const float4 *>(p + q);
             o[q] = a.x; o[q + 1] = a.y; o[q + 2] = a.z; o[q + 3] = a.w;
@@ -97,8 +87,9 @@ __device__ __forceinline__ void ld_w(const T *p, T (&o)[RPL]) {
 }
 template <class T, int RPL>
 __device__ __forceinline__ void st_w(T *p, const T (&v)[RPL]) {
+    constexpr int PER = 16 / (int)sizeof(T);
 #pragma unroll
-    for (int q = 0; q < RPL; q += 16 / (int)sizeof(T) < RPL ? 16 / (int)sizeof(T) : RPL) {
+    for (int q = 0; q < RPL; q += PER) {
         if (sizeof(T) == 4)
             *reinterpret_cast<float4 *>(p + q) =
                 make_float4((float)v[q], (float)v[q + 1], (float)v[q + 2], (float)v[q + 3]);
@@ -108,20 +99,97 @@ __device__ __forceinline__ void st_w(T *p, const T (&v)[RPL]) {
 }
 
 constexpr int ROWS_THREADS = 128;
+constexpr int ROWS_WARPS = ROWS_THREADS / 32;
+constexpr int ROWS_CB = 8;  // basis vectors loaded per batch
+
+// t = sum_col h[col] * V[col][r .. r+RPL) over all ncols vectors (one warp
+// row group), batched loads.
+template <class T, class VT, int RPL>
+__device__ __forceinline__ void rows_project(const GridCtx<T, VT> &c, int ncols, const T *hs,
+                                             int64_t r, T (&t)[RPL]) {
+#pragma unroll
+    for (int q = 0; q < RPL; ++q)
+        t[q] = 0;
+#pragma unroll
+    for (int c0 = 0; c0 < MMAX + 1; c0 += ROWS_CB) {
+        if (c0 < ncols) {
+            T v[ROWS_CB][RPL];
+#pragma unroll
+            for (int u = 0; u < ROWS_CB; ++u) {
+                if (c0 + u < ncols)
+                    ld_rows<T, VT, RPL>(c.V + (size_t)(c0 + u) * c.ldv + r, c.vinv, v[u]);
+                else {
+#pragma unroll
+                    for (int q = 0; q < RPL; ++q)
+                        v[u][q] = 0;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < ROWS_CB; ++u) {
+                const T hc = (c0 + u < ncols) ? hs[c0 + u] : T(0);
+#pragma unroll
+                for (int q = 0; q < RPL; ++q)
+                    t[q] += v[u][q] * hc;
+            }
+        }
+    }
+}
+
+// acc[k] += V[wid + 4k][slice rows] . ws (the slice's w, 4 row groups in
+// shared memory or registers), batched loads.
+template <class T, class VT, int RPL, int ACC>
+__device__ __forceinline__ void rows_dots(const GridCtx<T, VT> &c, int ncols, int64_t s0,
+                                          const T (&wv)[4][RPL], int wid, int lane,
+                                          T (&acc)[ACC]) {
+    constexpr int RW = 32 * RPL;
+    constexpr int KB = ROWS_CB / 4 > 0 ? ROWS_CB / 4 : 1;  // vectors per batch (x4 groups)
+#pragma unroll
+    for (int k0 = 0; k0 < ACC; k0 += KB) {
+        if (wid + ROWS_WARPS * k0 < ncols) {
+            T v[KB][4][RPL];
+#pragma unroll
+            for (int u = 0; u < KB; ++u) {
+                const int col = wid + ROWS_WARPS * (k0 + u);
+#pragma unroll
+                for (int g = 0; g < 4; ++g) {
+                    if (k0 + u < ACC && col < ncols)
+                        ld_rows<T, VT, RPL>(c.V + (size_t)col * c.ldv + s0 + g * RW + lane * RPL,
+                                            c.vinv, v[u][g]);
+                    else {
+#pragma unroll
+                        for (int q = 0; q < RPL; ++q)
+                            v[u][g][q] = 0;
+                    }
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < KB; ++u) {
+                if (k0 + u < ACC) {
+                    T a = 0;
+#pragma unroll
+                    for (int g = 0; g < 4; ++g)
+#pragma unroll
+                        for (int q = 0; q < RPL; ++q)
+                            a += v[u][g][q] * wv[g][q];
+                    acc[k0 + u] += a;
+                }
+            }
+        }
+    }
+}
 
 template <class T, class VT, int MODE>
 __global__ void __launch_bounds__(ROWS_THREADS)
-    k_cgs_rows(GridCtx<T, VT> c, int ncols) {
+    k_cgs_rows(GridCtx<T, VT> c, int ncols, T *part) {
     if (!c.ctl->active)
         return;
-    constexpr int RPL = RowsCfg<T, VT>::RPL, LPR = RowsCfg<T, VT>::LPR;
-    constexpr int ACC = (MMAX + 1 + LPR - 1) / LPR;   // columns per lane
-    constexpr int NW = ROWS_THREADS / 32;
-    constexpr int RW = (32 / LPR) * RPL;                // rows per warp-step
+    constexpr int RPL = RowsCfg<VT>::RPL;
+    constexpr int RW = 32 * RPL;                   // rows per warp-step
+    constexpr int SR = ROWS_WARPS * RW;            // rows per block slice
+    constexpr int ACC = (MMAX + 1 + ROWS_WARPS - 1) / ROWS_WARPS;
     __shared__ T hs[MMAX + 2];
-    __shared__ T red[NW][MMAX + 2];
+    __shared__ __align__(16) T wsl[SR];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int phase = lane % LPR, slot = lane / LPR;
     if (MODE >= 1) {
         const T *src = (MODE == 1) ? c.h1 : c.h2;
         for (int i = threadIdx.x; i < ncols; i += blockDim.x)
@@ -133,84 +201,58 @@ __global__ void __launch_bounds__(ROWS_THREADS)
     for (int k = 0; k < ACC; ++k)
         acc[k] = 0;
     T nsq = 0;
-    const int64_t nsteps = c.ldv / RW;
-    const int64_t gw = (int64_t)blockIdx.x * NW + wid;
-    const int64_t nwarps = (int64_t)gridDim.x * NW;
-    for (int64_t st = gw; st < nsteps; st += nwarps) {
-        const int64_t r = st * RW + (int64_t)slot * RPL;
-        T w[RPL];
-        ld_w<T, RPL>(c.w + r, w);
-        if (MODE >= 1) {
-            T t[RPL];
+    const int64_t nslices = c.ldv / SR;
+    for (int64_t sl = blockIdx.x; sl < nslices; sl += gridDim.x) {
+        const int64_t s0 = sl * SR;
+        T wv[4][RPL];
+        if (MODE == 0) {
 #pragma unroll
-            for (int q = 0; q < RPL; ++q)
-                t[q] = 0;
+            for (int g = 0; g < 4; ++g)
+                ld_w<T, RPL>(c.w + s0 + g * RW + lane * RPL, wv[g]);
+            if (wid == 0) {
 #pragma unroll
-            for (int k = 0; k < ACC; ++k) {
-                const int col = k * LPR + phase;
-                if (col < ncols) {
-                    T v[RPL];
-                    ld_rows<T, VT, RPL>(c.V + (size_t)col * c.ldv + r, c.vinv, v);
-                    const T hc = hs[col];
+                for (int g = 0; g < 4; ++g)
 #pragma unroll
                     for (int q = 0; q < RPL; ++q)
-                        t[q] += v[q] * hc;
-                }
+                        nsq += wv[g][q] * wv[g][q];
             }
-            if (LPR == 2) {
+        } else {
+            // update: warp wid owns row group wid of the slice
+            const int64_t r = s0 + wid * RW + lane * RPL;
+            T w[RPL], t[RPL];
+            ld_w<T, RPL>(c.w + r, w);
+            rows_project<T, VT, RPL>(c, ncols, hs, r, t);
 #pragma unroll
-                for (int q = 0; q < RPL; ++q)
-                    t[q] += __shfl_xor_sync(0xffffffffu, t[q], 1);
-            }
-#pragma unroll
-            for (int q = 0; q < RPL; ++q)
+            for (int q = 0; q < RPL; ++q) {
                 w[q] = w[q] - t[q];
-            if (phase == 0)
-                st_w<T, RPL>(c.w + r, w);
-        }
-        if (MODE == 0 || MODE == 2) {
-            if (phase == 0) {
-#pragma unroll
-                for (int q = 0; q < RPL; ++q)
+                if (MODE == 2)
                     nsq += w[q] * w[q];
             }
-        }
-        if (MODE <= 1) {
+            st_w<T, RPL>(c.w + r, w);
+            if (MODE == 1) {
 #pragma unroll
-            for (int k = 0; k < ACC; ++k) {
-                const int col = k * LPR + phase;
-                if (col < ncols) {
-                    T v[RPL];
-                    ld_rows<T, VT, RPL>(c.V + (size_t)col * c.ldv + r, c.vinv, v);
-                    T a = 0;
+                for (int q = 0; q < RPL; ++q)
+                    wsl[wid * RW + lane * RPL + q] = w[q];
+                __syncthreads();
+#pragma unroll
+                for (int g = 0; g < 4; ++g)
 #pragma unroll
                     for (int q = 0; q < RPL; ++q)
-                        a += v[q] * w[q];
-                    acc[k] += a;
-                }
+                        wv[g][q] = wsl[g * RW + lane * RPL + q];
+                __syncthreads();
             }
         }
+        if (MODE <= 1)
+            rows_dots<T, VT, RPL, ACC>(c, ncols, s0, wv, wid, lane, acc);
     }
-    T *mypart = c.part + (size_t)blockIdx.x * PSTRIDE;
+    T *mypart = part + (size_t)blockIdx.x * PSTRIDE;
     if (MODE <= 1) {
-        // lanes of one phase share their columns: butterfly over those lanes
 #pragma unroll
         for (int k = 0; k < ACC; ++k) {
-            T v = acc[k];
-#pragma unroll
-            for (int off = 16; off >= LPR; off >>= 1)
-                v += __shfl_xor_sync(0xffffffffu, v, off);
-            const int col = k * LPR + phase;
-            if (lane < LPR && col < ncols)
-                red[wid][col] = v;
-        }
-        __syncthreads();
-        for (int col = threadIdx.x; col < ncols; col += blockDim.x) {
-            T s = 0;
-#pragma unroll
-            for (int w_ = 0; w_ < NW; ++w_)
-                s += red[w_][col];
-            mypart[col] = s;
+            const int col = wid + ROWS_WARPS * k;
+            T v = warp_sum(acc[k]);
+            if (lane == 0 && col < ncols)
+                mypart[col] = v;
         }
     }
     if (MODE != 1) {
@@ -219,24 +261,40 @@ __global__ void __launch_bounds__(ROWS_THREADS)
         if (threadIdx.x == 0)
             mypart[MMAX + 1] = tot;
     }
-    if (!arrive_last(&c.ctl->counter[MODE + 1]))
+    if (MODE != 2)
+        return;
+    // MODE 2: ||w||^2 over blocks in the last block, then the Givens step
+    if (!arrive_last(&c.ctl->counter[3]))
         return;
     __shared__ T snorm;
-    if (MODE == 0) {
-        reduce_columns(c.part, gridDim.x, ncols, c.h1);
-        reduce_columns(c.part + MMAX + 1, gridDim.x, 1, &snorm);
-        __syncthreads();
-        if (threadIdx.x == 0)
-            c.ctl->wnorm0 = (double)wsqrt(snorm);
-    } else if (MODE == 1) {
-        reduce_columns(c.part, gridDim.x, ncols, c.h2);
-    } else {
-        reduce_columns(c.part + MMAX + 1, gridDim.x, 1, &snorm);
-        for (int i = threadIdx.x; i < ncols; i += blockDim.x)
-            c.h1[i] = ldcg(c.h1 + i) + ldcg(c.h2 + i);
-        __threadfence_block();
-        __syncthreads();
-        givens_step(c, ncols - 1, c.h1, wsqrt(snorm));
+    reduce_columns(part + MMAX + 1, gridDim.x, 1, &snorm);
+    for (int i = threadIdx.x; i < ncols; i += blockDim.x)
+        c.h1[i] = ldcg(c.h1 + i) + ldcg(c.h2 + i);
+    __threadfence();
+    __syncthreads();
+    givens_step(c, ncols - 1, c.h1, wsqrt(snorm));
+}
+
+// out[col] = sum over the blocks of part[b][col], col < ncols, and, when
+// `extra` >= 0, ctl->wnorm0 = sqrt(sum of part[b][MMAX+1]) (the ||A v_j||
+// reference of pass A).  One block per column, fixed-order tree.
+template <class T>
+__global__ void __launch_bounds__(256) k_reduce_cols(const T *part, int nblocks, int ncols,
+                                                     T *out, Ctl *ctl, int with_norm) {
+    if (!ctl->active)
+        return;
+    __shared__ T sred[32];
+    const int col = blockIdx.x;
+    const int slot = (col < ncols) ? col : MMAX + 1;
+    T a = 0;
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
+        a += part[(size_t)b * PSTRIDE + slot];
+    a = block_sum1(a, sred);
+    if (threadIdx.x == 0) {
+        if (col < ncols)
+            out[col] = a;
+        else if (with_norm)
+            ctl->wnorm0 = (double)wsqrt(a);
     }
 }
 

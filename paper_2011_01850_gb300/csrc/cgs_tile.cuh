@@ -119,6 +119,7 @@ __global__ void __launch_bounds__(CGS_THREADS, 1)
         acc[k] = 0;
     T nsq = 0;
     bool timed_out = false;
+    int64_t kbreak = 0;
 
     for (int64_t k = 0; k < my_tiles; ++k) {
         const int s = (int)(k % CGS_STAGES);
@@ -127,6 +128,7 @@ __global__ void __launch_bounds__(CGS_THREADS, 1)
         const bool ok = mbar_wait(&bars[s], parity, spin_limit);
         if (__syncthreads_or(!ok)) {
             timed_out = true;
+            kbreak = k;
             break;
         }
         const int64_t t = blockIdx.x + k * gridDim.x;
@@ -189,8 +191,20 @@ __global__ void __launch_bounds__(CGS_THREADS, 1)
             issue(k + CGS_STAGES);
     }
     if (__syncthreads_or(timed_out)) {
-        if (tid == 0)
+        // Before the block's shared memory goes away, let every bulk copy it
+        // issued land: wait (with its own bound) on each stage that was
+        // issued and not yet consumed, then report the timeout.
+        // Tiles 0 .. kbreak-1 were consumed; tiles kbreak .. kbreak+S-1 (within
+        // the block's count) were issued and may still be in flight.
+        if (tid == 0) {
+            const long long drain = 1LL << 26;
+            const int64_t issued = my_tiles < kbreak + CGS_STAGES ? my_tiles
+                                                                  : kbreak + CGS_STAGES;
+            for (int64_t k = kbreak; k < issued; ++k)
+                mbar_wait(&bars[k % CGS_STAGES], (uint32_t)((k / CGS_STAGES) & 1), drain);
             atomicExch(&c.ctl->timeout, 1);
+        }
+        __syncthreads();
         return;
     }
 
@@ -227,7 +241,7 @@ __global__ void __launch_bounds__(CGS_THREADS, 1)
         reduce_columns(c.part + MMAX + 1, gridDim.x, 1, &snorm);
         for (int i = tid; i < ncols; i += blockDim.x)
             c.h1[i] = ldcg(c.h1 + i) + ldcg(c.h2 + i);
-        __threadfence_block();
+        __threadfence();
         __syncthreads();
         givens_step(c, ncols - 1, c.h1, wsqrt(snorm));
     }

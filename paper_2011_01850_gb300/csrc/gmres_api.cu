@@ -14,6 +14,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <new>
 #include <vector>
 
@@ -21,6 +22,7 @@
 #include "block_solver.cuh"
 #include "cgs_rows.cuh"
 #include "cgs_tile.cuh"
+#include "mgs_persist.cuh"
 #include "grid_kernels.cuh"
 #include "handle.hpp"
 #include "host_util.hpp"
@@ -198,6 +200,38 @@ int lanes_for(gmres_handle *h) {
     return L;
 }
 
+// Whether the cooperative MGS kernel can run: cooperative launches supported,
+// one 512-thread block per SM resident with w's row chunk in shared memory.
+template <class T, class VT>
+bool mgs_persist_ok(gmres_handle *h) {
+    const int key = (int)sizeof(T) * 16 + (int)sizeof(VT);
+    auto it = h->mgs_ok_cache.find(key);
+    if (it != h->mgs_ok_cache.end())
+        return it->second;
+    bool ok = false;
+    int coop = 0;
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, h->device);
+    const int64_t chunk = round_up((h->ldv + h->nsm - 1) / h->nsm, 4);
+    const size_t smem = (size_t)chunk * sizeof(T) + 16;
+    int optin = 0;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
+    cudaFuncAttributes fa;
+    if (coop && cudaFuncGetAttributes(&fa, k_mgs_persist<T, VT>) == cudaSuccess &&
+        smem + fa.sharedSizeBytes <= (size_t)optin &&
+        cudaFuncSetAttribute(k_mgs_persist<T, VT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) == cudaSuccess) {
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mgs_persist<T, VT>,
+                                                          MGSP_THREADS, smem) == cudaSuccess &&
+            per_sm >= 1)
+            ok = true;
+    }
+    cudaGetLastError();
+    h->mgs_chunk = chunk;
+    h->mgs_ok_cache[key] = ok;
+    return ok;
+}
+
 // Enqueue one inner step (column index `col` of the basis -> new column
 // col+1).  Kernels return at once when the cycle has ended.
 template <class T, class VT>
@@ -229,18 +263,21 @@ gmres_status enqueue_step(gmres_handle *h, GridCtx<T, VT> &c, int col, gmres_ort
         // one resident wave per kernel: grid = SMs x resident blocks per SM
         static int per_sm[3] = {0, 0, 0};
         if (per_sm[0] == 0) {
-            void (*fns[3])(GridCtx<T, VT>, int) = {k_cgs_rows<T, VT, 0>, k_cgs_rows<T, VT, 1>,
-                                                   k_cgs_rows<T, VT, 2>};
+            void (*fns[3])(GridCtx<T, VT>, int, T *) = {
+                k_cgs_rows<T, VT, 0>, k_cgs_rows<T, VT, 1>, k_cgs_rows<T, VT, 2>};
             for (int k = 0; k < 3; ++k) {
-                int b = 0;
-                CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fns[k], ROWS_THREADS, 0));
-                per_sm[k] = std::max(1, std::min(b, h->rows_blocks_per_sm));
+                int bpsm = 0;
+                CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpsm, fns[k], ROWS_THREADS, 0));
+                per_sm[k] = std::max(1, std::min(bpsm, h->rows_blocks_per_sm));
             }
         }
-        k_cgs_rows<T, VT, 0><<<h->nsm * per_sm[0], ROWS_THREADS, 0, h->stream>>>(c, ncols);
-        k_cgs_rows<T, VT, 1><<<h->nsm * per_sm[1], ROWS_THREADS, 0, h->stream>>>(c, ncols);
-        k_cgs_rows<T, VT, 2><<<h->nsm * per_sm[2], ROWS_THREADS, 0, h->stream>>>(c, ncols);
-        acct.launches[GMRES_K_ORTHO] += 3;
+        const int g0 = h->nsm * per_sm[0], g1 = h->nsm * per_sm[1], g2 = h->nsm * per_sm[2];
+        k_cgs_rows<T, VT, 0><<<g0, ROWS_THREADS, 0, h->stream>>>(c, ncols, c.part);
+        k_reduce_cols<T><<<ncols + 1, 256, 0, h->stream>>>(c.part, g0, ncols, c.h1, c.ctl, 1);
+        k_cgs_rows<T, VT, 1><<<g1, ROWS_THREADS, 0, h->stream>>>(c, ncols, c.part);
+        k_reduce_cols<T><<<ncols, 256, 0, h->stream>>>(c.part, g1, ncols, c.h2, c.ctl, 0);
+        k_cgs_rows<T, VT, 2><<<g2, ROWS_THREADS, 0, h->stream>>>(c, ncols, c.part);
+        acct.launches[GMRES_K_ORTHO] += 5;
     } else if (ortho == GMRES_ORTHO_CGSR) {
         const int TR = cgs_choose_tr<VT>(ncols);
         const size_t sm = cgs_smem_bytes<T, VT>(ncols, TR);
@@ -270,6 +307,20 @@ gmres_status enqueue_step(gmres_handle *h, GridCtx<T, VT> &c, int col, gmres_ort
         k_cgs_tile<T, VT, 1><<<gt, CGS_THREADS, sm, h->stream>>>(c, ncols, TR, spin);
         k_cgs_tile<T, VT, 2><<<gt, CGS_THREADS, sm, h->stream>>>(c, ncols, TR, spin);
         acct.launches[GMRES_K_ORTHO] += 3;
+    } else if (h->opts.mgs_kernel == 0 && mgs_persist_ok<T, VT>(h)) {
+        // one cooperative kernel: w stays in shared memory, v_{j+1} written
+        int64_t chunk = h->mgs_chunk;
+        long long spin = h->opts.spin_limit > 0 ? h->opts.spin_limit : (1LL << 24);
+        unsigned *bar = &h->ctl.as<Ctl>()->counter[5];
+        GridCtx<T, VT> cc = c;
+        int nc = ncols;
+        void *args[] = {&cc, &nc, &chunk, &spin, &bar};
+        CK(cudaLaunchCooperativeKernel((const void *)k_mgs_persist<T, VT>, dim3(h->nsm),
+                                       dim3(MGSP_THREADS), args,
+                                       (size_t)chunk * sizeof(T) + 16, h->stream));
+        acct.launches[GMRES_K_ORTHO] += 1;
+        h->timer.end(GMRES_K_ORTHO, e);
+        return GMRES_OK;
     } else {
         for (int i = 0; i < ncols; ++i)
             k_mgs_step<T, VT><<<g, b, 0, h->stream>>>(c, i);
@@ -429,6 +480,11 @@ gmres_status solve_grid(gmres_handle *h, const double *b, double *x, int m, doub
         h->timer.harvest(info->kernel_ms);
         const int j = h->hctl->last_j;
         account_cycle<T, VT>(h, j, ortho, acct);
+        if (h->hctl->timeout) {
+            result = GMRES_ERR_TIMEOUT;
+            info->iters += j;
+            break;
+        }
         info->iters += j;
         info->restarts += 1;
         if (info->restarts == 1) {
@@ -568,7 +624,7 @@ gmres_status validate_opts(const gmres_opts *o) {
     if (!(o->inner_factor >= 0) || o->path < 0 || o->path > 2 || o->spin_limit < 0 ||
         (o->spmv_lanes != 0 && (o->spmv_lanes < 1 || o->spmv_lanes > 32 ||
                                 (o->spmv_lanes & (o->spmv_lanes - 1)))) ||
-        o->cgs_kernel < 0 || o->cgs_kernel > 1 ||
+        o->cgs_kernel < 0 || o->cgs_kernel > 1 || o->mgs_kernel < 0 || o->mgs_kernel > 1 ||
         o->repeat_first < -1 || o->repeat_first > 1 || o->precond < 0 || o->precond > 1)
         return GMRES_ERR_ARG;
     return GMRES_OK;
@@ -672,7 +728,7 @@ gmres_status gmres_create(gmres_t *out, int32_t n, const int32_t *rowptr, const 
     if (cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess)
         return fail(GMRES_ERR_CUDA);
     h->grid = 2 * h->nsm;
-    h->rows_blocks_per_sm = 8;
+    h->rows_blocks_per_sm = 16;
     h->chunk = round_up((h->ldv + h->grid - 1) / h->grid, 4);
     const double avg = (double)nnz / n;
     h->lanes32 = h->lanes64 = pow2_lanes(avg / 2.0);

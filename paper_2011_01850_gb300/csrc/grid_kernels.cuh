@@ -480,7 +480,7 @@ __global__ void __launch_bounds__(256) k_cgs_update_norm(GridCtx<T, VT> c, int n
     // Hessenberg column = h1 + h2 (sum of the two classical passes)
     for (int i = threadIdx.x; i < ncols; i += blockDim.x)
         c.h1[i] = ldcg(c.h1 + i) + ldcg(c.h2 + i);
-    __threadfence_block();
+    __threadfence();
     __syncthreads();
     T hnext = wsqrt(stot);
     givens_step(c, ncols - 1, c.h1, hnext);

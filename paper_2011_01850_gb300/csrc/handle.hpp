@@ -5,6 +5,7 @@
 
 #include <cuda_runtime.h>
 
+#include <map>
 #include <vector>
 
 #include "common.cuh"
@@ -81,6 +82,8 @@ struct gmres_handle {
     int lanes32 = 4, lanes64 = 4;
     int grid = 0;          // blocks of the reduction kernels
     int rows_blocks_per_sm = 4;  // blocks per SM of the register-streaming CGSR kernels
+    int64_t mgs_chunk = 0;       // rows per block of the cooperative MGS kernel
+    std::map<int, bool> mgs_ok_cache;  // cooperative MGS feasible, per (T, VT)
     int64_t chunk = 0;     // rows per block
     // matrix
     DevBuf rowptr, colind, vals64, vals32;

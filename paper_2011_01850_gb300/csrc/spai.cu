@@ -13,6 +13,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <vector>
 
@@ -296,14 +297,15 @@ __global__ void __launch_bounds__(BWD_THREADS) k_mlp_bwd(int64_t nnz, const floa
 }
 
 // Adam (Kingma & Ba): m = b1 m + (1-b1) g, v = b2 v + (1-b2) g^2,
-// p -= lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps).
-__global__ void k_adam(int np, float *p, float *m, float *v, const float *g, int t, float lr,
-                       float b1, float b2, float eps) {
-    const float c1 = 1.f - powf(b1, (float)t), c2 = 1.f - powf(b2, (float)t);
+// p -= lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps).  The factors
+// (1 - b), and the bias corrections come from the host in binary64 rounded
+// once to binary32 (forming 1 - b2 from a rounded b2 would lose ~1e-5).
+__global__ void k_adam(int np, float *p, float *m, float *v, const float *g, float lr, float b1,
+                       float omb1, float b2, float omb2, float c1, float c2, float eps) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < np; i += gridDim.x * blockDim.x) {
         const float gi = g[i];
-        const float mi = b1 * m[i] + (1.f - b1) * gi;
-        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        const float mi = b1 * m[i] + omb1 * gi;
+        const float vi = b2 * v[i] + omb2 * gi * gi;
         m[i] = mi;
         v[i] = vi;
         p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
@@ -529,8 +531,11 @@ gmres_status gmres_spai_adam(gmres_t h, float *params, float *adam_m, float *ada
         !is_device_ptr(params) || !is_device_ptr(adam_m) || !is_device_ptr(adam_v) ||
         !is_device_ptr(grad))
         return GMRES_ERR_ARG;
-    k_adam<<<(NPARAM + 255) / 256, 256, 0, h->stream>>>(NPARAM, params, adam_m, adam_v, grad,
-                                                        step, lr, 0.9f, 0.999f, 1e-8f);
+    const double b1 = 0.9, b2 = 0.999;
+    k_adam<<<(NPARAM + 255) / 256, 256, 0, h->stream>>>(
+        NPARAM, params, adam_m, adam_v, grad, lr, (float)b1, (float)(1.0 - b1), (float)b2,
+        (float)(1.0 - b2), (float)(1.0 - std::pow(b1, step)), (float)(1.0 - std::pow(b2, step)),
+        1e-8f);
     CKL();
     CK(cudaStreamSynchronize(h->stream));
     return GMRES_OK;

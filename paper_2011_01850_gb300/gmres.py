@@ -50,7 +50,8 @@ class Opts(ctypes.Structure):
         ("fallback", ctypes.c_int32),
         ("spmv_lanes", ctypes.c_int32),
         ("cgs_kernel", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 4),
+        ("mgs_kernel", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 3),
     ]
 
 

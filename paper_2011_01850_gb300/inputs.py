@@ -85,6 +85,52 @@ def _stencil_csr(shape, eps, vel):
     return rowptr.astype(np.int32), colind, values
 
 
+class StencilFamily3D:
+    """Matrices of the 3-D 7-point upwind family on one N^3 grid.
+
+    The sparsity pattern (and the order of the entries) is fixed by the grid,
+    so it is built once; ``values(eps, seed)`` returns only the value array of
+    the matrix ``convdiff3d(N, eps, seed)`` would build (same entries, same
+    order)."""
+
+    def __init__(self, N):
+        self.N = N
+        n = N ** 3
+        self.n = n
+        idx = np.arange(n, dtype=np.int64)
+        self.coords = [idx % N, (idx // N) % N, idx // (N * N)]
+        self.strides = [1, N, N * N]
+        valid = []
+        for a in reversed(range(3)):
+            valid.append(self.coords[a] > 0)
+        valid.append(np.ones(n, dtype=bool))
+        for a in range(3):
+            valid.append(self.coords[a] < N - 1)
+        self.mask = np.stack(valid, axis=1)
+        A = convdiff3d(N, seed=0)
+        self.rowptr, self.colind = A[0], A[1]
+
+    def values(self, eps, seed):
+        N = self.N
+        n = self.n
+        h = 1.0 / (N + 1)
+        v = np.random.default_rng(seed).uniform(-1.0, 1.0, size=(n, 3))
+        eps = np.asarray(eps, dtype=np.float64)
+        diag = np.zeros(n)
+        lower, upper = [], []
+        for a in range(3):
+            d = eps[a] / eps[0]
+            c = h * v[:, a] / eps[0]
+            diag += 2.0 * d + np.abs(c)
+            lower.append(-d - np.maximum(c, 0.0))
+            upper.append(-d - np.maximum(-c, 0.0))
+        vals = [lower[a] for a in reversed(range(3))] + [diag] + upper
+        return np.stack(vals, axis=1)[self.mask].astype(np.float64)
+
+    def matrix(self, eps, seed):
+        return self.rowptr, self.colind, self.values(eps, seed)
+
+
 def convdiff2d(nx, ny=None, pe=10.0, vel=None, seed=0):
     """2-D 5-point upwind convection-diffusion, eps = 1/pe on both axes.
 

@@ -39,13 +39,19 @@ def init_params(seed=0, noise=0.02):
     return (jacobi_params() + noise * rng.standard_normal(NPARAM)).astype(np.float32)
 
 
+_FAMILIES = {}
+
+
 def training_matrix(N, index, seed=20110185):
     """Training system `index` of the 3-D family: 7-point upwind
     convection-diffusion on N^3, v ~ U[-1, 1]^3 per node, diffusion
     0.1 * (1, r1, r2) with r1, r2 log-uniform in [1, 100]."""
+    if N not in _FAMILIES:
+        _FAMILIES[N] = I.StencilFamily3D(N)
+    fam = _FAMILIES[N]
     rng = np.random.default_rng(seed + 7919 * (index + 1))
     r = np.exp(rng.uniform(0.0, math.log(100.0), size=2))
-    A = I.convdiff3d(N, eps=(0.1, 0.1 * r[0], 0.1 * r[1]), seed=seed + index)
+    A = fam.matrix((0.1, 0.1 * r[0], 0.1 * r[1]), seed + index)
     b = I.rhs_ones_noise(A, 1e-3, seed + 100000 + index)
     return A, b
 

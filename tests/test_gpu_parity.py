@@ -306,3 +306,46 @@ def test_memory_model(gpulib, stream):
     ldv = ((n + 2047) // 2048) * 2048
     assert wb64 - wb32 >= 51 * ldv * 4
     assert wb32 - wb16 == 51 * ldv * 2
+
+
+def test_mgs_cooperative_matches_per_column(gpulib, stream):
+    """The cooperative MGS kernel (w in shared memory, one launch per step)
+    and the per-basis-vector kernels agree: binary64 takes the same schedule
+    and solutions agree to 1e-11; mixed both reach the binary64 target."""
+    A = I.powerlaw_random(60000, seed=21)
+    b = I.rhs_ones_noise(A, 1e-3, 3)
+    n = len(A[0]) - 1
+    out = {}
+    for kern in (0, 1):
+        for prec in ("fp64", "mixed_bf16"):
+            s = G.Solver(A, stream=stream)
+            s.set_opts(path=G.PATH_GRID, mgs_kernel=kern)
+            x, st, info = s.solve(b, np.zeros(n), m=40, ortho="mgs", prec=prec)
+            s.close()
+            assert st == G.OK
+            assert O.residual_norm(A, b, x) / np.linalg.norm(b) <= 1e-10
+            out[(kern, prec)] = (x, info)
+    x0, i0 = out[(0, "fp64")]
+    x1, i1 = out[(1, "fp64")]
+    assert i0["iters"] == i1["iters"] and i0["restarts"] == i1["restarts"]
+    assert np.linalg.norm(x0 - x1) / np.linalg.norm(x1) <= 1e-11
+    assert i0["kernel_launches"]["ortho"] < i1["kernel_launches"]["ortho"]
+
+
+def test_bounded_wait_reports_timeout(gpulib, stream):
+    """With the spin limit at 1 the grid barrier of the cooperative MGS kernel
+    gives up at once: the solve ends with GMRES_ERR_TIMEOUT instead of
+    waiting, and the handle stays usable."""
+    A = I.powerlaw_random(200000, seed=5)
+    b = I.rhs_ones_noise(A, 1e-3, 4)
+    n = len(A[0]) - 1
+    s = G.Solver(A, stream=stream)
+    s.set_opts(path=G.PATH_GRID, mgs_kernel=0, spin_limit=1)
+    with pytest.raises(G.GmresError) as e:
+        s.solve(b, np.zeros(n), m=10, ortho="mgs", prec="mixed")
+    assert e.value.status == G.ERR_TIMEOUT
+    s.set_opts(spin_limit=0)
+    x, st, info = s.solve(b, np.zeros(n), m=30, ortho="mgs", prec="mixed")
+    s.close()
+    assert st == G.OK
+    assert O.residual_norm(A, b, x) / np.linalg.norm(b) <= 1e-10
