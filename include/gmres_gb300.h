@@ -288,6 +288,36 @@ gmres_status gmres_batch_solve(gmres_batch_t b, const double *rhs, double *x, in
                                int32_t maxiter, int32_t lanes, gmres_batch_result *results,
                                gmres_info *info);
 
+/* ---------------------------------------------------------------------------
+ * Solve without allocating device memory.  The paper has no counterpart; this
+ * is for callers that cannot allocate at the point of the solve: cudaMalloc /
+ * cudaFree may synchronise the whole device, are not allowed while a stream
+ * is being captured into a CUDA graph, and some frameworks own the entire
+ * device budget through their own allocator.
+ *
+ * gmres_solve_noalloc runs the single-block whole-solve kernel (the block path
+ * of gmres_solve) on the caller's DEVICE arrays: CSR rowptr (n+1), colind and
+ * vals (nnz, binary64), b and x (n, binary64; x = x_0 on entry, the result on
+ * exit).  m, tol, ortho, prec, maxiter, info: as for gmres_solve; stream is a
+ * cudaStream_t.  The caller guarantees a valid CSR matrix (not checked).
+ * All workspace (Krylov basis, work vectors, binary32 values, result record)
+ * comes from one file-scope device array of GMRES_NOALLOC_SCRATCH_BYTES that
+ * every GPU loading the library holds until the process exits; a system whose
+ * workspace (about (m+1) n s_V + 8 n + 4 nnz bytes) exceeds it is rejected with
+ * GMRES_ERR_ARG and a message on stderr.  No call allocates: neither
+ * cudaMalloc, cudaFree nor any allocating library routine.  The first call on
+ * a device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture.  All
+ * calls share the array and each overwrites it: calls that overlap on the GPU
+ * race and must be serialised by the caller.  Host pointers: GMRES_ERR_ARG.
+ * ------------------------------------------------------------------------- */
+#define GMRES_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
+
+gmres_status gmres_solve_noalloc(int32_t n, const int32_t *rowptr, const int32_t *colind,
+                                 const double *vals, int64_t nnz, const double *b, double *x,
+                                 int32_t m, double tol, gmres_ortho ortho, gmres_precision prec,
+                                 int32_t maxiter, void *stream, gmres_info *info);
+
 /* Device bytes the handle holds for the matrix (both value copies, shared
  * indices) and, for a solve with restart length m in precision prec, the
  * workspace (basis, vectors, Hessenberg).  Matches the paper's storage model

@@ -117,6 +117,8 @@ SIGNATURES = {
     "gmres_spai_set": (_st, [_vp, _vp]),
     "gmres_spai_values": (_st, [_vp, _vp]),
     "gmres_spai_clear": (_st, [_vp]),
+    "gmres_solve_noalloc": (_st, [_i32, _vp, _vp, _vp, ctypes.c_int64, _vp, _vp, _i32, _f64,
+                                  _i32, _i32, _i32, _vp, ctypes.POINTER(Info)]),
     "gmres_status_str": (ctypes.c_char_p, [_st]),
     "gmres_version": (ctypes.c_char_p, []),
 }
@@ -363,6 +365,21 @@ def pack_batch(systems):
     rowptr = np.concatenate(rps + [np.array([nnz0])]).astype(np.int32)
     return (np.array(sys_ptr, np.int64), rowptr, np.concatenate(cis).astype(np.int32),
             np.concatenate(vas), np.concatenate(bs))
+
+
+NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
+
+
+def gmres_solve_noalloc(n, rowptr, colind, vals, nnz, b, x, m, tol, ortho, prec, maxiter,
+                        stream=None):
+    """Solve on caller-owned device arrays with no device allocation.
+    Returns (status, Info); negative statuses raise GmresError."""
+    info = Info()
+    st = lib().gmres_solve_noalloc(int(n), _ptr(rowptr), _ptr(colind), _ptr(vals), int(nnz),
+                                   _ptr(b), _ptr(x), int(m), float(tol), int(ortho), int(prec),
+                                   int(maxiter), _stream_ptr(stream), ctypes.byref(info))
+    _check(st, "gmres_solve_noalloc")
+    return st, info
 
 
 def gmres_status_str(s):
