@@ -79,7 +79,8 @@ typedef enum {
 typedef struct gmres_opts {
     double tau;           /* restart when |s_{j+1}| <= tau * beta (Sec. 3, second
                              strategy); < 0 selects the precision's default:
-                             0 (off) for FP64, 1e-6 MIXED, 1e-2 BF16, 1e-3 FP16 */
+                             0 (off) for FP64, 1e-6 MIXED, 2^-8 BF16, 2^-11
+                             FP16 (one unit roundoff of the basis format)      */
     double inner_factor;  /* end a cycle once |s_{j+1}| <= inner_factor * tol *
                              ||b|| (the binary64 residual then decides); 0.5    */
     int32_t repeat_first; /* 1: cycles after the first run as long as the first

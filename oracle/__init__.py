@@ -232,9 +232,10 @@ def arnoldi_cycle(A, r0, m, ortho=CGSR, prec=FP64, kmax=None, tau=0.0, inner_abs
 
 def default_tau(prec):
     """Restart threshold on the Arnoldi-residual gain per precision (Sec. 3,
-    second strategy; the performance study's 1e-6 for binary32, scaled to the
-    unit roundoff for the 16-bit bases)."""
-    return {FP64: 0.0, MIXED: 1e-6, MIXED_BF16: 1e-2, MIXED_FP16: 1e-3, ALL_FP32: 1e-6}[prec]
+    second strategy): the performance study's 1e-6 for binary32; for the
+    16-bit bases one unit roundoff of the storage format (2^-8, 2^-11)."""
+    return {FP64: 0.0, MIXED: 1e-6, MIXED_BF16: 2.0 ** -8, MIXED_FP16: 2.0 ** -11,
+            ALL_FP32: 1e-6}[prec]
 
 
 def gmres(A, b, x0=None, m=30, tol=1e-10, ortho=CGSR, prec=FP64, maxiter=10000, tau=None,

@@ -87,8 +87,8 @@ inline double default_tau(gmres_precision p) {
     switch (p) {
     case GMRES_FP64: return 0.0;
     case GMRES_MIXED: return 1e-6;
-    case GMRES_MIXED_BF16: return 1e-2;
-    default: return 1e-3;
+    case GMRES_MIXED_BF16: return 0.00390625;     // 2^-8, the bfloat16 unit roundoff
+    default: return 0.00048828125;                // 2^-11, the binary16 unit roundoff
     }
 }
 
