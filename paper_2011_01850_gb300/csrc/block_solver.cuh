@@ -8,11 +8,75 @@
 // (xor-butterfly + shared memory, deterministic); the Hessenberg matrix, the
 // rotations and s live in shared memory; vectors and the basis live in the
 // system's global workspace (L1/L2 resident for small n).
+//
+// The same routine also runs on a thread-block cluster (CS > 1 CTAs): the
+// system's rows are split into CS contiguous chunks, every reduction is a
+// block reduction followed by an exchange of the CTAs' partials through
+// distributed shared memory (double-buffered slots, summed in rank order so
+// every CTA gets the same value bit for bit), the Givens step and the back
+// substitution run redundantly in every CTA, and cluster barriers order the
+// global writes other CTAs gather (x, v_1, v_{j+1}).  Large systems of a batch
+// use clusters so that one system is not the critical path of the batch.
 #pragma once
+
+#include <cooperative_groups.h>
 
 #include "common.cuh"
 
 namespace gmres {
+
+namespace cg = cooperative_groups;
+
+constexpr int TEAM_KMAX = 8;  // values per team reduction
+
+// A team is one thread block (CS = 1) or one thread-block cluster (CS > 1).
+template <int CS>
+struct Team {
+    __device__ __forceinline__ static int rank() { return (int)cg::this_cluster().block_rank(); }
+    __device__ __forceinline__ static void sync() { cg::this_cluster().sync(); }
+};
+template <>
+struct Team<1> {
+    __device__ __forceinline__ static int rank() { return 0; }
+    __device__ __forceinline__ static void sync() { __syncthreads(); }
+};
+
+// Team-wide sums of K values (every thread receives them).  red: K*32 block
+// scratch; slots: 2*TEAM_KMAX shared slots (double-buffered by *buf); bc:
+// TEAM_KMAX broadcast cells.
+template <class T, int K, int CS>
+__device__ __forceinline__ void team_sum(T (&v)[K], T *red, T *slots, T *bc, int *buf) {
+    block_sum<T, K>(v, red);
+    if (CS == 1)
+        return;
+    T *mine = slots + (*buf) * TEAM_KMAX;
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+            mine[k] = v[k];
+    }
+    Team<CS>::sync();
+    if (threadIdx.x < K) {
+        cg::cluster_group cl = cg::this_cluster();
+        T a = 0;
+        for (int r = 0; r < CS; ++r)
+            a += cl.map_shared_rank(mine, r)[threadIdx.x];
+        bc[threadIdx.x] = a;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+        v[k] = bc[k];
+    __syncthreads();
+    *buf ^= 1;
+}
+
+template <class T, int CS>
+__device__ __forceinline__ T team_sum1(T v, T *red, T *slots, T *bc, int *buf) {
+    T a[1] = {v};
+    team_sum<T, 1, CS>(a, red, slots, bc, buf);
+    return a[0];
+}
 
 // One system of a block solve.  All pointers are device pointers; V and the
 // work vectors (w, r) are library workspace of at least ldv rows.
@@ -54,11 +118,11 @@ template <class T, class XT, int L>
 __device__ __forceinline__ void block_spmv(const int *__restrict__ rowptr,
                                            const int *__restrict__ colind,
                                            const T *__restrict__ a, const XT *x, float xinv, T *y,
-                                           int n) {
+                                           int rb, int n) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int nw = blockDim.x >> 5;
     const int G = 32 / L, gl = lane % L, gi = lane / L;
-    for (int base = wid * G; base < n; base += nw * G) {
+    for (int base = rb + wid * G; base < n; base += nw * G) {
         int row = base + gi;
         T acc = 0;
         if (row < n) {

@@ -29,25 +29,52 @@ struct RowsCfg {
     static constexpr int RPL = 16 / (int)sizeof(VT);  // rows per 16-byte vector
 };
 
+// L2 eviction policies for the basis stream: lines a pass reads once are
+// marked evict-first; lines pass B reads twice are marked evict-last on the
+// first read (so they are still in L2 for the second) and evict-first on the
+// second.
+__device__ __forceinline__ uint64_t l2_policy_first() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t l2_policy_last() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+// 16 bytes through the read-only path with an L2 cache policy.
+__device__ __forceinline__ uint4 ld16(const void *p, uint64_t pol) {
+    uint4 r;
+    asm volatile("ld.global.nc.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+                 : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+                 : "l"(p), "l"(pol));
+    return r;
+}
+
 // RPL consecutive basis entries (16 bytes) widened to the working type.
 template <class T, class VT, int RPL>
-__device__ __forceinline__ void ld_rows(const VT *p, float vinv, T (&o)[RPL]);
+__device__ __forceinline__ void ld_rows(const VT *p, float vinv, T (&o)[RPL], uint64_t pol);
 
 template <>
-__device__ __forceinline__ void ld_rows<float, float, 4>(const float *p, float, float (&o)[4]) {
-    float4 a = __ldg(reinterpret_cast<const float4 *>(p));
-    o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w;
+__device__ __forceinline__ void ld_rows<float, float, 4>(const float *p, float, float (&o)[4],
+                                                         uint64_t pol) {
+    uint4 u = ld16(p, pol);
+    o[0] = __uint_as_float(u.x); o[1] = __uint_as_float(u.y);
+    o[2] = __uint_as_float(u.z); o[3] = __uint_as_float(u.w);
 }
 template <>
 __device__ __forceinline__ void ld_rows<double, double, 2>(const double *p, float,
-                                                            double (&o)[2]) {
-    double2 a = __ldg(reinterpret_cast<const double2 *>(p));
-    o[0] = a.x; o[1] = a.y;
+                                                            double (&o)[2], uint64_t pol) {
+    uint4 u = ld16(p, pol);
+    o[0] = __hiloint2double((int)u.y, (int)u.x);
+    o[1] = __hiloint2double((int)u.w, (int)u.z);
 }
 template <>
 __device__ __forceinline__ void ld_rows<float, __nv_bfloat16, 8>(const __nv_bfloat16 *p, float,
-                                                                 float (&o)[8]) {
-    uint4 u = __ldg(reinterpret_cast<const uint4 *>(p));
+                                                                 float (&o)[8], uint64_t pol) {
+    uint4 u = ld16(p, pol);
     const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&u);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -58,8 +85,8 @@ __device__ __forceinline__ void ld_rows<float, __nv_bfloat16, 8>(const __nv_bflo
 }
 template <>
 __device__ __forceinline__ void ld_rows<float, __half, 8>(const __half *p, float vinv,
-                                                          float (&o)[8]) {
-    uint4 u = __ldg(reinterpret_cast<const uint4 *>(p));
+                                                          float (&o)[8], uint64_t pol) {
+    uint4 u = ld16(p, pol);
     const __half2 *h = reinterpret_cast<const __half2 *>(&u);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -106,7 +133,7 @@ constexpr int ROWS_CB = 8;  // basis vectors loaded per batch
 // row group), batched loads.
 template <class T, class VT, int RPL>
 __device__ __forceinline__ void rows_project(const GridCtx<T, VT> &c, int ncols, const T *hs,
-                                             int64_t r, T (&t)[RPL]) {
+                                             int64_t r, T (&t)[RPL], uint64_t pol) {
 #pragma unroll
     for (int q = 0; q < RPL; ++q)
         t[q] = 0;
@@ -117,7 +144,7 @@ __device__ __forceinline__ void rows_project(const GridCtx<T, VT> &c, int ncols,
 #pragma unroll
             for (int u = 0; u < ROWS_CB; ++u) {
                 if (c0 + u < ncols)
-                    ld_rows<T, VT, RPL>(c.V + (size_t)(c0 + u) * c.ldv + r, c.vinv, v[u]);
+                    ld_rows<T, VT, RPL>(c.V + (size_t)(c0 + u) * c.ldv + r, c.vinv, v[u], pol);
                 else {
 #pragma unroll
                     for (int q = 0; q < RPL; ++q)
@@ -140,7 +167,7 @@ __device__ __forceinline__ void rows_project(const GridCtx<T, VT> &c, int ncols,
 template <class T, class VT, int RPL, int ACC>
 __device__ __forceinline__ void rows_dots(const GridCtx<T, VT> &c, int ncols, int64_t s0,
                                           const T (&wv)[4][RPL], int wid, int lane,
-                                          T (&acc)[ACC]) {
+                                          T (&acc)[ACC], uint64_t pol) {
     constexpr int RW = 32 * RPL;
     constexpr int KB = ROWS_CB / 4 > 0 ? ROWS_CB / 4 : 1;  // vectors per batch (x4 groups)
 #pragma unroll
@@ -154,7 +181,7 @@ __device__ __forceinline__ void rows_dots(const GridCtx<T, VT> &c, int ncols, in
                 for (int g = 0; g < 4; ++g) {
                     if (k0 + u < ACC && col < ncols)
                         ld_rows<T, VT, RPL>(c.V + (size_t)col * c.ldv + s0 + g * RW + lane * RPL,
-                                            c.vinv, v[u][g]);
+                                            c.vinv, v[u][g], pol);
                     else {
 #pragma unroll
                         for (int q = 0; q < RPL; ++q)
@@ -180,7 +207,7 @@ __device__ __forceinline__ void rows_dots(const GridCtx<T, VT> &c, int ncols, in
 
 template <class T, class VT, int MODE>
 __global__ void __launch_bounds__(ROWS_THREADS)
-    k_cgs_rows(GridCtx<T, VT> c, int ncols, T *part) {
+    k_cgs_rows(GridCtx<T, VT> c, int ncols, T *part, int64_t slices_per_block) {
     if (!c.ctl->active)
         return;
     constexpr int RPL = RowsCfg<VT>::RPL;
@@ -201,8 +228,16 @@ __global__ void __launch_bounds__(ROWS_THREADS)
     for (int k = 0; k < ACC; ++k)
         acc[k] = 0;
     T nsq = 0;
+    const uint64_t pol_once = l2_policy_first();
+    const uint64_t pol_keep = (MODE == 1) ? l2_policy_last() : pol_once;
+    // each block takes an equal run of consecutive slices (the host sizes the
+    // grid so the runs cover the basis with at most one short run)
     const int64_t nslices = c.ldv / SR;
-    for (int64_t sl = blockIdx.x; sl < nslices; sl += gridDim.x) {
+    const int64_t sl0 = (int64_t)blockIdx.x * slices_per_block;
+    int64_t sl1 = sl0 + slices_per_block;
+    if (sl1 > nslices)
+        sl1 = nslices;
+    for (int64_t sl = sl0; sl < sl1; ++sl) {
         const int64_t s0 = sl * SR;
         T wv[4][RPL];
         if (MODE == 0) {
@@ -221,7 +256,7 @@ __global__ void __launch_bounds__(ROWS_THREADS)
             const int64_t r = s0 + wid * RW + lane * RPL;
             T w[RPL], t[RPL];
             ld_w<T, RPL>(c.w + r, w);
-            rows_project<T, VT, RPL>(c, ncols, hs, r, t);
+            rows_project<T, VT, RPL>(c, ncols, hs, r, t, pol_keep);
 #pragma unroll
             for (int q = 0; q < RPL; ++q) {
                 w[q] = w[q] - t[q];
@@ -243,7 +278,7 @@ __global__ void __launch_bounds__(ROWS_THREADS)
             }
         }
         if (MODE <= 1)
-            rows_dots<T, VT, RPL, ACC>(c, ncols, s0, wv, wid, lane, acc);
+            rows_dots<T, VT, RPL, ACC>(c, ncols, s0, wv, wid, lane, acc, pol_once);
     }
     T *mypart = part + (size_t)blockIdx.x * PSTRIDE;
     if (MODE <= 1) {

@@ -204,7 +204,9 @@ int lanes_for(gmres_handle *h) {
 // one 512-thread block per SM resident with w's row chunk in shared memory.
 template <class T, class VT>
 bool mgs_persist_ok(gmres_handle *h) {
-    const int key = (int)sizeof(T) * 16 + (int)sizeof(VT);
+    // one entry per kernel instantiation (bfloat16 and binary16 bases have the
+    // same sizes but are different kernels with their own attributes)
+    const void *key = (const void *)k_mgs_persist<T, VT>;
     auto it = h->mgs_ok_cache.find(key);
     if (it != h->mgs_ok_cache.end())
         return it->second;
@@ -263,7 +265,7 @@ gmres_status enqueue_step(gmres_handle *h, GridCtx<T, VT> &c, int col, gmres_ort
         // one resident wave per kernel: grid = SMs x resident blocks per SM
         static int per_sm[3] = {0, 0, 0};
         if (per_sm[0] == 0) {
-            void (*fns[3])(GridCtx<T, VT>, int, T *) = {
+            void (*fns[3])(GridCtx<T, VT>, int, T *, int64_t) = {
                 k_cgs_rows<T, VT, 0>, k_cgs_rows<T, VT, 1>, k_cgs_rows<T, VT, 2>};
             for (int k = 0; k < 3; ++k) {
                 int bpsm = 0;
@@ -271,12 +273,21 @@ gmres_status enqueue_step(gmres_handle *h, GridCtx<T, VT> &c, int col, gmres_ort
                 per_sm[k] = std::max(1, std::min(bpsm, h->rows_blocks_per_sm));
             }
         }
-        const int g0 = h->nsm * per_sm[0], g1 = h->nsm * per_sm[1], g2 = h->nsm * per_sm[2];
-        k_cgs_rows<T, VT, 0><<<g0, ROWS_THREADS, 0, h->stream>>>(c, ncols, c.part);
-        k_reduce_cols<T><<<ncols + 1, 256, 0, h->stream>>>(c.part, g0, ncols, c.h1, c.ctl, 1);
-        k_cgs_rows<T, VT, 1><<<g1, ROWS_THREADS, 0, h->stream>>>(c, ncols, c.part);
-        k_reduce_cols<T><<<ncols, 256, 0, h->stream>>>(c.part, g1, ncols, c.h2, c.ctl, 0);
-        k_cgs_rows<T, VT, 2><<<g2, ROWS_THREADS, 0, h->stream>>>(c, ncols, c.part);
+        // balanced grids: k = ceil(slices / resident blocks) consecutive
+        // slices per block, grid = ceil(slices / k), one resident wave
+        const int64_t nsl = h->ldv / (ROWS_WARPS * 32 * (16 / (int64_t)sizeof(VT)));
+        int64_t kpb[3];
+        int gsz[3];
+        for (int k = 0; k < 3; ++k) {
+            const int64_t cap = (int64_t)h->nsm * per_sm[k];
+            kpb[k] = (nsl + cap - 1) / cap;
+            gsz[k] = (int)((nsl + kpb[k] - 1) / kpb[k]);
+        }
+        k_cgs_rows<T, VT, 0><<<gsz[0], ROWS_THREADS, 0, h->stream>>>(c, ncols, c.part, kpb[0]);
+        k_reduce_cols<T><<<ncols + 1, 256, 0, h->stream>>>(c.part, gsz[0], ncols, c.h1, c.ctl, 1);
+        k_cgs_rows<T, VT, 1><<<gsz[1], ROWS_THREADS, 0, h->stream>>>(c, ncols, c.part, kpb[1]);
+        k_reduce_cols<T><<<ncols, 256, 0, h->stream>>>(c.part, gsz[1], ncols, c.h2, c.ctl, 0);
+        k_cgs_rows<T, VT, 2><<<gsz[2], ROWS_THREADS, 0, h->stream>>>(c, ncols, c.part, kpb[2]);
         acct.launches[GMRES_K_ORTHO] += 5;
     } else if (ortho == GMRES_ORTHO_CGSR) {
         const int TR = cgs_choose_tr<VT>(ncols);

@@ -83,7 +83,7 @@ struct gmres_handle {
     int grid = 0;          // blocks of the reduction kernels
     int rows_blocks_per_sm = 4;  // blocks per SM of the register-streaming CGSR kernels
     int64_t mgs_chunk = 0;       // rows per block of the cooperative MGS kernel
-    std::map<int, bool> mgs_ok_cache;  // cooperative MGS feasible, per (T, VT)
+    std::map<const void *, bool> mgs_ok_cache;  // cooperative MGS feasible, per kernel
     int64_t chunk = 0;     // rows per block
     // matrix
     DevBuf rowptr, colind, vals64, vals32;
