@@ -35,9 +35,18 @@ struct gmres_batch {
     std::vector<int64_t> ws_ofs;    // padded row offset of each system's workspace
     int64_t ws_rows = 0;            // total padded rows
     std::vector<int> order;         // largest system first
+    int nlarge = 0;                 // systems solved by clusters (the first nlarge of order)
+    cudaStream_t aux = nullptr;     // stream of the cluster launch
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     DevBuf rowptr, colind, vals64, vals32;
     DevBuf V, w, r, xb, bb, sys, res, ord, queue;
 };
+
+// Systems of at least this many rows are solved by a cluster of CLUSTER_CTAS
+// thread blocks (distributed-shared-memory reductions); smaller ones by one
+// block.  Both launches run concurrently, each over its own work queue.
+constexpr int CLUSTER_MIN_ROWS = 16384;
+constexpr int CLUSTER_CTAS = 8;
 
 namespace {
 
@@ -79,7 +88,6 @@ gmres_status batch_run(gmres_batch *B, const double *db, double *dx, int m, doub
     CK(B->res.ensure(sizeof(BlockResult) * B->nsys));
     CK(cudaMemcpyAsync(B->sys.p, S.data(), sizeof(BlockSys<T, VT>) * B->nsys,
                        cudaMemcpyHostToDevice, B->stream));
-    CK(cudaMemsetAsync(B->queue.p, 0, sizeof(unsigned), B->stream));
     BlockParams P;
     P.m = m;
     P.maxiter = maxiter;
@@ -90,32 +98,76 @@ gmres_status batch_run(gmres_batch *B, const double *db, double *dx, int m, doub
     P.inner_factor = 0.5;
     P.brk = std::is_same<T, double>::value ? 1e-14 : 1e-6;
     P.nsys = B->nsys;
-    P.queue = B->queue.as<unsigned>();
-    P.order = B->ord.as<int>();
+    P.queue = nullptr;
+    P.order = nullptr;
     const int L = lanes > 0 ? lanes : pow2_lanes(B->avg_row / 2.0);
-    void (*kfn)(const BlockSys<T, VT> *, BlockParams, BlockResult *) = nullptr;
+    using KFn = void (*)(const BlockSys<T, VT> *, BlockParams, BlockResult *);
+    KFn kfn = nullptr, kcl = nullptr;
     switch (L) {
-    case 1: kfn = &k_block_solve<T, VT, 1>; break;
-    case 2: kfn = &k_block_solve<T, VT, 2>; break;
-    case 4: kfn = &k_block_solve<T, VT, 4>; break;
-    case 8: kfn = &k_block_solve<T, VT, 8>; break;
-    case 16: kfn = &k_block_solve<T, VT, 16>; break;
-    default: kfn = &k_block_solve<T, VT, 32>; break;
+    case 1: kfn = &k_block_solve<T, VT, 1>; kcl = &k_team_solve<T, VT, 1, CLUSTER_CTAS>; break;
+    case 2: kfn = &k_block_solve<T, VT, 2>; kcl = &k_team_solve<T, VT, 2, CLUSTER_CTAS>; break;
+    case 4: kfn = &k_block_solve<T, VT, 4>; kcl = &k_team_solve<T, VT, 4, CLUSTER_CTAS>; break;
+    case 8: kfn = &k_block_solve<T, VT, 8>; kcl = &k_team_solve<T, VT, 8, CLUSTER_CTAS>; break;
+    case 16: kfn = &k_block_solve<T, VT, 16>; kcl = &k_team_solve<T, VT, 16, CLUSTER_CTAS>; break;
+    default: kfn = &k_block_solve<T, VT, 32>; kcl = &k_team_solve<T, VT, 32, CLUSTER_CTAS>; break;
     }
     const size_t smem = block_smem_bytes<T>(m);
     CK(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    CK(cudaFuncSetAttribute(kcl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int threads = 256;
     int per_sm = 0;
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, threads, smem));
     per_sm = std::max(1, per_sm);
-    const int grid = std::min<int64_t>(B->nsys, (int64_t)B->nsm * per_sm);
+    const int nsmall = B->nsys - B->nlarge;
+    unsigned *q = B->queue.as<unsigned>();
+    const int *ord = B->ord.as<int>();
+    // cluster launch for the large systems (the first nlarge entries of order)
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    int ncl = 0;
+    if (B->nlarge > 0) {
+        cfg.blockDim = dim3(threads);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = B->aux;
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = CLUSTER_CTAS;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        cfg.gridDim = dim3(CLUSTER_CTAS * B->nsm);
+        CK(cudaOccupancyMaxActiveClusters(&ncl, kcl, &cfg));
+        ncl = std::max(1, std::min(ncl, B->nlarge));
+        cfg.gridDim = dim3(CLUSTER_CTAS * ncl);
+    }
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
+    CK(cudaMemsetAsync(q, 0, 2 * sizeof(unsigned), B->stream));
     CK(cudaEventRecord(e0, B->stream));
-    kfn<<<grid, threads, smem, B->stream>>>(B->sys.as<BlockSys<T, VT>>(), P,
-                                             B->res.as<BlockResult>());
-    CKL();
+    if (B->nlarge > 0) {
+        BlockParams PL = P;
+        PL.nsys = B->nlarge;
+        PL.queue = q + 1;
+        PL.order = ord;
+        CK(cudaEventRecord(B->ev_fork, B->stream));
+        CK(cudaStreamWaitEvent(B->aux, B->ev_fork, 0));
+        CK(cudaLaunchKernelEx(&cfg, kcl, (const BlockSys<T, VT> *)B->sys.as<BlockSys<T, VT>>(),
+                              PL, B->res.as<BlockResult>()));
+        CK(cudaEventRecord(B->ev_join, B->aux));
+    }
+    if (nsmall > 0) {
+        BlockParams PS = P;
+        PS.nsys = nsmall;
+        PS.queue = q;
+        PS.order = ord + B->nlarge;
+        const int grid = std::min<int64_t>(nsmall, (int64_t)B->nsm * per_sm);
+        kfn<<<grid, threads, smem, B->stream>>>(B->sys.as<BlockSys<T, VT>>(), PS,
+                                                 B->res.as<BlockResult>());
+        CKL();
+    }
+    if (B->nlarge > 0)
+        CK(cudaStreamWaitEvent(B->stream, B->ev_join, 0));
     CK(cudaEventRecord(e1, B->stream));
     std::vector<BlockResult> R(B->nsys);
     CK(cudaMemcpyAsync(R.data(), B->res.p, sizeof(BlockResult) * B->nsys,
@@ -162,8 +214,8 @@ gmres_status batch_run(gmres_batch *B, const double *db, double *dx, int m, doub
         info->converged = all_conv;
         info->kernel_ms[GMRES_K_BLOCK] = ms;
         info->kernel_bytes[GMRES_K_BLOCK] = bytes;
-        info->kernel_launches[GMRES_K_BLOCK] = 1;
-        info->launches = 1;
+        info->kernel_launches[GMRES_K_BLOCK] = (B->nlarge > 0) + (B->nsys - B->nlarge > 0);
+        info->launches = info->kernel_launches[GMRES_K_BLOCK];
         info->path = GMRES_PATH_BLOCK;
     }
     return worst;
@@ -232,6 +284,14 @@ gmres_status gmres_batch_create(gmres_batch_t *out, int32_t nsys, const int64_t 
     std::stable_sort(B->order.begin(), B->order.end(), [&](int a, int b) {
         return (sys_ptr[a + 1] - sys_ptr[a]) > (sys_ptr[b + 1] - sys_ptr[b]);
     });
+    B->nlarge = 0;
+    for (int i = 0; i < nsys; ++i)
+        if (sys_ptr[B->order[i] + 1] - sys_ptr[B->order[i]] >= CLUSTER_MIN_ROWS)
+            B->nlarge = i + 1;
+    if (cudaStreamCreateWithFlags(&B->aux, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&B->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&B->ev_join, cudaEventDisableTiming) != cudaSuccess)
+        return fail(GMRES_ERR_CUDA);
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&B->nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
@@ -267,9 +327,17 @@ void gmres_batch_destroy(gmres_batch_t B) {
         cudaStreamSynchronize(B->stream);
     else
         cudaDeviceSynchronize();
+    if (B->aux)
+        cudaStreamSynchronize(B->aux);
     for (DevBuf *b : {&B->rowptr, &B->colind, &B->vals64, &B->vals32, &B->V, &B->w, &B->r,
                       &B->xb, &B->bb, &B->sys, &B->res, &B->ord, &B->queue})
         b->release();
+    if (B->ev_fork)
+        cudaEventDestroy(B->ev_fork);
+    if (B->ev_join)
+        cudaEventDestroy(B->ev_join);
+    if (B->aux)
+        cudaStreamDestroy(B->aux);
     delete B;
 }
 

@@ -138,13 +138,19 @@ __device__ __forceinline__ void block_spmv(const int *__restrict__ rowptr,
     }
 }
 
-template <class T, class VT, int L>
-__device__ void block_solve_one(const BlockSys<T, VT> &S, const BlockParams &P, BlockResult *res,
-                                unsigned char *smem_raw) {
+template <class T, class VT, int L, int CS>
+__device__ void team_solve_one(const BlockSys<T, VT> &S, const BlockParams &P, BlockResult *res,
+                               unsigned char *smem_raw) {
     const int n = S.n, m = P.m, ld = m + 1;
     const int tid = threadIdx.x, nth = blockDim.x;
+    // this CTA's rows
+    const int chunk = (n + CS - 1) / CS;
+    const int rb = Team<CS>::rank() * chunk;
+    const int re = rb + chunk < n ? rb + chunk : n;
     double *redd = reinterpret_cast<double *>(smem_raw);       // 32 (first: 8-byte aligned)
-    T *H = reinterpret_cast<T *>(smem_raw + 32 * sizeof(double));  // ld x m (rotated)
+    double *slotd = redd + 32;                                 // 2 * TEAM_KMAX
+    double *bcd = slotd + 2 * TEAM_KMAX;                       // TEAM_KMAX
+    T *H = reinterpret_cast<T *>(bcd + TEAM_KMAX);             // ld x m (rotated)
     T *s = H + (size_t)ld * m;                   // m + 1
     T *cs = s + (m + 1);                         // m
     T *sn = cs + m;                              // m
@@ -152,13 +158,16 @@ __device__ void block_solve_one(const BlockSys<T, VT> &S, const BlockParams &P, 
     T *hc = y + m;                               // MMAX + 2 (current column)
     T *hc2 = hc + (MMAX + 2);                    // MMAX + 2 (second CGS pass)
     T *red = hc2 + (MMAX + 2);                   // 8 * 32
+    T *slot = red + 8 * 32;                      // 2 * TEAM_KMAX
+    T *bc = slot + 2 * TEAM_KMAX;                // TEAM_KMAX
     __shared__ int s_flag;
+    int bufd = 0, buft = 0;
 
     // ||b||
     double bb = 0;
-    for (int i = tid; i < n; i += nth)
+    for (int i = rb + tid; i < re; i += nth)
         bb += S.b[i] * S.b[i];
-    double bnorm = sqrt(block_sum1(bb, redd));
+    double bnorm = sqrt(team_sum1<double, CS>(bb, redd, slotd, bcd, &bufd));
     BlockResult out;
     out.iters = 0;
     out.restarts = 0;
@@ -168,12 +177,13 @@ __device__ void block_solve_one(const BlockSys<T, VT> &S, const BlockParams &P, 
     out.relres = 0;
     out.bnorm = bnorm;
     if (!(bnorm > 0)) {
-        for (int i = tid; i < n; i += nth)
+        for (int i = rb + tid; i < re; i += nth)
             S.x[i] = 0.0;
         out.converged = isfinite(bnorm) ? 1 : 0;
         out.status = isfinite(bnorm) ? 0 : -3;
-        if (tid == 0)
+        if (tid == 0 && Team<CS>::rank() == 0)
             *res = out;
+        Team<CS>::sync();
         return;
     }
     const double tol_abs = P.tol * bnorm;
@@ -182,17 +192,18 @@ __device__ void block_solve_one(const BlockSys<T, VT> &S, const BlockParams &P, 
     int cycle_len = m;
 
     for (;;) {
+        // every CTA's x rows are final before the residual gathers them
+        Team<CS>::sync();
         // z = b - A x (binary64), r = fl(z), ||z||, ||r||.
-        double ss = 0;
+        double acc2[2] = {0, 0};  // ||z||^2, non-finite count
         T sst = 0;
-        int bad = 0;
         {
             const int lane = tid & 31, wid = tid >> 5, nw = nth >> 5;
             const int G = 32 / L, gl = lane % L, gi = lane / L;
-            for (int base = wid * G; base < n; base += nw * G) {
+            for (int base = rb + wid * G; base < re; base += nw * G) {
                 int row = base + gi;
                 double acc = 0;
-                if (row < n) {
+                if (row < re) {
                     int beg = S.rowptr[row], end = S.rowptr[row + 1];
                     for (int k = beg + gl; k < end; k += L)
                         acc += S.a64[k] * S.x[S.colind[k]];
@@ -200,19 +211,20 @@ __device__ void block_solve_one(const BlockSys<T, VT> &S, const BlockParams &P, 
 #pragma unroll
                 for (int off = L / 2; off > 0; off >>= 1)
                     acc += __shfl_xor_sync(0xffffffffu, acc, off);
-                if (row < n && gl == 0) {
+                if (row < re && gl == 0) {
                     double zi = S.b[row] - acc;
                     T ri = (T)zi;
                     S.r[row] = ri;
-                    ss += zi * zi;
+                    acc2[0] += zi * zi;
                     sst += ri * ri;
-                    bad |= !isfinite(zi);
+                    acc2[1] += isfinite(zi) ? 0.0 : 1.0;
                 }
             }
         }
-        double rn = sqrt(block_sum1(ss, redd));
-        T beta = wsqrt(block_sum1(sst, red));
-        bad = __syncthreads_or(bad);
+        team_sum<double, 2, CS>(acc2, redd, slotd, bcd, &bufd);
+        double rn = sqrt(acc2[0]);
+        T beta = wsqrt(team_sum1<T, CS>(sst, red, slot, bc, &buft));
+        const bool bad = acc2[1] != 0.0;
         out.relres = rn / bnorm;
         if (bad || !isfinite(rn)) {
             out.status = -3;
@@ -235,32 +247,33 @@ __device__ void block_solve_one(const BlockSys<T, VT> &S, const BlockParams &P, 
         const double tau = (P.repeat_first && out.restarts > 0) ? 0.0 : P.tau;
 
         // v_1 = r / beta, s = beta e_1
-        for (int i = tid; i < n; i += nth)
+        for (int i = rb + tid; i < re; i += nth)
             Basis<VT>::st(S.V + i, S.r[i] / beta, S.vscale);
         for (int i = tid; i <= m; i += nth)
             s[i] = (i == 0) ? beta : T(0);
-        __syncthreads();
+        Team<CS>::sync();
 
         int j = 0;
+        int cyc_bad = 0;
         for (;;) {
             const int c = j;
             const VT *vj = S.V + (size_t)c * S.ldv;
-            block_spmv<T, VT, L>(S.rowptr, S.colind, S.a, vj, S.vinv, S.w, n);
+            block_spmv<T, VT, L>(S.rowptr, S.colind, S.a, vj, S.vinv, S.w, rb, re);
             __syncthreads();
             // ||A v_j|| (breakdown reference)
             T w0 = 0;
-            for (int i = tid; i < n; i += nth)
+            for (int i = rb + tid; i < re; i += nth)
                 w0 += S.w[i] * S.w[i];
-            T wnorm0 = wsqrt(block_sum1(w0, red));
+            T wnorm0 = wsqrt(team_sum1<T, CS>(w0, red, slot, bc, &buft));
             if (P.ortho == 0) {
                 // MGS: h_i = w . v_i, w <- w - h_i v_i, one column at a time
                 for (int i = 0; i <= c; ++i) {
                     const VT *vi = S.V + (size_t)i * S.ldv;
                     T d = 0;
-                    for (int r = tid; r < n; r += nth)
+                    for (int r = rb + tid; r < re; r += nth)
                         d += S.w[r] * Basis<VT>::ld(vi + r, S.vinv);
-                    T hi = block_sum1(d, red);
-                    for (int r = tid; r < n; r += nth)
+                    T hi = team_sum1<T, CS>(d, red, slot, bc, &buft);
+                    for (int r = rb + tid; r < re; r += nth)
                         S.w[r] = S.w[r] - hi * Basis<VT>::ld(vi + r, S.vinv);
                     if (tid == 0)
                         hc[i] = hi;
@@ -274,7 +287,7 @@ __device__ void block_solve_one(const BlockSys<T, VT> &S, const BlockParams &P, 
 #pragma unroll
                         for (int k = 0; k < 8; ++k)
                             acc[k] = 0;
-                        for (int r = tid; r < n; r += nth) {
+                        for (int r = rb + tid; r < re; r += nth) {
                             T wr = S.w[r];
 #pragma unroll
                             for (int k = 0; k < 8; ++k)
@@ -282,7 +295,7 @@ __device__ void block_solve_one(const BlockSys<T, VT> &S, const BlockParams &P, 
                                     acc[k] += Basis<VT>::ld(S.V + (size_t)(c0 + k) * S.ldv + r,
                                                             S.vinv) * wr;
                         }
-                        block_sum<T, 8>(acc, red);
+                        team_sum<T, 8, CS>(acc, red, slot, bc, &buft);
                         if (tid == 0) {
                             T *g = pass ? hc2 : hc;
 #pragma unroll
@@ -293,7 +306,7 @@ __device__ void block_solve_one(const BlockSys<T, VT> &S, const BlockParams &P, 
                     }
                     __syncthreads();
                     // w <- w - V g  (g = this pass's projections)
-                    for (int r = tid; r < n; r += nth) {
+                    for (int r = rb + tid; r < re; r += nth) {
                         T t = 0;
                         for (int i = 0; i <= c; ++i) {
                             T g = pass ? hc2[i] : hc[i];
@@ -309,10 +322,11 @@ __device__ void block_solve_one(const BlockSys<T, VT> &S, const BlockParams &P, 
             }
             // h_{j+1,j} = ||w||
             T nsq = 0;
-            for (int r = tid; r < n; r += nth)
+            for (int r = rb + tid; r < re; r += nth)
                 nsq += S.w[r] * S.w[r];
-            T hnext = wsqrt(block_sum1(nsq, red));
-            // Givens step (thread 0) and restart test
+            T hnext = wsqrt(team_sum1<T, CS>(nsq, red, slot, bc, &buft));
+            // Givens step (thread 0 of every CTA, on identical data) and the
+            // restart test
             if (tid == 0) {
                 T *col = H + (size_t)c * ld;
                 for (int i = 0; i <= c; ++i)
@@ -351,18 +365,18 @@ __device__ void block_solve_one(const BlockSys<T, VT> &S, const BlockParams &P, 
             const int flag = s_flag;
             j = c + 1;
             if (flag & 4) {
-                bad = 1;
+                cyc_bad = 1;
                 break;
             }
             if (flag & 1)
                 break;
-            // v_{j+1} = w / h_{j+1,j}
+            // v_{j+1} = w / h_{j+1,j}; every CTA's rows before the next SpMV
             VT *vn = S.V + (size_t)(c + 1) * S.ldv;
-            for (int r = tid; r < n; r += nth)
+            for (int r = rb + tid; r < re; r += nth)
                 Basis<VT>::st(vn + r, S.w[r] / hnext, S.vscale);
-            __syncthreads();
+            Team<CS>::sync();
         }
-        if (bad) {
+        if (cyc_bad) {
             out.status = -3;
             break;
         }
@@ -377,7 +391,7 @@ __device__ void block_solve_one(const BlockSys<T, VT> &S, const BlockParams &P, 
             }
         }
         __syncthreads();
-        for (int r = tid; r < n; r += nth) {
+        for (int r = rb + tid; r < re; r += nth) {
             T u = 0;
             for (int i = 0; i < j; ++i)
                 u += Basis<VT>::ld(S.V + (size_t)i * S.ldv + r, S.vinv) * y[i];
@@ -392,11 +406,45 @@ __device__ void block_solve_one(const BlockSys<T, VT> &S, const BlockParams &P, 
                 cycle_len = j;
         }
     }
-    if (tid == 0)
+    if (tid == 0 && Team<CS>::rank() == 0)
         *res = out;
+    Team<CS>::sync();
 }
 
-// Persistent grid over a work queue of systems (largest first).
+template <class T, class VT, int L>
+__device__ void block_solve_one(const BlockSys<T, VT> &S, const BlockParams &P, BlockResult *res,
+                                unsigned char *smem_raw) {
+    team_solve_one<T, VT, L, 1>(S, P, res, smem_raw);
+}
+
+// Persistent grid over a work queue of systems (largest first); one team
+// (block or cluster) per system.
+template <class T, class VT, int L, int CS>
+__global__ void __launch_bounds__(1024) k_team_solve(const BlockSys<T, VT> *sys, BlockParams P,
+                                                     BlockResult *res) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int s_idx;
+    for (;;) {
+        if (threadIdx.x == 0 && Team<CS>::rank() == 0) {
+            unsigned k = atomicAdd(P.queue, 1u);
+            s_idx = (k < (unsigned)P.nsys) ? (P.order ? P.order[k] : (int)k) : -1;
+        }
+        Team<CS>::sync();
+        int idx;
+        if (CS == 1) {
+            idx = s_idx;
+        } else {
+            cg::cluster_group cl = cg::this_cluster();
+            idx = *cl.map_shared_rank(&s_idx, 0);
+        }
+        Team<CS>::sync();
+        if (idx < 0)
+            return;
+        BlockSys<T, VT> S = sys[idx];
+        team_solve_one<T, VT, L, CS>(S, P, res + idx, smem_raw);
+    }
+}
+
 template <class T, class VT, int L>
 __global__ void __launch_bounds__(1024) k_block_solve(const BlockSys<T, VT> *sys, BlockParams P,
                                                       BlockResult *res) {
@@ -418,11 +466,12 @@ __global__ void __launch_bounds__(1024) k_block_solve(const BlockSys<T, VT> *sys
     }
 }
 
-// Shared-memory bytes of the block solver for restart length m.
+// Shared-memory bytes of the block / team solver for restart length m.
 template <class T>
 inline size_t block_smem_bytes(int m) {
-    size_t nt = (size_t)(m + 1) * m + (m + 1) + 3 * (size_t)m + 2 * (MMAX + 2) + 8 * 32;
-    return nt * sizeof(T) + 32 * sizeof(double) + 64;
+    size_t nt = (size_t)(m + 1) * m + (m + 1) + 3 * (size_t)m + 2 * (MMAX + 2) + 8 * 32 +
+                3 * TEAM_KMAX;
+    return nt * sizeof(T) + (32 + 3 * TEAM_KMAX) * sizeof(double) + 64;
 }
 
 }  // namespace gmres

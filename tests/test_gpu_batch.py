@@ -80,3 +80,33 @@ def test_batch_rejects_cross_system_columns(gpulib):
     with pytest.raises(G.GmresError) as e:
         G.gmres_batch_create(3, sys_ptr, rp, ci, va)
     assert e.value.status == G.ERR_ARG
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "mixed_fp16"])
+@pytest.mark.parametrize("ortho", ["mgs", "cgsr"])
+def test_batch_cluster_path(prec, ortho, gpulib):
+    """Systems of >= 16384 rows go to thread-block clusters (reductions over
+    distributed shared memory) while the small ones run one block each, in
+    a concurrent launch; both kinds must converge and match the oracle."""
+    systems = [(I.convdiff2d(130, 130, pe=20.0), None), (I.convdiff2d(128, 160, pe=5.0), None)]
+    systems += I.batched_convdiff2d(count=5, nmin=40, nmax=2000, seed=11)
+    out = []
+    for k, (A, b) in enumerate(systems):
+        out.append((A, I.rhs_ones_noise(A, 1e-3, 300 + k) if b is None else b))
+    sys_ptr, rp, ci, va, b = G.pack_batch(out)
+    nsys = len(out)
+    h = G.gmres_batch_create(nsys, sys_ptr, rp, ci, va)
+    x = np.zeros(len(b))
+    st, res, info = G.gmres_batch_solve(h, b, x, 30, 1e-10, G.ORTHOS[ortho],
+                                        G.PRECISIONS[prec], 20000, nsys=nsys)
+    G.gmres_batch_destroy(h)
+    assert st == G.OK, [(r.status, r.relres) for r in res]
+    assert info.kernel_launches[G.K_BLOCK] == 2
+    for i, (A, bi) in enumerate(out):
+        xi = x[sys_ptr[i]:sys_ptr[i + 1]]
+        rel = O.residual_norm(A, bi, xi) / np.linalg.norm(bi)
+        assert rel <= 1e-10, (i, rel)
+        assert res[i].converged == 1 and abs(res[i].relres - rel) <= 1e-3 * rel + 1e-14
+        xo, _ = O.gmres(A, bi, m=30, tol=1e-13, ortho=O.CGSR, prec=O.FP64, maxiter=40000)
+        err = np.linalg.norm(xi - xo) / np.linalg.norm(xo)
+        assert err <= 1e-6, (i, err)
