@@ -25,6 +25,7 @@ _lock = threading.Lock()
 _lib = None
 
 MGS, CGSR = 0, 1
+ORTH_OFF, ORTH_SPECTRAL, ORTH_FROBENIUS = 0, 1, 2
 FP64, MIXED, MIXED_BF16, MIXED_FP16, ALL_FP32 = 0, 1, 2, 3, 4
 
 _i32p = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
@@ -40,10 +41,29 @@ class Opts(ctypes.Structure):
         ("prec", ctypes.c_int32),
         ("maxiter", ctypes.c_int32),
         ("repeat_first", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("stall_window", ctypes.c_int32),
         ("tol", ctypes.c_double),
         ("tau", ctypes.c_double),
         ("inner_factor", ctypes.c_double),
+        ("stall_factor", ctypes.c_double),
+        ("orth_threshold", ctypes.c_double),
+        ("orth_norm", ctypes.c_int32),
+        ("orth_iters", ctypes.c_int32),
+    ]
+
+
+class Restart(ctypes.Structure):
+    """Mirror of ``orc_restart`` (see gmres_oracle.h)."""
+
+    _fields_ = [
+        ("tau", ctypes.c_double),
+        ("inner_abs", ctypes.c_double),
+        ("stall_factor", ctypes.c_double),
+        ("orth_threshold", ctypes.c_double),
+        ("stall_window", ctypes.c_int32),
+        ("orth_norm", ctypes.c_int32),
+        ("orth_iters", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
 
 
@@ -94,6 +114,15 @@ def _bind(L):
                                     ctypes.POINTER(ctypes.c_int32),
                                     ctypes.POINTER(ctypes.c_int32)]
     L.orc_arnoldi_cycle.restype = ctypes.c_int
+    L.orc_arnoldi_cycle_ex.argtypes = [ctypes.c_int32, _i32p, _i32p, _f64p, _f64p,
+                                       ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                       ctypes.c_int32, ctypes.POINTER(Restart),
+                                       vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp,
+                                       ctypes.POINTER(ctypes.c_int32),
+                                       ctypes.POINTER(ctypes.c_int32)]
+    L.orc_arnoldi_cycle_ex.restype = ctypes.c_int
+    L.orc_s_norm2.argtypes = [ctypes.c_int32, _f64p, ctypes.c_int32, ctypes.c_int32]
+    L.orc_s_norm2.restype = ctypes.c_double
     L.orc_gmres.argtypes = [ctypes.c_int32, _i32p, _i32p, _f64p, _f64p, _f64p,
                             ctypes.POINTER(Opts), vp, vp, vp, ctypes.POINTER(Info), vp, vp]
     L.orc_gmres.restype = ctypes.c_int
@@ -192,11 +221,14 @@ def round_basis(v, prec, n):
 
 
 def arnoldi_cycle(A, r0, m, ortho=CGSR, prec=FP64, kmax=None, tau=0.0, inner_abs=0.0, M=None,
-                  export_basis=True):
+                  export_basis=True, stall_factor=0.0, stall_window=0, orth_norm=ORTH_OFF,
+                  orth_threshold=1.0, orth_iters=10):
     """One restart cycle from residual r0; returns a dict of its quantities.
 
     V is (m+1, n) (row i = basis vector i), Hbar/H are (m+1, m), the first ``j``
-    columns valid.  ``export_basis=False`` skips copying V out (V is None)."""
+    columns valid.  ``export_basis=False`` skips copying V out (V is None).
+    ``orth`` holds ||S_k|| after each inner iteration when ``orth_norm`` is
+    set (third and fourth restart strategies of Sec. 3: stall_*, orth_*)."""
     rp, ci, va = _csr(A)
     n = len(rp) - 1
     kmax = m if kmax is None else kmax
@@ -218,16 +250,30 @@ def arnoldi_cycle(A, r0, m, ortho=CGSR, prec=FP64, kmax=None, tau=0.0, inner_abs
     else:
         keep = None
         margs = (None, None, None)
-    rc = _L().orc_arnoldi_cycle(n, rp, ci, va, np.ascontiguousarray(r0, np.float64), m, kmax,
-                                 ortho, prec, tau, inner_abs, *margs, _ptr(V), _ptr(Hb), _ptr(H),
-                                 _ptr(s), _ptr(cs), _ptr(sn), _ptr(y), _ptr(u), _ptr(arn),
-                                 ctypes.byref(j), ctypes.byref(bd))
+    rs = Restart()
+    rs.tau, rs.inner_abs = tau, inner_abs
+    rs.stall_factor = stall_factor
+    rs.stall_window = stall_window if stall_window > 0 else (m + 19) // 20
+    rs.orth_norm, rs.orth_threshold, rs.orth_iters = orth_norm, orth_threshold, orth_iters
+    orth = np.zeros(m)
+    rc = _L().orc_arnoldi_cycle_ex(n, rp, ci, va, np.ascontiguousarray(r0, np.float64), m, kmax,
+                                    ortho, prec, ctypes.byref(rs), *margs, _ptr(V), _ptr(Hb),
+                                    _ptr(H), _ptr(s), _ptr(cs), _ptr(sn), _ptr(y), _ptr(u),
+                                    _ptr(arn), _ptr(orth), ctypes.byref(j), ctypes.byref(bd))
     del keep
     if rc:
         raise ValueError("orc_arnoldi_cycle failed: %d" % rc)
     jj = j.value
     return dict(V=V, Hbar=Hb.T.copy(), H=H.T.copy(), s=s, cs=cs, sn=sn, y=y, u=u, arn=arn, j=jj,
-                breakdown=bool(bd.value))
+                breakdown=bool(bd.value), orth=orth)
+
+
+def s_norm2(S, iters=10):
+    """||S||_2 estimate of a strictly upper triangular S by the power method
+    the fourth restart strategy uses (Sec. 3; 10 iterations in Sec. 4.1)."""
+    S = np.asfortranarray(S, dtype=np.float64)
+    k = S.shape[0]
+    return _L().orc_s_norm2(k, S.ravel(order="F"), k, iters)
 
 
 def default_tau(prec):
@@ -239,8 +285,13 @@ def default_tau(prec):
 
 
 def gmres(A, b, x0=None, m=30, tol=1e-10, ortho=CGSR, prec=FP64, maxiter=10000, tau=None,
-          repeat_first=None, inner_factor=0.5, M=None, history=False):
-    """Restarted GMRES(m) (Algorithm 1).  Returns (x, info dict)."""
+          repeat_first=None, inner_factor=0.5, M=None, history=False, stall_factor=0.0,
+          stall_window=0, orth_norm=ORTH_OFF, orth_threshold=1.0, orth_iters=10):
+    """Restarted GMRES(m) (Algorithm 1).  Returns (x, info dict).
+
+    Restart strategies (Sec. 3): repeat_first (first), tau (second),
+    stall_factor/stall_window (third; window 0 = ceil(0.05 m)), orth_norm /
+    orth_threshold / orth_iters (fourth, loss of orthogonality via ||S_k||)."""
     rp, ci, va = _csr(A)
     n = len(rp) - 1
     b = np.ascontiguousarray(b, dtype=np.float64)
@@ -251,6 +302,8 @@ def gmres(A, b, x0=None, m=30, tol=1e-10, ortho=CGSR, prec=FP64, maxiter=10000, 
     o.tol = tol
     o.tau = default_tau(prec) if tau is None else tau
     o.inner_factor = inner_factor
+    o.stall_factor, o.stall_window = stall_factor, stall_window
+    o.orth_norm, o.orth_threshold, o.orth_iters = orth_norm, orth_threshold, orth_iters
     info = Info()
     arn = np.zeros(max(maxiter, 1)) if history else None
     cyc = np.zeros(maxiter + 2) if history else None

@@ -97,6 +97,58 @@ void orc_round_basis(int32_t count, const double *in, double *out, int32_t prec,
         out[i] = orc_store(in[i], prec, n);
 }
 
+/* ||S||_2 of a strictly upper triangular k x k S (column-major, leading
+ * dimension ld) by the power method on S^T S (Sec. 3, fourth strategy; Sec.
+ * 4.1 runs 10 iterations): x_0 has equal entries, x_t = S^T S x_{t-1}
+ * normalised, and the estimate is ||S x_iters||. */
+double orc_s_norm2(int32_t k, const double *S, int32_t ld, int32_t iters)
+{
+    if (k < 2)
+        return 0.0;
+    double *x = (double *)malloc(sizeof(double) * (size_t)k);
+    double *yv = (double *)malloc(sizeof(double) * (size_t)k);
+    if (!x || !yv) {
+        free(x); free(yv);
+        return NAN;
+    }
+    for (int32_t i = 0; i < k; ++i)
+        x[i] = 1.0 / sqrt((double)k);
+    for (int32_t t = 0; t < iters; ++t) {
+        /* y = S x: y_i = sum over l > i of S_il x_l */
+        for (int32_t i = 0; i < k; ++i) {
+            double acc = 0;
+            for (int32_t l = i + 1; l < k; ++l)
+                acc += S[(size_t)l * ld + i] * x[l];
+            yv[i] = acc;
+        }
+        /* x = S^T y: x_l = sum over i < l of S_il y_i, then normalise */
+        double nn = 0;
+        for (int32_t l = 0; l < k; ++l) {
+            double acc = 0;
+            for (int32_t i = 0; i < l; ++i)
+                acc += S[(size_t)l * ld + i] * yv[i];
+            x[l] = acc;
+            nn += acc * acc;
+        }
+        nn = sqrt(nn);
+        if (nn == 0) {
+            free(x); free(yv);
+            return 0.0;
+        }
+        for (int32_t l = 0; l < k; ++l)
+            x[l] /= nn;
+    }
+    double ss = 0;
+    for (int32_t i = 0; i < k; ++i) {
+        double acc = 0;
+        for (int32_t l = i + 1; l < k; ++l)
+            acc += S[(size_t)l * ld + i] * x[l];
+        ss += acc * acc;
+    }
+    free(x); free(yv);
+    return sqrt(ss);
+}
+
 /* ---------------------------------------------------------------------------
  * The restart cycle in binary64 and in binary32.
  * ------------------------------------------------------------------------- */
@@ -237,10 +289,10 @@ static void export_vec(double *dst, const void *src, size_t count, int is_f32)
 /* Run one cycle in the precision prec selects, from a binary64 residual r0. */
 static int run_cycle(int32_t n, const int32_t *rowptr, const int32_t *colind, const double *vals,
                      const double *r0, int32_t m, int32_t kmax, int32_t ortho, int32_t prec,
-                     double tau, double inner_abs,
+                     const orc_restart *rs,
                      const int32_t *pm_rowptr, const int32_t *pm_colind, const double *pm_vals,
                      double *V, double *Hb, double *H, double *s, double *cs, double *sn,
-                     double *y, double *u, double *arn, int32_t *jout, int32_t *bd)
+                     double *y, double *u, double *arn, double *orth, int32_t *jout, int32_t *bd)
 {
     const int is_f32 = (prec != ORC_FP64);
     const size_t el = is_f32 ? sizeof(float) : sizeof(double);
@@ -258,20 +310,21 @@ static int run_cycle(int32_t n, const int32_t *rowptr, const int32_t *colind, co
             r[i] = (float)r0[i];
         for (int32_t k = 0; k < pnnz; ++k)
             pm[k] = (float)pm_vals[k];
-        rc = cycle_f32(n, rowptr, colind, a, r, m, kmax, ortho, prec, tau, inner_abs,
+        rc = cycle_f32(n, rowptr, colind, a, r, m, kmax, ortho, prec, rs,
                        pm_rowptr, pm_colind, pm_vals ? pm : NULL,
                        (float *)c.V, (float *)c.Hb, (float *)c.H, (float *)c.s,
-                       (float *)c.cs, (float *)c.sn, (float *)c.y, (float *)c.u, arn, jout, bd);
+                       (float *)c.cs, (float *)c.sn, (float *)c.y, (float *)c.u, arn, orth, jout,
+                       bd);
     } else {
         memcpy(c.a, vals, sizeof(double) * (size_t)nnz);
         memcpy(c.r0, r0, sizeof(double) * (size_t)n);
         if (pm_vals)
             memcpy(c.pm, pm_vals, sizeof(double) * (size_t)pnnz);
         rc = cycle_f64(n, rowptr, colind, (double *)c.a, (double *)c.r0, m, kmax, ortho, prec,
-                       tau, inner_abs, pm_rowptr, pm_colind, pm_vals ? (double *)c.pm : NULL,
+                       rs, pm_rowptr, pm_colind, pm_vals ? (double *)c.pm : NULL,
                        (double *)c.V, (double *)c.Hb, (double *)c.H, (double *)c.s,
-                       (double *)c.cs, (double *)c.sn, (double *)c.y, (double *)c.u, arn, jout,
-                       bd);
+                       (double *)c.cs, (double *)c.sn, (double *)c.y, (double *)c.u, arn, orth,
+                       jout, bd);
     }
     if (rc == 0) {
         export_vec(V, c.V, (size_t)(m + 1) * n, is_f32);
@@ -287,6 +340,40 @@ static int run_cycle(int32_t n, const int32_t *rowptr, const int32_t *colind, co
     return rc;
 }
 
+static int restart_ok(const orc_restart *rs)
+{
+    return rs && rs->tau >= 0 && rs->inner_abs >= 0 && rs->stall_factor >= 0 &&
+           (rs->stall_factor == 0 || rs->stall_window >= 1) && rs->orth_norm >= ORC_ORTH_OFF &&
+           rs->orth_norm <= ORC_ORTH_FROBENIUS &&
+           (rs->orth_norm != ORC_ORTH_SPECTRAL || rs->orth_iters >= 1);
+}
+
+int orc_arnoldi_cycle_ex(int32_t n, const int32_t *rowptr, const int32_t *colind,
+                         const double *vals, const double *r0, int32_t m, int32_t kmax,
+                         int32_t ortho, int32_t prec, const orc_restart *rs,
+                         const int32_t *pm_rowptr, const int32_t *pm_colind,
+                         const double *pm_vals, double *V, double *Hbar, double *Hrot, double *s,
+                         double *cs, double *sn, double *y, double *u, double *arn, double *orth,
+                         int32_t *jout, int32_t *breakdown)
+{
+    if (n <= 0 || m < 1 || kmax < 1 || kmax > m || (ortho != ORC_MGS && ortho != ORC_CGSR) ||
+        prec < ORC_FP64 || prec > ORC_ALL_FP32 || !csr_ok(n, rowptr, colind) ||
+        !restart_ok(rs))
+        return -1;
+    if (pm_vals && !csr_ok(n, pm_rowptr, pm_colind))
+        return -1;
+    if (orth)
+        memset(orth, 0, sizeof(double) * (size_t)m);
+    int32_t j = 0, bd = 0;
+    int rc = run_cycle(n, rowptr, colind, vals, r0, m, kmax, ortho, prec, rs, pm_rowptr,
+                       pm_colind, pm_vals, V, Hbar, Hrot, s, cs, sn, y, u, arn, orth, &j, &bd);
+    if (jout)
+        *jout = j;
+    if (breakdown)
+        *breakdown = bd;
+    return rc;
+}
+
 int orc_arnoldi_cycle(int32_t n, const int32_t *rowptr, const int32_t *colind, const double *vals,
                       const double *r0, int32_t m, int32_t kmax, int32_t ortho, int32_t prec,
                       double tau, double inner_abs,
@@ -294,20 +381,13 @@ int orc_arnoldi_cycle(int32_t n, const int32_t *rowptr, const int32_t *colind, c
                       double *V, double *Hbar, double *Hrot, double *s, double *cs, double *sn,
                       double *y, double *u, double *arn, int32_t *jout, int32_t *breakdown)
 {
-    if (n <= 0 || m < 1 || kmax < 1 || kmax > m || (ortho != ORC_MGS && ortho != ORC_CGSR) ||
-        prec < ORC_FP64 || prec > ORC_ALL_FP32 || !csr_ok(n, rowptr, colind))
-        return -1;
-    if (pm_vals && !csr_ok(n, pm_rowptr, pm_colind))
-        return -1;
-    int32_t j = 0, bd = 0;
-    int rc = run_cycle(n, rowptr, colind, vals, r0, m, kmax, ortho, prec, tau, inner_abs,
-                       pm_rowptr, pm_colind, pm_vals, V, Hbar, Hrot, s, cs, sn, y, u, arn, &j,
-                       &bd);
-    if (jout)
-        *jout = j;
-    if (breakdown)
-        *breakdown = bd;
-    return rc;
+    orc_restart rs;
+    memset(&rs, 0, sizeof(rs));
+    rs.tau = tau;
+    rs.inner_abs = inner_abs;
+    return orc_arnoldi_cycle_ex(n, rowptr, colind, vals, r0, m, kmax, ortho, prec, &rs,
+                                pm_rowptr, pm_colind, pm_vals, V, Hbar, Hrot, s, cs, sn, y, u,
+                                arn, NULL, jout, breakdown);
 }
 
 /* Negative control (ORC_ALL_FP32): z = b - A x formed in binary32 from
@@ -333,7 +413,10 @@ int orc_gmres(int32_t n, const int32_t *rowptr, const int32_t *colind, const dou
 {
     if (!o || n <= 0 || o->m < 1 || o->maxiter < 0 || !(o->tol > 0) ||
         (o->ortho != ORC_MGS && o->ortho != ORC_CGSR) || o->prec < ORC_FP64 ||
-        o->prec > ORC_ALL_FP32 || !csr_ok(n, rowptr, colind) || !b || !x)
+        o->prec > ORC_ALL_FP32 || !csr_ok(n, rowptr, colind) || !b || !x ||
+        o->stall_factor < 0 || o->stall_window < 0 || o->orth_norm < ORC_ORTH_OFF ||
+        o->orth_norm > ORC_ORTH_FROBENIUS ||
+        (o->orth_norm == ORC_ORTH_SPECTRAL && o->orth_iters < 1))
         return -1;
     if (pm_vals && !csr_ok(n, pm_rowptr, pm_colind))
         return -1;
@@ -378,7 +461,14 @@ int orc_gmres(int32_t n, const int32_t *rowptr, const int32_t *colind, const dou
         return -2;
     }
 
-    const double inner_abs = o->inner_factor * o->tol * inf.bnorm;
+    orc_restart rs;
+    memset(&rs, 0, sizeof(rs));
+    rs.inner_abs = o->inner_factor * o->tol * inf.bnorm;
+    rs.stall_factor = o->stall_factor;
+    rs.stall_window = o->stall_window > 0 ? o->stall_window : (m + 19) / 20;
+    rs.orth_norm = o->orth_norm;
+    rs.orth_threshold = o->orth_threshold;
+    rs.orth_iters = o->orth_iters;
     int32_t cycle_len = m;
     int rc = 0;
     for (;;) {
@@ -414,11 +504,11 @@ int orc_gmres(int32_t n, const int32_t *rowptr, const int32_t *colind, const dou
         /* Two-stage restart (Sec. 3, first strategy; Sec. 4.2): with
          * repeat_first the gain threshold only ends the first cycle, later
          * cycles run for the first cycle's length. */
-        double tau = (o->repeat_first && inf.restarts > 0) ? 0.0 : o->tau;
+        rs.tau = (o->repeat_first && inf.restarts > 0) ? 0.0 : o->tau;
         int32_t j = 0, bd = 0;
-        rc = run_cycle(n, rowptr, colind, vals, z, m, kmax, o->ortho, o->prec, tau, inner_abs,
-                       pm_rowptr, pm_colind, pm_vals, NULL, NULL, NULL, NULL, NULL, NULL, NULL, u,
-                       arn, &j, &bd);
+        rc = run_cycle(n, rowptr, colind, vals, z, m, kmax, o->ortho, o->prec, &rs, pm_rowptr,
+                       pm_colind, pm_vals, NULL, NULL, NULL, NULL, NULL, NULL, NULL, u, arn,
+                       NULL, &j, &bd);
         if (rc)
             break;
         if (j == 0)

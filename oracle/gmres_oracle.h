@@ -50,12 +50,38 @@ typedef struct {
     int32_t maxiter;      /* cap on the total number of inner iterations         */
     int32_t repeat_first; /* 1: after the first cycle, every cycle is limited to
                              the first cycle's length (Sec. 3, first strategy)  */
-    int32_t reserved;
+    int32_t stall_window; /* third strategy window w (inner iterations); 0 selects
+                             ceil(0.05 m)                                        */
     double tol;           /* stop when ||b - A x||_2 <= tol * ||b||_2 (binary64) */
     double tau;           /* restart when |s_{j+1}| <= tau * beta (Sec. 3,
                              second strategy); 0 disables                       */
     double inner_factor;  /* end a cycle once |s_{j+1}| <= inner_factor*tol*||b||*/
+    double stall_factor;  /* third strategy: restart once |s| improved by less
+                             than this factor over the last w iterations of the
+                             cycle (Sec. 4.1 uses 1.001); 0 disables             */
+    double orth_threshold;/* fourth strategy: restart once ||S_k|| >= this     */
+    int32_t orth_norm;    /* fourth strategy norm: 0 off, ORC_ORTH_SPECTRAL (power
+                             method), ORC_ORTH_FROBENIUS                        */
+    int32_t orth_iters;   /* power-method iterations (Sec. 4.1 uses 10)         */
 } orc_opts;
+
+enum { ORC_ORTH_OFF = 0, ORC_ORTH_SPECTRAL = 1, ORC_ORTH_FROBENIUS = 2 };
+
+/* The restart criteria one cycle checks after every inner iteration (Sec. 3):
+ * tau and inner_abs as in orc_opts (inner_abs absolute), the stall test with
+ * a window of stall_window (> 0) iterations, and the loss-of-orthogonality
+ * test on S_k = (I + U_k)^-1 U_k, U_k the strictly upper part of V_k^T V_k
+ * of the stored basis.  All-zero fields disable the optional tests. */
+typedef struct {
+    double tau;
+    double inner_abs;
+    double stall_factor;
+    double orth_threshold;
+    int32_t stall_window;
+    int32_t orth_norm;
+    int32_t orth_iters;
+    int32_t reserved;
+} orc_restart;
 
 typedef struct {
     int32_t iters;        /* total inner iterations                              */
@@ -107,6 +133,22 @@ int orc_arnoldi_cycle(int32_t n, const int32_t *rowptr, const int32_t *colind, c
                       const int32_t *pm_rowptr, const int32_t *pm_colind, const double *pm_vals,
                       double *V, double *Hbar, double *Hrot, double *s, double *cs, double *sn,
                       double *y, double *u, double *arn, int32_t *jout, int32_t *breakdown);
+
+/* orc_arnoldi_cycle with every restart criterion of orc_restart; orth
+ * (length m, may be NULL) receives ||S_k|| after each inner iteration (0
+ * where the test is off or the cycle broke down). */
+int orc_arnoldi_cycle_ex(int32_t n, const int32_t *rowptr, const int32_t *colind,
+                         const double *vals, const double *r0, int32_t m, int32_t kmax,
+                         int32_t ortho, int32_t prec, const orc_restart *rs,
+                         const int32_t *pm_rowptr, const int32_t *pm_colind,
+                         const double *pm_vals, double *V, double *Hbar, double *Hrot, double *s,
+                         double *cs, double *sn, double *y, double *u, double *arn, double *orth,
+                         int32_t *jout, int32_t *breakdown);
+
+/* ||S||_2 estimate of a k x k strictly upper triangular S (column-major,
+ * leading dimension ld) by `iters` power-method iterations on S^T S from the
+ * vector of equal entries; exposed for the tests. */
+double orc_s_norm2(int32_t k, const double *S, int32_t ld, int32_t iters);
 
 /* Restarted GMRES(m) (Alg. 1).  x holds x_0 on entry and the result on exit.
  * arn_hist (length maxiter) receives |s_{j+1}| of every inner iteration;

@@ -503,6 +503,106 @@ def pin_adam_first_step():
     assert np.allclose(m1, 0.1 * g) and np.allclose(v1, 0.001 * g * g)
 
 
+def _cyclic(n):
+    P = np.zeros((n, n))
+    for i in range(n):
+        P[(i + 1) % n, i] = 1.0
+    b = np.zeros(n)
+    b[0] = 1.0
+    return I.dense_to_csr(P), b
+
+
+def pin_stall_restart():
+    """Third strategy (Sec. 3): on the cyclic shift the Arnoldi residual stays
+    exactly 1 for n-1 steps (complete stagnation), so with a window of w
+    iterations the first possible test, at iteration w, already sees no gain
+    and ends the cycle there; a factor of 1 (no gain needed) never triggers,
+    and neither does the default off."""
+    A, b = _cyclic(16)
+    for w in (1, 3, 5):
+        for ortho in (O.MGS, O.CGSR):
+            cyc = O.arnoldi_cycle(A, b, m=16, ortho=ortho, prec=O.FP64, stall_factor=1.001,
+                                  stall_window=w)
+            assert cyc["j"] == w, (w, cyc["j"])
+    assert O.arnoldi_cycle(A, b, m=16, prec=O.FP64, stall_factor=1.0, stall_window=2)["j"] == 16
+    assert O.arnoldi_cycle(A, b, m=16, prec=O.FP64)["j"] == 16
+    # default window: ceil(0.05 m)
+    x, info = O.gmres(A, b, m=40, prec=O.FP64, stall_factor=1.001, maxiter=10)
+    assert info["first_len"] == 2 and info["iters"] == 10
+    # a real stall (mixed MGS, binary32 basis): the cycle ends at the first
+    # iteration whose residual is within the factor of the one w steps back
+    # in the history of the same cycle run without the test
+    A2 = I.convdiff2d(30, pe=1.0)
+    b2 = I.rhs_ones_noise(A2, 1e-3, 1)
+    full = O.arnoldi_cycle(A2, b2, m=100, ortho=O.MGS, prec=O.MIXED)
+    hist = np.concatenate([[np.linalg.norm(b2)], full["arn"][: full["j"]]])
+    for w in (3, 5, 8):
+        want = next(j for j in range(w, 101) if hist[j - w] < 1.001 * hist[j])
+        cyc = O.arnoldi_cycle(A2, b2, m=100, ortho=O.MGS, prec=O.MIXED, stall_factor=1.001,
+                              stall_window=w)
+        assert cyc["j"] == want < 100, (w, cyc["j"], want)
+
+
+def pin_s_matrix():
+    """Fourth strategy (Sec. 3): ||S_k|| of S_k = (I + U_k)^-1 U_k, U_k the
+    strictly upper part of V_k^T V_k.  The Frobenius norms the cycle reports
+    equal those of S formed densely (numpy solve) from the basis it exports;
+    the spectral estimate is the power method's, bounded by the exact 2-norm
+    and converging to it with more iterations; an orthonormal binary64 CGSR
+    basis has ||S|| ~ 0; unit vectors with a repeated one give ||S||_2 = 1
+    (Paige: S is a contraction for unit columns, of norm 1 exactly when they
+    are dependent)."""
+    A = I.convdiff2d(12, pe=5.0)
+    b = I.rhs_ones_noise(A, 1e-3, 2)
+    cyc = O.arnoldi_cycle(A, b, m=30, ortho=O.MGS, prec=O.MIXED, orth_norm=O.ORTH_FROBENIUS,
+                          orth_threshold=10.0)
+    j = cyc["j"]
+    assert j >= 10
+    for c in (1, 4, j - 1):
+        k = c + 2
+        Vk = cyc["V"][:k].T
+        U = np.triu(Vk.T @ Vk, 1)
+        S = np.linalg.solve(np.eye(k) + U, U)
+        assert abs(cyc["orth"][c] - np.linalg.norm(S, "fro")) <= 1e-9 * max(1e-300, cyc["orth"][c]) + 1e-15
+    rng = np.random.default_rng(4)
+    for k in (3, 7, 20):
+        S = np.triu(rng.standard_normal((k, k)), 1)
+        exact = np.linalg.norm(S, 2)
+        assert O.s_norm2(S, 10) <= exact * (1 + 1e-12)
+        assert abs(O.s_norm2(S, 2000) - exact) <= 1e-8 * exact
+    # orthonormal basis: S ~ 0
+    cyc = O.arnoldi_cycle(A, b, m=30, ortho=O.CGSR, prec=O.FP64, orth_norm=O.ORTH_SPECTRAL,
+                          orth_threshold=10.0)
+    assert np.max(cyc["orth"][: cyc["j"]]) <= 1e-12
+    # dependent unit vectors: ||S||_2 = 1
+    v = rng.standard_normal((5, 40))
+    v /= np.linalg.norm(v, axis=1, keepdims=True)
+    v[4] = v[1]
+    U = np.triu(v @ v.T, 1)
+    S = np.linalg.solve(np.eye(5) + U, U)
+    assert abs(O.s_norm2(S, 3000) - 1.0) <= 1e-6
+
+
+def pin_orthogonality_loss_restart():
+    """Mixed MGS on a fast-converging system: the binary32 basis loses
+    independence as the Arnoldi residual stalls, ||S_k||_2 climbs to 1
+    (Sec. 4.1 observes the same), and a threshold ends the cycle at the first
+    iteration whose norm reaches it."""
+    A = I.convdiff2d(30, pe=1.0)
+    b = I.rhs_ones_noise(A, 1e-3, 1)
+    full = O.arnoldi_cycle(A, b, m=100, ortho=O.MGS, prec=O.MIXED, orth_norm=O.ORTH_SPECTRAL,
+                           orth_threshold=10.0)
+    orth, arn = full["orth"][: full["j"]], full["arn"][: full["j"]]
+    assert full["j"] == 100 and orth[-1] >= 0.99 and orth[-1] <= 1 + 1e-5
+    assert arn[-1] >= 0.999 * arn[-10]  # stalled
+    assert orth[5] <= 1e-3
+    for thr in (0.1, 0.5, 0.9):
+        first = int(np.argmax(orth >= thr))
+        cyc = O.arnoldi_cycle(A, b, m=100, ortho=O.MGS, prec=O.MIXED,
+                              orth_norm=O.ORTH_SPECTRAL, orth_threshold=thr)
+        assert cyc["j"] == first + 1, (thr, cyc["j"], first)
+
+
 ALL_PINS = [
     pin_lu_fp64, pin_exact_convergence, pin_identity, pin_diag_distinct, pin_cyclic_shift,
     pin_hand_2x2, pin_arnoldi_relation, pin_orthonormality, pin_mgs_equals_cgsr,
@@ -510,5 +610,6 @@ ALL_PINS = [
     pin_mixed_reaches_double, pin_negative_control, pin_monotone_restarts, pin_repeat_first,
     pin_spmv_and_residual, pin_basis_rounding,
     pin_spai_grad_m_fd, pin_spai_grad_params_fd, pin_spai_special_cases, pin_spai_optimum,
-    pin_spai_feature_invariants, pin_adam_first_step,
+    pin_spai_feature_invariants, pin_adam_first_step, pin_stall_restart, pin_s_matrix,
+    pin_orthogonality_loss_restart,
 ]

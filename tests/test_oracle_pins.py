@@ -61,6 +61,14 @@ MUTATIONS = [
      "binary16 scale"),
     ("gmres_oracle.c", "return (double)(float)v;\n", "return v;\n",
      "binary32 basis not rounded"),
+    ("cycle_impl.inc", "acc -= U[(size_t)l * ld + i] * scol[l];", "",
+     "S taken as U (inverse of I + U dropped)"),
+    ("cycle_impl.inc", "ah[j - rs->stall_window] < rs->stall_factor * arnres",
+     "ah[j - rs->stall_window + 1] < rs->stall_factor * arnres", "stall window one short"),
+    ("cycle_impl.inc", "ah[j - rs->stall_window] < rs->stall_factor * arnres",
+     "ah[j - rs->stall_window] < arnres", "stall factor dropped"),
+    ("gmres_oracle.c", "acc += S[(size_t)l * ld + i] * yv[i];",
+     "acc += S[(size_t)i * ld + l] * yv[i];", "power method multiplies by S, not S^T"),
     ("spai_oracle.c", "atr[colind[k]] += vals[k] * r[i];", "atr[i] += vals[k] * r[colind[k]];",
      "A instead of A^T in the preconditioner gradient"),
     ("spai_oracle.c", "d2[o] = z2[o] > 0 ? dgk * params[P_W3 + o] : 0;",
