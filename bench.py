@@ -29,10 +29,12 @@ sys.path.insert(0, ROOT)
 
 WORKLOAD = "convdiff3d_160"
 SEED = 20110185
-# Inner iterations and restart cycles the mixed CGSR GMRES(100) solve of this
-# workload takes (same schedule on the GPU and in the oracle, see the parity
-# tests); used to scale the oracle's per-iteration samples to a full solve.
-SCHEDULE = {"convdiff3d_160": {"mixed": None, "fp64": None}}
+# Inner iterations and restart cycles of the oracle's own full solves of the
+# workloads (python -m oracle.schedule <workload> <precision>; the 160^3
+# mixed CGSR GMRES(100) solve took 1085 s on one x86 core); used to scale the
+# oracle's per-cycle samples to a full solve.  The GPU solves take the same
+# schedules.
+SCHEDULE = {"convdiff3d_160": {"mixed": {"iters": 1300, "restarts": 13}}}
 
 
 def parse():
@@ -46,6 +48,10 @@ def parse():
     p.add_argument("--spai-params", default=None)
     p.add_argument("--cgs-kernel", type=int, default=0,
                    help="CGSR kernel family: 0 register-streaming rows, 1 TMA tiles")
+    p.add_argument("--l2-prefetch", type=int, default=None,
+                   help="CGSR rows kernels: slices prefetched ahead into L2 (library default)")
+    p.add_argument("--spmv-lanes", type=int, default=0,
+                   help="lanes per CSR row (0: autotuned)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     return p.parse_args()
@@ -165,8 +171,14 @@ def bench_ours(args):
     m, ortho, prec = spec["m"], spec["ortho"], spec["prec"]
     stream = torch.cuda.current_stream()
     solver = G.Solver(A, stream=stream)
-    lanes32, lanes64 = G.gmres_autotune(solver.h)
+    if args.spmv_lanes:
+        lanes32 = lanes64 = args.spmv_lanes
+        solver.set_opts(spmv_lanes=args.spmv_lanes)
+    else:
+        lanes32, lanes64 = G.gmres_autotune(solver.h)
     solver.set_opts(profile=1, cgs_kernel=args.cgs_kernel)
+    if args.l2_prefetch is not None:
+        solver.set_opts(l2_prefetch=args.l2_prefetch)
     learned = spec.get("precond") == "learned"
     spai_params = None
     if learned:
@@ -310,6 +322,7 @@ def bench_ours(args):
             "parallelism": "replicas" if world > 1 else "single GPU",
             "spmv_lanes": {"f32": lanes32, "f64": lanes64},
             "cgs_kernel": ["register-streaming rows", "TMA tiles"][args.cgs_kernel],
+            "l2_prefetch": int(G.gmres_get_opts(solver.h).l2_prefetch),
         },
         "iters": iters, "restarts": restarts,
         "compare": compare,

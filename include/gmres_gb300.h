@@ -75,6 +75,12 @@ typedef enum {
 #define GMRES_PATH_GRID 1  /* whole-GPU kernels per inner step (large n)      */
 #define GMRES_PATH_BLOCK 2 /* one thread block runs the whole solve (small n) */
 
+/* Loss-of-orthogonality restart test (Sec. 3, fourth strategy): the norm of
+ * S_k = (I + U_k)^-1 U_k, U_k the strictly upper part of V_k^T V_k. */
+#define GMRES_ORTH_OFF 0
+#define GMRES_ORTH_SPECTRAL 1  /* power method on S^T S                        */
+#define GMRES_ORTH_FROBENIUS 2 /* ||S||_F, an upper bound of ||S||_2          */
+
 /* Solver options (gmres_default_opts gives the defaults). */
 typedef struct gmres_opts {
     double tau;           /* restart when |s_{j+1}| <= tau * beta (Sec. 3, second
@@ -102,7 +108,21 @@ typedef struct gmres_opts {
     int32_t mgs_kernel;   /* MGS: 0 = one cooperative kernel per inner step with
                              w in shared memory (default; used when w's row
                              chunk fits), 1 = one kernel per basis vector       */
-    int32_t reserved[3];
+    int32_t l2_prefetch;  /* register-streaming CGSR: each block prefetches the
+                             basis rows of the slice this many slices ahead of
+                             the one it is reading into L2 (bulk prefetch);
+                             0 = off, 1..4                                      */
+    int32_t reserved[2];
+    double stall_factor;  /* third restart strategy (Sec. 3; Sec. 4.1 uses 1.001):
+                             end the cycle once |s_{j+1}| improved by less than
+                             this factor over the last stall_window inner
+                             iterations; 0 = off (default)                      */
+    int32_t stall_window; /* window of the stall test; 0 = ceil(0.05 m)        */
+    int32_t orth_norm;    /* fourth restart strategy: GMRES_ORTH_* (default off);
+                             grid path only (GMRES_PATH_AUTO picks it)          */
+    double orth_threshold;/* end the cycle once ||S_k|| >= this (default 1.0)  */
+    int32_t orth_iters;   /* power-method iterations (default 10, as Sec. 4.1) */
+    int32_t reserved2;
 } gmres_opts;
 
 /* Kernel classes reported in gmres_info (index into kernel_ms / kernel_bytes). */
@@ -327,6 +347,14 @@ gmres_status gmres_memory_bytes(gmres_t h, int32_t m, gmres_precision prec, int6
                                 int64_t *workspace_bytes);
 
 /* Static text for a status code. */
+/* ||S_k|| of the loss-of-orthogonality test after each inner iteration of
+ * the last restart cycle the handle ran (gmres_solve or gmres_arnoldi), for
+ * k = 2 .. j+1 basis vectors: out[c] belongs to inner iteration c+1; entries
+ * past the cycle's end, or with the test off, are 0.  out is a host array of
+ * count <= 128 entries.  The paper reports these norms (Sec. 4.1) and has no
+ * separate interface for them. */
+gmres_status gmres_orth_norms(gmres_t h, double *out, int32_t count);
+
 const char *gmres_status_str(gmres_status s);
 
 /* Library version string. */

@@ -111,6 +111,10 @@ struct BlockParams {
     int nsys;
     unsigned *queue;  // work-queue counter (reset by the host)
     const int *order; // system order (largest first)
+    // third restart strategy (Sec. 3): end the cycle once |s_{j+1}| improved
+    // by less than stall_factor over the last stall_w iterations (0 = off)
+    double stall_factor = 0;
+    int stall_w = 1;
 };
 
 // w[row] = A x for the system's rows, L lanes per row.
@@ -150,7 +154,8 @@ __device__ void team_solve_one(const BlockSys<T, VT> &S, const BlockParams &P, B
     double *redd = reinterpret_cast<double *>(smem_raw);       // 32 (first: 8-byte aligned)
     double *slotd = redd + 32;                                 // 2 * TEAM_KMAX
     double *bcd = slotd + 2 * TEAM_KMAX;                       // TEAM_KMAX
-    T *H = reinterpret_cast<T *>(bcd + TEAM_KMAX);             // ld x m (rotated)
+    double *ahist = bcd + TEAM_KMAX;                           // MMAX + 2: |s_{j+1}|, j = 0..
+    T *H = reinterpret_cast<T *>(ahist + MMAX + 2);            // ld x m (rotated)
     T *s = H + (size_t)ld * m;                   // m + 1
     T *cs = s + (m + 1);                         // m
     T *sn = cs + m;                              // m
@@ -251,6 +256,8 @@ __device__ void team_solve_one(const BlockSys<T, VT> &S, const BlockParams &P, B
             Basis<VT>::st(S.V + i, S.r[i] / beta, S.vscale);
         for (int i = tid; i <= m; i += nth)
             s[i] = (i == 0) ? beta : T(0);
+        if (tid == 0)
+            ahist[0] = (double)beta;
         Team<CS>::sync();
 
         int j = 0;
@@ -355,10 +362,13 @@ __device__ void team_solve_one(const BlockSys<T, VT> &S, const BlockParams &P, B
                 col[c] = al * hjj + be * hj1;
                 col[c + 1] = -be * hjj + al * hj1;
                 double arn = fabs((double)s[c + 1]);
+                ahist[c + 1] = arn;
                 int bd = hnext <= brk * wnorm0;
                 int nf = !isfinite(arn);
+                int stall = P.stall_factor > 0 && c + 1 >= P.stall_w &&
+                            ahist[c + 1 - P.stall_w] < P.stall_factor * arn;
                 int end = bd || nf || (tau > 0 && arn <= tau * (double)beta) || arn <= inner_abs ||
-                          (c + 1 >= kmax);
+                          stall || (c + 1 >= kmax);
                 s_flag = (end ? 1 : 0) | (bd ? 2 : 0) | (nf ? 4 : 0);
             }
             __syncthreads();
@@ -471,7 +481,7 @@ template <class T>
 inline size_t block_smem_bytes(int m) {
     size_t nt = (size_t)(m + 1) * m + (m + 1) + 3 * (size_t)m + 2 * (MMAX + 2) + 8 * 32 +
                 3 * TEAM_KMAX;
-    return nt * sizeof(T) + (32 + 3 * TEAM_KMAX) * sizeof(double) + 64;
+    return nt * sizeof(T) + (32 + 3 * TEAM_KMAX + MMAX + 2) * sizeof(double) + 64;
 }
 
 }  // namespace gmres

@@ -4,6 +4,8 @@
 //   MODE 0  partial h1 = V^T w per block            (+ ||w||^2)
 //   MODE 1  w <- w - V h1, then partial h2 = V^T w per block
 //   MODE 2  w <- w - V h2, ||w||^2 -> h_{j+1,j}; column h1 + h2; Givens step
+//   MODE 3  partial u = V^T v_k per block, v_k = basis column `ncols` (the
+//           loss-of-orthogonality test, Sec. 3 fourth strategy)
 // k_reduce_cols sums the per-block partials of MODE 0 / 1 (one block per
 // basis vector, fixed order) between the passes.
 //
@@ -125,6 +127,11 @@ __device__ __forceinline__ void st_w(T *p, const T (&v)[RPL]) {
     }
 }
 
+// Bulk prefetch of `bytes` (a multiple of 16, 16-byte aligned) into L2.
+__device__ __forceinline__ void prefetch_l2(const void *p, unsigned bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 constexpr int ROWS_THREADS = 128;
 constexpr int ROWS_WARPS = ROWS_THREADS / 32;
 constexpr int ROWS_CB = 8;  // basis vectors loaded per batch
@@ -207,8 +214,11 @@ __device__ __forceinline__ void rows_dots(const GridCtx<T, VT> &c, int ncols, in
 
 template <class T, class VT, int MODE>
 __global__ void __launch_bounds__(ROWS_THREADS)
-    k_cgs_rows(GridCtx<T, VT> c, int ncols, T *part, int64_t slices_per_block) {
-    if (!c.ctl->active)
+    k_cgs_rows(GridCtx<T, VT> c, int ncols, T *part, int64_t slices_per_block, int pf) {
+    // MODE 3 follows the step that appended basis column ncols, also when
+    // that step ended the cycle
+    if (MODE == 3 ? !(c.ctl->j == ncols && !c.ctl->breakdown && !c.ctl->nonfinite)
+                  : !c.ctl->active)
         return;
     constexpr int RPL = RowsCfg<VT>::RPL;
     constexpr int RW = 32 * RPL;                   // rows per warp-step
@@ -217,7 +227,7 @@ __global__ void __launch_bounds__(ROWS_THREADS)
     __shared__ T hs[MMAX + 2];
     __shared__ __align__(16) T wsl[SR];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (MODE >= 1) {
+    if (MODE == 1 || MODE == 2) {
         const T *src = (MODE == 1) ? c.h1 : c.h2;
         for (int i = threadIdx.x; i < ncols; i += blockDim.x)
             hs[i] = src[i];
@@ -239,8 +249,24 @@ __global__ void __launch_bounds__(ROWS_THREADS)
         sl1 = nslices;
     for (int64_t sl = sl0; sl < sl1; ++sl) {
         const int64_t s0 = sl * SR;
+        // slice sl + pf of this block's run: one 16-byte-aligned 2 KB row
+        // block per basis vector (ldv is a multiple of SR) and w's rows
+        if (pf > 0 && sl + pf < sl1) {
+            const int64_t p0 = (sl + pf) * SR;
+            for (int col = threadIdx.x; col <= ncols; col += ROWS_THREADS) {
+                if (col < ncols || MODE == 3)
+                    prefetch_l2(c.V + (size_t)col * c.ldv + p0, SR * (unsigned)sizeof(VT));
+                else
+                    prefetch_l2(c.w + p0, SR * (unsigned)sizeof(T));
+            }
+        }
         T wv[4][RPL];
-        if (MODE == 0) {
+        if (MODE == 3) {
+            const VT *vk = c.V + (size_t)ncols * c.ldv + s0 + lane * RPL;
+#pragma unroll
+            for (int g = 0; g < 4; ++g)
+                ld_rows<T, VT, RPL>(vk + g * RW, c.vinv, wv[g], pol_once);
+        } else if (MODE == 0) {
 #pragma unroll
             for (int g = 0; g < 4; ++g)
                 ld_w<T, RPL>(c.w + s0 + g * RW + lane * RPL, wv[g]);
@@ -277,11 +303,11 @@ __global__ void __launch_bounds__(ROWS_THREADS)
                 __syncthreads();
             }
         }
-        if (MODE <= 1)
+        if (MODE != 2)
             rows_dots<T, VT, RPL, ACC>(c, ncols, s0, wv, wid, lane, acc, pol_once);
     }
     T *mypart = part + (size_t)blockIdx.x * PSTRIDE;
-    if (MODE <= 1) {
+    if (MODE != 2) {
 #pragma unroll
         for (int k = 0; k < ACC; ++k) {
             const int col = wid + ROWS_WARPS * k;
@@ -290,7 +316,7 @@ __global__ void __launch_bounds__(ROWS_THREADS)
                 mypart[col] = v;
         }
     }
-    if (MODE != 1) {
+    if (MODE == 0 || MODE == 2) {
         __shared__ T sred[32];
         T tot = block_sum1(nsq, sred);
         if (threadIdx.x == 0)
@@ -316,7 +342,9 @@ __global__ void __launch_bounds__(ROWS_THREADS)
 template <class T>
 __global__ void __launch_bounds__(256) k_reduce_cols(const T *part, int nblocks, int ncols,
                                                      T *out, Ctl *ctl, int with_norm) {
-    if (!ctl->active)
+    // with_norm 2: the Gram column of MODE 3 (runs under its condition)
+    if (with_norm == 2 ? !(ctl->j == ncols && !ctl->breakdown && !ctl->nonfinite)
+                       : !ctl->active)
         return;
     __shared__ T sred[32];
     const int col = blockIdx.x;

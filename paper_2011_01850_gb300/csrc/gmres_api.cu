@@ -24,6 +24,7 @@
 #include "cgs_tile.cuh"
 #include "mgs_persist.cuh"
 #include "grid_kernels.cuh"
+#include "orth_monitor.cuh"
 #include "handle.hpp"
 #include "host_util.hpp"
 
@@ -47,6 +48,12 @@ template <class T>
 struct SmallPtrs {
     T *H, *Hb, *s, *cs, *sn, *y, *h1, *h2;
 };
+
+// Restart-test buffers (binary64): |s_{j+1}| history of the cycle, ||S_k||
+// history, then U and S of the loss-of-orthogonality test.
+inline double *mon_ahist(gmres_handle *h) { return h->mon.as<double>(); }
+inline double *mon_hist(gmres_handle *h) { return h->mon.as<double>() + (MMAX + 2); }
+constexpr size_t MON_DOUBLES = 2 * (MMAX + 2) + 2 * (size_t)(MMAX + 1) * (MMAX + 1);
 
 template <class T>
 SmallPtrs<T> small_ptrs(gmres_handle *h) {
@@ -85,6 +92,10 @@ gmres_status ensure_workspace(gmres_handle *h, int m, gmres_precision prec) {
     CK(h->small.ensure((size_t)(2 * (MMAX + 1) * MMAX + 6 * (MMAX + 2)) * 8));
     CK(h->part.ensure((size_t)std::max(h->grid, h->nsm * h->rows_blocks_per_sm) * PSTRIDE * 8));
     CK(h->part64.ensure((size_t)h->grid * 4 * 8));
+    if (h->mon.bytes < MON_DOUBLES * sizeof(double)) {
+        CK(h->mon.ensure(MON_DOUBLES * sizeof(double)));
+        CK(cudaMemsetAsync(h->mon.p, 0, h->mon.bytes, h->stream));
+    }
     bool cgrow = sizeof(Ctl) > h->ctl.bytes;
     CK(h->ctl.ensure(sizeof(Ctl)));
     if (cgrow)
@@ -131,6 +142,9 @@ GridCtx<T, VT> make_ctx(gmres_handle *h, int m) {
     c.ctl = h->ctl.as<Ctl>();
     c.brk = std::is_same<T, double>::value ? T(1e-14) : T(1e-6);
     c.kmax = m;
+    c.ahist = mon_ahist(h);
+    c.stall_factor = h->opts.stall_factor;
+    c.stall_w = h->opts.stall_window > 0 ? h->opts.stall_window : (m + 19) / 20;
     if (h->has_precond && h->opts.precond) {
         c.prowptr = c.rowptr;
         c.pcolind = c.colind;
@@ -213,6 +227,8 @@ bool mgs_persist_ok(gmres_handle *h) {
     bool ok = false;
     int coop = 0;
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, h->device);
+    if (h->nsm > MGSP_MAXGRID)
+        coop = 0;  // one warp reads every block's exchange slots
     const int64_t chunk = round_up((h->ldv + h->nsm - 1) / h->nsm, 4);
     const size_t smem = (size_t)chunk * sizeof(T) + 16;
     int optin = 0;
@@ -235,10 +251,11 @@ bool mgs_persist_ok(gmres_handle *h) {
 }
 
 // Enqueue one inner step (column index `col` of the basis -> new column
-// col+1).  Kernels return at once when the cycle has ended.
+// col+1) without the optional loss-of-orthogonality test.  Kernels return at
+// once when the cycle has ended.
 template <class T, class VT>
-gmres_status enqueue_step(gmres_handle *h, GridCtx<T, VT> &c, int col, gmres_ortho ortho,
-                          Acct &acct) {
+gmres_status enqueue_step_core(gmres_handle *h, GridCtx<T, VT> &c, int col, gmres_ortho ortho,
+                               Acct &acct) {
     const int L = lanes_for<T, VT>(h);
     const VT *vj = c.V + (size_t)col * c.ldv;
     cudaEvent_t e = h->timer.begin();
@@ -265,7 +282,7 @@ gmres_status enqueue_step(gmres_handle *h, GridCtx<T, VT> &c, int col, gmres_ort
         // one resident wave per kernel: grid = SMs x resident blocks per SM
         static int per_sm[3] = {0, 0, 0};
         if (per_sm[0] == 0) {
-            void (*fns[3])(GridCtx<T, VT>, int, T *, int64_t) = {
+            void (*fns[3])(GridCtx<T, VT>, int, T *, int64_t, int) = {
                 k_cgs_rows<T, VT, 0>, k_cgs_rows<T, VT, 1>, k_cgs_rows<T, VT, 2>};
             for (int k = 0; k < 3; ++k) {
                 int bpsm = 0;
@@ -283,11 +300,12 @@ gmres_status enqueue_step(gmres_handle *h, GridCtx<T, VT> &c, int col, gmres_ort
             kpb[k] = (nsl + cap - 1) / cap;
             gsz[k] = (int)((nsl + kpb[k] - 1) / kpb[k]);
         }
-        k_cgs_rows<T, VT, 0><<<gsz[0], ROWS_THREADS, 0, h->stream>>>(c, ncols, c.part, kpb[0]);
+        const int pf = h->opts.l2_prefetch;
+        k_cgs_rows<T, VT, 0><<<gsz[0], ROWS_THREADS, 0, h->stream>>>(c, ncols, c.part, kpb[0], pf);
         k_reduce_cols<T><<<ncols + 1, 256, 0, h->stream>>>(c.part, gsz[0], ncols, c.h1, c.ctl, 1);
-        k_cgs_rows<T, VT, 1><<<gsz[1], ROWS_THREADS, 0, h->stream>>>(c, ncols, c.part, kpb[1]);
+        k_cgs_rows<T, VT, 1><<<gsz[1], ROWS_THREADS, 0, h->stream>>>(c, ncols, c.part, kpb[1], pf);
         k_reduce_cols<T><<<ncols, 256, 0, h->stream>>>(c.part, gsz[1], ncols, c.h2, c.ctl, 0);
-        k_cgs_rows<T, VT, 2><<<gsz[2], ROWS_THREADS, 0, h->stream>>>(c, ncols, c.part, kpb[2]);
+        k_cgs_rows<T, VT, 2><<<gsz[2], ROWS_THREADS, 0, h->stream>>>(c, ncols, c.part, kpb[2], pf);
         acct.launches[GMRES_K_ORTHO] += 5;
     } else if (ortho == GMRES_ORTHO_CGSR) {
         const int TR = cgs_choose_tr<VT>(ncols);
@@ -322,10 +340,20 @@ gmres_status enqueue_step(gmres_handle *h, GridCtx<T, VT> &c, int col, gmres_ort
         // one cooperative kernel: w stays in shared memory, v_{j+1} written
         int64_t chunk = h->mgs_chunk;
         long long spin = h->opts.spin_limit > 0 ? h->opts.spin_limit : (1LL << 24);
-        unsigned *bar = &h->ctl.as<Ctl>()->counter[5];
+        // exchange slots: 2 parities x 4 words per block, round numbers
+        // never reused (cleared before they wrap)
+        const size_t slot_bytes = (size_t)h->nsm * 2 * 4 * sizeof(unsigned long long);
+        if (h->mgs_seq.bytes < slot_bytes || h->mgs_round > 0x7fffff00u - (unsigned)(ncols + 1)) {
+            CK(h->mgs_seq.ensure(slot_bytes));
+            CK(cudaMemsetAsync(h->mgs_seq.p, 0, h->mgs_seq.bytes, h->stream));
+            h->mgs_round = 1;
+        }
+        unsigned long long *slots = h->mgs_seq.as<unsigned long long>();
+        unsigned round0 = h->mgs_round;
+        h->mgs_round += (unsigned)(ncols + 1);
         GridCtx<T, VT> cc = c;
         int nc = ncols;
-        void *args[] = {&cc, &nc, &chunk, &spin, &bar};
+        void *args[] = {&cc, &nc, &chunk, &spin, &slots, &round0};
         CK(cudaLaunchCooperativeKernel((const void *)k_mgs_persist<T, VT>, dim3(h->nsm),
                                        dim3(MGSP_THREADS), args,
                                        (size_t)chunk * sizeof(T) + 16, h->stream));
@@ -341,10 +369,50 @@ gmres_status enqueue_step(gmres_handle *h, GridCtx<T, VT> &c, int col, gmres_ort
     CKL();
     h->timer.end(GMRES_K_ORTHO, e);
     e = h->timer.begin();
-    k_normalize<T, VT><<<g, b, 0, h->stream>>>(c, col + 1);
+    k_normalize<T, VT><<<g, b, 0, h->stream>>>(c, col + 1, h->opts.orth_norm != GMRES_ORTH_OFF);
     CKL();
     h->timer.end(GMRES_K_NORMALIZE, e);
     acct.launches[GMRES_K_NORMALIZE]++;
+    return GMRES_OK;
+}
+
+// The inner step plus, when enabled, the loss-of-orthogonality test (Sec. 3,
+// fourth strategy): u = V^T v_{col+2} by the Gram pass of the rows kernel,
+// then the S column, its norm and the restart decision in one block.
+template <class T, class VT>
+gmres_status enqueue_step(gmres_handle *h, GridCtx<T, VT> &c, int col, gmres_ortho ortho,
+                          Acct &acct) {
+    gmres_status st = enqueue_step_core(h, c, col, ortho, acct);
+    if (st != GMRES_OK || h->opts.orth_norm == GMRES_ORTH_OFF)
+        return st;
+    const int k = col + 2;  // stored vectors v_1 .. v_{col+2}
+    const int ncols = k - 1;
+    cudaEvent_t e = h->timer.begin();
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        int bpsm = 0;
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpsm, k_cgs_rows<T, VT, 3>,
+                                                         ROWS_THREADS, 0));
+        per_sm = std::max(1, std::min(bpsm, h->rows_blocks_per_sm));
+    }
+    const int64_t nsl = h->ldv / (ROWS_WARPS * 32 * (16 / (int64_t)sizeof(VT)));
+    const int64_t cap = (int64_t)h->nsm * per_sm;
+    const int64_t kpb = (nsl + cap - 1) / cap;
+    const int gsz = (int)((nsl + kpb - 1) / kpb);
+    k_cgs_rows<T, VT, 3><<<gsz, ROWS_THREADS, 0, h->stream>>>(c, ncols, c.part, kpb,
+                                                              h->opts.l2_prefetch);
+    k_reduce_cols<T><<<ncols, 256, 0, h->stream>>>(c.part, gsz, ncols, c.h2, c.ctl, 2);
+    OrthMon M;
+    M.U = h->mon.as<double>() + 2 * (MMAX + 2);
+    M.S = M.U + (size_t)ORTH_LD * ORTH_LD;
+    M.hist = mon_hist(h);
+    M.threshold = h->opts.orth_threshold;
+    M.norm = h->opts.orth_norm;
+    M.iters = h->opts.orth_iters > 0 ? h->opts.orth_iters : 10;
+    k_orth_monitor<T><<<1, ORTH_THREADS, 0, h->stream>>>(c.ctl, c.h2, k, M);
+    CKL();
+    h->timer.end(GMRES_K_ORTHO, e);
+    acct.launches[GMRES_K_ORTHO] += 3;
     return GMRES_OK;
 }
 
@@ -364,6 +432,8 @@ void account_cycle(gmres_handle *h, int j, gmres_ortho ortho, Acct &acct) {
             acct.bytes[GMRES_K_ORTHO] += 3 * c * n * sV + 5 * n * sT;
         else
             acct.bytes[GMRES_K_ORTHO] += c * n * sV + 2 * n * sT;
+        if (h->opts.orth_norm != GMRES_ORTH_OFF)
+            acct.bytes[GMRES_K_ORTHO] += (c + 1) * n * sV;  // u = V^T v_{j+1}
         if (it + 1 < j)
             acct.bytes[GMRES_K_NORMALIZE] += n * sT + n * sV;
     }
@@ -453,6 +523,8 @@ gmres_status solve_grid(gmres_handle *h, const double *b, double *x, int m, doub
         const int kmax = std::min(cycle_len, maxiter - info->iters);
         c.kmax = kmax;
         c.tau = (repeat_first && info->restarts > 0) ? 0.0 : tau;
+        if (h->opts.orth_norm != GMRES_ORTH_OFF)
+            CK(cudaMemsetAsync(mon_hist(h), 0, (MMAX + 2) * sizeof(double), h->stream));
         e = h->timer.begin();
         k_init<T, VT><<<h->grid, kThreads, 0, h->stream>>>(c);
         CKL();
@@ -579,6 +651,8 @@ gmres_status solve_block(gmres_handle *h, const double *b, double *x, int m, dou
     P.tau = h->opts.tau >= 0 ? h->opts.tau : default_tau(prec);
     P.inner_factor = h->opts.inner_factor;
     P.brk = std::is_same<T, double>::value ? 1e-14 : 1e-6;
+    P.stall_factor = h->opts.stall_factor;
+    P.stall_w = h->opts.stall_window > 0 ? h->opts.stall_window : (m + 19) / 20;
     P.nsys = 1;
     P.queue = queue;
     P.order = nullptr;
@@ -620,9 +694,13 @@ gmres_status solve_dispatch_path(gmres_handle *h, const double *b, double *x, in
                                  gmres_ortho ortho, gmres_precision prec, int maxiter,
                                  gmres_info *info) {
     int path = h->opts.path;
+    const bool orth = h->opts.orth_norm != GMRES_ORTH_OFF;
     if (path == GMRES_PATH_AUTO)
-        path = (h->n <= 16384 && !(h->has_precond && h->opts.precond)) ? GMRES_PATH_BLOCK
-                                                                        : GMRES_PATH_GRID;
+        path = (h->n <= 16384 && !(h->has_precond && h->opts.precond) && !orth)
+                   ? GMRES_PATH_BLOCK
+                   : GMRES_PATH_GRID;
+    if (path == GMRES_PATH_BLOCK && orth)
+        return GMRES_ERR_ARG;  // the loss-of-orthogonality test runs on the grid path
     info->path = path;
     if (path == GMRES_PATH_BLOCK)
         return solve_block<T, VT>(h, b, x, m, tol, ortho, prec, maxiter, info);
@@ -636,6 +714,10 @@ gmres_status validate_opts(const gmres_opts *o) {
         (o->spmv_lanes != 0 && (o->spmv_lanes < 1 || o->spmv_lanes > 32 ||
                                 (o->spmv_lanes & (o->spmv_lanes - 1)))) ||
         o->cgs_kernel < 0 || o->cgs_kernel > 1 || o->mgs_kernel < 0 || o->mgs_kernel > 1 ||
+        o->l2_prefetch < 0 || o->l2_prefetch > 4 || !(o->stall_factor >= 0) ||
+        o->stall_window < 0 || o->stall_window > MMAX || o->orth_norm < GMRES_ORTH_OFF ||
+        o->orth_norm > GMRES_ORTH_FROBENIUS || o->orth_iters < 0 ||
+        (o->orth_norm != GMRES_ORTH_OFF && !(o->orth_threshold > 0)) ||
         o->repeat_first < -1 || o->repeat_first > 1 || o->precond < 0 || o->precond > 1)
         return GMRES_ERR_ARG;
     return GMRES_OK;
@@ -658,6 +740,11 @@ void gmres_default_opts(gmres_opts *o) {
     o->precond = 0;
     o->fallback = 1;
     o->spmv_lanes = 0;
+    o->stall_factor = 0.0;
+    o->stall_window = 0;
+    o->orth_norm = GMRES_ORTH_OFF;
+    o->orth_threshold = 1.0;
+    o->orth_iters = 10;
 }
 
 const char *gmres_status_str(gmres_status s) {
@@ -806,7 +893,7 @@ void gmres_destroy(gmres_t h) {
                       &h->part, &h->part64, &h->ctl, &h->bsys, &h->bres, &h->pvals64,
                       &h->pvals32, &h->spai_feat, &h->spai_rowv, &h->tvals32, &h->spai_params,
                       &h->spai_m, &h->spai_gm, &h->spai_H, &h->spai_vec, &h->spai_part,
-                      &h->spai_Z, &h->spai_grad})
+                      &h->spai_Z, &h->spai_grad, &h->mgs_seq, &h->mon})
         b->release();
     if (h->hctl)
         cudaFreeHost(h->hctl);
@@ -985,6 +1072,7 @@ gmres_status arnoldi_impl(gmres_handle *h, const double *r0, int m, int kmax, gm
     // r = fl(r0): the residual kernel with x = 0 gives z = r0 exactly
     CK(cudaMemsetAsync(h->xb.p, 0, sizeof(double) * h->ldv, h->stream));
     CK(launch_residual(h, c, r0, h->xb.as<double>(), nullptr, 1));
+    CK(cudaMemsetAsync(mon_hist(h), 0, (MMAX + 2) * sizeof(double), h->stream));
     k_init<T, VT><<<h->grid, kThreads, 0, h->stream>>>(c);
     CKL();
     std::vector<double> arnv;
@@ -1160,6 +1248,21 @@ gmres_status gmres_memory_bytes(gmres_t h, int32_t m, gmres_precision prec, int6
                            + 2 * (int64_t)(m + 1) * m * sT      // H, Hbar
                            + 6 * (int64_t)(m + 2) * sT;         // s, cs, sn, y, h1, h2
     }
+    return GMRES_OK;
+}
+
+gmres_status gmres_orth_norms(gmres_t h, double *out, int32_t count) {
+    if (!h || !out || count < 0 || count > MMAX)
+        return GMRES_ERR_ARG;
+    if (count == 0)
+        return GMRES_OK;
+    if (h->mon.bytes < MON_DOUBLES * sizeof(double)) {
+        memset(out, 0, sizeof(double) * (size_t)count);
+        return GMRES_OK;
+    }
+    CK(cudaMemcpyAsync(out, mon_hist(h), sizeof(double) * (size_t)count, cudaMemcpyDeviceToHost,
+                       h->stream));
+    CK(cudaStreamSynchronize(h->stream));
     return GMRES_OK;
 }
 

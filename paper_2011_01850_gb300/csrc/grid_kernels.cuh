@@ -44,6 +44,11 @@ struct GridCtx {
     const int *prowptr;
     const int *pcolind;
     const T *pvals;
+    // third restart strategy (Sec. 3): |s_{j+1}| of the cycle (entry 0 =
+    // beta) and the stall test's factor (0 = off) and window
+    double *ahist;
+    double stall_factor;
+    int stall_w;
 };
 
 // 4 consecutive basis entries starting at p (16-byte aligned for fp32 /
@@ -140,7 +145,22 @@ __device__ __forceinline__ T csr_row(const int *__restrict__ rowptr, const int *
     T acc = 0;
     if (row < n) {
         int beg = __ldg(rowptr + row), end = __ldg(rowptr + row + 1);
-        for (int k = beg + gl; k < end; k += L)
+        int k = beg + gl;
+        // four independent gathers in flight per lane; the sum keeps the
+        // sequential order of k
+        for (; k + 3 * L < end; k += 4 * L) {
+            const int c0 = __ldg(colind + k), c1 = __ldg(colind + k + L);
+            const int c2 = __ldg(colind + k + 2 * L), c3 = __ldg(colind + k + 3 * L);
+            const T a0 = __ldg(a + k), a1 = __ldg(a + k + L);
+            const T a2 = __ldg(a + k + 2 * L), a3 = __ldg(a + k + 3 * L);
+            const T x0 = (T)Basis<XT>::ld(x + c0, xinv), x1 = (T)Basis<XT>::ld(x + c1, xinv);
+            const T x2 = (T)Basis<XT>::ld(x + c2, xinv), x3 = (T)Basis<XT>::ld(x + c3, xinv);
+            acc += a0 * x0;
+            acc += a1 * x1;
+            acc += a2 * x2;
+            acc += a3 * x3;
+        }
+        for (; k < end; k += L)
             acc += __ldg(a + k) * (T)Basis<XT>::ld(x + __ldg(colind + k), xinv);
     }
 #pragma unroll
@@ -267,6 +287,8 @@ __global__ void __launch_bounds__(256) k_init(GridCtx<T, VT> c) {
     if (!c.ctl->active)
         return;
     const T beta = (T)c.ctl->beta;
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        c.ahist[0] = c.ctl->beta;
     int64_t rb, re;
     block_rows(c, rb, re);
     for (int64_t r = rb + 4 * threadIdx.x; r < re; r += 4 * blockDim.x) {
@@ -337,8 +359,11 @@ __device__ void givens_step(GridCtx<T, VT> &c, int col, const T *hc_global, T hn
         k->breakdown = bd;
         if (nf)
             k->nonfinite = 1;
+        c.ahist[col + 1] = arn;
+        int stall = c.stall_factor > 0 && col + 1 >= c.stall_w &&
+                    c.ahist[col + 1 - c.stall_w] < c.stall_factor * arn;
         int end = bd || nf || (c.tau > 0 && arn <= c.tau * k->beta) || arn <= c.inner_abs ||
-                  (col + 1 >= c.kmax);
+                  stall || (col + 1 >= c.kmax);
         k->active = !end;
     }
     __syncthreads();
@@ -572,8 +597,11 @@ __global__ void __launch_bounds__(256) k_mgs_last(GridCtx<T, VT> c, int ncols) {
 // v_{col} = w / h_{j+1,j} (Alg. 1 "v_{j+1} <- w / h_{j+1,j}"), rounded to the
 // basis type.  Skipped when the cycle has ended.
 template <class T, class VT>
-__global__ void __launch_bounds__(256) k_normalize(GridCtx<T, VT> c, int col) {
-    if (!c.ctl->active)
+__global__ void __launch_bounds__(256) k_normalize(GridCtx<T, VT> c, int col, int force) {
+    // force: also on the step that ended the cycle (the loss-of-orthogonality
+    // test reads v_{j+1}); never after a breakdown or a skipped step
+    if (!c.ctl->active &&
+        !(force && c.ctl->j == col && !c.ctl->breakdown && !c.ctl->nonfinite))
         return;
     const T h = (T)c.ctl->hnext;
     int64_t rb, re;

@@ -84,6 +84,9 @@ struct gmres_handle {
     int rows_blocks_per_sm = 4;  // blocks per SM of the register-streaming CGSR kernels
     int64_t mgs_chunk = 0;       // rows per block of the cooperative MGS kernel
     std::map<const void *, bool> mgs_ok_cache;  // cooperative MGS feasible, per kernel
+    DevBuf mgs_seq;              // exchange slots of the cooperative MGS kernel
+    DevBuf mon;                  // restart-test histories and the U, S matrices
+    unsigned mgs_round = 0;      // next exchange round number (0: flags not set up)
     int64_t chunk = 0;     // rows per block
     // matrix
     DevBuf rowptr, colind, vals64, vals32;

@@ -6,17 +6,18 @@
 // reductions in sequence.  Here every block keeps its row chunk of w in shared
 // memory for the whole step; per basis vector it makes one sweep over its
 // rows that applies the previous projection (w <- w - h_{i-1} v_{i-1}) and
-// accumulates w . v_i, writes its partial, and meets the other blocks at a
-// grid barrier; then every block sums all partials in block order (so all
-// blocks see the same h_i, bit for bit).  The last sweep applies the final
-// projection and takes ||w||; the blocks then write v_{j+1} = w / h_{j+1,j}
-// straight into the basis and block 0 runs the Givens step.  w never goes
-// back to global memory and the basis is read once from HBM per step (the
-// previous vector comes back from L1/L2).
+// accumulates w . v_i, then takes part in one exchange round: it publishes
+// its partial with a release flag and sums every block's partial in block
+// order as the flags arrive (so all blocks see the same h_i, bit for bit;
+// the flags are the only synchronisation, no separate barrier).  The last
+// sweep applies the final projection and takes ||w||; the blocks then write
+// v_{j+1} = w / h_{j+1,j} straight into the basis and block 0 runs the
+// Givens step.  w never goes back to global memory and the basis is read once
+// from HBM per step (the previous vector comes back from L1/L2).
 //
-// The grid is launched cooperatively (all blocks resident).  Every barrier
-// wait is bounded: after `spin` polls the block records a timeout in the
-// control block, the other blocks see it at their next poll, and all return.
+// The grid is launched cooperatively (all blocks resident).  Every wait is
+// bounded: after `spin` polls the block records a timeout in the control
+// block, the other blocks see it at their next poll, and all return.
 #pragma once
 
 #include "grid_kernels.cuh"
@@ -25,75 +26,145 @@ namespace gmres {
 
 constexpr int MGSP_THREADS = 512;
 
-__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p) {
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+constexpr int MGSP_MAXGRID = 256;  // exchange slots read by one warp: <= 8 per lane
+constexpr int MGSP_QMAX = MGSP_MAXGRID / 32;
+
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
 }
-__device__ __forceinline__ void st_release_gpu(unsigned *p, unsigned v) {
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long *p, unsigned long long v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ void st_release_u64(unsigned long long *p, unsigned long long v) {
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ void fence_acq_rel_gpu() {
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
 }
 
-// Grid barrier over co-resident blocks: bar[0] arrival count, bar[1]
-// generation.  Returns false (in every thread of the block) when this block
-// gave up after `limit` polls or saw another block give up (*err != 0).
-__device__ __forceinline__ bool grid_barrier(unsigned *bar, int *err, long long limit) {
-    __shared__ int s_ok;
-    __syncthreads();
+// One round of the grid-wide exchange that replaces "barrier, then sum the
+// per-block partials".  Every block owns 4 words per parity p in `slots`.
+// Thread 0 publishes the block's NV partials: for binary32 each word holds
+// (round << 32 | value bits), so one 64-bit store publishes a value together
+// with its round; for binary64 the values go first and a release store of
+// the round into word 3 follows.  Warp 0 of every block polls the words of
+// all blocks at once (lane l takes blocks l, l+32, ...; every poll issues all
+// of a lane's loads together), and once every block has published the round
+// sums the values in block order (per lane, then an xor butterfly, so every
+// block gets the same sums bit for bit) and broadcasts them.  A block may
+// overwrite its words of parity p only after it has seen every block publish
+// the round in between, which every block does only after reading round
+// k-2's values, so two parities suffice.  Round numbers grow across launches
+// and never repeat (the host clears the slots before they wrap), so a stale
+// word never matches.  Returns false in every thread of the block when a
+// wait gave up after `limit` polls or another block reported a timeout in
+// *err.
+template <class T, int NV>
+__device__ __forceinline__ bool exchange_round(unsigned long long *slots, int p, unsigned round,
+                                               const T (&mine)[NV], T (&out)[NV], int *err,
+                                               long long limit, T *sbuf) {
+    constexpr bool F32 = sizeof(T) == 4;
+    const int G = (int)gridDim.x;
     if (threadIdx.x == 0) {
-        int ok = 1;
-        const unsigned g = ld_acquire_gpu(bar + 1);
-        __threadfence();
-        const unsigned arrived = atomicAdd(bar, 1u);
-        if (arrived == gridDim.x - 1) {
-            atomicExch(bar, 0u);
-            __threadfence();
-            st_release_gpu(bar + 1, g + 1);
+        unsigned long long *my = slots + ((size_t)blockIdx.x * 2 + p) * 4;
+        if constexpr (F32) {
+#pragma unroll
+            for (int v = 0; v < NV; ++v)
+                st_relaxed_u64(my + v, ((unsigned long long)round << 32) |
+                                           (unsigned long long)__float_as_uint((float)mine[v]));
         } else {
-            long long it = 0;
-            while (ld_acquire_gpu(bar + 1) == g) {
-                if (*(volatile int *)err != 0 || ++it > limit) {
-                    atomicExch(err, 1);
-                    ok = 0;
-                    break;
+#pragma unroll
+            for (int v = 0; v < NV; ++v)
+                st_relaxed_u64(my + v, (unsigned long long)__double_as_longlong((double)mine[v]));
+            st_release_u64(my + 3, (unsigned long long)round);
+        }
+    }
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        unsigned long long w[MGSP_QMAX][NV];
+        bool ok = true;
+        long long it = 0;
+        for (;;) {
+            bool ready = true;
+#pragma unroll
+            for (int q = 0; q < MGSP_QMAX; ++q) {
+                const int b = lane + 32 * q;
+                if (b < G) {
+                    const unsigned long long *ws = slots + ((size_t)b * 2 + p) * 4;
+                    if constexpr (F32) {
+#pragma unroll
+                        for (int v = 0; v < NV; ++v) {
+                            w[q][v] = ld_relaxed_u64(ws + v);
+                            ready = ready && (unsigned)(w[q][v] >> 32) == round;
+                        }
+                    } else {
+                        ready = ready && (unsigned)ld_relaxed_u64(ws + 3) == round;
+                    }
                 }
-                __nanosleep(64);
+            }
+            if (__all_sync(0xffffffffu, ready))
+                break;
+            if (*(volatile int *)err != 0 || ++it > limit) {
+                ok = false;
+                break;
             }
         }
-        __threadfence();
-        s_ok = ok && (*(volatile int *)err == 0);
+        ok = __all_sync(0xffffffffu, ok);
+        T acc[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v)
+            acc[v] = 0;
+        if (ok) {
+            if constexpr (!F32)
+                fence_acq_rel_gpu();
+#pragma unroll
+            for (int q = 0; q < MGSP_QMAX; ++q) {
+                const int b = lane + 32 * q;
+                if (b < G) {
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) {
+                        if constexpr (F32)
+                            acc[v] += (T)__uint_as_float((unsigned)(w[q][v] & 0xffffffffull));
+                        else
+                            acc[v] += (T)__longlong_as_double((long long)ld_relaxed_u64(
+                                slots + ((size_t)b * 2 + p) * 4 + v));
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int v = 0; v < NV; ++v)
+            acc[v] = warp_sum(acc[v]);
+        if (lane == 0) {
+            if (!ok)
+                atomicExch(err, 1);
+#pragma unroll
+            for (int v = 0; v < NV; ++v)
+                sbuf[v] = acc[v];
+            sbuf[NV] = ok ? T(1) : T(0);
+        }
     }
     __syncthreads();
-    return s_ok != 0;
-}
-
-// Sum of slot `slot` of every block's partials, in block order, broadcast to
-// the whole block.
-template <class T>
-__device__ __forceinline__ T sum_partials(const T *part, int slot, T *sbuf) {
-    if (threadIdx.x < 32) {
-        T a = 0;
-        for (int b = threadIdx.x; b < (int)gridDim.x; b += 32)
-            a += ldcg(part + (size_t)b * PSTRIDE + slot);
-        a = warp_sum(a);
-        if (threadIdx.x == 0)
-            *sbuf = a;
-    }
+#pragma unroll
+    for (int v = 0; v < NV; ++v)
+        out[v] = sbuf[v];
+    const bool ok = sbuf[NV] != T(0);
     __syncthreads();
-    T v = *sbuf;
-    __syncthreads();
-    return v;
+    return ok;
 }
 
 template <class T, class VT>
 __global__ void __launch_bounds__(MGSP_THREADS, 1)
-    k_mgs_persist(GridCtx<T, VT> c, int ncols, int64_t chunk, long long spin, unsigned *bar) {
+    k_mgs_persist(GridCtx<T, VT> c, int ncols, int64_t chunk, long long spin,
+                  unsigned long long *slots, unsigned round0) {
     if (!c.ctl->active)
         return;
     extern __shared__ __align__(16) unsigned char mgs_smem[];
     T *ws = reinterpret_cast<T *>(mgs_smem);
     __shared__ T sred[2 * 32];
-    __shared__ T sval;
+    __shared__ T sx[3];
     __shared__ T hcol[MMAX + 2];
     const int tid = threadIdx.x, nth = blockDim.x;
     const int64_t rb = (int64_t)blockIdx.x * chunk;
@@ -101,7 +172,6 @@ __global__ void __launch_bounds__(MGSP_THREADS, 1)
     if (re > c.ldv)
         re = c.ldv;
     const int64_t len = re > rb ? re - rb : 0;
-    T *mypart = c.part + (size_t)blockIdx.x * PSTRIDE;
     int *err = &c.ctl->timeout;
 
     for (int64_t q = 4 * tid; q < len; q += 4 * nth) {
@@ -113,6 +183,7 @@ __global__ void __launch_bounds__(MGSP_THREADS, 1)
     }
     __syncthreads();
     // h_0 = w . v_0 and ||w||^2 (breakdown reference)
+    T hprev, wn0sq;
     {
         T acc[2] = {0, 0};
         for (int64_t q = 4 * tid; q < len; q += 4 * nth) {
@@ -125,15 +196,12 @@ __global__ void __launch_bounds__(MGSP_THREADS, 1)
             }
         }
         block_sum<T, 2>(acc, sred);
-        if (tid == 0) {
-            mypart[0] = acc[0];
-            mypart[2] = acc[1];
-        }
+        T tot[2];
+        if (!exchange_round<T, 2>(slots, 0, round0, acc, tot, err, spin, sx))
+            return;
+        hprev = tot[0];
+        wn0sq = tot[1];
     }
-    if (!grid_barrier(bar, err, spin))
-        return;
-    T hprev = sum_partials(c.part, 0, &sval);
-    const T wn0sq = sum_partials(c.part, 2, &sval);
     if (tid == 0)
         hcol[0] = hprev;
     // h_i for i >= 1: one sweep applies projection i-1 and dots with v_i
@@ -152,16 +220,15 @@ __global__ void __launch_bounds__(MGSP_THREADS, 1)
                 d += wv * b[k];
             }
         }
-        d = block_sum1(d, sred);
-        if (tid == 0)
-            mypart[i & 1] = d;
-        if (!grid_barrier(bar, err, spin))
+        T dv[1] = {block_sum1(d, sred)}, hv[1];
+        if (!exchange_round<T, 1>(slots, i & 1, round0 + (unsigned)i, dv, hv, err, spin, sx))
             return;
-        hprev = sum_partials(c.part, i & 1, &sval);
+        hprev = hv[0];
         if (tid == 0)
             hcol[i] = hprev;
     }
     // last projection and ||w||^2
+    T hnext;
     {
         const VT *vp = c.V + (size_t)(ncols - 1) * c.ldv + rb;
         T nsq = 0;
@@ -175,13 +242,12 @@ __global__ void __launch_bounds__(MGSP_THREADS, 1)
                 nsq += wv * wv;
             }
         }
-        nsq = block_sum1(nsq, sred);
-        if (tid == 0)
-            mypart[3] = nsq;
+        T nv[1] = {block_sum1(nsq, sred)}, tv[1];
+        if (!exchange_round<T, 1>(slots, ncols & 1, round0 + (unsigned)ncols, nv, tv, err,
+                                  spin, sx))
+            return;
+        hnext = wsqrt(tv[0]);
     }
-    if (!grid_barrier(bar, err, spin))
-        return;
-    const T hnext = wsqrt(sum_partials(c.part, 3, &sval));
     // v_{j+1} = w / h_{j+1,j} into basis column ncols (unused if the cycle ends)
     if (hnext > T(0)) {
         VT *dst = c.V + (size_t)ncols * c.ldv + rb;

@@ -24,6 +24,7 @@ OK, MAXITER, ERR_ARG, ERR_CUDA, ERR_NONFINITE, ERR_BREAKDOWN, ERR_TIMEOUT, ERR_O
     0, 1, -1, -2, -3, -4, -5, -6)
 CREATE_DEVICE_PTRS, CREATE_TRANSPOSE = 1, 2
 PATH_AUTO, PATH_GRID, PATH_BLOCK = 0, 1, 2
+ORTH_OFF, ORTH_SPECTRAL, ORTH_FROBENIUS = 0, 1, 2
 K_RESIDUAL, K_SPMV, K_ORTHO, K_NORMALIZE, K_UPDATE, K_PRECOND, K_BLOCK = range(7)
 K_COUNT = 8
 KERNEL_CLASS_NAMES = ["residual", "spmv", "ortho", "normalize", "update", "precond", "block"]
@@ -51,7 +52,14 @@ class Opts(ctypes.Structure):
         ("spmv_lanes", ctypes.c_int32),
         ("cgs_kernel", ctypes.c_int32),
         ("mgs_kernel", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 3),
+        ("l2_prefetch", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 2),
+        ("stall_factor", ctypes.c_double),
+        ("stall_window", ctypes.c_int32),
+        ("orth_norm", ctypes.c_int32),
+        ("orth_threshold", ctypes.c_double),
+        ("orth_iters", ctypes.c_int32),
+        ("reserved2", ctypes.c_int32),
     ]
 
 
@@ -104,6 +112,7 @@ SIGNATURES = {
     "gmres_autotune": (_st, [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
     "gmres_memory_bytes": (_st, [_vp, _i32, _i32, ctypes.POINTER(ctypes.c_int64),
                                  ctypes.POINTER(ctypes.c_int64)]),
+    "gmres_orth_norms": (_st, [_vp, _vp, _i32]),
     "gmres_batch_create": (_st, [ctypes.POINTER(_vp), _i32, _vp, _vp, _vp, _vp, _vp]),
     "gmres_batch_destroy": (None, [_vp]),
     "gmres_batch_solve": (_st, [_vp, _vp, _vp, _i32, _f64, _i32, _i32, _i32, _i32, _vp,
@@ -264,6 +273,13 @@ def gmres_autotune(h):
     b = ctypes.c_int32()
     _check(lib().gmres_autotune(h, ctypes.byref(a), ctypes.byref(b)), "gmres_autotune")
     return a.value, b.value
+
+
+def gmres_orth_norms(h, count):
+    """||S_k|| after each inner iteration of the handle's last cycle."""
+    out = np.zeros(int(count))
+    _check(lib().gmres_orth_norms(h, out.ctypes.data_as(_vp), int(count)), "gmres_orth_norms")
+    return out
 
 
 def gmres_memory_bytes(h, m, prec):

@@ -333,8 +333,8 @@ def test_mgs_cooperative_matches_per_column(gpulib, stream):
 
 
 def test_bounded_wait_reports_timeout(gpulib, stream):
-    """With the spin limit at 1 the grid barrier of the cooperative MGS kernel
-    gives up at once: the solve ends with GMRES_ERR_TIMEOUT instead of
+    """With the spin limit at 1 the exchange waits of the cooperative MGS
+    kernel give up at once: the solve ends with GMRES_ERR_TIMEOUT instead of
     waiting, and the handle stays usable."""
     A = I.powerlaw_random(200000, seed=5)
     b = I.rhs_ones_noise(A, 1e-3, 4)
