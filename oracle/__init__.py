@@ -26,7 +26,7 @@ _lib = None
 
 MGS, CGSR = 0, 1
 ORTH_OFF, ORTH_SPECTRAL, ORTH_FROBENIUS = 0, 1, 2
-FP64, MIXED, MIXED_BF16, MIXED_FP16, ALL_FP32 = 0, 1, 2, 3, 4
+FP64, MIXED, MIXED_BF16, MIXED_FP16, ALL_FP32, MIXED_LIMITED = 0, 1, 2, 3, 4, 5
 
 _i32p = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
 _f64p = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
@@ -281,7 +281,7 @@ def default_tau(prec):
     second strategy): the performance study's 1e-6 for binary32; for the
     16-bit bases one unit roundoff of the storage format (2^-8, 2^-11)."""
     return {FP64: 0.0, MIXED: 1e-6, MIXED_BF16: 2.0 ** -8, MIXED_FP16: 2.0 ** -11,
-            ALL_FP32: 1e-6}[prec]
+            ALL_FP32: 1e-6, MIXED_LIMITED: 1e-6}[prec]
 
 
 def gmres(A, b, x0=None, m=30, tol=1e-10, ortho=CGSR, prec=FP64, maxiter=10000, tau=None,

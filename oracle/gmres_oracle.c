@@ -294,7 +294,8 @@ static int run_cycle(int32_t n, const int32_t *rowptr, const int32_t *colind, co
                      double *V, double *Hb, double *H, double *s, double *cs, double *sn,
                      double *y, double *u, double *arn, double *orth, int32_t *jout, int32_t *bd)
 {
-    const int is_f32 = (prec != ORC_FP64);
+    const int is_f32 = (prec != ORC_FP64 && prec != ORC_MIXED_LIMITED);
+    const int limited = (prec == ORC_MIXED_LIMITED);
     const size_t el = is_f32 ? sizeof(float) : sizeof(double);
     const int32_t nnz = rowptr[n];
     const int32_t pnnz = pm_vals ? pm_rowptr[n] : -1;
@@ -316,10 +317,15 @@ static int run_cycle(int32_t n, const int32_t *rowptr, const int32_t *colind, co
                        (float *)c.cs, (float *)c.sn, (float *)c.y, (float *)c.u, arn, orth, jout,
                        bd);
     } else {
-        memcpy(c.a, vals, sizeof(double) * (size_t)nnz);
+        /* limited mixed: A for the next Krylov vector and M stored in
+         * binary32, used in binary64 arithmetic (the basis is rounded by
+         * orc_store) */
+        double *a = (double *)c.a, *pm = (double *)c.pm;
+        for (int32_t k = 0; k < nnz; ++k)
+            a[k] = limited ? (double)(float)vals[k] : vals[k];
         memcpy(c.r0, r0, sizeof(double) * (size_t)n);
-        if (pm_vals)
-            memcpy(c.pm, pm_vals, sizeof(double) * (size_t)pnnz);
+        for (int32_t k = 0; k < pnnz; ++k)
+            pm[k] = limited ? (double)(float)pm_vals[k] : pm_vals[k];
         rc = cycle_f64(n, rowptr, colind, (double *)c.a, (double *)c.r0, m, kmax, ortho, prec,
                        rs, pm_rowptr, pm_colind, pm_vals ? (double *)c.pm : NULL,
                        (double *)c.V, (double *)c.Hb, (double *)c.H, (double *)c.s,
@@ -357,7 +363,7 @@ int orc_arnoldi_cycle_ex(int32_t n, const int32_t *rowptr, const int32_t *colind
                          int32_t *jout, int32_t *breakdown)
 {
     if (n <= 0 || m < 1 || kmax < 1 || kmax > m || (ortho != ORC_MGS && ortho != ORC_CGSR) ||
-        prec < ORC_FP64 || prec > ORC_ALL_FP32 || !csr_ok(n, rowptr, colind) ||
+        prec < ORC_FP64 || prec > ORC_MIXED_LIMITED || !csr_ok(n, rowptr, colind) ||
         !restart_ok(rs))
         return -1;
     if (pm_vals && !csr_ok(n, pm_rowptr, pm_colind))
@@ -413,7 +419,7 @@ int orc_gmres(int32_t n, const int32_t *rowptr, const int32_t *colind, const dou
 {
     if (!o || n <= 0 || o->m < 1 || o->maxiter < 0 || !(o->tol > 0) ||
         (o->ortho != ORC_MGS && o->ortho != ORC_CGSR) || o->prec < ORC_FP64 ||
-        o->prec > ORC_ALL_FP32 || !csr_ok(n, rowptr, colind) || !b || !x ||
+        o->prec > ORC_MIXED_LIMITED || !csr_ok(n, rowptr, colind) || !b || !x ||
         o->stall_factor < 0 || o->stall_window < 0 || o->orth_norm < ORC_ORTH_OFF ||
         o->orth_norm > ORC_ORTH_FROBENIUS ||
         (o->orth_norm == ORC_ORTH_SPECTRAL && o->orth_iters < 1))

@@ -40,13 +40,18 @@ enum { ORC_MGS = 0, ORC_CGSR = 1 };
  *   ORC_MIXED_FP16 as ORC_MIXED, with each Krylov vector stored as binary16
  *                  after scaling by the power of two 2^floor(log2(n)/2).
  *   ORC_ALL_FP32   negative control: residual and update in binary32 as well,
- *                  which Sec. 2 predicts cannot pass single-precision accuracy. */
-enum { ORC_FP64 = 0, ORC_MIXED = 1, ORC_MIXED_BF16 = 2, ORC_MIXED_FP16 = 3, ORC_ALL_FP32 = 4 };
+ *                  which Sec. 2 predicts cannot pass single-precision accuracy.
+ *   ORC_MIXED_LIMITED the paper's "limited" mixed solver (Sec. 4.1): binary32
+ *                  only for storing A as used for the next Krylov vector, the
+ *                  preconditioner M and the Krylov basis V; every operation
+ *                  and every other variable in binary64. */
+enum { ORC_FP64 = 0, ORC_MIXED = 1, ORC_MIXED_BF16 = 2, ORC_MIXED_FP16 = 3, ORC_ALL_FP32 = 4,
+       ORC_MIXED_LIMITED = 5 };
 
 typedef struct {
     int32_t m;            /* maximum inner iterations per restart cycle         */
     int32_t ortho;        /* ORC_MGS or ORC_CGSR                                 */
-    int32_t prec;         /* ORC_FP64 ... ORC_ALL_FP32                           */
+    int32_t prec;         /* ORC_FP64 ... ORC_MIXED_LIMITED                      */
     int32_t maxiter;      /* cap on the total number of inner iterations         */
     int32_t repeat_first; /* 1: after the first cycle, every cycle is limited to
                              the first cycle's length (Sec. 3, first strategy)  */

@@ -268,12 +268,42 @@ def pin_mixed_reaches_double():
     A = I.convdiff2d(16, pe=10.0)
     b = I.rhs_ones_noise(A, 1e-3, 9)
     xl = np.linalg.solve(_dense(A), b)
-    for prec in (O.MIXED, O.MIXED_BF16, O.MIXED_FP16):
+    for prec in (O.MIXED, O.MIXED_BF16, O.MIXED_FP16, O.MIXED_LIMITED):
         for ortho in (O.MGS, O.CGSR):
             x, info = O.gmres(A, b, m=30, tol=1e-10, ortho=ortho, prec=prec, maxiter=3000)
             assert info["converged"] and info["relres"] <= 1e-10, (prec, ortho, info)
             assert np.linalg.norm(b - _dense(A) @ x) <= 1e-10 * np.linalg.norm(b)
             assert np.linalg.norm(x - xl) / np.linalg.norm(xl) <= 1e-8
+
+
+def pin_limited_mixed():
+    """Sec. 4.1: keeping every operation in binary64 and storing only A (for
+    the next Krylov vector) and the basis in binary32 lets MGS improve further
+    before it stalls than the fully mixed solver does; the first Arnoldi steps
+    agree with binary64 to binary32 accuracy, a basis
+    vector it stores is exactly a binary32 number, and the first Hessenberg
+    entry is v_1^T A_32 v_1 with A_32 the binary32 rounding of A."""
+    A = I.convdiff2d(30, pe=1.0)
+    b = I.rhs_ones_noise(A, 1e-3, 1)
+    nb = np.linalg.norm(b)
+    full = O.arnoldi_cycle(A, b, 100, ortho=O.MGS, prec=O.MIXED)
+    lim = O.arnoldi_cycle(A, b, 100, ortho=O.MGS, prec=O.MIXED_LIMITED)
+    f64 = O.arnoldi_cycle(A, b, 100, ortho=O.MGS, prec=O.FP64)
+    floor_full = full["arn"][: full["j"]].min() / nb
+    floor_lim = lim["arn"][: lim["j"]].min() / nb
+    assert floor_lim <= 0.1 * floor_full, (floor_lim, floor_full)
+    assert floor_lim >= f64["arn"][: f64["j"]].min() / nb
+    V = lim["V"][: lim["j"]]
+    assert np.array_equal(V, V.astype(np.float32).astype(np.float64))
+    rel = np.abs(lim["arn"][:5] - f64["arn"][:5]) / f64["arn"][:5]
+    assert rel.max() <= 1e-5
+    # the first Hessenberg entry is v_1^T (A_32 v_1) in binary64, A_32 the
+    # matrix rounded to binary32 (A itself would differ at ~1e-8)
+    A32 = _dense(A).astype(np.float32).astype(np.float64)
+    v1 = lim["V"][0]
+    h11 = v1 @ (A32 @ v1)
+    assert abs(lim["Hbar"][0, 0] - h11) <= 1e-13 * abs(h11)
+    assert abs(v1 @ (_dense(A) @ v1) - h11) > 1e-12 * abs(h11)
 
 
 def pin_negative_control():
@@ -611,5 +641,5 @@ ALL_PINS = [
     pin_spmv_and_residual, pin_basis_rounding,
     pin_spai_grad_m_fd, pin_spai_grad_params_fd, pin_spai_special_cases, pin_spai_optimum,
     pin_spai_feature_invariants, pin_adam_first_step, pin_stall_restart, pin_s_matrix,
-    pin_orthogonality_loss_restart,
+    pin_orthogonality_loss_restart, pin_limited_mixed,
 ]
