@@ -49,6 +49,8 @@ class Opts(ctypes.Structure):
         ("orth_threshold", ctypes.c_double),
         ("orth_norm", ctypes.c_int32),
         ("orth_iters", ctypes.c_int32),
+        ("split_bytes", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
 
 
@@ -63,7 +65,7 @@ class Restart(ctypes.Structure):
         ("stall_window", ctypes.c_int32),
         ("orth_norm", ctypes.c_int32),
         ("orth_iters", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("split_bytes", ctypes.c_int32),
     ]
 
 
@@ -123,6 +125,8 @@ def _bind(L):
     L.orc_arnoldi_cycle_ex.restype = ctypes.c_int
     L.orc_s_norm2.argtypes = [ctypes.c_int32, _f64p, ctypes.c_int32, ctypes.c_int32]
     L.orc_s_norm2.restype = ctypes.c_double
+    L.orc_high_part.argtypes = [ctypes.c_double]
+    L.orc_high_part.restype = ctypes.c_double
     L.orc_gmres.argtypes = [ctypes.c_int32, _i32p, _i32p, _f64p, _f64p, _f64p,
                             ctypes.POINTER(Opts), vp, vp, vp, ctypes.POINTER(Info), vp, vp]
     L.orc_gmres.restype = ctypes.c_int
@@ -222,7 +226,7 @@ def round_basis(v, prec, n):
 
 def arnoldi_cycle(A, r0, m, ortho=CGSR, prec=FP64, kmax=None, tau=0.0, inner_abs=0.0, M=None,
                   export_basis=True, stall_factor=0.0, stall_window=0, orth_norm=ORTH_OFF,
-                  orth_threshold=1.0, orth_iters=10):
+                  orth_threshold=1.0, orth_iters=10, split_bytes=False):
     """One restart cycle from residual r0; returns a dict of its quantities.
 
     V is (m+1, n) (row i = basis vector i), Hbar/H are (m+1, m), the first ``j``
@@ -255,6 +259,7 @@ def arnoldi_cycle(A, r0, m, ortho=CGSR, prec=FP64, kmax=None, tau=0.0, inner_abs
     rs.stall_factor = stall_factor
     rs.stall_window = stall_window if stall_window > 0 else (m + 19) // 20
     rs.orth_norm, rs.orth_threshold, rs.orth_iters = orth_norm, orth_threshold, orth_iters
+    rs.split_bytes = int(bool(split_bytes))
     orth = np.zeros(m)
     rc = _L().orc_arnoldi_cycle_ex(n, rp, ci, va, np.ascontiguousarray(r0, np.float64), m, kmax,
                                     ortho, prec, ctypes.byref(rs), *margs, _ptr(V), _ptr(Hb),
@@ -266,6 +271,11 @@ def arnoldi_cycle(A, r0, m, ortho=CGSR, prec=FP64, kmax=None, tau=0.0, inner_abs
     jj = j.value
     return dict(V=V, Hbar=Hb.T.copy(), H=H.T.copy(), s=s, cs=cs, sn=sn, y=y, u=u, arn=arn, j=jj,
                 breakdown=bool(bd.value), orth=orth)
+
+
+def high_part(v):
+    """The high-order 32 bits of the binary64 value v, as a binary64 value."""
+    return _L().orc_high_part(float(v))
 
 
 def s_norm2(S, iters=10):
@@ -286,12 +296,15 @@ def default_tau(prec):
 
 def gmres(A, b, x0=None, m=30, tol=1e-10, ortho=CGSR, prec=FP64, maxiter=10000, tau=None,
           repeat_first=None, inner_factor=0.5, M=None, history=False, stall_factor=0.0,
-          stall_window=0, orth_norm=ORTH_OFF, orth_threshold=1.0, orth_iters=10):
+          stall_window=0, orth_norm=ORTH_OFF, orth_threshold=1.0, orth_iters=10,
+          split_bytes=False):
     """Restarted GMRES(m) (Algorithm 1).  Returns (x, info dict).
 
     Restart strategies (Sec. 3): repeat_first (first), tau (second),
     stall_factor/stall_window (third; window 0 = ceil(0.05 m)), orth_norm /
-    orth_threshold / orth_iters (fourth, loss of orthogonality via ||S_k||)."""
+    orth_threshold / orth_iters (fourth, loss of orthogonality via ||S_k||).
+    split_bytes: A stored as high/low 32-bit halves, the Krylov step reading
+    the high-order half (Sec. 4)."""
     rp, ci, va = _csr(A)
     n = len(rp) - 1
     b = np.ascontiguousarray(b, dtype=np.float64)
@@ -304,6 +317,7 @@ def gmres(A, b, x0=None, m=30, tol=1e-10, ortho=CGSR, prec=FP64, maxiter=10000, 
     o.inner_factor = inner_factor
     o.stall_factor, o.stall_window = stall_factor, stall_window
     o.orth_norm, o.orth_threshold, o.orth_iters = orth_norm, orth_threshold, orth_iters
+    o.split_bytes = int(bool(split_bytes))
     info = Info()
     arn = np.zeros(max(maxiter, 1)) if history else None
     cyc = np.zeros(maxiter + 2) if history else None

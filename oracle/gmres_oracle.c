@@ -97,6 +97,15 @@ void orc_round_basis(int32_t count, const double *in, double *out, int32_t prec,
         out[i] = orc_store(in[i], prec, n);
 }
 
+double orc_high_part(double v)
+{
+    uint64_t u;
+    memcpy(&u, &v, sizeof(u));
+    u &= 0xFFFFFFFF00000000ull;
+    memcpy(&v, &u, sizeof(v));
+    return v;
+}
+
 /* ||S||_2 of a strictly upper triangular k x k S (column-major, leading
  * dimension ld) by the power method on S^T S (Sec. 3, fourth strategy; Sec.
  * 4.1 runs 10 iterations): x_0 has equal entries, x_t = S^T S x_{t-1}
@@ -305,8 +314,10 @@ static int run_cycle(int32_t n, const int32_t *rowptr, const int32_t *colind, co
     int rc;
     if (is_f32) {
         float *a = (float *)c.a, *r = (float *)c.r0, *pm = (float *)c.pm;
+        /* the Krylov step's copy of A: binary32, from the high-order part
+         * when A is stored split */
         for (int32_t k = 0; k < nnz; ++k)
-            a[k] = (float)vals[k];
+            a[k] = (float)(rs->split_bytes ? orc_high_part(vals[k]) : vals[k]);
         for (int32_t i = 0; i < n; ++i)
             r[i] = (float)r0[i];
         for (int32_t k = 0; k < pnnz; ++k)
@@ -322,7 +333,8 @@ static int run_cycle(int32_t n, const int32_t *rowptr, const int32_t *colind, co
          * orc_store) */
         double *a = (double *)c.a, *pm = (double *)c.pm;
         for (int32_t k = 0; k < nnz; ++k)
-            a[k] = limited ? (double)(float)vals[k] : vals[k];
+            a[k] = !limited ? vals[k]
+                            : (rs->split_bytes ? orc_high_part(vals[k]) : (double)(float)vals[k]);
         memcpy(c.r0, r0, sizeof(double) * (size_t)n);
         for (int32_t k = 0; k < pnnz; ++k)
             pm[k] = limited ? (double)(float)pm_vals[k] : pm_vals[k];
@@ -475,6 +487,7 @@ int orc_gmres(int32_t n, const int32_t *rowptr, const int32_t *colind, const dou
     rs.orth_norm = o->orth_norm;
     rs.orth_threshold = o->orth_threshold;
     rs.orth_iters = o->orth_iters;
+    rs.split_bytes = o->split_bytes;
     int32_t cycle_len = m;
     int rc = 0;
     for (;;) {

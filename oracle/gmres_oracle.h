@@ -68,6 +68,11 @@ typedef struct {
     int32_t orth_norm;    /* fourth strategy norm: 0 off, ORC_ORTH_SPECTRAL (power
                              method), ORC_ORTH_FROBENIUS                        */
     int32_t orth_iters;   /* power-method iterations (Sec. 4.1 uses 10)         */
+    int32_t split_bytes;  /* 1: A stored once as the high- and low-order 32 bits
+                             of each binary64 value (Sec. 4 outlook); the Krylov
+                             step reads the high-order part only (a value
+                             truncated to 20 fraction bits), the residual both */
+    int32_t reserved;
 } orc_opts;
 
 enum { ORC_ORTH_OFF = 0, ORC_ORTH_SPECTRAL = 1, ORC_ORTH_FROBENIUS = 2 };
@@ -85,7 +90,7 @@ typedef struct {
     int32_t stall_window;
     int32_t orth_norm;
     int32_t orth_iters;
-    int32_t reserved;
+    int32_t split_bytes;  /* as in orc_opts */
 } orc_restart;
 
 typedef struct {
@@ -154,6 +159,10 @@ int orc_arnoldi_cycle_ex(int32_t n, const int32_t *rowptr, const int32_t *colind
  * leading dimension ld) by `iters` power-method iterations on S^T S from the
  * vector of equal entries; exposed for the tests. */
 double orc_s_norm2(int32_t k, const double *S, int32_t ld, int32_t iters);
+
+/* The high-order 32 bits of a binary64 value as a binary64 value (the low
+ * 32 bits cleared: sign, exponent and the top 20 fraction bits). */
+double orc_high_part(double v);
 
 /* Restarted GMRES(m) (Alg. 1).  x holds x_0 on entry and the result on exit.
  * arn_hist (length maxiter) receives |s_{j+1}| of every inner iteration;

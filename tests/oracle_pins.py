@@ -306,6 +306,41 @@ def pin_limited_mixed():
     assert abs(v1 @ (_dense(A) @ v1) - h11) > 1e-12 * abs(h11)
 
 
+def _high_np(v):
+    """High-order 32 bits of binary64 values by bit masking in numpy."""
+    u = np.ascontiguousarray(v, dtype=np.float64).view(np.uint64) & np.uint64(0xFFFFFFFF00000000)
+    return u.view(np.float64)
+
+
+def pin_split_bytes():
+    """A stored once as high/low 32-bit halves (Sec. 4 outlook): the high
+    part is the value with its low 32 bits cleared (checked against numpy
+    bit masking; relative truncation below 2^-20); the Krylov step uses it
+    (limited mixed: the first Hessenberg entry is v_1^T A_hi v_1 in binary64);
+    binary64 GMRES is unaffected; mixed GMRES on split storage still reaches
+    the binary64 target and the LAPACK solution."""
+    rng = np.random.default_rng(8)
+    v = rng.standard_normal(1000) * np.exp(rng.uniform(-30, 30, 1000))
+    hi = np.array([O.high_part(x) for x in v])
+    assert np.array_equal(hi, _high_np(v))
+    assert np.all(np.abs(v - hi) <= 2.0 ** -20 * np.abs(v))
+    A = I.convdiff2d(16, pe=10.0)
+    b = I.rhs_ones_noise(A, 1e-3, 9)
+    Ahi = _high_np(_dense(A))
+    cyc = O.arnoldi_cycle(A, b, 10, ortho=O.MGS, prec=O.MIXED_LIMITED, split_bytes=True)
+    v1 = cyc["V"][0]
+    h11 = v1 @ (Ahi @ v1)
+    assert abs(cyc["Hbar"][0, 0] - h11) <= 1e-13 * abs(h11)
+    assert abs(v1 @ (_dense(A).astype(np.float32).astype(np.float64) @ v1) - h11) > 1e-12 * abs(h11)
+    c64 = O.arnoldi_cycle(A, b, 10, ortho=O.MGS, prec=O.FP64)
+    c64s = O.arnoldi_cycle(A, b, 10, ortho=O.MGS, prec=O.FP64, split_bytes=True)
+    assert np.array_equal(c64["Hbar"], c64s["Hbar"])
+    xl = np.linalg.solve(_dense(A), b)
+    for prec in (O.MIXED, O.MIXED_BF16, O.MIXED_LIMITED):
+        x, info = O.gmres(A, b, m=30, tol=1e-10, ortho=O.CGSR, prec=prec, split_bytes=True)
+        assert info["converged"] and np.linalg.norm(x - xl) / np.linalg.norm(xl) <= 1e-8
+
+
 def pin_negative_control():
     """A residual and update in binary32 cannot pass single-precision accuracy
     (Sec. 2, Sec. 4.1): the all-binary32 solver stalls above 1e-8."""
@@ -641,5 +676,5 @@ ALL_PINS = [
     pin_spmv_and_residual, pin_basis_rounding,
     pin_spai_grad_m_fd, pin_spai_grad_params_fd, pin_spai_special_cases, pin_spai_optimum,
     pin_spai_feature_invariants, pin_adam_first_step, pin_stall_restart, pin_s_matrix,
-    pin_orthogonality_loss_restart, pin_limited_mixed,
+    pin_orthogonality_loss_restart, pin_limited_mixed, pin_split_bytes,
 ]

@@ -69,8 +69,12 @@ MUTATIONS = [
      "ah[j - rs->stall_window] < arnres", "stall factor dropped"),
     ("gmres_oracle.c", "acc += S[(size_t)l * ld + i] * yv[i];",
      "acc += S[(size_t)i * ld + l] * yv[i];", "power method multiplies by S, not S^T"),
-    ("gmres_oracle.c", "a[k] = limited ? (double)(float)vals[k] : vals[k];",
-     "a[k] = vals[k];", "limited mode keeps A in binary64"),
+    ("gmres_oracle.c", "a[k] = !limited ? vals[k]", "a[k] = 1 ? vals[k]",
+     "limited mode keeps A in binary64"),
+    ("gmres_oracle.c", "u &= 0xFFFFFFFF00000000ull;", "u &= 0xFFFFFFFFF0000000ull;",
+     "high part keeps four low-order bits"),
+    ("gmres_oracle.c", "(rs->split_bytes ? orc_high_part(vals[k]) : (double)(float)vals[k])",
+     "(double)(float)vals[k]", "split storage ignored in the Krylov step"),
     ("spai_oracle.c", "atr[colind[k]] += vals[k] * r[i];", "atr[i] += vals[k] * r[colind[k]];",
      "A instead of A^T in the preconditioner gradient"),
     ("spai_oracle.c", "d2[o] = z2[o] > 0 ? dgk * params[P_W3 + o] : 0;",
