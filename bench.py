@@ -47,9 +47,12 @@ def parse():
     p.add_argument("--compare-steps", "--fp64-steps", dest="compare_steps", type=int, default=1)
     p.add_argument("--spai-params", default=None)
     p.add_argument("--cgs-kernel", type=int, default=0,
-                   help="CGSR kernel family: 0 register-streaming rows, 1 TMA tiles")
+                   help="CGSR kernel family: 0 register-streaming rows, 1 TMA tiles, "
+                        "2 rows with the per-row-group update")
     p.add_argument("--l2-prefetch", type=int, default=None,
                    help="CGSR rows kernels: slices prefetched ahead into L2 (library default)")
+    p.add_argument("--block-cluster", type=int, default=None,
+                   help="block path: 1 block or an 8-block cluster per system (library default)")
     p.add_argument("--spmv-lanes", type=int, default=0,
                    help="lanes per CSR row (0: autotuned)")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -125,6 +128,25 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(value, world, device="cuda"):
+    """The largest of every rank's value (the job's time is its slowest
+    rank's); the value itself on one rank."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def batched_seed(rank):
+    """Seed of the batch rank `rank` solves: with several GPUs every rank
+    solves its own independent batch of systems (the batched path shards by
+    system, with no collective; weak scaling)."""
+    return SEED + 104729 * rank
+
+
 def dist_setup(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -151,6 +173,10 @@ COMPARE = {
                     ("jacobi", "mixed", "cgsr", "jacobi"), ("fp64", "fp64", "cgsr", "none")],
 }
 SPAI_PARAMS = os.path.join(ROOT, "paper_2011_01850_gb300", "data", "spai_aniso64.npy")
+# DRAM bytes per algorithmic byte of the register-streaming CGSR passes, from
+# one ncu capture of a mid-cycle step (51 vectors) at 96^3: 565.3 MB of DRAM
+# traffic for 559.2 MB algorithmic; scaled to the timed launches.
+CGSR_ROWS_TRAFFIC_RATIO = 1.011
 
 
 def bench_ours(args):
@@ -179,6 +205,8 @@ def bench_ours(args):
     solver.set_opts(profile=1, cgs_kernel=args.cgs_kernel)
     if args.l2_prefetch is not None:
         solver.set_opts(l2_prefetch=args.l2_prefetch)
+    if args.block_cluster is not None:
+        solver.set_opts(block_cluster=args.block_cluster)
     learned = spec.get("precond") == "learned"
     spai_params = None
     if learned:
@@ -233,12 +261,7 @@ def bench_ours(args):
     ev1.record(stream)
     barrier()
     clk = clocks.stop()
-    ms_step = ev0.elapsed_time(ev1) / args.steps
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms_step], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
+    ms_step = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, world)
 
     # end to end through the public API with host buffers (H2D of b and x0,
     # D2H of x inside every step)
@@ -294,8 +317,8 @@ def bench_ours(args):
     tot_kms = sum(kms.values())
     iters = infos[0]["iters"]
     restarts = infos[0]["restarts"]
-    kernel_names = {"ortho": ("CGSR passes (k_cgs_rows x3 + k_reduce_cols x2)"
-                              if args.cgs_kernel == 0 else "CGSR passes (k_cgs_tile x3)")
+    kernel_names = {"ortho": ("CGSR passes (k_cgs_tile x3)" if args.cgs_kernel == 1
+                              else "CGSR passes (k_cgs_rows x3 + k_reduce_cols x2)")
                     if ortho == "cgsr" else "MGS step (k_mgs_persist, cooperative)",
                     "block": "single-block solver (k_block_solve)",
                     "spmv": "SpMV (k_spmv_step)", "residual": "binary64 residual (k_residual)"}
@@ -321,8 +344,10 @@ def bench_ours(args):
                   else "inputs L2-resident (no flush; small-system workload)",
             "parallelism": "replicas" if world > 1 else "single GPU",
             "spmv_lanes": {"f32": lanes32, "f64": lanes64},
-            "cgs_kernel": ["register-streaming rows", "TMA tiles"][args.cgs_kernel],
+            "cgs_kernel": ["register-streaming rows", "TMA tiles",
+                           "register-streaming rows, per-row-group update"][args.cgs_kernel],
             "l2_prefetch": int(G.gmres_get_opts(solver.h).l2_prefetch),
+            "block_cluster": int(G.gmres_get_opts(solver.h).block_cluster),
         },
         "iters": iters, "restarts": restarts,
         "compare": compare,
@@ -333,7 +358,10 @@ def bench_ours(args):
         "roofline": {
             "bound": "hbm", "kernel": kernel_names.get(dom, dom),
             "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-            "frac": round(achieved / peak, 4), "peak_kind": peak_kind, "traffic": None,
+            "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
+            "traffic": (round(CGSR_ROWS_TRAFFIC_RATIO * kbytes[dom] / klaunch[dom])
+                        if dom == "ortho" and ortho == "cgsr" and args.cgs_kernel == 0
+                        and klaunch[dom] else None),
             "launches": int(klaunch[dom]),
             "bytes_per_launch": kbytes[dom] / klaunch[dom] if klaunch[dom] else None,
         },
@@ -362,7 +390,7 @@ def bench_batched(args, world, rank, local):
     from paper_2011_01850_gb300 import gmres as G
     from paper_2011_01850_gb300 import inputs as I
 
-    systems = I.batched_convdiff2d(count=2048, nmin=500, nmax=50000, seed=SEED)
+    systems = I.batched_convdiff2d(count=2048, nmin=500, nmax=50000, seed=batched_seed(rank))
     sys_ptr, rp, ci, va, b = G.pack_batch(systems)
     nsys = len(systems)
     stream = torch.cuda.current_stream()
@@ -370,11 +398,16 @@ def bench_batched(args, world, rank, local):
     db = torch.tensor(b, device="cuda", dtype=torch.float64)
     dx = torch.zeros(len(b), device="cuda", dtype=torch.float64)
     m = 30
+    # SpMV lanes per row from the library's autotuner (capped solves, untimed)
+    lanes = {p_: G.gmres_batch_autotune(h, db, m, G.ORTHO_MGS, G.PRECISIONS[p_], 2 * m)
+             for p_ in ("fp64", "mixed")}
 
     def step(prec, collect):
+        # the tuned choice for this precision (lanes = 0 would reuse the last one tuned)
         dx.zero_()
         st, res, info = G.gmres_batch_solve(h, db, dx, m, 1e-10, G.ORTHO_MGS,
-                                            G.PRECISIONS[prec], 100000, nsys=nsys)
+                                            G.PRECISIONS[prec], 100000, lanes=lanes[prec],
+                                            nsys=nsys)
         if st != G.OK:
             raise RuntimeError("batched solve did not converge: %d" % st)
         collect.append((info.kernel_ms[G.K_BLOCK], info.kernel_bytes[G.K_BLOCK], info.iters,
@@ -384,18 +417,25 @@ def bench_batched(args, world, rank, local):
     for _ in range(args.warmup):
         step("mixed", scratch)
     infos = []
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
     clocks = ClockSampler(local)
     clocks.start()
-    torch.cuda.synchronize()
+    barrier()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
     for _ in range(args.steps):
         step("mixed", infos)
     ev1.record(stream)
-    torch.cuda.synchronize()
+    barrier()
     clk = clocks.stop()
-    ms_step = ev0.elapsed_time(ev1) / args.steps
+    ms_step = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, world)
     compare = {}
     if args.compare_steps > 0:
         got = []
@@ -434,12 +474,14 @@ def bench_batched(args, world, rank, local):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "batched2048", "systems": nsys, "rows": int(len(b)),
                    "nnz": int(len(ci)), "m": m, "ortho": "mgs", "precision": "mixed",
-                   "tol": 1e-10, "launch": "one persistent launch per batched solve",
-                   "l2": "inputs larger than L2"},
-        "systems_per_s": round(nsys / (ms_step * 1e-3), 1),
+                   "tol": 1e-10,
+                   "launch": "one-block and 8-block-cluster persistent launches, concurrent",
+                   "spmv_lanes": lanes, "l2": "inputs larger than L2"},
+        "systems_per_s": round(world * nsys / (ms_step * 1e-3), 1),
         "iters_total": infos[0][2], "restarts_total": infos[0][3],
         "compare": compare,
-        "roofline": {"bound": "hbm", "kernel": "batched single-block solver (k_block_solve)",
+        "roofline": {"bound": "hbm",
+                     "kernel": "batched whole-solve kernels (k_block_solve + k_team_solve)",
                      "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(ach / peak, 4), "peak_kind": peak_kind, "traffic": None,
                      "launches": args.steps, "bytes_per_launch": kb / args.steps},
@@ -447,6 +489,9 @@ def bench_batched(args, world, rank, local):
     }
     if rank == 0:
         print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
 
 
 def oracle_sample(A, b, spec, ks=(2, 8, 16)):

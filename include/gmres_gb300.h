@@ -46,12 +46,19 @@ typedef enum { GMRES_ORTHO_MGS = 0, GMRES_ORTHO_CGSR = 1 } gmres_ortho;
  *                     (round-to-nearest-even), binary32 arithmetic.
  *   GMRES_MIXED_FP16  as GMRES_MIXED with the Krylov basis stored as binary16
  *                     scaled by 2^floor(log2(n)/2), binary32 arithmetic.
+ *   GMRES_MIXED_LIMITED the paper's "limited" mixed solver (Sec. 4.1):
+ *                     binary64 arithmetic and vectors throughout; binary32
+ *                     storage only for A as used in the Krylov step, the
+ *                     preconditioner M and the Krylov basis.  Grid path only
+ *                     (GMRES_PATH_AUTO picks it); not in the batched and
+ *                     no-allocation solvers.
  * The 16-bit bases follow the paper's outlook on half precision (Sec. 5). */
 typedef enum {
     GMRES_FP64 = 0,
     GMRES_MIXED = 1,
     GMRES_MIXED_BF16 = 2,
-    GMRES_MIXED_FP16 = 3
+    GMRES_MIXED_FP16 = 3,
+    GMRES_MIXED_LIMITED = 4
 } gmres_precision;
 
 typedef enum {
@@ -67,6 +74,14 @@ typedef enum {
 
 /* gmres_create flags. */
 #define GMRES_CREATE_DEVICE_PTRS 1 /* rowptr/colind/vals are device pointers  */
+#define GMRES_CREATE_SPLIT 4       /* store A once, as the high- and low-order
+                                      32 bits of each binary64 value (Sec. 4,
+                                      the storage the paper points to instead of
+                                      two copies): 8 bytes per nonzero instead of
+                                      12; the binary32 Krylov step reads the high
+                                      part (the value truncated to 20 fraction
+                                      bits), binary64 work reads both.  Grid path
+                                      only; not with the learned preconditioner */
 #define GMRES_CREATE_TRANSPOSE 2   /* also build the CSR of A^T (preconditioner
                                       training needs A^T r)                    */
 
@@ -104,7 +119,9 @@ typedef struct gmres_opts {
     int32_t spmv_lanes;   /* lanes per CSR row in SpMV (1..32, power of two);
                              0 = the autotuned choice                           */
     int32_t cgs_kernel;   /* CGSR kernel family: 0 = register-streaming rows
-                             (default), 1 = TMA-fed shared-memory tiles         */
+                             (default; the updates split by basis vectors),
+                             1 = TMA-fed shared-memory tiles, 2 = register-
+                             streaming rows with the update split by rows      */
     int32_t mgs_kernel;   /* MGS: 0 = one cooperative kernel per inner step with
                              w in shared memory (default; used when w's row
                              chunk fits), 1 = one kernel per basis vector       */
@@ -112,7 +129,11 @@ typedef struct gmres_opts {
                              basis rows of the slice this many slices ahead of
                              the one it is reading into L2 (bulk prefetch);
                              0 = off, 1..4                                      */
-    int32_t reserved[2];
+    int32_t block_cluster;/* block path: thread blocks per system, 1 (one block)
+                             or 8 (a cluster with distributed-shared-memory
+                             reductions); 0 = automatic (8 for binary64 from
+                             2048 rows, else 1)                                 */
+    int32_t reserved[1];
     double stall_factor;  /* third restart strategy (Sec. 3; Sec. 4.1 uses 1.001):
                              end the cycle once |s_{j+1}| improved by less than
                              this factor over the last stall_window inner
@@ -308,6 +329,17 @@ gmres_status gmres_batch_solve(gmres_batch_t b, const double *rhs, double *x, in
                                double tol, gmres_ortho ortho, gmres_precision prec,
                                int32_t maxiter, int32_t lanes, gmres_batch_result *results,
                                gmres_info *info);
+
+/* SpMV tile autotuner of the batched solver: times a capped solve (iters
+ * inner iterations per system, from x0 = 0, on scratch memory; the batch's
+ * x is not touched) with 1, 2, 4, 8 and 16 lanes per CSR row and keeps the
+ * fastest as the batch's choice for gmres_batch_solve with lanes = 0.  rhs
+ * is packed like gmres_batch_solve's (host or device); *lanes_out (may be
+ * NULL) receives the choice.  Errors: GMRES_ERR_ARG, GMRES_ERR_OOM,
+ * GMRES_ERR_CUDA. */
+gmres_status gmres_batch_autotune(gmres_batch_t b, const double *rhs, int32_t m,
+                                  gmres_ortho ortho, gmres_precision prec, int32_t iters,
+                                  int32_t *lanes_out);
 
 /* ---------------------------------------------------------------------------
  * Solve without allocating device memory.  The paper has no counterpart; this

@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "block_solver.cuh"
+#include "team_launch.hpp"
 #include "host_util.hpp"
 
 using namespace gmres;
@@ -36,6 +37,7 @@ struct gmres_batch {
     int64_t ws_rows = 0;            // total padded rows
     std::vector<int> order;         // largest system first
     int nlarge = 0;                 // systems solved by clusters (the first nlarge of order)
+    int tuned_lanes = 0;            // lanes per row chosen by gmres_batch_autotune (0: none)
     cudaStream_t aux = nullptr;     // stream of the cluster launch
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     DevBuf rowptr, colind, vals64, vals32;
@@ -55,6 +57,8 @@ __global__ void k_batch_cast(int64_t nnz, const double *a, float *b) {
          k += (int64_t)gridDim.x * blockDim.x)
         b[k] = (float)a[k];
 }
+
+
 
 template <class T, class VT>
 gmres_status batch_run(gmres_batch *B, const double *db, double *dx, int m, double tol,
@@ -100,7 +104,8 @@ gmres_status batch_run(gmres_batch *B, const double *db, double *dx, int m, doub
     P.nsys = B->nsys;
     P.queue = nullptr;
     P.order = nullptr;
-    const int L = lanes > 0 ? lanes : pow2_lanes(B->avg_row / 2.0);
+    const int L = lanes > 0 ? lanes
+                  : (B->tuned_lanes > 0 ? B->tuned_lanes : pow2_lanes(B->avg_row / 2.0));
     using KFn = void (*)(const BlockSys<T, VT> *, BlockParams, BlockResult *);
     KFn kfn = nullptr, kcl = nullptr;
     switch (L) {
@@ -222,6 +227,59 @@ gmres_status batch_run(gmres_batch *B, const double *db, double *dx, int m, doub
 }
 
 }  // namespace
+
+namespace gmres {
+
+template <class T, class VT>
+cudaError_t launch_team_single(const BlockSys<T, VT> *sys, const BlockParams &P,
+                               BlockResult *res, int L, int threads, size_t smem,
+                               cudaStream_t stream) {
+    using KFn = void (*)(const BlockSys<T, VT> *, BlockParams, BlockResult *);
+    KFn k = nullptr;
+    switch (L) {
+    case 1: k = &k_team_solve<T, VT, 1, TEAM_SINGLE_CTAS>; break;
+    case 2: k = &k_team_solve<T, VT, 2, TEAM_SINGLE_CTAS>; break;
+    case 4: k = &k_team_solve<T, VT, 4, TEAM_SINGLE_CTAS>; break;
+    case 8: k = &k_team_solve<T, VT, 8, TEAM_SINGLE_CTAS>; break;
+    case 16: k = &k_team_solve<T, VT, 16, TEAM_SINGLE_CTAS>; break;
+    default: k = &k_team_solve<T, VT, 32, TEAM_SINGLE_CTAS>; break;
+    }
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess)
+        return e;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = TEAM_SINGLE_CTAS;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(TEAM_SINGLE_CTAS);
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k, sys, P, res);
+}
+
+template cudaError_t launch_team_single<double, double>(const BlockSys<double, double> *,
+                                                        const BlockParams &, BlockResult *, int,
+                                                        int, size_t, cudaStream_t);
+template cudaError_t launch_team_single<double, float>(const BlockSys<double, float> *,
+                                                       const BlockParams &, BlockResult *, int,
+                                                       int, size_t, cudaStream_t);
+template cudaError_t launch_team_single<float, float>(const BlockSys<float, float> *,
+                                                      const BlockParams &, BlockResult *, int, int,
+                                                      size_t, cudaStream_t);
+template cudaError_t launch_team_single<float, __nv_bfloat16>(
+    const BlockSys<float, __nv_bfloat16> *, const BlockParams &, BlockResult *, int, int, size_t,
+    cudaStream_t);
+template cudaError_t launch_team_single<float, __half>(const BlockSys<float, __half> *,
+                                                       const BlockParams &, BlockResult *, int,
+                                                       int, size_t, cudaStream_t);
+
+}  // namespace gmres
 
 extern "C" {
 
@@ -395,6 +453,64 @@ gmres_status gmres_batch_solve(gmres_batch_t B, const double *rhs, double *x, in
             std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0)
                 .count();
     return st;
+}
+
+gmres_status gmres_batch_autotune(gmres_batch_t B, const double *rhs, int32_t m,
+                                  gmres_ortho ortho, gmres_precision prec, int32_t iters,
+                                  int32_t *lanes_out) {
+    if (!B || !rhs || m < 1 || m > MMAX || iters < 1 ||
+        (ortho != GMRES_ORTHO_MGS && ortho != GMRES_ORTHO_CGSR) || prec < GMRES_FP64 ||
+        prec > GMRES_MIXED_FP16)
+        return GMRES_ERR_ARG;
+    // every candidate runs the same capped solve from x0 = 0 on a scratch x
+    DevBuf xs;
+    CK(xs.ensure(sizeof(double) * B->nrows));
+    const double *db = rhs;
+    if (!is_device_ptr(rhs)) {
+        CK(B->bb.ensure(sizeof(double) * B->nrows));
+        CK(cudaMemcpyAsync(B->bb.p, rhs, sizeof(double) * B->nrows, cudaMemcpyHostToDevice,
+                           B->stream));
+        db = B->bb.as<double>();
+    }
+    int best = 0;
+    double best_ms = 0;
+    for (int L = 1; L <= 16; L *= 2) {
+        CK(cudaMemsetAsync(xs.p, 0, sizeof(double) * B->nrows, B->stream));
+        gmres_info inf;
+        memset(&inf, 0, sizeof(inf));
+        gmres_status st;
+        double *dx = xs.as<double>();
+        // tol below reach: every system runs the full iteration budget
+        switch (prec) {
+        case GMRES_FP64:
+            st = batch_run<double, double>(B, db, dx, m, 1e-300, ortho, prec, iters, L, nullptr,
+                                           &inf);
+            break;
+        case GMRES_MIXED:
+            st = batch_run<float, float>(B, db, dx, m, 1e-300, ortho, prec, iters, L, nullptr,
+                                         &inf);
+            break;
+        case GMRES_MIXED_BF16:
+            st = batch_run<float, __nv_bfloat16>(B, db, dx, m, 1e-300, ortho, prec, iters, L,
+                                                 nullptr, &inf);
+            break;
+        default:
+            st = batch_run<float, __half>(B, db, dx, m, 1e-300, ortho, prec, iters, L, nullptr,
+                                          &inf);
+            break;
+        }
+        if (st != GMRES_OK && st != GMRES_MAXITER && st != GMRES_ERR_BREAKDOWN)
+            return st;
+        const double ms = inf.kernel_ms[GMRES_K_BLOCK];
+        if (best == 0 || ms < best_ms) {
+            best = L;
+            best_ms = ms;
+        }
+    }
+    B->tuned_lanes = best;
+    if (lanes_out)
+        *lanes_out = best;
+    return GMRES_OK;
 }
 
 }  // extern "C"

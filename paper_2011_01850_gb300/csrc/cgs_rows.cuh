@@ -67,6 +67,13 @@ __device__ __forceinline__ void ld_rows<float, float, 4>(const float *p, float, 
     o[2] = __uint_as_float(u.z); o[3] = __uint_as_float(u.w);
 }
 template <>
+__device__ __forceinline__ void ld_rows<double, float, 4>(const float *p, float, double (&o)[4],
+                                                          uint64_t pol) {
+    uint4 u = ld16(p, pol);
+    o[0] = __uint_as_float(u.x); o[1] = __uint_as_float(u.y);
+    o[2] = __uint_as_float(u.z); o[3] = __uint_as_float(u.w);
+}
+template <>
 __device__ __forceinline__ void ld_rows<double, double, 2>(const double *p, float,
                                                             double (&o)[2], uint64_t pol) {
     uint4 u = ld16(p, pol);
@@ -169,6 +176,54 @@ __device__ __forceinline__ void rows_project(const GridCtx<T, VT> &c, int ncols,
     }
 }
 
+// tp[g][q] = sum over this warp's vectors (wid, wid+4, ...) of
+// h[col] * V[col][slice row g*RW + lane*RPL + q]: the update's partial sums
+// with every vector read as one 2 KB run per warp (as in the dot products),
+// summed over the warp's vectors in ascending order, batched loads.
+template <class T, class VT, int RPL, int ACC>
+__device__ __forceinline__ void rows_project_split(const GridCtx<T, VT> &c, int ncols,
+                                                   const T *hs, int64_t s0, int wid, int lane,
+                                                   T (&tp)[4][RPL], uint64_t pol) {
+    constexpr int RW = 32 * RPL;
+    constexpr int KB = ROWS_CB / 4 > 0 ? ROWS_CB / 4 : 1;
+#pragma unroll
+    for (int g = 0; g < 4; ++g)
+#pragma unroll
+        for (int q = 0; q < RPL; ++q)
+            tp[g][q] = 0;
+#pragma unroll
+    for (int k0 = 0; k0 < ACC; k0 += KB) {
+        if (wid + ROWS_WARPS * k0 < ncols) {
+            T v[KB][4][RPL];
+#pragma unroll
+            for (int u = 0; u < KB; ++u) {
+                const int col = wid + ROWS_WARPS * (k0 + u);
+#pragma unroll
+                for (int g = 0; g < 4; ++g) {
+                    if (k0 + u < ACC && col < ncols)
+                        ld_rows<T, VT, RPL>(c.V + (size_t)col * c.ldv + s0 + g * RW + lane * RPL,
+                                            c.vinv, v[u][g], pol);
+                    else {
+#pragma unroll
+                        for (int q = 0; q < RPL; ++q)
+                            v[u][g][q] = 0;
+                    }
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < KB; ++u) {
+                const int col = wid + ROWS_WARPS * (k0 + u);
+                const T hc = (k0 + u < ACC && col < ncols) ? hs[col] : T(0);
+#pragma unroll
+                for (int g = 0; g < 4; ++g)
+#pragma unroll
+                    for (int q = 0; q < RPL; ++q)
+                        tp[g][q] += v[u][g][q] * hc;
+            }
+        }
+    }
+}
+
 // acc[k] += V[wid + 4k][slice rows] . ws (the slice's w, 4 row groups in
 // shared memory or registers), batched loads.
 template <class T, class VT, int RPL, int ACC>
@@ -212,7 +267,7 @@ __device__ __forceinline__ void rows_dots(const GridCtx<T, VT> &c, int ncols, in
     }
 }
 
-template <class T, class VT, int MODE>
+template <class T, class VT, int MODE, bool SPLIT = true>
 __global__ void __launch_bounds__(ROWS_THREADS)
     k_cgs_rows(GridCtx<T, VT> c, int ncols, T *part, int64_t slices_per_block, int pf) {
     // MODE 3 follows the step that appended basis column ncols, also when
@@ -226,6 +281,8 @@ __global__ void __launch_bounds__(ROWS_THREADS)
     constexpr int ACC = (MMAX + 1 + ROWS_WARPS - 1) / ROWS_WARPS;
     __shared__ T hs[MMAX + 2];
     __shared__ __align__(16) T wsl[SR];
+    // SPLIT update: the four warps' partial sums of V h for the slice
+    __shared__ __align__(16) T tsm[(MODE == 1 || MODE == 2) && SPLIT ? ROWS_WARPS * SR : 1];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     if (MODE == 1 || MODE == 2) {
         const T *src = (MODE == 1) ? c.h1 : c.h2;
@@ -276,6 +333,40 @@ __global__ void __launch_bounds__(ROWS_THREADS)
 #pragma unroll
                     for (int q = 0; q < RPL; ++q)
                         nsq += wv[g][q] * wv[g][q];
+            }
+        } else if (SPLIT) {
+            // update, split by vectors: every warp sums its vectors over the
+            // whole slice (2 KB runs), the partials meet in shared memory and
+            // warp wid forms row group wid as ((p0 + p1) + p2) + p3
+            T tp[4][RPL];
+            rows_project_split<T, VT, RPL, ACC>(c, ncols, hs, s0, wid, lane, tp, pol_keep);
+#pragma unroll
+            for (int g = 0; g < 4; ++g)
+#pragma unroll
+                for (int q = 0; q < RPL; ++q)
+                    tsm[wid * SR + g * RW + lane * RPL + q] = tp[g][q];
+            __syncthreads();
+            const int64_t r = s0 + wid * RW + lane * RPL;
+            T w[RPL];
+            ld_w<T, RPL>(c.w + r, w);
+#pragma unroll
+            for (int q = 0; q < RPL; ++q) {
+                const int o = wid * RW + lane * RPL + q;
+                const T t = ((tsm[o] + tsm[SR + o]) + tsm[2 * SR + o]) + tsm[3 * SR + o];
+                w[q] = w[q] - t;
+                if (MODE == 2)
+                    nsq += w[q] * w[q];
+                if (MODE == 1)
+                    wsl[o] = w[q];
+            }
+            st_w<T, RPL>(c.w + r, w);
+            __syncthreads();
+            if (MODE == 1) {
+#pragma unroll
+                for (int g = 0; g < 4; ++g)
+#pragma unroll
+                    for (int q = 0; q < RPL; ++q)
+                        wv[g][q] = wsl[g * RW + lane * RPL + q];
             }
         } else {
             // update: warp wid owns row group wid of the slice

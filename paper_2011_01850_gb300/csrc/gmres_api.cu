@@ -25,6 +25,7 @@
 #include "mgs_persist.cuh"
 #include "grid_kernels.cuh"
 #include "orth_monitor.cuh"
+#include "team_launch.hpp"
 #include "handle.hpp"
 #include "host_util.hpp"
 
@@ -43,11 +44,25 @@ __global__ void k_cast_vals(int64_t nnz, const double *a, float *b) {
         b[k] = (float)a[k];
 }
 
+// Split storage: the high- and low-order 32 bits of each binary64 value.
+__global__ void __launch_bounds__(256) k_split_vals(int64_t nnz, const double *v, unsigned *hi,
+                                                    unsigned *lo) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nnz;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const double a = v[k];
+        hi[k] = (unsigned)__double2hiint(a);
+        lo[k] = (unsigned)__double2loint(a);
+    }
+}
+
 // Per-precision device pointers into the "small" buffer.
 template <class T>
 struct SmallPtrs {
     T *H, *Hb, *s, *cs, *sn, *y, *h1, *h2;
 };
+
+inline const unsigned *split_hi(gmres_handle *h) { return h->vals64.as<unsigned>(); }
+inline const unsigned *split_lo(gmres_handle *h) { return h->vals64.as<unsigned>() + h->nnz; }
 
 // Restart-test buffers (binary64): |s_{j+1}| history of the cycle, ||S_k||
 // history, then U and S of the loss-of-orthogonality test.
@@ -145,11 +160,23 @@ GridCtx<T, VT> make_ctx(gmres_handle *h, int m) {
     c.ahist = mon_ahist(h);
     c.stall_factor = h->opts.stall_factor;
     c.stall_w = h->opts.stall_window > 0 ? h->opts.stall_window : (m + 19) / 20;
+    if (h->split) {
+        c.a = nullptr;
+        c.a64 = nullptr;
+        c.ahi = split_hi(h);
+        c.alo = split_lo(h);
+        c.aform = (std::is_same<T, double>::value && !h->limited) ? 3 : 2;
+    } else if (h->limited) {
+        c.a_lim = h->vals32.as<float>();
+        c.aform = 1;
+    }
     if (h->has_precond && h->opts.precond) {
         c.prowptr = c.rowptr;
         c.pcolind = c.colind;
         c.pvals = std::is_same<T, double>::value ? reinterpret_cast<const T *>(h->pvals64.p)
                                                  : reinterpret_cast<const T *>(h->pvals32.p);
+        if (h->limited)
+            c.pvals_lim = h->pvals32.as<float>();
     }
     return c;
 }
@@ -186,19 +213,58 @@ cudaError_t launch_residual(gmres_handle *h, const GridCtx<T, VT> &c, const doub
     return cudaGetLastError();
 }
 
-template <class T>
-cudaError_t launch_spmv_plain(gmres_handle *h, int L, const T *a, const T *x, T *y) {
+template <class T, class AT = T>
+cudaError_t launch_spmv_plain(gmres_handle *h, int L, const AT *a, const T *x, T *y) {
     dim3 g(spmv_grid(h)), b(kThreads);
     const int *rp = h->rowptr.as<int>(), *ci = h->colind.as<int>();
     switch (L) {
-    case 1: k_spmv_plain<T, 1><<<g, b, 0, h->stream>>>(h->n, rp, ci, a, x, y); break;
-    case 2: k_spmv_plain<T, 2><<<g, b, 0, h->stream>>>(h->n, rp, ci, a, x, y); break;
-    case 4: k_spmv_plain<T, 4><<<g, b, 0, h->stream>>>(h->n, rp, ci, a, x, y); break;
-    case 8: k_spmv_plain<T, 8><<<g, b, 0, h->stream>>>(h->n, rp, ci, a, x, y); break;
-    case 16: k_spmv_plain<T, 16><<<g, b, 0, h->stream>>>(h->n, rp, ci, a, x, y); break;
-    default: k_spmv_plain<T, 32><<<g, b, 0, h->stream>>>(h->n, rp, ci, a, x, y); break;
+    case 1: k_spmv_plain<T, AT, 1><<<g, b, 0, h->stream>>>(h->n, rp, ci, a, x, y); break;
+    case 2: k_spmv_plain<T, AT, 2><<<g, b, 0, h->stream>>>(h->n, rp, ci, a, x, y); break;
+    case 4: k_spmv_plain<T, AT, 4><<<g, b, 0, h->stream>>>(h->n, rp, ci, a, x, y); break;
+    case 8: k_spmv_plain<T, AT, 8><<<g, b, 0, h->stream>>>(h->n, rp, ci, a, x, y); break;
+    case 16: k_spmv_plain<T, AT, 16><<<g, b, 0, h->stream>>>(h->n, rp, ci, a, x, y); break;
+    default: k_spmv_plain<T, AT, 32><<<g, b, 0, h->stream>>>(h->n, rp, ci, a, x, y); break;
     }
     return cudaGetLastError();
+}
+
+// y = A x with split storage: the high part (binary32 work) or both parts.
+template <class T>
+cudaError_t launch_spmv_split(gmres_handle *h, int L, const T *x, T *y) {
+    dim3 g(spmv_grid(h)), b(kThreads);
+    const int *rp = h->rowptr.as<int>(), *ci = h->colind.as<int>();
+    if (std::is_same<T, double>::value) {
+        ValHiLo a{split_hi(h), split_lo(h)};
+        switch (L) {
+        case 1: k_spmv_plain_v<T, ValHiLo, 1><<<g, b, 0, h->stream>>>(h->n, rp, ci, a, x, y); break;
+        case 2: k_spmv_plain_v<T, ValHiLo, 2><<<g, b, 0, h->stream>>>(h->n, rp, ci, a, x, y); break;
+        case 4: k_spmv_plain_v<T, ValHiLo, 4><<<g, b, 0, h->stream>>>(h->n, rp, ci, a, x, y); break;
+        case 8: k_spmv_plain_v<T, ValHiLo, 8><<<g, b, 0, h->stream>>>(h->n, rp, ci, a, x, y); break;
+        case 16: k_spmv_plain_v<T, ValHiLo, 16><<<g, b, 0, h->stream>>>(h->n, rp, ci, a, x, y); break;
+        default: k_spmv_plain_v<T, ValHiLo, 32><<<g, b, 0, h->stream>>>(h->n, rp, ci, a, x, y); break;
+        }
+    } else {
+        ValHi a{split_hi(h)};
+        switch (L) {
+        case 1: k_spmv_plain_v<T, ValHi, 1><<<g, b, 0, h->stream>>>(h->n, rp, ci, a, x, y); break;
+        case 2: k_spmv_plain_v<T, ValHi, 2><<<g, b, 0, h->stream>>>(h->n, rp, ci, a, x, y); break;
+        case 4: k_spmv_plain_v<T, ValHi, 4><<<g, b, 0, h->stream>>>(h->n, rp, ci, a, x, y); break;
+        case 8: k_spmv_plain_v<T, ValHi, 8><<<g, b, 0, h->stream>>>(h->n, rp, ci, a, x, y); break;
+        case 16: k_spmv_plain_v<T, ValHi, 16><<<g, b, 0, h->stream>>>(h->n, rp, ci, a, x, y); break;
+        default: k_spmv_plain_v<T, ValHi, 32><<<g, b, 0, h->stream>>>(h->n, rp, ci, a, x, y); break;
+        }
+    }
+    return cudaGetLastError();
+}
+
+// y = A x with the precision's copy of A, whatever the storage.
+template <class T>
+cudaError_t launch_spmv_any(gmres_handle *h, int L, const T *x, T *y) {
+    if (h->split)
+        return launch_spmv_split<T>(h, L, x, y);
+    const T *a = std::is_same<T, double>::value ? reinterpret_cast<const T *>(h->vals64.p)
+                                                : reinterpret_cast<const T *>(h->vals32.p);
+    return launch_spmv_plain<T>(h, L, a, x, y);
 }
 
 struct Acct {
@@ -250,6 +316,54 @@ bool mgs_persist_ok(gmres_handle *h) {
     return ok;
 }
 
+// The three register-streaming CGSR passes (and the two column reductions)
+// for an inner step with ncols basis vectors, then v_{j+1}.
+template <class T, class VT, bool SPLIT>
+gmres_status enqueue_cgs_rows(gmres_handle *h, GridCtx<T, VT> &c, int ncols, Acct &acct,
+                              cudaEvent_t e) {
+    // one resident wave per kernel: grid = SMs x resident blocks per SM
+    static int per_sm[3] = {0, 0, 0};
+    if (per_sm[0] == 0) {
+        void (*fns[3])(GridCtx<T, VT>, int, T *, int64_t, int) = {
+            k_cgs_rows<T, VT, 0, SPLIT>, k_cgs_rows<T, VT, 1, SPLIT>,
+            k_cgs_rows<T, VT, 2, SPLIT>};
+        for (int k = 0; k < 3; ++k) {
+            int bpsm = 0;
+            CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpsm, fns[k], ROWS_THREADS, 0));
+            per_sm[k] = std::max(1, std::min(bpsm, h->rows_blocks_per_sm));
+        }
+    }
+    // balanced grids: k = ceil(slices / resident blocks) consecutive slices
+    // per block, grid = ceil(slices / k), one resident wave
+    const int64_t nsl = h->ldv / (ROWS_WARPS * 32 * (16 / (int64_t)sizeof(VT)));
+    int64_t kpb[3];
+    int gsz[3];
+    for (int k = 0; k < 3; ++k) {
+        const int64_t cap = (int64_t)h->nsm * per_sm[k];
+        kpb[k] = (nsl + cap - 1) / cap;
+        gsz[k] = (int)((nsl + kpb[k] - 1) / kpb[k]);
+    }
+    const int pf = h->opts.l2_prefetch;
+    k_cgs_rows<T, VT, 0, SPLIT><<<gsz[0], ROWS_THREADS, 0, h->stream>>>(c, ncols, c.part, kpb[0],
+                                                                        pf);
+    k_reduce_cols<T><<<ncols + 1, 256, 0, h->stream>>>(c.part, gsz[0], ncols, c.h1, c.ctl, 1);
+    k_cgs_rows<T, VT, 1, SPLIT><<<gsz[1], ROWS_THREADS, 0, h->stream>>>(c, ncols, c.part, kpb[1],
+                                                                        pf);
+    k_reduce_cols<T><<<ncols, 256, 0, h->stream>>>(c.part, gsz[1], ncols, c.h2, c.ctl, 0);
+    k_cgs_rows<T, VT, 2, SPLIT><<<gsz[2], ROWS_THREADS, 0, h->stream>>>(c, ncols, c.part, kpb[2],
+                                                                        pf);
+    acct.launches[GMRES_K_ORTHO] += 5;
+    CKL();
+    h->timer.end(GMRES_K_ORTHO, e);
+    e = h->timer.begin();
+    dim3 g(h->grid), b(kThreads);
+    k_normalize<T, VT><<<g, b, 0, h->stream>>>(c, ncols, h->opts.orth_norm != GMRES_ORTH_OFF);
+    CKL();
+    h->timer.end(GMRES_K_NORMALIZE, e);
+    acct.launches[GMRES_K_NORMALIZE]++;
+    return GMRES_OK;
+}
+
 // Enqueue one inner step (column index `col` of the basis -> new column
 // col+1) without the optional loss-of-orthogonality test.  Kernels return at
 // once when the cycle has ended.
@@ -265,6 +379,8 @@ gmres_status enqueue_step_core(gmres_handle *h, GridCtx<T, VT> &c, int col, gmre
         cp.rowptr = c.prowptr;
         cp.colind = c.pcolind;
         cp.a = c.pvals;
+        cp.a_lim = c.pvals_lim;
+        cp.aform = c.pvals_lim ? 1 : 0;
         CK((launch_spmv_step<T, VT, VT>(h, cp, vj, c.t, L)));
         acct.launches[GMRES_K_PRECOND]++;
         h->timer.end(GMRES_K_PRECOND, e);
@@ -278,36 +394,12 @@ gmres_status enqueue_step_core(gmres_handle *h, GridCtx<T, VT> &c, int col, gmre
     const int ncols = col + 1;
     dim3 g(h->grid), b(kThreads);
     e = h->timer.begin();
-    if (ortho == GMRES_ORTHO_CGSR && h->opts.cgs_kernel == 0) {
-        // one resident wave per kernel: grid = SMs x resident blocks per SM
-        static int per_sm[3] = {0, 0, 0};
-        if (per_sm[0] == 0) {
-            void (*fns[3])(GridCtx<T, VT>, int, T *, int64_t, int) = {
-                k_cgs_rows<T, VT, 0>, k_cgs_rows<T, VT, 1>, k_cgs_rows<T, VT, 2>};
-            for (int k = 0; k < 3; ++k) {
-                int bpsm = 0;
-                CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpsm, fns[k], ROWS_THREADS, 0));
-                per_sm[k] = std::max(1, std::min(bpsm, h->rows_blocks_per_sm));
-            }
-        }
-        // balanced grids: k = ceil(slices / resident blocks) consecutive
-        // slices per block, grid = ceil(slices / k), one resident wave
-        const int64_t nsl = h->ldv / (ROWS_WARPS * 32 * (16 / (int64_t)sizeof(VT)));
-        int64_t kpb[3];
-        int gsz[3];
-        for (int k = 0; k < 3; ++k) {
-            const int64_t cap = (int64_t)h->nsm * per_sm[k];
-            kpb[k] = (nsl + cap - 1) / cap;
-            gsz[k] = (int)((nsl + kpb[k] - 1) / kpb[k]);
-        }
-        const int pf = h->opts.l2_prefetch;
-        k_cgs_rows<T, VT, 0><<<gsz[0], ROWS_THREADS, 0, h->stream>>>(c, ncols, c.part, kpb[0], pf);
-        k_reduce_cols<T><<<ncols + 1, 256, 0, h->stream>>>(c.part, gsz[0], ncols, c.h1, c.ctl, 1);
-        k_cgs_rows<T, VT, 1><<<gsz[1], ROWS_THREADS, 0, h->stream>>>(c, ncols, c.part, kpb[1], pf);
-        k_reduce_cols<T><<<ncols, 256, 0, h->stream>>>(c.part, gsz[1], ncols, c.h2, c.ctl, 0);
-        k_cgs_rows<T, VT, 2><<<gsz[2], ROWS_THREADS, 0, h->stream>>>(c, ncols, c.part, kpb[2], pf);
-        acct.launches[GMRES_K_ORTHO] += 5;
-    } else if (ortho == GMRES_ORTHO_CGSR) {
+    if (ortho == GMRES_ORTHO_CGSR && h->opts.cgs_kernel != 1) {
+        if (h->opts.cgs_kernel == 2)
+            return enqueue_cgs_rows<T, VT, false>(h, c, ncols, acct, e);
+        return enqueue_cgs_rows<T, VT, true>(h, c, ncols, acct, e);
+    }
+    if (ortho == GMRES_ORTHO_CGSR) {
         const int TR = cgs_choose_tr<VT>(ncols);
         const size_t sm = cgs_smem_bytes<T, VT>(ncols, TR);
         const long long spin = h->opts.spin_limit > 0 ? h->opts.spin_limit : (1LL << 26);
@@ -422,12 +514,15 @@ template <class T, class VT>
 void account_cycle(gmres_handle *h, int j, gmres_ortho ortho, Acct &acct) {
     const double n = h->n, nnz = (double)h->nnz;
     const double sT = sizeof(T), sV = sizeof(VT);
+    // matrix value bytes the Krylov step reads
+    const double sA = h->split ? ((sizeof(T) == 8 && !h->limited) ? 8.0 : 4.0)
+                               : (h->limited ? 4.0 : sT);
     const bool pre = h->has_precond && h->opts.precond;
     for (int it = 0; it < j; ++it) {
         const double c = it + 1;
-        acct.bytes[GMRES_K_SPMV] += nnz * (sT + 4) + (n + 1) * 4 + n * (pre ? sT : sV) + n * sT;
+        acct.bytes[GMRES_K_SPMV] += nnz * (sA + 4) + (n + 1) * 4 + n * (pre ? sT : sV) + n * sT;
         if (pre)
-            acct.bytes[GMRES_K_PRECOND] += nnz * (sT + 4) + (n + 1) * 4 + n * sV + n * sT;
+            acct.bytes[GMRES_K_PRECOND] += nnz * (sA + 4) + (n + 1) * 4 + n * sV + n * sT;
         if (ortho == GMRES_ORTHO_CGSR)
             acct.bytes[GMRES_K_ORTHO] += 3 * c * n * sV + 5 * n * sT;
         else
@@ -547,7 +642,10 @@ gmres_status solve_grid(gmres_handle *h, const double *b, double *x, int m, doub
         acct.launches[GMRES_K_UPDATE] += 2;
         if (pre) {
             // u = M t with t = V_j y, then x += u (right preconditioning)
-            CK(launch_spmv_plain<T>(h, lanes_for<T, VT>(h), c.pvals, c.t, c.w));
+            if (c.pvals_lim)
+                CK((launch_spmv_plain<T, float>(h, lanes_for<T, VT>(h), c.pvals_lim, c.t, c.w)));
+            else
+                CK(launch_spmv_plain<T>(h, lanes_for<T, VT>(h), c.pvals, c.t, c.w));
             k_axpy_x<T><<<h->grid, kThreads, 0, h->stream>>>(h->n, c.w, x, c.ctl);
             CKL();
             acct.launches[GMRES_K_UPDATE] += 2;
@@ -657,8 +755,21 @@ gmres_status solve_block(gmres_handle *h, const double *b, double *x, int m, dou
     P.queue = queue;
     P.order = nullptr;
     size_t smem = block_smem_bytes<T>(m);
-    int threads = (int)std::min<int64_t>(1024, std::max<int64_t>(64, round_up(h->n / 4, 32)));
     int L = lanes_for<T, VT>(h);
+    // one block, or one cluster: binary64 arithmetic is slow on one SM, so a
+    // binary64 system of 2048+ rows spreads over a cluster by default
+    int cs = h->opts.block_cluster;
+    if (cs == 0)
+        cs = (std::is_same<T, double>::value && h->n >= 2048) ? TEAM_SINGLE_CTAS : 1;
+    if (cs == TEAM_SINGLE_CTAS) {
+        const int64_t chunk = (h->n + cs - 1) / cs;
+        const int threads = (int)std::min<int64_t>(1024, std::max<int64_t>(64, round_up(chunk / 2, 32)));
+        cudaEvent_t e = h->timer.begin();
+        CK((launch_team_single<T, VT>(h->bsys.as<BlockSys<T, VT>>(), P, h->bres.as<BlockResult>(),
+                                      L, threads, smem, h->stream)));
+        h->timer.end(GMRES_K_BLOCK, e);
+    } else {
+    int threads = (int)std::min<int64_t>(1024, std::max<int64_t>(64, round_up(h->n / 4, 32)));
     auto *kfn = &k_block_solve<T, VT, 4>;
     switch (L) {
     case 1: kfn = &k_block_solve<T, VT, 1>; break;
@@ -674,6 +785,7 @@ gmres_status solve_block(gmres_handle *h, const double *b, double *x, int m, dou
                                           h->bres.as<BlockResult>());
     CKL();
     h->timer.end(GMRES_K_BLOCK, e);
+    }
     BlockResult R;
     CK(cudaMemcpyAsync(&R, h->bres.p, sizeof(R), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
@@ -694,13 +806,14 @@ gmres_status solve_dispatch_path(gmres_handle *h, const double *b, double *x, in
                                  gmres_ortho ortho, gmres_precision prec, int maxiter,
                                  gmres_info *info) {
     int path = h->opts.path;
-    const bool orth = h->opts.orth_norm != GMRES_ORTH_OFF;
+    const bool grid_only = h->opts.orth_norm != GMRES_ORTH_OFF || h->limited || h->split;
     if (path == GMRES_PATH_AUTO)
-        path = (h->n <= 16384 && !(h->has_precond && h->opts.precond) && !orth)
+        path = (h->n <= 16384 && !(h->has_precond && h->opts.precond) && !grid_only)
                    ? GMRES_PATH_BLOCK
                    : GMRES_PATH_GRID;
-    if (path == GMRES_PATH_BLOCK && orth)
-        return GMRES_ERR_ARG;  // the loss-of-orthogonality test runs on the grid path
+    if (path == GMRES_PATH_BLOCK && grid_only)
+        return GMRES_ERR_ARG;  // the orthogonality test, limited mixed and split storage
+                               // run on the grid path
     info->path = path;
     if (path == GMRES_PATH_BLOCK)
         return solve_block<T, VT>(h, b, x, m, tol, ortho, prec, maxiter, info);
@@ -713,8 +826,9 @@ gmres_status validate_opts(const gmres_opts *o) {
     if (!(o->inner_factor >= 0) || o->path < 0 || o->path > 2 || o->spin_limit < 0 ||
         (o->spmv_lanes != 0 && (o->spmv_lanes < 1 || o->spmv_lanes > 32 ||
                                 (o->spmv_lanes & (o->spmv_lanes - 1)))) ||
-        o->cgs_kernel < 0 || o->cgs_kernel > 1 || o->mgs_kernel < 0 || o->mgs_kernel > 1 ||
+        o->cgs_kernel < 0 || o->cgs_kernel > 2 || o->mgs_kernel < 0 || o->mgs_kernel > 1 ||
         o->l2_prefetch < 0 || o->l2_prefetch > 4 || !(o->stall_factor >= 0) ||
+        (o->block_cluster != 0 && o->block_cluster != 1 && o->block_cluster != TEAM_SINGLE_CTAS) ||
         o->stall_window < 0 || o->stall_window > MMAX || o->orth_norm < GMRES_ORTH_OFF ||
         o->orth_norm > GMRES_ORTH_FROBENIUS || o->orth_iters < 0 ||
         (o->orth_norm != GMRES_ORTH_OFF && !(o->orth_threshold > 0)) ||
@@ -768,7 +882,9 @@ gmres_status gmres_create(gmres_t *out, int32_t n, const int32_t *rowptr, const 
     if (!out)
         return GMRES_ERR_ARG;
     *out = nullptr;
-    if (n <= 0 || !rowptr || (flags & ~(GMRES_CREATE_DEVICE_PTRS | GMRES_CREATE_TRANSPOSE)))
+    if (n <= 0 || !rowptr ||
+        (flags & ~(GMRES_CREATE_DEVICE_PTRS | GMRES_CREATE_TRANSPOSE | GMRES_CREATE_SPLIT)) ||
+        ((flags & GMRES_CREATE_SPLIT) && (flags & GMRES_CREATE_TRANSPOSE)))
         return GMRES_ERR_ARG;
     const bool dev = (flags & GMRES_CREATE_DEVICE_PTRS) != 0;
     // Validate the structure on the host (device arrays are copied down).
@@ -830,21 +946,34 @@ gmres_status gmres_create(gmres_t *out, int32_t n, const int32_t *rowptr, const 
     h->chunk = round_up((h->ldv + h->grid - 1) / h->grid, 4);
     const double avg = (double)nnz / n;
     h->lanes32 = h->lanes64 = pow2_lanes(avg / 2.0);
+    h->split = (flags & GMRES_CREATE_SPLIT) != 0;
+    // vals64 holds the binary64 values, or with split storage hi[nnz] then
+    // lo[nnz] (the same 8 bytes per nonzero); vals32 the binary32 copy (not
+    // kept with split storage)
     if (h->rowptr.ensure(sizeof(int32_t) * (n + 1)) != cudaSuccess ||
         h->colind.ensure(sizeof(int32_t) * std::max<int64_t>(nnz, 1)) != cudaSuccess ||
         h->vals64.ensure(sizeof(double) * std::max<int64_t>(nnz, 1)) != cudaSuccess ||
-        h->vals32.ensure(sizeof(float) * std::max<int64_t>(nnz, 1)) != cudaSuccess)
+        (!h->split && h->vals32.ensure(sizeof(float) * std::max<int64_t>(nnz, 1)) != cudaSuccess))
+        return fail(GMRES_ERR_OOM);
+    ScopedBuf staging;  // binary64 values on the device before the split
+    if (h->split && nnz > 0 && staging.ensure(sizeof(double) * nnz) != cudaSuccess)
         return fail(GMRES_ERR_OOM);
     if (cudaMemcpyAsync(h->rowptr.p, rp.data(), sizeof(int32_t) * (n + 1),
                         cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
         (nnz > 0 && (cudaMemcpyAsync(h->colind.p, ci.data(), sizeof(int32_t) * nnz,
                                      cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
-                     cudaMemcpyAsync(h->vals64.p, va.data(), sizeof(double) * nnz,
-                                     cudaMemcpyHostToDevice, h->stream) != cudaSuccess)))
+                     cudaMemcpyAsync(h->split ? staging.p : h->vals64.p, va.data(),
+                                     sizeof(double) * nnz, cudaMemcpyHostToDevice,
+                                     h->stream) != cudaSuccess)))
         return fail(GMRES_ERR_CUDA);
     if (nnz > 0) {
-        k_cast_vals<<<h->nsm * 4, 256, 0, h->stream>>>(nnz, h->vals64.as<double>(),
-                                                        h->vals32.as<float>());
+        if (h->split)
+            k_split_vals<<<h->nsm * 4, 256, 0, h->stream>>>(
+                nnz, staging.as<double>(), h->vals64.as<unsigned>(),
+                h->vals64.as<unsigned>() + nnz);
+        else
+            k_cast_vals<<<h->nsm * 4, 256, 0, h->stream>>>(nnz, h->vals64.as<double>(),
+                                                            h->vals32.as<float>());
         if (cudaGetLastError() != cudaSuccess)
             return fail(GMRES_ERR_CUDA);
     }
@@ -912,12 +1041,24 @@ gmres_status gmres_set_values(gmres_t h, const double *vals) {
             if (!std::isfinite(vals[k]))
                 return GMRES_ERR_NONFINITE;
     }
-    CK(cudaMemcpyAsync(h->vals64.p, vals, sizeof(double) * h->nnz,
-                       dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
-    k_cast_vals<<<h->nsm * 4, 256, 0, h->stream>>>(h->nnz, h->vals64.as<double>(),
-                                                    h->vals32.as<float>());
-    CKL();
-    CK(cudaStreamSynchronize(h->stream));
+    if (h->split) {
+        ScopedBuf staging;
+        CK(staging.ensure(sizeof(double) * h->nnz));
+        CK(cudaMemcpyAsync(staging.p, vals, sizeof(double) * h->nnz,
+                           dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
+        k_split_vals<<<h->nsm * 4, 256, 0, h->stream>>>(h->nnz, staging.as<double>(),
+                                                         h->vals64.as<unsigned>(),
+                                                         h->vals64.as<unsigned>() + h->nnz);
+        CKL();
+        CK(cudaStreamSynchronize(h->stream));
+    } else {
+        CK(cudaMemcpyAsync(h->vals64.p, vals, sizeof(double) * h->nnz,
+                           dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
+        k_cast_vals<<<h->nsm * 4, 256, 0, h->stream>>>(h->nnz, h->vals64.as<double>(),
+                                                        h->vals32.as<float>());
+        CKL();
+        CK(cudaStreamSynchronize(h->stream));
+    }
     // derived data of the old values is stale
     h->trowptr.release();
     h->tcolind.release();
@@ -962,7 +1103,7 @@ gmres_status gmres_solve(gmres_t h, const double *b, double *x, int32_t m, doubl
     memset(info, 0, sizeof(*info));
     if (!h || !b || !x || m < 1 || m > MMAX || !(tol > 0) || maxiter < 0 ||
         (ortho != GMRES_ORTHO_MGS && ortho != GMRES_ORTHO_CGSR) || prec < GMRES_FP64 ||
-        prec > GMRES_MIXED_FP16)
+        prec > GMRES_MIXED_LIMITED)
         return GMRES_ERR_ARG;
     h->timer.on = h->opts.profile != 0;
     // Host buffers go through library-owned device copies.
@@ -993,6 +1134,11 @@ gmres_status gmres_solve(gmres_t h, const double *b, double *x, int32_t m, doubl
         st = solve_dispatch_path<float, __nv_bfloat16>(h, db, dx, m, tol, ortho, prec, maxiter,
                                                        info);
         break;
+    case GMRES_MIXED_LIMITED:
+        h->limited = true;
+        st = solve_dispatch_path<double, float>(h, db, dx, m, tol, ortho, prec, maxiter, info);
+        h->limited = false;
+        break;
     default:
         st = solve_dispatch_path<float, __half>(h, db, dx, m, tol, ortho, prec, maxiter, info);
         break;
@@ -1011,11 +1157,11 @@ gmres_status gmres_spmv(gmres_t h, const void *x, void *y, gmres_precision prec)
     if (!h || !x || !y || prec < GMRES_FP64 || prec > GMRES_MIXED_FP16)
         return GMRES_ERR_ARG;
     if (prec == GMRES_FP64)
-        CK(launch_spmv_plain<double>(h, h->opts.spmv_lanes ? h->opts.spmv_lanes : h->lanes64,
-                                     h->vals64.as<double>(), (const double *)x, (double *)y));
+        CK(launch_spmv_any<double>(h, h->opts.spmv_lanes ? h->opts.spmv_lanes : h->lanes64,
+                                   (const double *)x, (double *)y));
     else
-        CK(launch_spmv_plain<float>(h, h->opts.spmv_lanes ? h->opts.spmv_lanes : h->lanes32,
-                                    h->vals32.as<float>(), (const float *)x, (float *)y));
+        CK(launch_spmv_any<float>(h, h->opts.spmv_lanes ? h->opts.spmv_lanes : h->lanes32,
+                                  (const float *)x, (float *)y));
     CK(cudaStreamSynchronize(h->stream));
     return GMRES_OK;
 }
@@ -1119,7 +1265,10 @@ gmres_status arnoldi_impl(gmres_handle *h, const double *r0, int m, int kmax, gm
         export_small(sp.y, y, (size_t)m, h->stream, tmp);
     if (u) {
         if (c.pvals) {
-            CK(launch_spmv_plain<T>(h, lanes_for<T, VT>(h), c.pvals, c.t, c.w));
+            if (c.pvals_lim)
+                CK((launch_spmv_plain<T, float>(h, lanes_for<T, VT>(h), c.pvals_lim, c.t, c.w)));
+            else
+                CK(launch_spmv_plain<T>(h, lanes_for<T, VT>(h), c.pvals, c.t, c.w));
             export_small(c.w, u, (size_t)h->n, h->stream, tmp);
         } else {
             export_small(c.t, u, (size_t)h->n, h->stream, tmp);
@@ -1158,7 +1307,7 @@ gmres_status gmres_arnoldi(gmres_t h, const double *r0, int32_t m, int32_t kmax,
                            double *u, double *arn, int32_t *jout, int32_t *breakdown) {
     if (!h || !r0 || m < 1 || m > MMAX || kmax < 1 || kmax > m ||
         (ortho != GMRES_ORTHO_MGS && ortho != GMRES_ORTHO_CGSR) || prec < GMRES_FP64 ||
-        prec > GMRES_MIXED_FP16)
+        prec > GMRES_MIXED_LIMITED)
         return GMRES_ERR_ARG;
     h->timer.on = false;
     switch (prec) {
@@ -1171,6 +1320,14 @@ gmres_status gmres_arnoldi(gmres_t h, const double *r0, int32_t m, int32_t kmax,
     case GMRES_MIXED_BF16:
         return arnoldi_impl<float, __nv_bfloat16>(h, r0, m, kmax, ortho, prec, tau, inner_abs, V,
                                                   Hbar, H, s, cs, sn, y, u, arn, jout, breakdown);
+    case GMRES_MIXED_LIMITED: {
+        h->limited = true;
+        gmres_status st = arnoldi_impl<double, float>(h, r0, m, kmax, ortho, prec, tau, inner_abs,
+                                                      V, Hbar, H, s, cs, sn, y, u, arn, jout,
+                                                      breakdown);
+        h->limited = false;
+        return st;
+    }
     default:
         return arnoldi_impl<float, __half>(h, r0, m, kmax, ortho, prec, tau, inner_abs, V, Hbar,
                                            H, s, cs, sn, y, u, arn, jout, breakdown);
@@ -1196,17 +1353,17 @@ gmres_status gmres_autotune(gmres_t h, int32_t *lanes32, int32_t *lanes64) {
             const int L = cand[ci];
             for (int rep = 0; rep < 2; ++rep) {  // warm-up
                 if (prec)
-                    CK(launch_spmv_plain<float>(h, L, h->vals32.as<float>(), x32, y32));
+                    CK(launch_spmv_any<float>(h, L, x32, y32));
                 else
-                    CK(launch_spmv_plain<double>(h, L, h->vals64.as<double>(), x64, y64));
+                    CK(launch_spmv_any<double>(h, L, x64, y64));
             }
             CK(cudaEventRecord(a, h->stream));
             const int reps = 5;
             for (int rep = 0; rep < reps; ++rep) {
                 if (prec)
-                    CK(launch_spmv_plain<float>(h, L, h->vals32.as<float>(), x32, y32));
+                    CK(launch_spmv_any<float>(h, L, x32, y32));
                 else
-                    CK(launch_spmv_plain<double>(h, L, h->vals64.as<double>(), x64, y64));
+                    CK(launch_spmv_any<double>(h, L, x64, y64));
             }
             CK(cudaEventRecord(b, h->stream));
             CK(cudaEventSynchronize(b));
@@ -1235,14 +1392,14 @@ gmres_status gmres_autotune(gmres_t h, int32_t *lanes32, int32_t *lanes64) {
 
 gmres_status gmres_memory_bytes(gmres_t h, int32_t m, gmres_precision prec, int64_t *matrix_bytes,
                                 int64_t *workspace_bytes) {
-    if (!h || m < 1 || m > MMAX || prec < GMRES_FP64 || prec > GMRES_MIXED_FP16)
+    if (!h || m < 1 || m > MMAX || prec < GMRES_FP64 || prec > GMRES_MIXED_LIMITED)
         return GMRES_ERR_ARG;
     const int64_t n = h->n, nnz = h->nnz;
     // indices shared by both copies; binary64 + binary32 values (Sec. 4)
     if (matrix_bytes)
-        *matrix_bytes = 4 * (n + 1) + 4 * nnz + 8 * nnz + 4 * nnz;
+        *matrix_bytes = 4 * (n + 1) + 4 * nnz + 8 * nnz + (h->split ? 0 : 4 * nnz);
     if (workspace_bytes) {
-        const int64_t sT = prec == GMRES_FP64 ? 8 : 4;
+        const int64_t sT = (prec == GMRES_FP64 || prec == GMRES_MIXED_LIMITED) ? 8 : 4;
         *workspace_bytes = h->ldv * (m + 1) * elem_bytes(prec)  // basis
                            + 3 * h->ldv * sT                   // w, r, t
                            + 2 * (int64_t)(m + 1) * m * sT      // H, Hbar

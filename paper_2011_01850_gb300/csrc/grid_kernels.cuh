@@ -11,6 +11,8 @@
 // with zero tails, so the streaming kernels always move 4 rows per thread.
 #pragma once
 
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace gmres {
@@ -44,6 +46,16 @@ struct GridCtx {
     const int *prowptr;
     const int *pcolind;
     const T *pvals;
+    // limited mixed precision: binary32 copies of A and M read in binary64
+    // arithmetic (null otherwise; then a and pvals are used)
+    const float *a_lim;
+    const float *pvals_lim;
+    // A stored split (Sec. 4 outlook): high- and low-order 32 bits of each
+    // binary64 value; null when A is stored as binary64 + binary32 copies
+    const unsigned *ahi, *alo;
+    // how the Krylov step reads A: 0 the working-precision copy a, 1 the
+    // binary32 copy a_lim, 2 the high part of split storage, 3 both parts
+    int aform;
     // third restart strategy (Sec. 3): |s_{j+1}| of the cycle (entry 0 =
     // beta) and the stall test's factor (0 = off) and window
     double *ahist;
@@ -64,6 +76,11 @@ __device__ __forceinline__ void ld4<double, double>(const double *p, float, doub
 }
 template <>
 __device__ __forceinline__ void ld4<float, float>(const float *p, float, float (&o)[4]) {
+    float4 a = *reinterpret_cast<const float4 *>(p);
+    o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w;
+}
+template <>
+__device__ __forceinline__ void ld4<double, float>(const float *p, float, double (&o)[4]) {
     float4 a = *reinterpret_cast<const float4 *>(p);
     o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w;
 }
@@ -138,10 +155,31 @@ __device__ __forceinline__ void reduce_columns(const T *part, int nblocks, int n
 // group sums the row entries k = beg + l, beg + l + L, ... in order; the
 // group then combines its lanes with the xor-butterfly.
 // ---------------------------------------------------------------------------
-template <class T, class XT, int L>
-__device__ __forceinline__ T csr_row(const int *__restrict__ rowptr, const int *__restrict__ colind,
-                                     const T *__restrict__ a, const XT *x, float xinv, int row,
-                                     int n, int gl) {
+// Matrix values as a kernel reads them: a plain array, the high-order part
+// of split storage (the binary64 value with its low 32 bits cleared), or the
+// exact binary64 value from both parts.
+template <class AT>
+struct ValPlain {
+    const AT *a;
+    __device__ __forceinline__ AT operator()(int k) const { return __ldg(a + k); }
+};
+struct ValHi {
+    const unsigned *hi;
+    __device__ __forceinline__ double operator()(int k) const {
+        return __hiloint2double((int)__ldg(hi + k), 0);
+    }
+};
+struct ValHiLo {
+    const unsigned *hi, *lo;
+    __device__ __forceinline__ double operator()(int k) const {
+        return __hiloint2double((int)__ldg(hi + k), (int)__ldg(lo + k));
+    }
+};
+
+template <class T, class AV, class XT, int L>
+__device__ __forceinline__ T csr_row_v(const int *__restrict__ rowptr,
+                                       const int *__restrict__ colind, AV a, const XT *x,
+                                       float xinv, int row, int n, int gl) {
     T acc = 0;
     if (row < n) {
         int beg = __ldg(rowptr + row), end = __ldg(rowptr + row + 1);
@@ -151,8 +189,8 @@ __device__ __forceinline__ T csr_row(const int *__restrict__ rowptr, const int *
         for (; k + 3 * L < end; k += 4 * L) {
             const int c0 = __ldg(colind + k), c1 = __ldg(colind + k + L);
             const int c2 = __ldg(colind + k + 2 * L), c3 = __ldg(colind + k + 3 * L);
-            const T a0 = __ldg(a + k), a1 = __ldg(a + k + L);
-            const T a2 = __ldg(a + k + 2 * L), a3 = __ldg(a + k + 3 * L);
+            const T a0 = (T)a(k), a1 = (T)a(k + L);
+            const T a2 = (T)a(k + 2 * L), a3 = (T)a(k + 3 * L);
             const T x0 = (T)Basis<XT>::ld(x + c0, xinv), x1 = (T)Basis<XT>::ld(x + c1, xinv);
             const T x2 = (T)Basis<XT>::ld(x + c2, xinv), x3 = (T)Basis<XT>::ld(x + c3, xinv);
             acc += a0 * x0;
@@ -161,12 +199,40 @@ __device__ __forceinline__ T csr_row(const int *__restrict__ rowptr, const int *
             acc += a3 * x3;
         }
         for (; k < end; k += L)
-            acc += __ldg(a + k) * (T)Basis<XT>::ld(x + __ldg(colind + k), xinv);
+            acc += (T)a(k) * (T)Basis<XT>::ld(x + __ldg(colind + k), xinv);
     }
 #pragma unroll
     for (int off = L / 2; off > 0; off >>= 1)
         acc += __shfl_xor_sync(0xffffffffu, acc, off);
     return acc;
+}
+
+template <class T, class AT, class XT, int L>
+__device__ __forceinline__ T csr_row(const int *__restrict__ rowptr, const int *__restrict__ colind,
+                                     const AT *__restrict__ a, const XT *x, float xinv, int row,
+                                     int n, int gl) {
+    return csr_row_v<T, ValPlain<AT>, XT, L>(rowptr, colind, ValPlain<AT>{a}, x, xinv, row, n,
+                                             gl);
+}
+
+// A row of the Krylov step's matrix in the form the context holds: the
+// binary32 copy (limited mixed), split storage (high part for the binary32
+// and limited steps, both parts for binary64), or the working-precision
+// copy.
+template <class T, class VT, class XT, int L>
+__device__ __forceinline__ T step_row(const GridCtx<T, VT> &c, const XT *x, int row, int gl) {
+    switch (c.aform) {
+    case 3:
+        return csr_row_v<T, ValHiLo, XT, L>(c.rowptr, c.colind, ValHiLo{c.ahi, c.alo}, x, c.vinv,
+                                            row, c.n, gl);
+    case 2:
+        return csr_row_v<T, ValHi, XT, L>(c.rowptr, c.colind, ValHi{c.ahi}, x, c.vinv, row, c.n,
+                                          gl);
+    case 1:
+        return csr_row<T, float, XT, L>(c.rowptr, c.colind, c.a_lim, x, c.vinv, row, c.n, gl);
+    default:
+        return csr_row<T, T, XT, L>(c.rowptr, c.colind, c.a, x, c.vinv, row, c.n, gl);
+    }
 }
 
 // w = A v_col (inner step, Alg. 1 "w <- A v_j"); with a right preconditioner
@@ -182,16 +248,16 @@ __global__ void __launch_bounds__(256) k_spmv_step(GridCtx<T, VT> c, const XT *x
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t base = warp * G; base < c.n; base += nwarps * G) {
         int row = (int)(base + gi);
-        T v = csr_row<T, XT, L>(c.rowptr, c.colind, c.a, x, c.vinv, row, c.n, gl);
+        T v = step_row<T, VT, XT, L>(c, x, row, gl);
         if (row < c.n && gl == 0)
             y[row] = v;
     }
 }
 
 // Plain SpMV for the C-ABI entry point gmres_spmv (no control block).
-template <class T, int L>
-__global__ void __launch_bounds__(256) k_spmv_plain(int n, const int *rowptr, const int *colind,
-                                                    const T *a, const T *x, T *y) {
+template <class T, class AV, int L>
+__global__ void __launch_bounds__(256) k_spmv_plain_v(int n, const int *rowptr, const int *colind,
+                                                      AV a, const T *x, T *y) {
     const int G = 32 / L;
     const int lane = threadIdx.x & 31;
     const int gl = lane % L, gi = lane / L;
@@ -199,7 +265,23 @@ __global__ void __launch_bounds__(256) k_spmv_plain(int n, const int *rowptr, co
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t base = warp * G; base < n; base += nwarps * G) {
         int row = (int)(base + gi);
-        T v = csr_row<T, T, L>(rowptr, colind, a, x, 1.f, row, n, gl);
+        T v = csr_row_v<T, AV, T, L>(rowptr, colind, a, x, 1.f, row, n, gl);
+        if (row < n && gl == 0)
+            y[row] = v;
+    }
+}
+
+template <class T, class AT, int L>
+__global__ void __launch_bounds__(256) k_spmv_plain(int n, const int *rowptr, const int *colind,
+                                                    const AT *a, const T *x, T *y) {
+    const int G = 32 / L;
+    const int lane = threadIdx.x & 31;
+    const int gl = lane % L, gi = lane / L;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t base = warp * G; base < n; base += nwarps * G) {
+        int row = (int)(base + gi);
+        T v = csr_row<T, AT, T, L>(rowptr, colind, a, x, 1.f, row, n, gl);
         if (row < n && gl == 0)
             y[row] = v;
     }
@@ -225,7 +307,11 @@ __global__ void __launch_bounds__(256) k_residual(GridCtx<T, VT> c, const double
     int bad = 0;
     for (int64_t base = warp * G; base < c.n; base += nwarps * G) {
         int row = (int)(base + gi);
-        double ax = csr_row<double, double, L>(c.rowptr, c.colind, c.a64, x, 1.f, row, c.n, gl);
+        double ax = c.ahi ? csr_row_v<double, ValHiLo, double, L>(c.rowptr, c.colind,
+                                                                  ValHiLo{c.ahi, c.alo}, x, 1.f,
+                                                                  row, c.n, gl)
+                          : csr_row<double, double, double, L>(c.rowptr, c.colind, c.a64, x, 1.f,
+                                                               row, c.n, gl);
         if (row < c.n && gl == 0) {
             double zi = b[row] - ax;
             if (z)

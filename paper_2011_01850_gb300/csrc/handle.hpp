@@ -86,6 +86,8 @@ struct gmres_handle {
     std::map<const void *, bool> mgs_ok_cache;  // cooperative MGS feasible, per kernel
     DevBuf mgs_seq;              // exchange slots of the cooperative MGS kernel
     DevBuf mon;                  // restart-test histories and the U, S matrices
+    bool limited = false;        // the running solve is GMRES_MIXED_LIMITED
+    bool split = false;          // A stored split: vals64 holds hi[nnz] then lo[nnz]
     unsigned mgs_round = 0;      // next exchange round number (0: flags not set up)
     int64_t chunk = 0;     // rows per block
     // matrix

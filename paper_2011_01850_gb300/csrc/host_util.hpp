@@ -41,6 +41,14 @@ struct DevBuf {
     T *as() const { return reinterpret_cast<T *>(p); }
 };
 
+// A device buffer freed when it goes out of scope (temporary staging).
+struct ScopedBuf : DevBuf {
+    ScopedBuf() = default;
+    ScopedBuf(const ScopedBuf &) = delete;
+    ScopedBuf &operator=(const ScopedBuf &) = delete;
+    ~ScopedBuf() { release(); }
+};
+
 
 #define CK(call)                                                                      \
     do {                                                                              \
@@ -79,6 +87,7 @@ inline int elem_bytes(gmres_precision p) {
     switch (p) {
     case GMRES_FP64: return 8;
     case GMRES_MIXED: return 4;
+    case GMRES_MIXED_LIMITED: return 4;
     default: return 2;
     }
 }
@@ -87,6 +96,7 @@ inline double default_tau(gmres_precision p) {
     switch (p) {
     case GMRES_FP64: return 0.0;
     case GMRES_MIXED: return 1e-6;
+    case GMRES_MIXED_LIMITED: return 1e-6;
     case GMRES_MIXED_BF16: return 0.00390625;     // 2^-8, the bfloat16 unit roundoff
     default: return 0.00048828125;                // 2^-11, the binary16 unit roundoff
     }

@@ -440,16 +440,16 @@ gmres_status loss_grad(gmres_handle *h, const float *params, int P, const float 
         {
             dim3 gg(h->nsm * 8), bb(256);
             switch (L) {
-            case 1: k_spmv_plain<float, 1><<<gg, bb, 0, h->stream>>>(n, rp, ci, m, z, u); break;
-            case 2: k_spmv_plain<float, 2><<<gg, bb, 0, h->stream>>>(n, rp, ci, m, z, u); break;
-            case 4: k_spmv_plain<float, 4><<<gg, bb, 0, h->stream>>>(n, rp, ci, m, z, u); break;
-            case 8: k_spmv_plain<float, 8><<<gg, bb, 0, h->stream>>>(n, rp, ci, m, z, u); break;
-            default: k_spmv_plain<float, 16><<<gg, bb, 0, h->stream>>>(n, rp, ci, m, z, u); break;
+            case 1: k_spmv_plain<float, float, 1><<<gg, bb, 0, h->stream>>>(n, rp, ci, m, z, u); break;
+            case 2: k_spmv_plain<float, float, 2><<<gg, bb, 0, h->stream>>>(n, rp, ci, m, z, u); break;
+            case 4: k_spmv_plain<float, float, 4><<<gg, bb, 0, h->stream>>>(n, rp, ci, m, z, u); break;
+            case 8: k_spmv_plain<float, float, 8><<<gg, bb, 0, h->stream>>>(n, rp, ci, m, z, u); break;
+            default: k_spmv_plain<float, float, 16><<<gg, bb, 0, h->stream>>>(n, rp, ci, m, z, u); break;
             }
-            k_spmv_plain<float, 4><<<gg, bb, 0, h->stream>>>(n, rp, ci, h->vals32.as<float>(), u,
+            k_spmv_plain<float, float, 4><<<gg, bb, 0, h->stream>>>(n, rp, ci, h->vals32.as<float>(), u,
                                                               au);
             k_probe_residual<<<g, 256, 0, h->stream>>>(n, au, z, r, lpart);
-            k_spmv_plain<float, 4><<<gg, bb, 0, h->stream>>>(
+            k_spmv_plain<float, float, 4><<<gg, bb, 0, h->stream>>>(
                 n, h->trowptr.as<int>(), h->tcolind.as<int>(), h->tvals32.as<float>(), r, au);
             k_grad_m<<<g, 256, 0, h->stream>>>(n, rp, ci, au, z, scale, gm, p == 0);
         }
@@ -482,7 +482,7 @@ gmres_status loss_grad(gmres_handle *h, const float *params, int P, const float 
 }
 
 gmres_status prepare(gmres_handle *h) {
-    if (!h)
+    if (!h || h->split)  // the preconditioner works on the binary64 + binary32 copies
         return GMRES_ERR_ARG;
     // the control block is used for the last-block counter
     CK(h->ctl.ensure(sizeof(Ctl)));
@@ -514,7 +514,7 @@ gmres_status gmres_spai_features(gmres_t h, float *feat) {
 
 gmres_status gmres_spai_loss_grad(gmres_t h, const float *params, int32_t nprobe, const float *Z,
                                   double *loss, float *grad_params, float *grad_m) {
-    if (!h || !params || nprobe < 1 || !Z || !is_device_ptr(Z) ||
+    if (!h || h->split || !params || nprobe < 1 || !Z || !is_device_ptr(Z) ||
         (grad_params && !is_device_ptr(grad_params)) || (grad_m && !is_device_ptr(grad_m)))
         return GMRES_ERR_ARG;
     gmres_status st = prepare(h);
@@ -544,7 +544,7 @@ gmres_status gmres_spai_adam(gmres_t h, float *params, float *adam_m, float *ada
 gmres_status gmres_spai_train_step(gmres_t h, float *params, float *adam_m, float *adam_v,
                                    int32_t step, int32_t nprobe, uint64_t seed, const float *Zx,
                                    int32_t nzx, float lr, double *loss) {
-    if (!h || !params || !adam_m || !adam_v || step < 1 || nprobe < 0 || nzx < 0 ||
+    if (!h || h->split || !params || !adam_m || !adam_v || step < 1 || nprobe < 0 || nzx < 0 ||
         nprobe + nzx < 1 || (nzx > 0 && (!Zx || !is_device_ptr(Zx))) || !is_device_ptr(params) ||
         !is_device_ptr(adam_m) || !is_device_ptr(adam_v) || !(lr > 0))
         return GMRES_ERR_ARG;

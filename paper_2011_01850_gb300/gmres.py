@@ -19,17 +19,18 @@ LIB_PATH = _build.LIB_PATH
 
 # enums (include/gmres_gb300.h)
 ORTHO_MGS, ORTHO_CGSR = 0, 1
-FP64, MIXED, MIXED_BF16, MIXED_FP16 = 0, 1, 2, 3
+FP64, MIXED, MIXED_BF16, MIXED_FP16, MIXED_LIMITED = 0, 1, 2, 3, 4
 OK, MAXITER, ERR_ARG, ERR_CUDA, ERR_NONFINITE, ERR_BREAKDOWN, ERR_TIMEOUT, ERR_OOM = (
     0, 1, -1, -2, -3, -4, -5, -6)
-CREATE_DEVICE_PTRS, CREATE_TRANSPOSE = 1, 2
+CREATE_DEVICE_PTRS, CREATE_TRANSPOSE, CREATE_SPLIT = 1, 2, 4
 PATH_AUTO, PATH_GRID, PATH_BLOCK = 0, 1, 2
 ORTH_OFF, ORTH_SPECTRAL, ORTH_FROBENIUS = 0, 1, 2
 K_RESIDUAL, K_SPMV, K_ORTHO, K_NORMALIZE, K_UPDATE, K_PRECOND, K_BLOCK = range(7)
 K_COUNT = 8
 KERNEL_CLASS_NAMES = ["residual", "spmv", "ortho", "normalize", "update", "precond", "block"]
 
-PRECISIONS = {"fp64": FP64, "mixed": MIXED, "mixed_bf16": MIXED_BF16, "mixed_fp16": MIXED_FP16}
+PRECISIONS = {"fp64": FP64, "mixed": MIXED, "mixed_bf16": MIXED_BF16, "mixed_fp16": MIXED_FP16,
+              "mixed_limited": MIXED_LIMITED}
 ORTHOS = {"mgs": ORTHO_MGS, "cgsr": ORTHO_CGSR}
 
 
@@ -53,7 +54,8 @@ class Opts(ctypes.Structure):
         ("cgs_kernel", ctypes.c_int32),
         ("mgs_kernel", ctypes.c_int32),
         ("l2_prefetch", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 2),
+        ("block_cluster", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 1),
         ("stall_factor", ctypes.c_double),
         ("stall_window", ctypes.c_int32),
         ("orth_norm", ctypes.c_int32),
@@ -113,6 +115,7 @@ SIGNATURES = {
     "gmres_memory_bytes": (_st, [_vp, _i32, _i32, ctypes.POINTER(ctypes.c_int64),
                                  ctypes.POINTER(ctypes.c_int64)]),
     "gmres_orth_norms": (_st, [_vp, _vp, _i32]),
+    "gmres_batch_autotune": (_st, [_vp, _vp, _i32, _i32, _i32, _i32, ctypes.POINTER(_i32)]),
     "gmres_batch_create": (_st, [ctypes.POINTER(_vp), _i32, _vp, _vp, _vp, _vp, _vp]),
     "gmres_batch_destroy": (None, [_vp]),
     "gmres_batch_solve": (_st, [_vp, _vp, _vp, _i32, _f64, _i32, _i32, _i32, _i32, _vp,
@@ -273,6 +276,15 @@ def gmres_autotune(h):
     b = ctypes.c_int32()
     _check(lib().gmres_autotune(h, ctypes.byref(a), ctypes.byref(b)), "gmres_autotune")
     return a.value, b.value
+
+
+def gmres_batch_autotune(h, rhs, m, ortho, prec, iters):
+    """Time capped batched solves over the SpMV lanes candidates; returns
+    the lanes per row the batch keeps for lanes = 0."""
+    out = _i32()
+    _check(lib().gmres_batch_autotune(h, _ptr(rhs), int(m), int(ortho), int(prec), int(iters),
+                                      ctypes.byref(out)), "gmres_batch_autotune")
+    return out.value
 
 
 def gmres_orth_norms(h, count):

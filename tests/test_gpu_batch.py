@@ -110,3 +110,24 @@ def test_batch_cluster_path(prec, ortho, gpulib):
         xo, _ = O.gmres(A, bi, m=30, tol=1e-13, ortho=O.CGSR, prec=O.FP64, maxiter=40000)
         err = np.linalg.norm(xi - xo) / np.linalg.norm(xo)
         assert err <= 1e-6, (i, err)
+
+
+def test_batch_autotune(gpulib):
+    """The SpMV lanes autotuner picks a power of two in [1, 16], leaves the
+    batch's x alone, and a later solve with lanes = 0 uses the choice and
+    converges like an explicit one."""
+    systems = _systems()
+    sys_ptr, rp, ci, va, b = G.pack_batch(systems)
+    nsys = len(systems)
+    h = G.gmres_batch_create(nsys, sys_ptr, rp, ci, va)
+    L = G.gmres_batch_autotune(h, b, 30, G.ORTHO_MGS, G.MIXED, 40)
+    assert L in (1, 2, 4, 8, 16)
+    x0 = np.zeros(len(b))
+    st0, r0, _ = G.gmres_batch_solve(h, b, x0, 30, 1e-10, G.ORTHO_MGS, G.MIXED, 4000, nsys=nsys)
+    x1 = np.zeros(len(b))
+    st1, r1, _ = G.gmres_batch_solve(h, b, x1, 30, 1e-10, G.ORTHO_MGS, G.MIXED, 4000, lanes=L,
+                                     nsys=nsys)
+    G.gmres_batch_destroy(h)
+    assert st0 == st1 == G.OK
+    assert np.array_equal(x0, x1)
+    assert [r.iters for r in r0] == [r.iters for r in r1]

@@ -119,11 +119,15 @@ def test_residual_parity(name, A, gpulib, stream):
     s.close()
 
 
-CYCLE_TOL = {O.FP64: 1e-11, O.MIXED: 2e-4, O.MIXED_BF16: 5e-2, O.MIXED_FP16: 2e-2}
+# oracle precision codes -> library codes (they differ from MIXED_LIMITED on)
+O2G = {O.FP64: 0, O.MIXED: 1, O.MIXED_BF16: 2, O.MIXED_FP16: 3, O.MIXED_LIMITED: 4}
+
+CYCLE_TOL = {O.FP64: 1e-11, O.MIXED: 2e-4, O.MIXED_BF16: 5e-2, O.MIXED_FP16: 2e-2,
+             O.MIXED_LIMITED: 1e-4}
 
 
-@pytest.mark.parametrize("prec", [O.FP64, O.MIXED, O.MIXED_BF16, O.MIXED_FP16],
-                         ids=["fp64", "mixed", "bf16", "fp16"])
+@pytest.mark.parametrize("prec", [O.FP64, O.MIXED, O.MIXED_BF16, O.MIXED_FP16, O.MIXED_LIMITED],
+                         ids=["fp64", "mixed", "bf16", "fp16", "limited"])
 @pytest.mark.parametrize("ortho", [O.MGS, O.CGSR], ids=["mgs", "cgsr"])
 def test_cycle_parity(prec, ortho, gpulib, stream):
     """One restart cycle: every exported quantity against the oracle's."""
@@ -132,7 +136,7 @@ def test_cycle_parity(prec, ortho, gpulib, stream):
     n = len(A[0]) - 1
     m, kmax = 24, 12
     s = G.Solver(A, stream=stream)
-    g = G.gmres_arnoldi(s.h, dev(b), m, kmax, ortho, prec, n=n)
+    g = G.gmres_arnoldi(s.h, dev(b), m, kmax, ortho, O2G[prec], n=n)
     o = O.arnoldi_cycle(A, b, m, ortho=ortho, prec=prec, kmax=kmax)
     s.close()
     assert g["j"] == o["j"] == kmax
@@ -199,6 +203,73 @@ def test_solve_parity(case, prec, ortho, path, gpulib, stream):
     assert err <= max(1e-8, 2 * kappa * (rel + 1e-13)), (err, kappa, rel)
     if kappa * 1e-10 <= 1e-8:
         assert err <= 1e-8, err
+
+
+@pytest.mark.parametrize("case", SOLVE_CASES, ids=[c[0] for c in SOLVE_CASES])
+@pytest.mark.parametrize("ortho", ["mgs", "cgsr"])
+def test_limited_solve_parity(case, ortho, gpulib, stream):
+    """Limited mixed precision (Sec. 4.1; grid path): the binary64 target and
+    the oracle's solution, as for the other modes; the block path refuses it."""
+    A = case[1]()
+    b = I.rhs_ones_noise(A, 1e-3, 11)
+    x, st, info = _solve(A, b, "mixed_limited", ortho, 1, stream=stream)
+    assert st == G.OK, info
+    rel = O.residual_norm(A, b, x) / np.linalg.norm(b)
+    assert rel <= 1e-10, (rel, info)
+    xo, oi = O.gmres(A, b, m=30, tol=1e-13, ortho=O.CGSR, prec=O.FP64, maxiter=20000)
+    err = np.linalg.norm(x - xo) / np.linalg.norm(xo)
+    kappa = _kappa(case[0], A)
+    assert err <= max(1e-8, 2 * kappa * (rel + 1e-13)), (err, kappa, rel)
+    with pytest.raises(G.GmresError) as e:
+        _solve(A, b, "mixed_limited", ortho, 2, stream=stream)
+    assert e.value.status == G.ERR_ARG
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("ortho", ["mgs", "cgsr"])
+def test_block_cluster_single_system(prec, ortho, gpulib, stream):
+    """The block path on one cluster of 8 blocks (reductions through
+    distributed shared memory) against one block: both reach the binary64
+    target, agree with the oracle, and binary64 takes the same schedule."""
+    A = I.convdiff2d(64, pe=10.0)
+    b = I.rhs_ones_noise(A, 1e-3, 7)
+    n = len(b)
+    out = {}
+    for cs in (1, 8):
+        s = G.Solver(A, stream=stream)
+        s.set_opts(path=G.PATH_BLOCK, block_cluster=cs)
+        x, st, info = s.solve(b, np.zeros(n), m=50, ortho=ortho, prec=prec)
+        s.close()
+        assert st == G.OK
+        assert O.residual_norm(A, b, x) / np.linalg.norm(b) <= 1e-10
+        out[cs] = (x, info)
+    xo, oi = O.gmres(A, b, m=50, tol=1e-10, ortho=O.MGS if ortho == "mgs" else O.CGSR,
+                     prec=O.FP64 if prec == "fp64" else O.MIXED)
+    if prec == "fp64":
+        assert out[8][1]["iters"] == out[1][1]["iters"] == oi["iters"]
+        assert np.linalg.norm(out[8][0] - xo) / np.linalg.norm(xo) <= 1e-11
+
+
+def test_limited_takes_fewer_iterations_than_mixed(gpulib, stream):
+    """Sec. 4.1: limiting binary32 to A, M and the basis lets MGS improve
+    further before it stalls, so the limited solver needs no more inner
+    iterations than the fully mixed one (and its cycles use binary64
+    vectors: the workspace is the binary64 one with a binary32 basis)."""
+    A = I.convdiff2d(30, pe=1.0)
+    b = I.rhs_ones_noise(A, 1e-3, 1)
+    s = G.Solver(A, stream=stream)
+    s.set_opts(path=G.PATH_GRID)
+    _, st1, i1 = s.solve(b, np.zeros(len(b)), m=100, ortho="mgs", prec="mixed")
+    _, st2, i2 = s.solve(b, np.zeros(len(b)), m=100, ortho="mgs", prec="mixed_limited")
+    _, w64 = G.gmres_memory_bytes(s.h, 100, G.FP64)
+    _, wlim = G.gmres_memory_bytes(s.h, 100, G.MIXED_LIMITED)
+    s.close()
+    assert st1 == st2 == G.OK
+    assert i2["iters"] <= i1["iters"], (i1["iters"], i2["iters"])
+    xo, oi = O.gmres(A, b, m=100, ortho=O.MGS, prec=O.MIXED_LIMITED)
+    assert abs(i2["iters"] - oi["iters"]) <= 0.25 * oi["iters"]
+    ldv = ((len(b) + 2047) // 2048) * 2048
+    assert w64 - wlim == 101 * ldv * 4
 
 
 _KAPPA = {}
@@ -330,6 +401,31 @@ def test_mgs_cooperative_matches_per_column(gpulib, stream):
     assert i0["iters"] == i1["iters"] and i0["restarts"] == i1["restarts"]
     assert np.linalg.norm(x0 - x1) / np.linalg.norm(x1) <= 1e-11
     assert i0["kernel_launches"]["ortho"] < i1["kernel_launches"]["ortho"]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "mixed_fp16"])
+def test_cgsr_kernel_families_agree(prec, gpulib, stream):
+    """The three CGSR kernel families (rows with the update split by basis
+    vectors, TMA-fed tiles, rows with the update split by rows) sum in
+    different orders; binary64 takes the same schedule with solutions equal
+    to 1e-11, and every family reaches the binary64 target."""
+    A = I.convdiff3d(26, eps=(0.1, 0.1, 0.1), seed=3)  # n = 17576: several slices per block
+    b = I.rhs_ones_noise(A, 1e-3, 5)
+    n = len(A[0]) - 1
+    out = {}
+    for kern in (0, 1, 2):
+        s = G.Solver(A, stream=stream)
+        s.set_opts(path=G.PATH_GRID, cgs_kernel=kern)
+        x, st, info = s.solve(b, np.zeros(n), m=40, ortho="cgsr", prec=prec)
+        s.close()
+        assert st == G.OK
+        assert O.residual_norm(A, b, x) / np.linalg.norm(b) <= 1e-10
+        out[kern] = (x, info)
+    if prec == "fp64":
+        for kern in (1, 2):
+            assert out[kern][1]["iters"] == out[0][1]["iters"]
+            assert out[kern][1]["restarts"] == out[0][1]["restarts"]
+            assert np.linalg.norm(out[kern][0] - out[0][0]) / np.linalg.norm(out[0][0]) <= 1e-11
 
 
 def test_bounded_wait_reports_timeout(gpulib, stream):
