@@ -19,7 +19,7 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SOURCES = ["gmres_oracle.c", "gmres_oracle.h", "cycle_impl.inc", "spai_oracle.c"]
+_SOURCES = ["gmres_oracle.c", "gmres_oracle.h", "cycle_impl.inc", "spai_oracle.c", "ilu_oracle.c"]
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -50,7 +50,8 @@ class Opts(ctypes.Structure):
         ("orth_norm", ctypes.c_int32),
         ("orth_iters", ctypes.c_int32),
         ("split_bytes", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("left_precond", ctypes.c_int32),
+        ("ilu32", ctypes.c_int32),
     ]
 
 
@@ -66,6 +67,8 @@ class Restart(ctypes.Structure):
         ("orth_norm", ctypes.c_int32),
         ("orth_iters", ctypes.c_int32),
         ("split_bytes", ctypes.c_int32),
+        ("left_precond", ctypes.c_int32),
+        ("ilu32", ctypes.c_int32),
     ]
 
 
@@ -127,6 +130,10 @@ def _bind(L):
     L.orc_s_norm2.restype = ctypes.c_double
     L.orc_high_part.argtypes = [ctypes.c_double]
     L.orc_high_part.restype = ctypes.c_double
+    L.orc_ilu0.argtypes = [ctypes.c_int32, _i32p, _i32p, _f64p, _f64p]
+    L.orc_ilu0.restype = ctypes.c_int
+    L.orc_ilu_apply.argtypes = [ctypes.c_int32, _i32p, _i32p, _f64p, _f64p, _f64p]
+    L.orc_ilu_apply.restype = ctypes.c_int
     L.orc_gmres.argtypes = [ctypes.c_int32, _i32p, _i32p, _f64p, _f64p, _f64p,
                             ctypes.POINTER(Opts), vp, vp, vp, ctypes.POINTER(Info), vp, vp]
     L.orc_gmres.restype = ctypes.c_int
@@ -226,7 +233,8 @@ def round_basis(v, prec, n):
 
 def arnoldi_cycle(A, r0, m, ortho=CGSR, prec=FP64, kmax=None, tau=0.0, inner_abs=0.0, M=None,
                   export_basis=True, stall_factor=0.0, stall_window=0, orth_norm=ORTH_OFF,
-                  orth_threshold=1.0, orth_iters=10, split_bytes=False):
+                  orth_threshold=1.0, orth_iters=10, split_bytes=False, ilu=None,
+                  ilu32=False):
     """One restart cycle from residual r0; returns a dict of its quantities.
 
     V is (m+1, n) (row i = basis vector i), Hbar/H are (m+1, m), the first ``j``
@@ -247,6 +255,18 @@ def arnoldi_cycle(A, r0, m, ortho=CGSR, prec=FP64, kmax=None, tau=0.0, inner_abs
     arn = np.zeros(m)
     j = ctypes.c_int32(0)
     bd = ctypes.c_int32(0)
+    rs = Restart()
+    rs.tau, rs.inner_abs = tau, inner_abs
+    rs.stall_factor = stall_factor
+    rs.stall_window = stall_window if stall_window > 0 else (m + 19) // 20
+    rs.orth_norm, rs.orth_threshold, rs.orth_iters = orth_norm, orth_threshold, orth_iters
+    rs.split_bytes = int(bool(split_bytes))
+    if ilu is not None:
+        if M is not None:
+            raise ValueError("one preconditioner at a time")
+        M = ilu
+        rs.left_precond = 1
+        rs.ilu32 = int(bool(ilu32))
     if M is not None:
         mp, mc, mv = _csr(M)
         keep = (mp, mc, mv)
@@ -254,12 +274,6 @@ def arnoldi_cycle(A, r0, m, ortho=CGSR, prec=FP64, kmax=None, tau=0.0, inner_abs
     else:
         keep = None
         margs = (None, None, None)
-    rs = Restart()
-    rs.tau, rs.inner_abs = tau, inner_abs
-    rs.stall_factor = stall_factor
-    rs.stall_window = stall_window if stall_window > 0 else (m + 19) // 20
-    rs.orth_norm, rs.orth_threshold, rs.orth_iters = orth_norm, orth_threshold, orth_iters
-    rs.split_bytes = int(bool(split_bytes))
     orth = np.zeros(m)
     rc = _L().orc_arnoldi_cycle_ex(n, rp, ci, va, np.ascontiguousarray(r0, np.float64), m, kmax,
                                     ortho, prec, ctypes.byref(rs), *margs, _ptr(V), _ptr(Hb),
@@ -271,6 +285,29 @@ def arnoldi_cycle(A, r0, m, ortho=CGSR, prec=FP64, kmax=None, tau=0.0, inner_abs
     jj = j.value
     return dict(V=V, Hbar=Hb.T.copy(), H=H.T.copy(), s=s, cs=cs, sn=sn, y=y, u=u, arn=arn, j=jj,
                 breakdown=bool(bd.value), orth=orth)
+
+
+def ilu0(A):
+    """ILU(0) factors of A on its pattern (Sec. 4's preconditioner): a CSR
+    triple (rowptr, colind, lu) with L's strictly lower entries (unit
+    diagonal implied) and U's upper entries including the diagonal."""
+    rp, ci, va = _csr(A)
+    lu = np.zeros(len(va))
+    rc = _L().orc_ilu0(len(rp) - 1, rp, ci, va, lu)
+    if rc:
+        raise ValueError("orc_ilu0 failed: %d" % rc)
+    return rp, ci, lu
+
+
+def ilu_apply(LU, z):
+    """(L U)^-1 z in binary64."""
+    rp, ci, lu = _csr(LU)
+    z = np.ascontiguousarray(z, dtype=np.float64)
+    out = np.zeros(len(rp) - 1)
+    rc = _L().orc_ilu_apply(len(rp) - 1, rp, ci, lu, z, out)
+    if rc:
+        raise ValueError("orc_ilu_apply failed: %d" % rc)
+    return out
 
 
 def high_part(v):
@@ -297,7 +334,7 @@ def default_tau(prec):
 def gmres(A, b, x0=None, m=30, tol=1e-10, ortho=CGSR, prec=FP64, maxiter=10000, tau=None,
           repeat_first=None, inner_factor=0.5, M=None, history=False, stall_factor=0.0,
           stall_window=0, orth_norm=ORTH_OFF, orth_threshold=1.0, orth_iters=10,
-          split_bytes=False):
+          split_bytes=False, ilu=None, ilu32=False):
     """Restarted GMRES(m) (Algorithm 1).  Returns (x, info dict).
 
     Restart strategies (Sec. 3): repeat_first (first), tau (second),
@@ -318,6 +355,12 @@ def gmres(A, b, x0=None, m=30, tol=1e-10, ortho=CGSR, prec=FP64, maxiter=10000, 
     o.stall_factor, o.stall_window = stall_factor, stall_window
     o.orth_norm, o.orth_threshold, o.orth_iters = orth_norm, orth_threshold, orth_iters
     o.split_bytes = int(bool(split_bytes))
+    if ilu is not None:
+        if M is not None:
+            raise ValueError("one preconditioner at a time")
+        M = ilu
+        o.left_precond = 1
+        o.ilu32 = int(bool(ilu32))
     info = Info()
     arn = np.zeros(max(maxiter, 1)) if history else None
     cyc = np.zeros(maxiter + 2) if history else None

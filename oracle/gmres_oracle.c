@@ -336,8 +336,10 @@ static int run_cycle(int32_t n, const int32_t *rowptr, const int32_t *colind, co
             a[k] = !limited ? vals[k]
                             : (rs->split_bytes ? orc_high_part(vals[k]) : (double)(float)vals[k]);
         memcpy(c.r0, r0, sizeof(double) * (size_t)n);
+        /* M in binary32 for limited mixed and for the binary32 ILU factors */
         for (int32_t k = 0; k < pnnz; ++k)
-            pm[k] = limited ? (double)(float)pm_vals[k] : pm_vals[k];
+            pm[k] = (limited || (rs->left_precond && rs->ilu32)) ? (double)(float)pm_vals[k]
+                                                                   : pm_vals[k];
         rc = cycle_f64(n, rowptr, colind, (double *)c.a, (double *)c.r0, m, kmax, ortho, prec,
                        rs, pm_rowptr, pm_colind, pm_vals ? (double *)c.pm : NULL,
                        (double *)c.V, (double *)c.Hb, (double *)c.H, (double *)c.s,
@@ -488,6 +490,8 @@ int orc_gmres(int32_t n, const int32_t *rowptr, const int32_t *colind, const dou
     rs.orth_threshold = o->orth_threshold;
     rs.orth_iters = o->orth_iters;
     rs.split_bytes = o->split_bytes;
+    rs.left_precond = o->left_precond;
+    rs.ilu32 = o->ilu32;
     int32_t cycle_len = m;
     int rc = 0;
     for (;;) {

@@ -72,7 +72,13 @@ typedef struct {
                              of each binary64 value (Sec. 4 outlook); the Krylov
                              step reads the high-order part only (a value
                              truncated to 20 fraction bits), the residual both */
-    int32_t reserved;
+    int32_t left_precond; /* 1: the preconditioner arguments of orc_gmres hold
+                             ILU(0) factors (orc_ilu0) on their pattern, applied
+                             on the left as Alg. 1 does: r = M^-1 z and
+                             w = M^-1 A v_j (0: they hold a right
+                             preconditioner M, applied as w = A M v_j)        */
+    int32_t ilu32;        /* with left_precond in ORC_FP64: the factors stored in
+                             binary32 (the paper's FP32-ILU variant, Sec. 4.2) */
 } orc_opts;
 
 enum { ORC_ORTH_OFF = 0, ORC_ORTH_SPECTRAL = 1, ORC_ORTH_FROBENIUS = 2 };
@@ -91,6 +97,8 @@ typedef struct {
     int32_t orth_norm;
     int32_t orth_iters;
     int32_t split_bytes;  /* as in orc_opts */
+    int32_t left_precond; /* as in orc_opts */
+    int32_t ilu32;        /* as in orc_opts */
 } orc_restart;
 
 typedef struct {
@@ -159,6 +167,17 @@ int orc_arnoldi_cycle_ex(int32_t n, const int32_t *rowptr, const int32_t *colind
  * leading dimension ld) by `iters` power-method iterations on S^T S from the
  * vector of equal entries; exposed for the tests. */
 double orc_s_norm2(int32_t k, const double *S, int32_t ld, int32_t iters);
+
+/* ILU(0) of A (Sec. 4's preconditioner): lu receives L (strictly lower part,
+ * unit diagonal implied) and U (upper part with the diagonal) on A's pattern.
+ * Rows must be sorted with a diagonal entry.  Returns 0, -1 (bad input) or
+ * -3 (zero or non-finite pivot). */
+int orc_ilu0(int32_t n, const int32_t *rowptr, const int32_t *colind, const double *vals,
+             double *lu);
+
+/* out = (L U)^-1 z in binary64 (forward then backward substitution). */
+int orc_ilu_apply(int32_t n, const int32_t *rowptr, const int32_t *colind, const double *lu,
+                  const double *z, double *out);
 
 /* The high-order 32 bits of a binary64 value as a binary64 value (the low
  * 32 bits cleared: sign, exponent and the top 20 fraction bits). */

@@ -41,8 +41,8 @@ MUTATIONS = [
      "for (int32_t l = i + 2; l < j; ++l)", "dropped term in back substitution"),
     ("cycle_impl.inc", "V[(size_t)(c + 1) * n + r] = (R)orc_store(w[r] / hnext, prec, n);",
      "V[(size_t)(c + 1) * n + r] = (R)orc_store(w[r], prec, n);", "v_{j+1} not normalised"),
-    ("cycle_impl.inc", "V[r] = (R)orc_store(r0[r] / beta, prec, n);",
-     "V[r] = (R)orc_store(r0[r], prec, n);", "v_1 not normalised"),
+    ("cycle_impl.inc", "V[r] = (R)orc_store(rr[r] / beta, prec, n);",
+     "V[r] = (R)orc_store(rr[r], prec, n);", "v_1 not normalised"),
     ("cycle_impl.inc", "for (int32_t i = 0; i < j; ++i) {\n        const R *v = V + (size_t)i * n;",
      "for (int32_t i = 0; i + 1 < j; ++i) {\n        const R *v = V + (size_t)i * n;",
      "MGS skips the last projection"),
@@ -75,6 +75,15 @@ MUTATIONS = [
      "high part keeps four low-order bits"),
     ("gmres_oracle.c", "(rs->split_bytes ? orc_high_part(vals[k]) : (double)(float)vals[k])",
      "(double)(float)vals[k]", "split storage ignored in the Krylov step"),
+    ("ilu_oracle.c", "lu[p] = lu[p] / pivot; /* l_ik */", "lu[p] = lu[p]; /* l_ik */",
+     "ILU(0) without the division by the pivot"),
+    ("ilu_oracle.c", "lu[q] = lu[q] - lu[p] * lu[kj];", "lu[q] = lu[q] + lu[p] * lu[kj];",
+     "ILU(0) update sign"),
+    ("cycle_impl.inc", "FN(ilu_apply)(n, pm_rowptr, pm_colind, pm, r0, rl);\n        rr = rl;",
+     "rr = r0;", "left preconditioner not applied to the residual"),
+    ("cycle_impl.inc", "for (int32_t p = rowptr[i]; p < rowptr[i + 1] && colind[p] < i; ++p)\n            acc -= lu[p] * out[colind[p]];",
+     "for (int32_t p = rowptr[i]; p < rowptr[i + 1] && colind[p] <= i; ++p)\n            acc -= lu[p] * out[colind[p]];",
+     "forward substitution takes in the diagonal"),
     ("spai_oracle.c", "atr[colind[k]] += vals[k] * r[i];", "atr[i] += vals[k] * r[colind[k]];",
      "A instead of A^T in the preconditioner gradient"),
     ("spai_oracle.c", "d2[o] = z2[o] > 0 ? dgk * params[P_W3 + o] : 0;",
