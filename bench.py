@@ -165,6 +165,8 @@ def make_workload(name):
 # (label, precision, ortho, preconditioner)
 COMPARE = {
     "convdiff3d_160": [("fp64", "fp64", "cgsr", None)],
+    "convdiff3d_96_ilu": [("unpreconditioned", "mixed", "cgsr", "none"),
+                          ("fp64_ilu0", "fp64", "cgsr", "ilu")],
     "convdiff3d_96": [("fp64", "fp64", "cgsr", None)],
     "convdiff2d_64": [("mixed_mgs", "mixed", "mgs", None), ("fp64_grid", "fp64", "mgs", "grid")],
     "powerlaw_2m": [("mixed_fp16", "mixed_fp16", "mgs", None), ("mixed_fp32", "mixed", "mgs", None),
@@ -216,6 +218,8 @@ def bench_ours(args):
     db = torch.tensor(b, device="cuda", dtype=torch.float64)
     dx = torch.zeros(n, device="cuda", dtype=torch.float64)
 
+    ilu_state = {}
+
     def set_pre(kind):
         o = G.gmres_get_opts(solver.h)
         o.path = G.PATH_AUTO
@@ -224,6 +228,13 @@ def bench_ours(args):
         elif kind == "grid":
             o.precond = 0
             o.path = G.PATH_GRID
+        elif kind == "ilu":
+            if not ilu_state:
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                G.gmres_ilu0(solver.h)
+                ilu_state["setup_ms"] = round((time.perf_counter() - t0) * 1e3, 2)
+            o.precond = 2
         else:
             G.gmres_spai_set(solver.h, spai_params if kind == "learned" else jac)
             o.precond = 1
@@ -244,7 +255,7 @@ def bench_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    main_pre = "learned" if learned else None
+    main_pre = {"learned": "learned", "ilu": "ilu"}.get(spec.get("precond"))
     set_pre(main_pre)
     scratch = []
     for _ in range(args.warmup):
@@ -301,6 +312,8 @@ def bench_ours(args):
                               "restarts": got[0]["restarts"],
                               "speedup_of_headline": round(cms / ms_step, 3)}
         set_pre(main_pre)
+        if "setup_ms" in ilu_state:
+            compare["ilu_factor_ms"] = ilu_state["setup_ms"]
 
     def agg(key, cls):
         return sum(i[key][cls] for i in infos)
@@ -338,7 +351,7 @@ def bench_ours(args):
         "config": {
             "workload": args.workload, "description": spec.get("desc"),
             "n": n, "nnz": nnz, "m": m, "ortho": ortho, "precision": prec, "tol": 1e-10,
-            "precond": "learned SpAI" if learned else None,
+            "precond": {"learned": "learned SpAI", "ilu": "ILU(0), left"}.get(spec.get("precond")),
             "rhs": "b = A 1 + N(0, sigma^2), sigma = 1e-3, x0 = 0", "seed": SEED,
             "l2": "inputs larger than L2" if nnz * 12 > 129e6
                   else "inputs L2-resident (no flush; small-system workload)",
@@ -510,12 +523,15 @@ def oracle_sample(A, b, spec, ks=(2, 8, 16)):
     ts = []
     # a preconditioned workload costs one more SpMV per step: time the oracle
     # with an M on A's pattern computed by the oracle itself (Jacobi values)
-    M = None
-    if spec.get("precond"):
+    M = ilu = None
+    if spec.get("precond") == "ilu":
+        ilu = O.ilu0(A)  # the oracle's own factors (their time is not counted)
+    elif spec.get("precond"):
         M = (A[0], A[1], O.spai_values(A, O.spai_jacobi_params()))
     for k in ks:
         t0 = time.perf_counter()
-        O.arnoldi_cycle(A, b, m, ortho=ortho, prec=prec, kmax=k, export_basis=False, M=M)
+        O.arnoldi_cycle(A, b, m, ortho=ortho, prec=prec, kmax=k, export_basis=False, M=M,
+                        ilu=ilu)
         ts.append(time.perf_counter() - t0)
     M = np.array([[1.0, k, k * (k + 1) / 2.0] for k in ks])
     c, a, bco = np.linalg.lstsq(M, np.array(ts), rcond=None)[0]

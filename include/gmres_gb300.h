@@ -113,7 +113,8 @@ typedef struct gmres_opts {
     int32_t spin_limit;   /* iterations a device-side wait may spin before it
                              gives up with GMRES_ERR_TIMEOUT; 0 = default       */
     int32_t precond;      /* 0: none; 1: the learned right preconditioner set
-                             by gmres_spai_set                                  */
+                             by gmres_spai_set; 2: ILU(0) on the left as in
+                             Alg. 1 (factors made by gmres_ilu0)               */
     int32_t fallback;     /* 1: on stagnation of the preconditioned solve,
                              continue unpreconditioned (default 1)              */
     int32_t spmv_lanes;   /* lanes per CSR row in SpMV (1..32, power of two);
@@ -133,7 +134,9 @@ typedef struct gmres_opts {
                              or 8 (a cluster with distributed-shared-memory
                              reductions); 0 = automatic (8 for binary64 from
                              2048 rows, else 1)                                 */
-    int32_t reserved[1];
+    int32_t ilu_binary32; /* 1: with precond 2 in GMRES_FP64, use the ILU(0)
+                             factors stored in binary32 (the paper's FP32-ILU
+                             variant, Sec. 4.2); the binary32 cycle always does */
     double stall_factor;  /* third restart strategy (Sec. 3; Sec. 4.1 uses 1.001):
                              end the cycle once |s_{j+1}| improved by less than
                              this factor over the last stall_window inner
@@ -379,6 +382,29 @@ gmres_status gmres_memory_bytes(gmres_t h, int32_t m, gmres_precision prec, int6
                                 int64_t *workspace_bytes);
 
 /* Static text for a status code. */
+/* ILU(0) of the handle's A, the paper's preconditioner (Sec. 4): L (unit
+ * lower) and U on A's sparsity pattern, factored on the GPU one level of the
+ * row-dependency graph per launch (the levels come from a host analysis of
+ * the pattern), kept in binary64 and binary32.  Select it with opts.precond
+ * = 2: every solve then applies M^-1 = (L U)^-1 on the left (Alg. 1:
+ * r = M^-1 z, w = M^-1 A v_j; the convergence test stays on ||b - A x||), on
+ * the grid path, with sync-free triangular solves (ready flags, bounded
+ * waits).  gmres_set_values drops the factors.  Errors: GMRES_ERR_ARG (rows
+ * not sorted, a missing diagonal entry, split storage), GMRES_ERR_BREAKDOWN
+ * (a zero or non-finite pivot), GMRES_ERR_OOM, GMRES_ERR_CUDA. */
+gmres_status gmres_ilu0(gmres_t h);
+
+/* Copy the binary64 ILU(0) factors to the host array lu (nnz entries, on
+ * A's pattern: L's strictly lower entries, U's upper entries with the
+ * diagonal).  GMRES_ERR_ARG before gmres_ilu0. */
+gmres_status gmres_ilu_factors(gmres_t h, double *lu);
+
+/* out = (L U)^-1 z with the factors of gmres_ilu0: z, out device vectors of
+ * n binary64 (GMRES_FP64) or binary32 (otherwise) values, binary64 or
+ * binary32 factors to match.  GMRES_ERR_ARG before gmres_ilu0;
+ * GMRES_ERR_TIMEOUT if a bounded wait ran out. */
+gmres_status gmres_ilu_apply(gmres_t h, const void *z, void *out, gmres_precision prec);
+
 /* ||S_k|| of the loss-of-orthogonality test after each inner iteration of
  * the last restart cycle the handle ran (gmres_solve or gmres_arnoldi), for
  * k = 2 .. j+1 basis vectors: out[c] belongs to inner iteration c+1; entries

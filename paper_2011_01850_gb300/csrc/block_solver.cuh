@@ -56,12 +56,21 @@ __device__ __forceinline__ void team_sum(T (&v)[K], T *red, T *slots, T *bc, int
             mine[k] = v[k];
     }
     Team<CS>::sync();
-    if (threadIdx.x < K) {
+    if (threadIdx.x < 32) {
+        // lane r reads rank r's partials (all ranks at once), then an xor
+        // butterfly over the CS lanes: every block forms the same sums
         cg::cluster_group cl = cg::this_cluster();
-        T a = 0;
-        for (int r = 0; r < CS; ++r)
-            a += cl.map_shared_rank(mine, r)[threadIdx.x];
-        bc[threadIdx.x] = a;
+        const int lane = threadIdx.x;
+        const T *src = cl.map_shared_rank(mine, lane < CS ? lane : 0);
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            T a = lane < CS ? src[k] : T(0);
+#pragma unroll
+            for (int off = CS / 2; off > 0; off >>= 1)
+                a += __shfl_xor_sync(0xffffffffu, a, off);
+            if (lane == 0)
+                bc[k] = a;
+        }
     }
     __syncthreads();
 #pragma unroll

@@ -26,6 +26,7 @@
 #include "grid_kernels.cuh"
 #include "orth_monitor.cuh"
 #include "team_launch.hpp"
+#include "ilu.hpp"
 #include "handle.hpp"
 #include "host_util.hpp"
 
@@ -60,6 +61,10 @@ template <class T>
 struct SmallPtrs {
     T *H, *Hb, *s, *cs, *sn, *y, *h1, *h2;
 };
+
+// The learned right preconditioner / the ILU(0) left preconditioner is on.
+inline bool spai_on(const gmres_handle *h) { return h->has_precond && h->opts.precond == 1; }
+inline bool ilu_on(const gmres_handle *h) { return h->ilu_ok && h->opts.precond == 2; }
 
 inline const unsigned *split_hi(gmres_handle *h) { return h->vals64.as<unsigned>(); }
 inline const unsigned *split_lo(gmres_handle *h) { return h->vals64.as<unsigned>() + h->nnz; }
@@ -107,6 +112,10 @@ gmres_status ensure_workspace(gmres_handle *h, int m, gmres_precision prec) {
     CK(h->small.ensure((size_t)(2 * (MMAX + 1) * MMAX + 6 * (MMAX + 2)) * 8));
     CK(h->part.ensure((size_t)std::max(h->grid, h->nsm * h->rows_blocks_per_sm) * PSTRIDE * 8));
     CK(h->part64.ensure((size_t)h->grid * 4 * 8));
+    if (ilu_on(h))
+        CK(h->t2.ensure(ldv * 8));
+    if (ilu_on(h))
+        CK(h->t2.ensure(ldv * 8));
     if (h->mon.bytes < MON_DOUBLES * sizeof(double)) {
         CK(h->mon.ensure(MON_DOUBLES * sizeof(double)));
         CK(cudaMemsetAsync(h->mon.p, 0, h->mon.bytes, h->stream));
@@ -170,7 +179,8 @@ GridCtx<T, VT> make_ctx(gmres_handle *h, int m) {
         c.a_lim = h->vals32.as<float>();
         c.aform = 1;
     }
-    if (h->has_precond && h->opts.precond) {
+    c.left = ilu_on(h) ? 1 : 0;
+    if (spai_on(h)) {
         c.prowptr = c.rowptr;
         c.pcolind = c.colind;
         c.pvals = std::is_same<T, double>::value ? reinterpret_cast<const T *>(h->pvals64.p)
@@ -316,6 +326,35 @@ bool mgs_persist_ok(gmres_handle *h) {
     return ok;
 }
 
+// out = (L U)^-1 z with the ILU(0) factors in the precision the solve uses:
+// binary64 factors for binary64 work, binary32 factors for the binary32
+// cycle, for limited mixed and on request (opts.ilu_binary32).
+template <class T, class VT>
+cudaError_t apply_ilu(gmres_handle *h, const T *z, T *tmp, T *out) {
+    int *err = &h->ctl.as<Ctl>()->timeout;
+    if constexpr (std::is_same<T, double>::value) {
+        if (!h->limited && !h->opts.ilu_binary32)
+            return ilu_apply<double, double>(h, h->ilu64.as<double>(), z, tmp, out, err);
+        return ilu_apply<double, float>(h, h->ilu32.as<float>(), z, tmp, out, err);
+    } else {
+        return ilu_apply<float, float>(h, h->ilu32.as<float>(), z, tmp, out, err);
+    }
+}
+
+// Cycle start with the left preconditioner: r <- M^-1 r, beta = ||r||.
+template <class T, class VT>
+gmres_status left_start(gmres_handle *h, GridCtx<T, VT> &c, Acct &acct) {
+    if (!c.left)
+        return GMRES_OK;
+    cudaEvent_t e = h->timer.begin();
+    CK((apply_ilu<T, VT>(h, c.r, c.t, c.r)));
+    k_pnorm<T, VT><<<h->grid, kThreads, 0, h->stream>>>(c);
+    CKL();
+    h->timer.end(GMRES_K_PRECOND, e);
+    acct.launches[GMRES_K_PRECOND] += 3;
+    return GMRES_OK;
+}
+
 // The three register-streaming CGSR passes (and the two column reductions)
 // for an inner step with ncols basis vectors, then v_{j+1}.
 template <class T, class VT, bool SPLIT>
@@ -373,7 +412,18 @@ gmres_status enqueue_step_core(gmres_handle *h, GridCtx<T, VT> &c, int col, gmre
     const int L = lanes_for<T, VT>(h);
     const VT *vj = c.V + (size_t)col * c.ldv;
     cudaEvent_t e = h->timer.begin();
-    if (c.pvals) {
+    if (c.left) {
+        // t = A v_j, w = M^-1 t (left preconditioning, Alg. 1)
+        CK((launch_spmv_step<T, VT, VT>(h, c, vj, c.t, L)));
+        h->timer.end(GMRES_K_SPMV, e);
+        acct.launches[GMRES_K_SPMV]++;
+        e = h->timer.begin();
+        CK((apply_ilu<T, VT>(h, c.t, h->t2.as<T>(), c.w)));
+        h->timer.end(GMRES_K_PRECOND, e);
+        acct.launches[GMRES_K_PRECOND] += 2;
+        e = h->timer.begin();
+        acct.launches[GMRES_K_SPMV]--;  // counted once below
+    } else if (c.pvals) {
         // t = M v_j, w = A t (right preconditioning)
         GridCtx<T, VT> cp = c;
         cp.rowptr = c.prowptr;
@@ -517,12 +567,19 @@ void account_cycle(gmres_handle *h, int j, gmres_ortho ortho, Acct &acct) {
     // matrix value bytes the Krylov step reads
     const double sA = h->split ? ((sizeof(T) == 8 && !h->limited) ? 8.0 : 4.0)
                                : (h->limited ? 4.0 : sT);
-    const bool pre = h->has_precond && h->opts.precond;
+    const bool pre = spai_on(h);
+    const bool ilu = ilu_on(h);
+    // ILU(0) factor bytes one triangular solve pair reads (values, indices,
+    // row pointers, diagonal positions) plus its vectors and ready flags
+    const double sL = (sizeof(T) == 8 && !h->limited && !h->opts.ilu_binary32) ? 8.0 : 4.0;
+    const double ilu_bytes = nnz * (sL + 4) + 2.0 * (n + 1) * 4 + n * 4 + 4.0 * n * sT + 8.0 * n;
     for (int it = 0; it < j; ++it) {
         const double c = it + 1;
         acct.bytes[GMRES_K_SPMV] += nnz * (sA + 4) + (n + 1) * 4 + n * (pre ? sT : sV) + n * sT;
         if (pre)
             acct.bytes[GMRES_K_PRECOND] += nnz * (sA + 4) + (n + 1) * 4 + n * sV + n * sT;
+        if (ilu)
+            acct.bytes[GMRES_K_PRECOND] += ilu_bytes;
         if (ortho == GMRES_ORTHO_CGSR)
             acct.bytes[GMRES_K_ORTHO] += 3 * c * n * sV + 5 * n * sT;
         else
@@ -584,6 +641,9 @@ gmres_status solve_grid(gmres_handle *h, const double *b, double *x, int m, doub
     CK(launch_residual(h, c, b, x, nullptr, 1));
     h->timer.end(GMRES_K_RESIDUAL, e);
     account_residual<T, VT>(h, acct);
+    st = left_start<T, VT>(h, c, acct);
+    if (st != GMRES_OK)
+        return st;
     st = read_ctl(h);
     if (st != GMRES_OK)
         return st;
@@ -655,6 +715,9 @@ gmres_status solve_grid(gmres_handle *h, const double *b, double *x, int m, doub
         CK(launch_residual(h, c, b, x, nullptr, 1));
         h->timer.end(GMRES_K_RESIDUAL, e);
         account_residual<T, VT>(h, acct);
+        st = left_start<T, VT>(h, c, acct);
+        if (st != GMRES_OK)
+            return st;
         st = read_ctl(h);
         if (st != GMRES_OK)
             return st;
@@ -806,9 +869,10 @@ gmres_status solve_dispatch_path(gmres_handle *h, const double *b, double *x, in
                                  gmres_ortho ortho, gmres_precision prec, int maxiter,
                                  gmres_info *info) {
     int path = h->opts.path;
-    const bool grid_only = h->opts.orth_norm != GMRES_ORTH_OFF || h->limited || h->split;
+    const bool grid_only =
+        h->opts.orth_norm != GMRES_ORTH_OFF || h->limited || h->split || ilu_on(h);
     if (path == GMRES_PATH_AUTO)
-        path = (h->n <= 16384 && !(h->has_precond && h->opts.precond) && !grid_only)
+        path = (h->n <= 16384 && !spai_on(h) && !grid_only)
                    ? GMRES_PATH_BLOCK
                    : GMRES_PATH_GRID;
     if (path == GMRES_PATH_BLOCK && grid_only)
@@ -832,7 +896,8 @@ gmres_status validate_opts(const gmres_opts *o) {
         o->stall_window < 0 || o->stall_window > MMAX || o->orth_norm < GMRES_ORTH_OFF ||
         o->orth_norm > GMRES_ORTH_FROBENIUS || o->orth_iters < 0 ||
         (o->orth_norm != GMRES_ORTH_OFF && !(o->orth_threshold > 0)) ||
-        o->repeat_first < -1 || o->repeat_first > 1 || o->precond < 0 || o->precond > 1)
+        o->repeat_first < -1 || o->repeat_first > 1 || o->precond < 0 || o->precond > 2 ||
+        o->ilu_binary32 < 0 || o->ilu_binary32 > 1)
         return GMRES_ERR_ARG;
     return GMRES_OK;
 }
@@ -1022,7 +1087,8 @@ void gmres_destroy(gmres_t h) {
                       &h->part, &h->part64, &h->ctl, &h->bsys, &h->bres, &h->pvals64,
                       &h->pvals32, &h->spai_feat, &h->spai_rowv, &h->tvals32, &h->spai_params,
                       &h->spai_m, &h->spai_gm, &h->spai_H, &h->spai_vec, &h->spai_part,
-                      &h->spai_Z, &h->spai_grad, &h->mgs_seq, &h->mon})
+                      &h->spai_Z, &h->spai_grad, &h->mgs_seq, &h->mon, &h->ilu64, &h->ilu32,
+                      &h->ilu_dpos, &h->ilu_flags, &h->t2, &h->ilu_order})
         b->release();
     if (h->hctl)
         cudaFreeHost(h->hctl);
@@ -1065,6 +1131,7 @@ gmres_status gmres_set_values(gmres_t h, const double *vals) {
     h->tvals64.release();
     h->spai_feat_ok = 0;
     h->has_precond = 0;
+    h->ilu_ok = 0;
     return GMRES_OK;
 }
 
@@ -1105,6 +1172,8 @@ gmres_status gmres_solve(gmres_t h, const double *b, double *x, int32_t m, doubl
         (ortho != GMRES_ORTHO_MGS && ortho != GMRES_ORTHO_CGSR) || prec < GMRES_FP64 ||
         prec > GMRES_MIXED_LIMITED)
         return GMRES_ERR_ARG;
+    if (h->opts.precond == 2 && !h->ilu_ok)
+        return GMRES_ERR_ARG;  // ILU(0) selected but not factored (gmres_ilu0)
     h->timer.on = h->opts.profile != 0;
     // Host buffers go through library-owned device copies.
     const bool bdev = is_device_ptr(b), xdev = is_device_ptr(x);
@@ -1218,6 +1287,9 @@ gmres_status arnoldi_impl(gmres_handle *h, const double *r0, int m, int kmax, gm
     // r = fl(r0): the residual kernel with x = 0 gives z = r0 exactly
     CK(cudaMemsetAsync(h->xb.p, 0, sizeof(double) * h->ldv, h->stream));
     CK(launch_residual(h, c, r0, h->xb.as<double>(), nullptr, 1));
+    st = left_start<T, VT>(h, c, acct);
+    if (st != GMRES_OK)
+        return st;
     CK(cudaMemsetAsync(mon_hist(h), 0, (MMAX + 2) * sizeof(double), h->stream));
     k_init<T, VT><<<h->grid, kThreads, 0, h->stream>>>(c);
     CKL();
@@ -1406,6 +1478,43 @@ gmres_status gmres_memory_bytes(gmres_t h, int32_t m, gmres_precision prec, int6
                            + 6 * (int64_t)(m + 2) * sT;         // s, cs, sn, y, h1, h2
     }
     return GMRES_OK;
+}
+
+gmres_status gmres_ilu0(gmres_t h) {
+    if (!h || h->split)
+        return GMRES_ERR_ARG;
+    if (h->nnz == 0)
+        return GMRES_ERR_ARG;
+    return ilu_factor(h);
+}
+
+gmres_status gmres_ilu_factors(gmres_t h, double *lu) {
+    if (!h || !lu || !h->ilu_ok)
+        return GMRES_ERR_ARG;
+    CK(cudaMemcpyAsync(lu, h->ilu64.p, sizeof(double) * h->nnz, cudaMemcpyDeviceToHost,
+                       h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return GMRES_OK;
+}
+
+gmres_status gmres_ilu_apply(gmres_t h, const void *z, void *out, gmres_precision prec) {
+    if (!h || !z || !out || !h->ilu_ok || prec < GMRES_FP64 || prec > GMRES_MIXED_LIMITED)
+        return GMRES_ERR_ARG;
+    CK(h->ctl.ensure(sizeof(Ctl)));
+    CK(cudaMemsetAsync(h->ctl.p, 0, sizeof(Ctl), h->stream));
+    ScopedBuf tmp;
+    CK(tmp.ensure(sizeof(double) * h->n));
+    int *err = &h->ctl.as<Ctl>()->timeout;
+    if (prec == GMRES_FP64)
+        CK((ilu_apply<double, double>(h, h->ilu64.as<double>(), (const double *)z,
+                                      tmp.as<double>(), (double *)out, err)));
+    else
+        CK((ilu_apply<float, float>(h, h->ilu32.as<float>(), (const float *)z, tmp.as<float>(),
+                                    (float *)out, err)));
+    int bad = 0;
+    CK(cudaMemcpyAsync(&bad, err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return bad ? GMRES_ERR_TIMEOUT : GMRES_OK;
 }
 
 gmres_status gmres_orth_norms(gmres_t h, double *out, int32_t count) {

@@ -56,6 +56,8 @@ struct GridCtx {
     // how the Krylov step reads A: 0 the working-precision copy a, 1 the
     // binary32 copy a_lim, 2 the high part of split storage, 3 both parts
     int aform;
+    // ILU(0) left preconditioning (Alg. 1: r = M^-1 z, w = M^-1 A v_j)
+    int left;
     // third restart strategy (Sec. 3): |s_{j+1}| of the cycle (entry 0 =
     // beta) and the stall test's factor (0 = off) and window
     double *ahist;
@@ -384,6 +386,49 @@ __global__ void __launch_bounds__(256) k_init(GridCtx<T, VT> c) {
         for (int k = 0; k < 4; ++k)
             v[k] = v[k] / beta;
         stb4<T, VT>(c.V + r, v, c.vscale);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Left preconditioning, cycle start: r holds M^-1 fl(z); beta = ||r|| in the
+// working precision replaces the residual kernel's set-up (Alg. 1: beta is
+// the norm of the preconditioned residual; the binary64 convergence test on
+// ||z|| has already been made).
+// ---------------------------------------------------------------------------
+template <class T, class VT>
+__global__ void __launch_bounds__(256) k_pnorm(GridCtx<T, VT> c) {
+    if (!c.ctl->active)
+        return;
+    __shared__ T st[32];
+    int64_t rb, re;
+    block_rows(c, rb, re);
+    T ss = 0;
+    for (int64_t r = rb + 4 * threadIdx.x; r < re; r += 4 * blockDim.x) {
+        T v[4];
+        ldv4(c.r + r, v);
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            ss += v[k] * v[k];
+    }
+    ss = block_sum1(ss, st);
+    if (threadIdx.x == 0)
+        c.part[(size_t)blockIdx.x * PSTRIDE] = ss;
+    if (!arrive_last(&c.ctl->counter[6]))
+        return;
+    T a = 0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+        a += ldcg(c.part + (size_t)b * PSTRIDE);
+    a = block_sum1(a, st);
+    if (threadIdx.x == 0) {
+        Ctl *k = c.ctl;
+        const T beta = wsqrt(a);
+        const bool fin = isfinite((double)beta);
+        if (!fin)
+            k->nonfinite = 1;
+        k->beta = (double)beta;
+        k->arn = (double)beta;
+        k->active = fin && beta > T(0);
+        c.s[0] = beta;
     }
 }
 

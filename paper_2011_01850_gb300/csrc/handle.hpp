@@ -88,6 +88,13 @@ struct gmres_handle {
     DevBuf mon;                  // restart-test histories and the U, S matrices
     bool limited = false;        // the running solve is GMRES_MIXED_LIMITED
     bool split = false;          // A stored split: vals64 holds hi[nnz] then lo[nnz]
+    // ILU(0) left preconditioner: factors (binary64 and binary32 copies),
+    // diagonal positions, ready flags of the two triangles + claim counters
+    DevBuf ilu64, ilu32, ilu_dpos, ilu_flags, t2;
+    DevBuf ilu_order;            // rows in level order: L's n entries, then U's
+    int ilu_ok = 0;
+    int ilu_levels = 0;
+    unsigned ilu_epoch = 1;
     unsigned mgs_round = 0;      // next exchange round number (0: flags not set up)
     int64_t chunk = 0;     // rows per block
     // matrix

@@ -1,0 +1,326 @@
+// ilu.cu -- ILU(0) left preconditioning, the preconditioner of the paper's
+// experiments (arXiv 2011.01850, Sec. 4; Alg. 1 applies M^-1 on the left:
+// r = M^-1 z at every restart and w = M^-1 A v_j in every inner step).
+//
+// Factorization.  ILU(0) keeps A's sparsity pattern; row i of the IKJ form
+// eliminates with every earlier row k of its pattern in ascending order
+// (l_ik = a_ik / u_kk, then a_ij -= l_ik u_kj for the j > k present in both
+// rows).  Row i depends on the rows k < i of its pattern, so the rows are
+// grouped into levels (host analysis of the pattern) and one launch per
+// level factors every row of the level, one thread per row.  The products
+// and differences are rounded separately (no fused multiply-add), as in a
+// plain restatement of the elimination, so the factors are reproducible bit
+// for bit.  A binary32 copy serves the binary32 restart cycle.
+//
+// Triangular solves.  L y = z (unit lower) and U x = y run as one persistent
+// launch each, without level barriers: each warp claims the next row of the
+// triangle's level schedule from a counter (every row a claimed row depends
+// on sits in an earlier level, so a running warp claimed it earlier, and a
+// whole level is in flight at once); its lanes wait on the dependencies'
+// ready flags in parallel, lane 0 subtracts the terms in column order,
+// stores the value and publishes its flag with a release store.
+// Flags hold an epoch that changes every call (the host clears them before
+// the 32-bit epoch wraps).  Every wait is bounded: after `spin` polls the
+// warp reports a timeout in the control block and returns, and the other
+// warps see the report and return too.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "../../include/gmres_gb300.h"
+#include "common.cuh"
+#include "handle.hpp"
+#include "host_util.hpp"
+#include "ilu.hpp"
+
+using namespace gmres;
+using namespace gmres_host;
+
+namespace {
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_u32(unsigned *p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Factor the rows rows[0..count) (one level) in place; err[0] = 1 on a zero
+// or non-finite pivot.
+__global__ void __launch_bounds__(256) k_ilu0_level(const int *rowptr, const int *colind,
+                                                    const int *dpos, double *lu, const int *rows,
+                                                    int count, int *err) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= count)
+        return;
+    const int i = rows[t];
+    const int end = rowptr[i + 1];
+    for (int p = rowptr[i]; p < dpos[i]; ++p) {
+        const int k = colind[p];
+        const double piv = lu[dpos[k]];
+        if (piv == 0.0 || !isfinite(piv)) {
+            atomicExch(err, 1);
+            return;
+        }
+        const double lik = __ddiv_rn(lu[p], piv);
+        lu[p] = lik;
+        // merge row i's entries after p with row k's entries after its diagonal
+        int kp = dpos[k] + 1;
+        const int kend = rowptr[k + 1];
+        for (int q = p + 1; q < end; ++q) {
+            const int j = colind[q];
+            while (kp < kend && colind[kp] < j)
+                ++kp;
+            if (kp < kend && colind[kp] == j)
+                lu[q] = __dsub_rn(lu[q], __dmul_rn(lik, lu[kp]));
+        }
+    }
+    const double d = lu[dpos[i]];
+    if (d == 0.0 || !isfinite(d))
+        atomicExch(err, 1);
+}
+
+__global__ void k_ilu_cast(int64_t nnz, const double *a, float *b) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nnz;
+         k += (int64_t)gridDim.x * blockDim.x)
+        b[k] = (float)a[k];
+}
+
+// One triangle of (L U) x = z.  LOWER: y_i = z_i - sum_{k<i} l_ik y_k (unit
+// diagonal), rows claimed in increasing order; upper: x_i = (y_i -
+// sum_{j>i} u_ij x_j) / u_ii, rows claimed in decreasing order.  T is the
+// arithmetic type, AT the stored factor type.
+// Separately rounded multiply and subtract (no fused multiply-add), so the
+// solves repeat the oracle's sums exactly.
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
+
+// One triangle of (L U) x = z.  LOWER: y_i = z_i - sum_{k<i} l_ik y_k (unit
+// diagonal); upper: x_i = (y_i - sum_{j>i} u_ij x_j) / u_ii.  A warp claims
+// the next row of the schedule; its lanes wait on the ready flags of the
+// row's dependencies (one dependency per lane, all at once) and form the
+// products, and lane 0 subtracts them one by one in column order, as the
+// oracle does.  T is the arithmetic type, AT the stored factor type.
+template <class T, class AT, bool LOWER>
+__global__ void __launch_bounds__(256) k_trsv(int n, const int *rowptr, const int *colind,
+                                              const int *dpos, const int *order, const AT *lu,
+                                              const T *in, T *out, unsigned *flags,
+                                              unsigned epoch, unsigned *counter, long long spin,
+                                              int *err) {
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        int claim = 0;
+        if (lane == 0)
+            claim = (int)atomicAdd(counter, 1u);
+        claim = __shfl_sync(0xffffffffu, claim, 0);
+        if (claim >= n)
+            return;
+        const int i = order[claim];
+        const int b = LOWER ? rowptr[i] : dpos[i] + 1;
+        const int e = LOWER ? dpos[i] : rowptr[i + 1];
+        T acc = lane == 0 ? in[i] : T(0);
+        bool ok = true;
+        for (int p0 = b; p0 < e; p0 += 32) {
+            const int p = p0 + lane;
+            T prod = 0;
+            if (p < e) {
+                const int j = colind[p];
+                long long it = 0;
+                while (ld_acquire_u32(flags + j) != epoch) {
+                    if (*(volatile int *)err != 0 || ++it > spin) {
+                        ok = false;
+                        break;
+                    }
+                }
+                if (ok)
+                    prod = mul_rn((T)lu[p], __ldcg(out + j));
+            }
+            if (!__all_sync(0xffffffffu, ok))
+                break;
+            const int cnt = e - p0 < 32 ? e - p0 : 32;
+            for (int q = 0; q < cnt; ++q) {
+                const T v = __shfl_sync(0xffffffffu, prod, q);
+                if (lane == 0)
+                    acc = sub_rn(acc, v);
+            }
+        }
+        if (!__all_sync(0xffffffffu, ok)) {
+            if (lane == 0)
+                atomicExch(err, 1);
+            return;
+        }
+        if (lane == 0) {
+            if (!LOWER)
+                acc = acc / (T)lu[dpos[i]];
+            out[i] = acc;
+            st_release_u32(flags + i, epoch);
+        }
+    }
+}
+
+template <class T, class AT, bool LOWER>
+cudaError_t launch_trsv(gmres_handle *h, const AT *lu, const T *in, T *out, unsigned *flags,
+                        unsigned epoch, unsigned *counter, long long spin, int *err) {
+    static int grid = 0;
+    if (grid == 0) {
+        int per_sm = 0;
+        cudaError_t e =
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trsv<T, AT, LOWER>, 256, 0);
+        if (e != cudaSuccess)
+            return e;
+        grid = std::max(1, per_sm) * h->nsm;
+    }
+    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned), h->stream);
+    if (e != cudaSuccess)
+        return e;
+    const int *order = h->ilu_order.as<int>() + (LOWER ? 0 : h->n);
+    k_trsv<T, AT, LOWER><<<grid, 256, 0, h->stream>>>(h->n, h->rowptr.as<int>(),
+                                                       h->colind.as<int>(), h->ilu_dpos.as<int>(),
+                                                       order, lu, in, out, flags, epoch, counter,
+                                                       spin, err);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+namespace gmres {
+
+gmres_status ilu_factor(gmres_handle *h) {
+    const int n = h->n;
+    const int64_t nnz = h->nnz;
+    std::vector<int32_t> rp(n + 1), ci(std::max<int64_t>(nnz, 1));
+    CK(cudaMemcpyAsync(rp.data(), h->rowptr.p, sizeof(int32_t) * (n + 1), cudaMemcpyDeviceToHost,
+                       h->stream));
+    if (nnz > 0)
+        CK(cudaMemcpyAsync(ci.data(), h->colind.p, sizeof(int32_t) * nnz, cudaMemcpyDeviceToHost,
+                           h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    // diagonal positions (rows sorted, diagonal present) and the levels of
+    // the lower-triangular dependency graph
+    std::vector<int32_t> dpos(n), level(n, 0);
+    int nlev = 0;
+    for (int i = 0; i < n; ++i) {
+        int d = -1, lv = 0;
+        for (int32_t p = rp[i]; p < rp[i + 1]; ++p) {
+            if (p > rp[i] && ci[p] <= ci[p - 1])
+                return GMRES_ERR_ARG;  // ILU(0) needs sorted rows
+            if (ci[p] == i)
+                d = p;
+            else if (ci[p] < i)
+                lv = std::max(lv, level[ci[p]] + 1);
+        }
+        if (d < 0)
+            return GMRES_ERR_ARG;  // and a diagonal entry in every row
+        dpos[i] = d;
+        level[i] = lv;
+        nlev = std::max(nlev, lv + 1);
+    }
+    std::vector<int32_t> lptr(nlev + 1, 0), order(n);
+    for (int i = 0; i < n; ++i)
+        lptr[level[i] + 1]++;
+    for (int l = 0; l < nlev; ++l)
+        lptr[l + 1] += lptr[l];
+    {
+        std::vector<int32_t> pos(lptr.begin(), lptr.end() - 1);
+        for (int i = 0; i < n; ++i)
+            order[pos[level[i]]++] = i;
+    }
+    // levels of the upper-triangular graph (row i waits for the j > i of its
+    // pattern), counted from the last row
+    std::vector<int32_t> ulevel(n, 0), uorder(n);
+    int nulev = 0;
+    for (int i = n - 1; i >= 0; --i) {
+        int lv = 0;
+        for (int32_t p = dpos[i] + 1; p < rp[i + 1]; ++p)
+            lv = std::max(lv, ulevel[ci[p]] + 1);
+        ulevel[i] = lv;
+        nulev = std::max(nulev, lv + 1);
+    }
+    {
+        std::vector<int32_t> uptr(nulev + 1, 0);
+        for (int i = 0; i < n; ++i)
+            uptr[ulevel[i] + 1]++;
+        for (int l = 0; l < nulev; ++l)
+            uptr[l + 1] += uptr[l];
+        for (int i = 0; i < n; ++i)
+            uorder[uptr[ulevel[i]]++] = i;
+    }
+    CK(h->ilu_order.ensure(sizeof(int32_t) * 2 * (size_t)n));
+    CK(cudaMemcpyAsync(h->ilu_order.p, order.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice,
+                       h->stream));
+    CK(cudaMemcpyAsync(h->ilu_order.as<int32_t>() + n, uorder.data(), sizeof(int32_t) * n,
+                       cudaMemcpyHostToDevice, h->stream));
+    CK(h->ilu64.ensure(sizeof(double) * std::max<int64_t>(nnz, 1)));
+    CK(h->ilu32.ensure(sizeof(float) * std::max<int64_t>(nnz, 1)));
+    CK(h->ilu_dpos.ensure(sizeof(int32_t) * n));
+    CK(h->ilu_flags.ensure(sizeof(unsigned) * 2 * (size_t)n + 64));
+    ScopedBuf dorder, derr;
+    CK(dorder.ensure(sizeof(int32_t) * n));
+    CK(derr.ensure(sizeof(int)));
+    CK(cudaMemcpyAsync(h->ilu_dpos.p, dpos.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice,
+                       h->stream));
+    CK(cudaMemcpyAsync(dorder.p, order.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice,
+                       h->stream));
+    CK(cudaMemsetAsync(derr.p, 0, sizeof(int), h->stream));
+    CK(cudaMemcpyAsync(h->ilu64.p, h->vals64.p, sizeof(double) * nnz, cudaMemcpyDeviceToDevice,
+                       h->stream));
+    for (int l = 0; l < nlev; ++l) {
+        const int cnt = lptr[l + 1] - lptr[l];
+        k_ilu0_level<<<(cnt + 255) / 256, 256, 0, h->stream>>>(
+            h->rowptr.as<int>(), h->colind.as<int>(), h->ilu_dpos.as<int>(), h->ilu64.as<double>(),
+            dorder.as<int>() + lptr[l], cnt, derr.as<int>());
+    }
+    CKL();
+    if (nnz > 0)
+        k_ilu_cast<<<h->nsm * 4, 256, 0, h->stream>>>(nnz, h->ilu64.as<double>(),
+                                                       h->ilu32.as<float>());
+    CKL();
+    CK(cudaMemsetAsync(h->ilu_flags.p, 0, h->ilu_flags.bytes, h->stream));
+    int bad = 0;
+    CK(cudaMemcpyAsync(&bad, derr.p, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    h->ilu_epoch = 1;
+    h->ilu_levels = nlev;
+    h->ilu_ok = bad ? 0 : 1;
+    return bad ? GMRES_ERR_BREAKDOWN : GMRES_OK;
+}
+
+template <class T, class AT>
+cudaError_t ilu_apply(gmres_handle *h, const AT *lu, const T *z, T *tmp, T *out, int *err) {
+    // one epoch per call (each triangle has its own flags); clear the flags
+    // before the epoch wraps
+    if (h->ilu_epoch > 0x7ffffff0u) {
+        cudaError_t e = cudaMemsetAsync(h->ilu_flags.p, 0, h->ilu_flags.bytes, h->stream);
+        if (e != cudaSuccess)
+            return e;
+        h->ilu_epoch = 1;
+    }
+    const unsigned e0 = h->ilu_epoch;
+    h->ilu_epoch += 1;
+    unsigned *lflags = h->ilu_flags.as<unsigned>();
+    unsigned *uflags = lflags + h->n;
+    unsigned *ctr = uflags + h->n;  // two counters after the flags
+    // a legitimate wait lasts at most the dependency chain (a few hundred
+    // rows of latency); 2^22 polls is seconds, far beyond it
+    const long long spin = h->opts.spin_limit > 0 ? h->opts.spin_limit : (1LL << 22);
+    cudaError_t e = launch_trsv<T, AT, true>(h, lu, z, tmp, lflags, e0, ctr, spin, err);
+    if (e != cudaSuccess)
+        return e;
+    return launch_trsv<T, AT, false>(h, lu, tmp, out, uflags, e0, ctr + 1, spin, err);
+}
+
+template cudaError_t ilu_apply<double, double>(gmres_handle *, const double *, const double *,
+                                               double *, double *, int *);
+template cudaError_t ilu_apply<float, float>(gmres_handle *, const float *, const float *,
+                                             float *, float *, int *);
+template cudaError_t ilu_apply<double, float>(gmres_handle *, const float *, const double *,
+                                              double *, double *, int *);
+
+}  // namespace gmres

@@ -24,6 +24,7 @@ OK, MAXITER, ERR_ARG, ERR_CUDA, ERR_NONFINITE, ERR_BREAKDOWN, ERR_TIMEOUT, ERR_O
     0, 1, -1, -2, -3, -4, -5, -6)
 CREATE_DEVICE_PTRS, CREATE_TRANSPOSE, CREATE_SPLIT = 1, 2, 4
 PATH_AUTO, PATH_GRID, PATH_BLOCK = 0, 1, 2
+PRECOND_NONE, PRECOND_SPAI, PRECOND_ILU0 = 0, 1, 2
 ORTH_OFF, ORTH_SPECTRAL, ORTH_FROBENIUS = 0, 1, 2
 K_RESIDUAL, K_SPMV, K_ORTHO, K_NORMALIZE, K_UPDATE, K_PRECOND, K_BLOCK = range(7)
 K_COUNT = 8
@@ -55,7 +56,7 @@ class Opts(ctypes.Structure):
         ("mgs_kernel", ctypes.c_int32),
         ("l2_prefetch", ctypes.c_int32),
         ("block_cluster", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 1),
+        ("ilu_binary32", ctypes.c_int32),
         ("stall_factor", ctypes.c_double),
         ("stall_window", ctypes.c_int32),
         ("orth_norm", ctypes.c_int32),
@@ -115,6 +116,9 @@ SIGNATURES = {
     "gmres_memory_bytes": (_st, [_vp, _i32, _i32, ctypes.POINTER(ctypes.c_int64),
                                  ctypes.POINTER(ctypes.c_int64)]),
     "gmres_orth_norms": (_st, [_vp, _vp, _i32]),
+    "gmres_ilu0": (_st, [_vp]),
+    "gmres_ilu_apply": (_st, [_vp, _vp, _vp, _i32]),
+    "gmres_ilu_factors": (_st, [_vp, _vp]),
     "gmres_batch_autotune": (_st, [_vp, _vp, _i32, _i32, _i32, _i32, ctypes.POINTER(_i32)]),
     "gmres_batch_create": (_st, [ctypes.POINTER(_vp), _i32, _vp, _vp, _vp, _vp, _vp]),
     "gmres_batch_destroy": (None, [_vp]),
@@ -285,6 +289,23 @@ def gmres_batch_autotune(h, rhs, m, ortho, prec, iters):
     _check(lib().gmres_batch_autotune(h, _ptr(rhs), int(m), int(ortho), int(prec), int(iters),
                                       ctypes.byref(out)), "gmres_batch_autotune")
     return out.value
+
+
+def gmres_ilu0(h):
+    """ILU(0) factors of the handle's matrix (select with precond=2)."""
+    return _check(lib().gmres_ilu0(h), "gmres_ilu0")
+
+
+def gmres_ilu_factors(h, nnz):
+    """The binary64 ILU(0) factors on A's pattern (host array)."""
+    lu = np.zeros(int(nnz))
+    _check(lib().gmres_ilu_factors(h, lu.ctypes.data_as(_vp)), "gmres_ilu_factors")
+    return lu
+
+
+def gmres_ilu_apply(h, z, out, prec):
+    """out = (L U)^-1 z on the device."""
+    return _check(lib().gmres_ilu_apply(h, _ptr(z), _ptr(out), int(prec)), "gmres_ilu_apply")
 
 
 def gmres_orth_norms(h, count):

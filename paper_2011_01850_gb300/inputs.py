@@ -288,6 +288,12 @@ WORKLOADS = {
                           prec="mixed"),
     "convdiff3d_96": dict(kind="3d", N=96, eps=(0.1, 0.1, 0.1), m=100, ortho="cgsr",
                           prec="mixed"),
+    "convdiff3d_160_ilu": dict(kind="3d", N=160, eps=(0.1, 0.1, 0.1), m=100, ortho="cgsr",
+                               prec="mixed", precond="ilu",
+                               desc="3-D convection-diffusion 160^3, ILU(0) left preconditioner"),
+    "convdiff3d_96_ilu": dict(kind="3d", N=96, eps=(0.1, 0.1, 0.1), m=100, ortho="cgsr",
+                              prec="mixed", precond="ilu",
+                              desc="3-D convection-diffusion 96^3, ILU(0) left preconditioner"),
     "powerlaw_2m": dict(kind="powerlaw", n=2_000_000, m=50, ortho="mgs", prec="mixed_bf16",
                         desc="random power-law rows 3-200 (mean 16), diagonal 1.2 x row sum"),
     "powerlaw_20k": dict(kind="powerlaw", n=20_000, m=50, ortho="mgs", prec="mixed_bf16"),
