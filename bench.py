@@ -175,10 +175,10 @@ COMPARE = {
                     ("jacobi", "mixed", "cgsr", "jacobi"), ("fp64", "fp64", "cgsr", "none")],
 }
 SPAI_PARAMS = os.path.join(ROOT, "paper_2011_01850_gb300", "data", "spai_aniso64.npy")
-# DRAM bytes per algorithmic byte of the register-streaming CGSR passes, from
-# one ncu capture of a mid-cycle step (51 vectors) at 96^3: 565.3 MB of DRAM
+# DRAM bytes per algorithmic byte of the CGSR passes (binary32 basis), from
+# one ncu capture of a mid-cycle step (51 vectors) at 96^3: 564.2 MB of DRAM
 # traffic for 559.2 MB algorithmic; scaled to the timed launches.
-CGSR_ROWS_TRAFFIC_RATIO = 1.011
+CGSR_ROWS_TRAFFIC_RATIO = 1.009
 
 
 def bench_ours(args):
@@ -331,6 +331,8 @@ def bench_ours(args):
     iters = infos[0]["iters"]
     restarts = infos[0]["restarts"]
     kernel_names = {"ortho": ("CGSR passes (k_cgs_tile x3)" if args.cgs_kernel == 1
+                              else "CGSR passes (k_cgs_rows x2 + k_cgs_passb_reg + "
+                                   "k_reduce_cols x2)" if args.cgs_kernel == 0 and prec == "mixed"
                               else "CGSR passes (k_cgs_rows x3 + k_reduce_cols x2)")
                     if ortho == "cgsr" else "MGS step (k_mgs_persist, cooperative)",
                     "block": "single-block solver (k_block_solve)",
@@ -357,8 +359,9 @@ def bench_ours(args):
                   else "inputs L2-resident (no flush; small-system workload)",
             "parallelism": "replicas" if world > 1 else "single GPU",
             "spmv_lanes": {"f32": lanes32, "f64": lanes64},
-            "cgs_kernel": ["register-streaming rows", "TMA tiles",
-                           "register-streaming rows, per-row-group update"][args.cgs_kernel],
+            "cgs_kernel": ["register-streaming rows, pass B slice in registers", "TMA tiles",
+                           "register-streaming rows, per-row-group update",
+                           "register-streaming rows, pass B re-read from L2"][args.cgs_kernel],
             "l2_prefetch": int(G.gmres_get_opts(solver.h).l2_prefetch),
             "block_cluster": int(G.gmres_get_opts(solver.h).block_cluster),
         },
@@ -373,8 +376,9 @@ def bench_ours(args):
             "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
             "traffic": (round(CGSR_ROWS_TRAFFIC_RATIO * kbytes[dom] / klaunch[dom])
-                        if dom == "ortho" and ortho == "cgsr" and args.cgs_kernel == 0
-                        and klaunch[dom] else None),
+                        if CGSR_ROWS_TRAFFIC_RATIO and dom == "ortho" and ortho == "cgsr"
+                        and args.cgs_kernel == 0 and prec == "mixed" and klaunch[dom]
+                        else None),
             "launches": int(klaunch[dom]),
             "bytes_per_launch": kbytes[dom] / klaunch[dom] if klaunch[dom] else None,
         },

@@ -120,9 +120,12 @@ typedef struct gmres_opts {
     int32_t spmv_lanes;   /* lanes per CSR row in SpMV (1..32, power of two);
                              0 = the autotuned choice                           */
     int32_t cgs_kernel;   /* CGSR kernel family: 0 = register-streaming rows
-                             (default; the updates split by basis vectors),
-                             1 = TMA-fed shared-memory tiles, 2 = register-
-                             streaming rows with the update split by rows      */
+                             (default; the updates split by basis vectors, and
+                             with a binary32 basis the second pass keeps each
+                             slice in registers between update and dot
+                             products), 1 = TMA-fed shared-memory tiles, 2 =
+                             rows with the update split by rows, 3 = as 0 but
+                             the second pass re-reads each slice from L2      */
     int32_t mgs_kernel;   /* MGS: 0 = one cooperative kernel per inner step with
                              w in shared memory (default; used when w's row
                              chunk fits), 1 = one kernel per basis vector       */

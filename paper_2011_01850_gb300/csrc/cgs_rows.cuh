@@ -427,6 +427,92 @@ __global__ void __launch_bounds__(ROWS_THREADS)
     givens_step(c, ncols - 1, c.h1, wsqrt(snorm));
 }
 
+// Pass B with the slice held in registers (binary32 basis): w <- w - V h1,
+// then partial h2 = V^T w, reading every basis vector once.  A block walks
+// 128-row slices; its 8 warps split the basis vectors (warp w takes vectors
+// w, w+8, ...) and every lane loads 4 rows of each of its at most KC vectors
+// (16-byte loads, all issued before use) and keeps them: the warps' partial
+// sums of V h1 meet in shared memory, threads 0..127 form the updated w of
+// the slice, and the dot products then use the vectors still in registers
+// instead of reading them again.  Partials of V h1 are summed over warps in
+// order; the dot partials per lane over the block's slices, then by an xor
+// butterfly.
+constexpr int PB_THREADS = 256;
+constexpr int PB_WARPS = PB_THREADS / 32;
+constexpr int PB_ROWS = 128;  // rows per slice (32 lanes x 4)
+
+template <int KC>
+__global__ void __launch_bounds__(PB_THREADS)
+    k_cgs_passb_reg(GridCtx<float, float> c, int ncols, float *part, int64_t slices_per_block) {
+    if (!c.ctl->active)
+        return;
+    __shared__ float hs[MMAX + 2];
+    __shared__ __align__(16) float tsm[PB_WARPS * PB_ROWS];
+    __shared__ __align__(16) float wsl[PB_ROWS];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < ncols; i += PB_THREADS)
+        hs[i] = c.h1[i];
+    __syncthreads();
+    const uint64_t pol = l2_policy_first();
+    float acc[KC];
+#pragma unroll
+    for (int k = 0; k < KC; ++k)
+        acc[k] = 0.f;
+    const int64_t nslices = c.ldv / PB_ROWS;
+    const int64_t sl0 = (int64_t)blockIdx.x * slices_per_block;
+    int64_t sl1 = sl0 + slices_per_block;
+    if (sl1 > nslices)
+        sl1 = nslices;
+    for (int64_t sl = sl0; sl < sl1; ++sl) {
+        const int64_t s0 = sl * PB_ROWS;
+        float v[KC][4];
+#pragma unroll
+        for (int k = 0; k < KC; ++k) {
+            const int col = wid + PB_WARPS * k;
+            if (col < ncols)
+                ld_rows<float, float, 4>(c.V + (size_t)col * c.ldv + s0 + lane * 4, 1.f, v[k],
+                                         pol);
+            else
+                v[k][0] = v[k][1] = v[k][2] = v[k][3] = 0.f;
+        }
+        float tp[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int k = 0; k < KC; ++k) {
+            const int col = wid + PB_WARPS * k;
+            const float hc = col < ncols ? hs[col] : 0.f;
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                tp[q] += v[k][q] * hc;
+        }
+        *reinterpret_cast<float4 *>(tsm + wid * PB_ROWS + lane * 4) =
+            make_float4(tp[0], tp[1], tp[2], tp[3]);
+        __syncthreads();
+        if (threadIdx.x < PB_ROWS) {
+            const int r = threadIdx.x;
+            float t = tsm[r];
+#pragma unroll
+            for (int w = 1; w < PB_WARPS; ++w)
+                t += tsm[w * PB_ROWS + r];
+            const float wn = c.w[s0 + r] - t;
+            c.w[s0 + r] = wn;
+            wsl[r] = wn;
+        }
+        __syncthreads();
+        const float4 wv = *reinterpret_cast<const float4 *>(wsl + lane * 4);
+#pragma unroll
+        for (int k = 0; k < KC; ++k)
+            acc[k] += ((v[k][0] * wv.x + v[k][1] * wv.y) + v[k][2] * wv.z) + v[k][3] * wv.w;
+    }
+    float *mypart = part + (size_t)blockIdx.x * PSTRIDE;
+#pragma unroll
+    for (int k = 0; k < KC; ++k) {
+        const int col = wid + PB_WARPS * k;
+        const float a = warp_sum(acc[k]);
+        if (lane == 0 && col < ncols)
+            mypart[col] = a;
+    }
+}
+
 // out[col] = sum over the blocks of part[b][col], col < ncols, and, when
 // `extra` >= 0, ctl->wnorm0 = sqrt(sum of part[b][MMAX+1]) (the ||A v_j||
 // reference of pass A).  One block per column, fixed-order tree.

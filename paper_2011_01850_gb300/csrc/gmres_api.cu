@@ -386,9 +386,37 @@ gmres_status enqueue_cgs_rows(gmres_handle *h, GridCtx<T, VT> &c, int ncols, Acc
     k_cgs_rows<T, VT, 0, SPLIT><<<gsz[0], ROWS_THREADS, 0, h->stream>>>(c, ncols, c.part, kpb[0],
                                                                         pf);
     k_reduce_cols<T><<<ncols + 1, 256, 0, h->stream>>>(c.part, gsz[0], ncols, c.h1, c.ctl, 1);
-    k_cgs_rows<T, VT, 1, SPLIT><<<gsz[1], ROWS_THREADS, 0, h->stream>>>(c, ncols, c.part, kpb[1],
-                                                                        pf);
-    k_reduce_cols<T><<<ncols, 256, 0, h->stream>>>(c.part, gsz[1], ncols, c.h2, c.ctl, 0);
+    if constexpr (std::is_same<T, float>::value && std::is_same<VT, float>::value) {
+        if (h->opts.cgs_kernel != 3) {
+            // pass B with the slice in registers; KC vectors per warp
+            const int kc = (ncols + PB_WARPS - 1) / PB_WARPS;
+            void (*kfn)(GridCtx<float, float>, int, float *, int64_t) =
+                kc <= 2 ? k_cgs_passb_reg<2>
+                        : kc <= 4 ? k_cgs_passb_reg<4>
+                                  : kc <= 8 ? k_cgs_passb_reg<8>
+                                            : kc <= 12 ? k_cgs_passb_reg<12> : k_cgs_passb_reg<17>;
+            static std::map<const void *, int> pb_per_sm;
+            int &bps = pb_per_sm[(const void *)kfn];
+            if (bps == 0) {
+                CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kfn, PB_THREADS, 0));
+                bps = std::max(1, bps);
+            }
+            const int64_t nsl_b = h->ldv / PB_ROWS;
+            const int64_t cap = (int64_t)h->nsm * bps;
+            const int64_t kb = (nsl_b + cap - 1) / cap;
+            const int gb = (int)((nsl_b + kb - 1) / kb);
+            kfn<<<gb, PB_THREADS, 0, h->stream>>>(c, ncols, c.part, kb);
+            k_reduce_cols<T><<<ncols, 256, 0, h->stream>>>(c.part, gb, ncols, c.h2, c.ctl, 0);
+        } else {
+            k_cgs_rows<T, VT, 1, SPLIT><<<gsz[1], ROWS_THREADS, 0, h->stream>>>(c, ncols, c.part,
+                                                                                kpb[1], pf);
+            k_reduce_cols<T><<<ncols, 256, 0, h->stream>>>(c.part, gsz[1], ncols, c.h2, c.ctl, 0);
+        }
+    } else {
+        k_cgs_rows<T, VT, 1, SPLIT><<<gsz[1], ROWS_THREADS, 0, h->stream>>>(c, ncols, c.part,
+                                                                            kpb[1], pf);
+        k_reduce_cols<T><<<ncols, 256, 0, h->stream>>>(c.part, gsz[1], ncols, c.h2, c.ctl, 0);
+    }
     k_cgs_rows<T, VT, 2, SPLIT><<<gsz[2], ROWS_THREADS, 0, h->stream>>>(c, ncols, c.part, kpb[2],
                                                                         pf);
     acct.launches[GMRES_K_ORTHO] += 5;
@@ -890,7 +918,7 @@ gmres_status validate_opts(const gmres_opts *o) {
     if (!(o->inner_factor >= 0) || o->path < 0 || o->path > 2 || o->spin_limit < 0 ||
         (o->spmv_lanes != 0 && (o->spmv_lanes < 1 || o->spmv_lanes > 32 ||
                                 (o->spmv_lanes & (o->spmv_lanes - 1)))) ||
-        o->cgs_kernel < 0 || o->cgs_kernel > 2 || o->mgs_kernel < 0 || o->mgs_kernel > 1 ||
+        o->cgs_kernel < 0 || o->cgs_kernel > 3 || o->mgs_kernel < 0 || o->mgs_kernel > 1 ||
         o->l2_prefetch < 0 || o->l2_prefetch > 4 || !(o->stall_factor >= 0) ||
         (o->block_cluster != 0 && o->block_cluster != 1 && o->block_cluster != TEAM_SINGLE_CTAS) ||
         o->stall_window < 0 || o->stall_window > MMAX || o->orth_norm < GMRES_ORTH_OFF ||

@@ -405,15 +405,16 @@ def test_mgs_cooperative_matches_per_column(gpulib, stream):
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed", "mixed_fp16"])
 def test_cgsr_kernel_families_agree(prec, gpulib, stream):
-    """The three CGSR kernel families (rows with the update split by basis
-    vectors, TMA-fed tiles, rows with the update split by rows) sum in
-    different orders; binary64 takes the same schedule with solutions equal
+    """The CGSR kernel families (rows with the update split by basis vectors
+    and pass B's slice in registers, TMA-fed tiles, rows with the update
+    split by rows, rows with pass B re-reading from L2) sum in different
+    orders; binary64 takes the same schedule with solutions equal
     to 1e-11, and every family reaches the binary64 target."""
     A = I.convdiff3d(26, eps=(0.1, 0.1, 0.1), seed=3)  # n = 17576: several slices per block
     b = I.rhs_ones_noise(A, 1e-3, 5)
     n = len(A[0]) - 1
     out = {}
-    for kern in (0, 1, 2):
+    for kern in (0, 1, 2, 3):
         s = G.Solver(A, stream=stream)
         s.set_opts(path=G.PATH_GRID, cgs_kernel=kern)
         x, st, info = s.solve(b, np.zeros(n), m=40, ortho="cgsr", prec=prec)
@@ -422,7 +423,7 @@ def test_cgsr_kernel_families_agree(prec, gpulib, stream):
         assert O.residual_norm(A, b, x) / np.linalg.norm(b) <= 1e-10
         out[kern] = (x, info)
     if prec == "fp64":
-        for kern in (1, 2):
+        for kern in (1, 2, 3):
             assert out[kern][1]["iters"] == out[0][1]["iters"]
             assert out[kern][1]["restarts"] == out[0][1]["restarts"]
             assert np.linalg.norm(out[kern][0] - out[0][0]) / np.linalg.norm(out[0][0]) <= 1e-11
