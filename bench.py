@@ -53,6 +53,8 @@ def parse():
                    help="CGSR rows kernels: slices prefetched ahead into L2 (library default)")
     p.add_argument("--block-cluster", type=int, default=None,
                    help="block path: 1 block or an 8-block cluster per system (library default)")
+    p.add_argument("--fuse-normalize", action="store_true",
+                   help="form v_{j+1} inside the next SpMV instead of in its own kernel")
     p.add_argument("--spmv-lanes", type=int, default=0,
                    help="lanes per CSR row (0: autotuned)")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -209,6 +211,8 @@ def bench_ours(args):
         solver.set_opts(l2_prefetch=args.l2_prefetch)
     if args.block_cluster is not None:
         solver.set_opts(block_cluster=args.block_cluster)
+    if args.fuse_normalize:
+        solver.set_opts(normalize_fused=1)
     learned = spec.get("precond") == "learned"
     spai_params = None
     if learned:
@@ -364,6 +368,7 @@ def bench_ours(args):
                            "register-streaming rows, pass B re-read from L2"][args.cgs_kernel],
             "l2_prefetch": int(G.gmres_get_opts(solver.h).l2_prefetch),
             "block_cluster": int(G.gmres_get_opts(solver.h).block_cluster),
+            "normalize_fused": int(G.gmres_get_opts(solver.h).normalize_fused),
         },
         "iters": iters, "restarts": restarts,
         "compare": compare,

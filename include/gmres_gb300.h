@@ -149,7 +149,10 @@ typedef struct gmres_opts {
                              grid path only (GMRES_PATH_AUTO picks it)          */
     double orth_threshold;/* end the cycle once ||S_k|| >= this (default 1.0)  */
     int32_t orth_iters;   /* power-method iterations (default 10, as Sec. 4.1) */
-    int32_t reserved2;
+    int32_t normalize_fused; /* 1: v_{j+1} = w / h_{j+1,j} is formed inside the
+                             next step's SpMV (same values, one pass less, but
+                             a division per gathered entry: measured slower on
+                             the 3-D stencil); 0 (default): its own kernel    */
 } gmres_opts;
 
 /* Kernel classes reported in gmres_info (index into kernel_ms / kernel_bytes). */

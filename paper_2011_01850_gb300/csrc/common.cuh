@@ -52,6 +52,8 @@ struct Basis<double> {
     static constexpr int bytes = 8;
     __device__ __forceinline__ static double ld(const double *p, float) { return *p; }
     __device__ __forceinline__ static void st(double *p, double v, float) { *p = v; }
+    // the value a store followed by a load gives (rt = round trip)
+    __device__ __forceinline__ static double rt(double v, float, float) { return v; }
 };
 
 template <>
@@ -59,6 +61,10 @@ struct Basis<float> {
     static constexpr int bytes = 4;
     __device__ __forceinline__ static float ld(const float *p, float) { return *p; }
     __device__ __forceinline__ static void st(float *p, float v, float) { *p = v; }
+    __device__ __forceinline__ static float rt(float v, float, float) { return v; }
+    __device__ __forceinline__ static double rt(double v, float, float) {
+        return (double)(float)v;
+    }
 };
 
 template <>
@@ -69,6 +75,9 @@ struct Basis<__nv_bfloat16> {
     }
     __device__ __forceinline__ static void st(__nv_bfloat16 *p, float v, float) {
         *p = __float2bfloat16_rn(v);
+    }
+    __device__ __forceinline__ static float rt(float v, float, float) {
+        return __bfloat162float(__float2bfloat16_rn(v));
     }
 };
 
@@ -82,6 +91,9 @@ struct Basis<__half> {
     }
     __device__ __forceinline__ static void st(__half *p, float v, float scale) {
         *p = __float2half_rn(v * scale);
+    }
+    __device__ __forceinline__ static float rt(float v, float scale, float inv_scale) {
+        return __half2float(__float2half_rn(v * scale)) * inv_scale;
     }
 };
 

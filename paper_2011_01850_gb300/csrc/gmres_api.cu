@@ -355,11 +355,32 @@ gmres_status left_start(gmres_handle *h, GridCtx<T, VT> &c, Acct &acct) {
     return GMRES_OK;
 }
 
+// Whether v_{j+1} = w / h is formed inside the next step's SpMV.
+template <class T, class VT>
+bool fused_normalize(const gmres_handle *h, const GridCtx<T, VT> &c, bool coop_mgs) {
+    return h->opts.normalize_fused && !c.left && !c.pvals &&
+           h->opts.orth_norm == GMRES_ORTH_OFF && !coop_mgs;
+}
+
+template <class T, class VT>
+cudaError_t launch_spmv_norm(gmres_handle *h, const GridCtx<T, VT> &c, int col, T *y, int L) {
+    dim3 g(spmv_grid(h)), b(kThreads);
+    switch (L) {
+    case 1: k_spmv_norm<T, VT, 1><<<g, b, 0, h->stream>>>(c, col, y); break;
+    case 2: k_spmv_norm<T, VT, 2><<<g, b, 0, h->stream>>>(c, col, y); break;
+    case 4: k_spmv_norm<T, VT, 4><<<g, b, 0, h->stream>>>(c, col, y); break;
+    case 8: k_spmv_norm<T, VT, 8><<<g, b, 0, h->stream>>>(c, col, y); break;
+    case 16: k_spmv_norm<T, VT, 16><<<g, b, 0, h->stream>>>(c, col, y); break;
+    default: k_spmv_norm<T, VT, 32><<<g, b, 0, h->stream>>>(c, col, y); break;
+    }
+    return cudaGetLastError();
+}
+
 // The three register-streaming CGSR passes (and the two column reductions)
 // for an inner step with ncols basis vectors, then v_{j+1}.
 template <class T, class VT, bool SPLIT>
 gmres_status enqueue_cgs_rows(gmres_handle *h, GridCtx<T, VT> &c, int ncols, Acct &acct,
-                              cudaEvent_t e) {
+                              cudaEvent_t e, bool fused) {
     // one resident wave per kernel: grid = SMs x resident blocks per SM
     static int per_sm[3] = {0, 0, 0};
     if (per_sm[0] == 0) {
@@ -422,6 +443,8 @@ gmres_status enqueue_cgs_rows(gmres_handle *h, GridCtx<T, VT> &c, int ncols, Acc
     acct.launches[GMRES_K_ORTHO] += 5;
     CKL();
     h->timer.end(GMRES_K_ORTHO, e);
+    if (fused)
+        return GMRES_OK;  // the next step's SpMV forms v_{j+1}
     e = h->timer.begin();
     dim3 g(h->grid), b(kThreads);
     k_normalize<T, VT><<<g, b, 0, h->stream>>>(c, ncols, h->opts.orth_norm != GMRES_ORTH_OFF);
@@ -440,7 +463,16 @@ gmres_status enqueue_step_core(gmres_handle *h, GridCtx<T, VT> &c, int col, gmre
     const int L = lanes_for<T, VT>(h);
     const VT *vj = c.V + (size_t)col * c.ldv;
     cudaEvent_t e = h->timer.begin();
-    if (c.left) {
+    // the previous step's normalisation moves into this step's SpMV unless a
+    // preconditioner, the orthogonality test or the cooperative MGS kernel
+    // (which writes v_{j+1} itself) is in use
+    const bool coop_mgs = ortho == GMRES_ORTHO_MGS && h->opts.mgs_kernel == 0 &&
+                          mgs_persist_ok<T, VT>(h);
+    const bool fused = fused_normalize(h, c, coop_mgs);
+    if (fused && col > 0) {
+        CK((launch_spmv_norm<T, VT>(h, c, col, c.t, L)));
+        std::swap(c.w, c.t);
+    } else if (c.left) {
         // t = A v_j, w = M^-1 t (left preconditioning, Alg. 1)
         CK((launch_spmv_step<T, VT, VT>(h, c, vj, c.t, L)));
         h->timer.end(GMRES_K_SPMV, e);
@@ -474,8 +506,8 @@ gmres_status enqueue_step_core(gmres_handle *h, GridCtx<T, VT> &c, int col, gmre
     e = h->timer.begin();
     if (ortho == GMRES_ORTHO_CGSR && h->opts.cgs_kernel != 1) {
         if (h->opts.cgs_kernel == 2)
-            return enqueue_cgs_rows<T, VT, false>(h, c, ncols, acct, e);
-        return enqueue_cgs_rows<T, VT, true>(h, c, ncols, acct, e);
+            return enqueue_cgs_rows<T, VT, false>(h, c, ncols, acct, e, fused);
+        return enqueue_cgs_rows<T, VT, true>(h, c, ncols, acct, e, fused);
     }
     if (ortho == GMRES_ORTHO_CGSR) {
         const int TR = cgs_choose_tr<VT>(ncols);
@@ -538,6 +570,8 @@ gmres_status enqueue_step_core(gmres_handle *h, GridCtx<T, VT> &c, int col, gmre
     }
     CKL();
     h->timer.end(GMRES_K_ORTHO, e);
+    if (fused)
+        return GMRES_OK;  // the next step's SpMV forms v_{j+1}
     e = h->timer.begin();
     k_normalize<T, VT><<<g, b, 0, h->stream>>>(c, col + 1, h->opts.orth_norm != GMRES_ORTH_OFF);
     CKL();
@@ -601,6 +635,10 @@ void account_cycle(gmres_handle *h, int j, gmres_ortho ortho, Acct &acct) {
     // row pointers, diagonal positions) plus its vectors and ready flags
     const double sL = (sizeof(T) == 8 && !h->limited && !h->opts.ilu_binary32) ? 8.0 : 4.0;
     const double ilu_bytes = nnz * (sL + 4) + 2.0 * (n + 1) * 4 + n * 4 + 4.0 * n * sT + 8.0 * n;
+    const bool coop = ortho == GMRES_ORTHO_MGS && h->opts.mgs_kernel == 0 &&
+                      mgs_persist_ok<T, VT>(h);
+    const bool fused = h->opts.normalize_fused && !pre && !ilu &&
+                       h->opts.orth_norm == GMRES_ORTH_OFF && !coop;
     for (int it = 0; it < j; ++it) {
         const double c = it + 1;
         acct.bytes[GMRES_K_SPMV] += nnz * (sA + 4) + (n + 1) * 4 + n * (pre ? sT : sV) + n * sT;
@@ -614,7 +652,9 @@ void account_cycle(gmres_handle *h, int j, gmres_ortho ortho, Acct &acct) {
             acct.bytes[GMRES_K_ORTHO] += c * n * sV + 2 * n * sT;
         if (h->opts.orth_norm != GMRES_ORTH_OFF)
             acct.bytes[GMRES_K_ORTHO] += (c + 1) * n * sV;  // u = V^T v_{j+1}
-        if (it + 1 < j)
+        if (fused && it > 0)
+            acct.bytes[GMRES_K_SPMV] += n * sT;  // x read as w (sT, not sV) + v written (sV)
+        else if (!fused && it + 1 < j)
             acct.bytes[GMRES_K_NORMALIZE] += n * sT + n * sV;
     }
     acct.bytes[GMRES_K_NORMALIZE] += n * sT + n * sV;  // v_1 = r / beta
@@ -925,7 +965,8 @@ gmres_status validate_opts(const gmres_opts *o) {
         o->orth_norm > GMRES_ORTH_FROBENIUS || o->orth_iters < 0 ||
         (o->orth_norm != GMRES_ORTH_OFF && !(o->orth_threshold > 0)) ||
         o->repeat_first < -1 || o->repeat_first > 1 || o->precond < 0 || o->precond > 2 ||
-        o->ilu_binary32 < 0 || o->ilu_binary32 > 1)
+        o->ilu_binary32 < 0 || o->ilu_binary32 > 1 || o->normalize_fused < 0 ||
+        o->normalize_fused > 1)
         return GMRES_ERR_ARG;
     return GMRES_OK;
 }
@@ -952,6 +993,7 @@ void gmres_default_opts(gmres_opts *o) {
     o->orth_norm = GMRES_ORTH_OFF;
     o->orth_threshold = 1.0;
     o->orth_iters = 10;
+    o->normalize_fused = 0;
 }
 
 const char *gmres_status_str(gmres_status s) {

@@ -178,10 +178,32 @@ struct ValHiLo {
     }
 };
 
-template <class T, class AV, class XT, int L>
-__device__ __forceinline__ T csr_row_v(const int *__restrict__ rowptr,
-                                       const int *__restrict__ colind, AV a, const XT *x,
-                                       float xinv, int row, int n, int gl) {
+// The vector a row gathers from: a stored vector of type XT (scaled for
+// binary16), or the next basis vector v = w / h formed on the fly from the
+// orthogonalised w, rounded through the basis format exactly as storing and
+// reloading it would.
+template <class T, class XT>
+struct XPlain {
+    const XT *x;
+    float xinv;
+    __device__ __forceinline__ T operator()(int col) const {
+        return (T)Basis<XT>::ld(x + col, xinv);
+    }
+};
+template <class T, class VT>
+struct XNorm {
+    const T *w;
+    T h;
+    float scale, inv;
+    __device__ __forceinline__ T operator()(int col) const {
+        return (T)Basis<VT>::rt(w[col] / h, scale, inv);
+    }
+};
+
+template <class T, class AV, class XV, int L>
+__device__ __forceinline__ T csr_row_g(const int *__restrict__ rowptr,
+                                       const int *__restrict__ colind, AV a, XV xv, int row,
+                                       int n, int gl) {
     T acc = 0;
     if (row < n) {
         int beg = __ldg(rowptr + row), end = __ldg(rowptr + row + 1);
@@ -193,20 +215,28 @@ __device__ __forceinline__ T csr_row_v(const int *__restrict__ rowptr,
             const int c2 = __ldg(colind + k + 2 * L), c3 = __ldg(colind + k + 3 * L);
             const T a0 = (T)a(k), a1 = (T)a(k + L);
             const T a2 = (T)a(k + 2 * L), a3 = (T)a(k + 3 * L);
-            const T x0 = (T)Basis<XT>::ld(x + c0, xinv), x1 = (T)Basis<XT>::ld(x + c1, xinv);
-            const T x2 = (T)Basis<XT>::ld(x + c2, xinv), x3 = (T)Basis<XT>::ld(x + c3, xinv);
+            const T x0 = xv(c0), x1 = xv(c1);
+            const T x2 = xv(c2), x3 = xv(c3);
             acc += a0 * x0;
             acc += a1 * x1;
             acc += a2 * x2;
             acc += a3 * x3;
         }
         for (; k < end; k += L)
-            acc += (T)a(k) * (T)Basis<XT>::ld(x + __ldg(colind + k), xinv);
+            acc += (T)a(k) * xv(__ldg(colind + k));
     }
 #pragma unroll
     for (int off = L / 2; off > 0; off >>= 1)
         acc += __shfl_xor_sync(0xffffffffu, acc, off);
     return acc;
+}
+
+template <class T, class AV, class XT, int L>
+__device__ __forceinline__ T csr_row_v(const int *__restrict__ rowptr,
+                                       const int *__restrict__ colind, AV a, const XT *x,
+                                       float xinv, int row, int n, int gl) {
+    return csr_row_g<T, AV, XPlain<T, XT>, L>(rowptr, colind, a, XPlain<T, XT>{x, xinv}, row, n,
+                                              gl);
 }
 
 template <class T, class AT, class XT, int L>
@@ -221,20 +251,26 @@ __device__ __forceinline__ T csr_row(const int *__restrict__ rowptr, const int *
 // binary32 copy (limited mixed), split storage (high part for the binary32
 // and limited steps, both parts for binary64), or the working-precision
 // copy.
-template <class T, class VT, class XT, int L>
-__device__ __forceinline__ T step_row(const GridCtx<T, VT> &c, const XT *x, int row, int gl) {
+template <class T, class VT, class XV, int L>
+__device__ __forceinline__ T step_row_g(const GridCtx<T, VT> &c, XV xv, int row, int gl) {
     switch (c.aform) {
     case 3:
-        return csr_row_v<T, ValHiLo, XT, L>(c.rowptr, c.colind, ValHiLo{c.ahi, c.alo}, x, c.vinv,
-                                            row, c.n, gl);
+        return csr_row_g<T, ValHiLo, XV, L>(c.rowptr, c.colind, ValHiLo{c.ahi, c.alo}, xv, row,
+                                            c.n, gl);
     case 2:
-        return csr_row_v<T, ValHi, XT, L>(c.rowptr, c.colind, ValHi{c.ahi}, x, c.vinv, row, c.n,
-                                          gl);
+        return csr_row_g<T, ValHi, XV, L>(c.rowptr, c.colind, ValHi{c.ahi}, xv, row, c.n, gl);
     case 1:
-        return csr_row<T, float, XT, L>(c.rowptr, c.colind, c.a_lim, x, c.vinv, row, c.n, gl);
+        return csr_row_g<T, ValPlain<float>, XV, L>(c.rowptr, c.colind, ValPlain<float>{c.a_lim},
+                                                    xv, row, c.n, gl);
     default:
-        return csr_row<T, T, XT, L>(c.rowptr, c.colind, c.a, x, c.vinv, row, c.n, gl);
+        return csr_row_g<T, ValPlain<T>, XV, L>(c.rowptr, c.colind, ValPlain<T>{c.a}, xv, row,
+                                                c.n, gl);
     }
+}
+
+template <class T, class VT, class XT, int L>
+__device__ __forceinline__ T step_row(const GridCtx<T, VT> &c, const XT *x, int row, int gl) {
+    return step_row_g<T, VT, XPlain<T, XT>, L>(c, XPlain<T, XT>{x, c.vinv}, row, gl);
 }
 
 // w = A v_col (inner step, Alg. 1 "w <- A v_j"); with a right preconditioner
@@ -253,6 +289,34 @@ __global__ void __launch_bounds__(256) k_spmv_step(GridCtx<T, VT> c, const XT *x
         T v = step_row<T, VT, XT, L>(c, x, row, gl);
         if (row < c.n && gl == 0)
             y[row] = v;
+    }
+}
+
+// The normalisation of the previous step fused into this step's SpMV:
+// v_col = w / h_{col,col-1} is written into the basis (rounded to its
+// format) by the owner of each row, and y = A v_col gathers the same
+// rounded values computed from w, so the result equals a separate
+// normalisation followed by the SpMV, without the extra pass over w and V.
+// y must not alias w (the host swaps the two work vectors afterwards).
+template <class T, class VT, int L>
+__global__ void __launch_bounds__(256) k_spmv_norm(GridCtx<T, VT> c, int col, T *y) {
+    if (!c.ctl->active)
+        return;
+    const T h = (T)c.ctl->hnext;
+    const XNorm<T, VT> xv{c.w, h, c.vscale, c.vinv};
+    VT *dst = c.V + (size_t)col * c.ldv;
+    const int G = 32 / L;
+    const int lane = threadIdx.x & 31;
+    const int gl = lane % L, gi = lane / L;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t base = warp * G; base < c.n; base += nwarps * G) {
+        int row = (int)(base + gi);
+        T v = step_row_g<T, VT, XNorm<T, VT>, L>(c, xv, row, gl);
+        if (row < c.n && gl == 0) {
+            y[row] = v;
+            Basis<VT>::st(dst + row, c.w[row] / h, c.vscale);
+        }
     }
 }
 

@@ -62,7 +62,7 @@ class Opts(ctypes.Structure):
         ("orth_norm", ctypes.c_int32),
         ("orth_threshold", ctypes.c_double),
         ("orth_iters", ctypes.c_int32),
-        ("reserved2", ctypes.c_int32),
+        ("normalize_fused", ctypes.c_int32),
     ]
 
 
