@@ -581,7 +581,7 @@ def bench_reference(args):
     vals = []
     spent = 0.0
     for i in range(args.warmup + args.steps):
-        t_res, c, a, bco, s = oracle_sample(A, b, spec, ks=(2, 4, 8))
+        t_res, c, a, bco, s = oracle_sample(A, b, spec, ks=(2, 8, 16))
         spent += s
         if i >= args.warmup:
             it = iters or 1
@@ -598,7 +598,7 @@ def bench_reference(args):
         "config": {"workload": args.workload, "m": m, "ortho": spec["ortho"],
                    "precision": spec["prec"], "tol": 1e-10, "seed": SEED},
         "cpu_baseline": {"value": round(v, 1), "unit": "ms", "cores": 1, "kind": "oracle",
-                         "sample": "per step: oracle restart cycles of 2, 4 and 8 inner "
+                         "sample": "per step: oracle restart cycles of 2, 8 and 16 inner "
                                    "iterations plus one residual on the full workload, "
                                    "scaled to %s iterations / %s cycles" % (iters, restarts)},
         "e2e": {"value": round(v, 1), "unit": "ms", "h2d_bytes_per_step": 0,
