@@ -55,6 +55,8 @@ def parse():
                    help="block path: 1 block or an 8-block cluster per system (library default)")
     p.add_argument("--fuse-normalize", action="store_true",
                    help="form v_{j+1} inside the next SpMV instead of in its own kernel")
+    p.add_argument("--cluster-rows", type=int, default=None,
+                   help="batched: systems of at least this many rows use 8-block clusters")
     p.add_argument("--spmv-lanes", type=int, default=0,
                    help="lanes per CSR row (0: autotuned)")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -277,6 +279,9 @@ def bench_ours(args):
     barrier()
     clk = clocks.stop()
     ms_step = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, world)
+    # the paper's accuracy measure on the last timed solution (outside the
+    # timed region)
+    bwd_err = G.gmres_backward_error(solver.h, db, dx)
 
     # end to end through the public API with host buffers (H2D of b and x0,
     # D2H of x inside every step)
@@ -391,6 +396,7 @@ def bench_ours(args):
         "clocks": clk,
         "e2e": e2e,
         "relres": infos[0]["relres"],
+        "backward_error": bwd_err,
     }
     if "fp64" in compare:
         out["speedup_vs_fp64"] = compare["fp64"]["speedup_of_headline"]
@@ -417,6 +423,8 @@ def bench_batched(args, world, rank, local):
     nsys = len(systems)
     stream = torch.cuda.current_stream()
     h = G.gmres_batch_create(nsys, sys_ptr, rp, ci, va, stream=stream)
+    if args.cluster_rows is not None:
+        G.gmres_batch_set_cluster_rows(h, args.cluster_rows)
     db = torch.tensor(b, device="cuda", dtype=torch.float64)
     dx = torch.zeros(len(b), device="cuda", dtype=torch.float64)
     m = 30

@@ -235,6 +235,13 @@ gmres_status gmres_spmv(gmres_t h, const void *x, void *y, gmres_precision prec)
 gmres_status gmres_residual(gmres_t h, const double *b, const double *x, double *z,
                             double *znorm);
 
+/* Normwise backward error of x, the paper's accuracy measure (Sec. 4: runs
+ * stop at a backward error of 1e-10; the formula is not printed):
+ *   eta = ||b - A x||_inf / (||A||_inf ||x||_inf + ||b||_inf),
+ * the infinity-norm form, in binary64 (maxima exact).  b and x are device
+ * vectors; *eta a host double. */
+gmres_status gmres_backward_error(gmres_t h, const double *b, const double *x, double *eta);
+
 /* One restart cycle from the binary64 device vector r0, for parity checks
  * (Alg. 1 from "beta <- ||r||" to the correction u).  The cycle is the one
  * gmres_solve runs.  kmax <= m inner iterations; the cycle also ends when
@@ -338,6 +345,12 @@ gmres_status gmres_batch_solve(gmres_batch_t b, const double *rhs, double *x, in
                                double tol, gmres_ortho ortho, gmres_precision prec,
                                int32_t maxiter, int32_t lanes, gmres_batch_result *results,
                                gmres_info *info);
+
+/* Systems of at least min_rows rows are solved by a cluster of 8 thread
+ * blocks (reductions through distributed shared memory), the others by one
+ * block each; 0 sends every system to a single block.  Default 8192.
+ * GMRES_ERR_ARG for min_rows < 0. */
+gmres_status gmres_batch_set_cluster_rows(gmres_batch_t b, int32_t min_rows);
 
 /* SpMV tile autotuner of the batched solver: times a capped solve (iters
  * inner iterations per system, from x0 = 0, on scratch memory; the batch's

@@ -47,8 +47,21 @@ struct gmres_batch {
 // Systems of at least this many rows are solved by a cluster of CLUSTER_CTAS
 // thread blocks (distributed-shared-memory reductions); smaller ones by one
 // block.  Both launches run concurrently, each over its own work queue.
-constexpr int CLUSTER_MIN_ROWS = 16384;
+constexpr int CLUSTER_MIN_ROWS = 8192;
 constexpr int CLUSTER_CTAS = 8;
+
+// The systems of at least min_rows rows (0: none) go to clusters: they are
+// the first nlarge entries of the largest-first order.
+void set_nlarge(gmres_batch *B, int64_t min_rows) {
+    B->nlarge = 0;
+    if (min_rows <= 0)
+        return;
+    for (int i = 0; i < B->nsys; ++i) {
+        const int s = B->order[i];
+        if (B->sys_ptr[s + 1] - B->sys_ptr[s] >= min_rows)
+            B->nlarge = i + 1;
+    }
+}
 
 namespace {
 
@@ -342,10 +355,7 @@ gmres_status gmres_batch_create(gmres_batch_t *out, int32_t nsys, const int64_t 
     std::stable_sort(B->order.begin(), B->order.end(), [&](int a, int b) {
         return (sys_ptr[a + 1] - sys_ptr[a]) > (sys_ptr[b + 1] - sys_ptr[b]);
     });
-    B->nlarge = 0;
-    for (int i = 0; i < nsys; ++i)
-        if (sys_ptr[B->order[i] + 1] - sys_ptr[B->order[i]] >= CLUSTER_MIN_ROWS)
-            B->nlarge = i + 1;
+    set_nlarge(B, CLUSTER_MIN_ROWS);
     if (cudaStreamCreateWithFlags(&B->aux, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&B->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&B->ev_join, cudaEventDisableTiming) != cudaSuccess)
@@ -453,6 +463,13 @@ gmres_status gmres_batch_solve(gmres_batch_t B, const double *rhs, double *x, in
             std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0)
                 .count();
     return st;
+}
+
+gmres_status gmres_batch_set_cluster_rows(gmres_batch_t B, int32_t min_rows) {
+    if (!B || min_rows < 0)
+        return GMRES_ERR_ARG;
+    set_nlarge(B, min_rows);
+    return GMRES_OK;
 }
 
 gmres_status gmres_batch_autotune(gmres_batch_t B, const double *rhs, int32_t m,

@@ -39,6 +39,34 @@ constexpr int kThreads = 256;
 
 namespace {
 
+// max over i of |v_i| (or of the absolute row sums of A when rowptr is
+// given): non-negative binary64 values order like their bit patterns, so an
+// integer atomicMax gives the exact maximum in any order.
+__global__ void __launch_bounds__(256) k_absmax(int n, const double *v, const int *rowptr,
+                                                const unsigned *hi, const unsigned *lo,
+                                                unsigned long long *out) {
+    __shared__ unsigned long long sm;
+    if (threadIdx.x == 0)
+        sm = 0ull;
+    __syncthreads();
+    unsigned long long best = 0ull;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double a = 0.0;
+        if (rowptr) {
+            for (int k = rowptr[i]; k < rowptr[i + 1]; ++k)
+                a += fabs(hi ? __hiloint2double((int)hi[k], (int)lo[k]) : v[k]);
+        } else {
+            a = fabs(v[i]);
+        }
+        const unsigned long long bits = (unsigned long long)__double_as_longlong(a);
+        best = bits > best ? bits : best;
+    }
+    atomicMax(&sm, best);
+    __syncthreads();
+    if (threadIdx.x == 0)
+        atomicMax(out, sm);
+}
+
 __global__ void k_cast_vals(int64_t nnz, const double *a, float *b) {
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nnz;
          k += (int64_t)gridDim.x * blockDim.x)
@@ -100,6 +128,16 @@ gmres_status ensure_workspace(gmres_handle *h, int m, gmres_precision prec) {
     CK(h->V.ensure(vbytes));
     if (vgrow)
         CK(cudaMemsetAsync(h->V.p, 0, h->V.bytes, h->stream));
+    // the work vectors' padding rows must read as zero in the working type:
+    // clear them when the working type changes (a binary64 solve leaves
+    // nonzero bytes where a binary32 view has its padding)
+    const int tbytes = (prec == GMRES_FP64 || prec == GMRES_MIXED_LIMITED) ? 8 : 4;
+    if (h->work_elem != 0 && h->work_elem != tbytes) {
+        for (DevBuf *b : {&h->w, &h->r, &h->t, &h->t2})
+            if (b->p)
+                CK(cudaMemsetAsync(b->p, 0, b->bytes, h->stream));
+    }
+    h->work_elem = tbytes;
     for (DevBuf *b : {&h->w, &h->r, &h->t}) {
         bool grow = ldv * 8 > b->bytes;
         CK(b->ensure(ldv * 8));
@@ -1320,6 +1358,38 @@ gmres_status gmres_residual(gmres_t h, const double *b, const double *x, double 
         return st;
     if (znorm)
         *znorm = h->hctl->rnorm;
+    return GMRES_OK;
+}
+
+gmres_status gmres_backward_error(gmres_t h, const double *b, const double *x, double *eta) {
+    if (!h || !b || !x || !eta || !is_device_ptr(b) || !is_device_ptr(x))
+        return GMRES_ERR_ARG;
+    gmres_status st = ensure_workspace(h, 1, GMRES_FP64);
+    if (st != GMRES_OK)
+        return st;
+    GridCtx<double, double> c = make_ctx<double, double>(h, 1);
+    c.tol_abs = -1.0;
+    double *z = h->z.as<double>();
+    CK(launch_residual(h, c, b, x, z, 0));
+    ScopedBuf mx;
+    CK(mx.ensure(4 * sizeof(unsigned long long)));
+    CK(cudaMemsetAsync(mx.p, 0, mx.bytes, h->stream));
+    unsigned long long *m = mx.as<unsigned long long>();
+    const int g = h->nsm * 4;
+    const unsigned *hi = h->split ? split_hi(h) : nullptr, *lo = h->split ? split_lo(h) : nullptr;
+    k_absmax<<<g, 256, 0, h->stream>>>(h->n, h->split ? nullptr : h->vals64.as<double>(),
+                                        h->rowptr.as<int>(), hi, lo, m + 0);
+    k_absmax<<<g, 256, 0, h->stream>>>(h->n, x, nullptr, nullptr, nullptr, m + 1);
+    k_absmax<<<g, 256, 0, h->stream>>>(h->n, b, nullptr, nullptr, nullptr, m + 2);
+    k_absmax<<<g, 256, 0, h->stream>>>(h->n, z, nullptr, nullptr, nullptr, m + 3);
+    CKL();
+    unsigned long long r[4];
+    CK(cudaMemcpyAsync(r, m, sizeof(r), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    double v[4];
+    memcpy(v, r, sizeof(v));
+    const double den = v[0] * v[1] + v[2];
+    *eta = den > 0 ? v[3] / den : 0.0;
     return GMRES_OK;
 }
 

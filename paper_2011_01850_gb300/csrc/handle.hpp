@@ -88,6 +88,7 @@ struct gmres_handle {
     DevBuf mon;                  // restart-test histories and the U, S matrices
     bool limited = false;        // the running solve is GMRES_MIXED_LIMITED
     bool split = false;          // A stored split: vals64 holds hi[nnz] then lo[nnz]
+    int work_elem = 0;           // bytes of the working type the work vectors last held
     // ILU(0) left preconditioner: factors (binary64 and binary32 copies),
     // diagonal positions, ready flags of the two triangles + claim counters
     DevBuf ilu64, ilu32, ilu_dpos, ilu_flags, t2;

@@ -116,10 +116,12 @@ SIGNATURES = {
     "gmres_memory_bytes": (_st, [_vp, _i32, _i32, ctypes.POINTER(ctypes.c_int64),
                                  ctypes.POINTER(ctypes.c_int64)]),
     "gmres_orth_norms": (_st, [_vp, _vp, _i32]),
+    "gmres_backward_error": (_st, [_vp, _vp, _vp, ctypes.POINTER(_f64)]),
     "gmres_ilu0": (_st, [_vp]),
     "gmres_ilu_apply": (_st, [_vp, _vp, _vp, _i32]),
     "gmres_ilu_factors": (_st, [_vp, _vp]),
     "gmres_batch_autotune": (_st, [_vp, _vp, _i32, _i32, _i32, _i32, ctypes.POINTER(_i32)]),
+    "gmres_batch_set_cluster_rows": (_st, [_vp, _i32]),
     "gmres_batch_create": (_st, [ctypes.POINTER(_vp), _i32, _vp, _vp, _vp, _vp, _vp]),
     "gmres_batch_destroy": (None, [_vp]),
     "gmres_batch_solve": (_st, [_vp, _vp, _vp, _i32, _f64, _i32, _i32, _i32, _i32, _vp,
@@ -282,6 +284,12 @@ def gmres_autotune(h):
     return a.value, b.value
 
 
+def gmres_batch_set_cluster_rows(h, min_rows):
+    """Systems of at least min_rows rows go to 8-block clusters (0: none)."""
+    return _check(lib().gmres_batch_set_cluster_rows(h, int(min_rows)),
+                  "gmres_batch_set_cluster_rows")
+
+
 def gmres_batch_autotune(h, rhs, m, ortho, prec, iters):
     """Time capped batched solves over the SpMV lanes candidates; returns
     the lanes per row the batch keeps for lanes = 0."""
@@ -306,6 +314,14 @@ def gmres_ilu_factors(h, nnz):
 def gmres_ilu_apply(h, z, out, prec):
     """out = (L U)^-1 z on the device."""
     return _check(lib().gmres_ilu_apply(h, _ptr(z), _ptr(out), int(prec)), "gmres_ilu_apply")
+
+
+def gmres_backward_error(h, b, x):
+    """||b - A x||_inf / (||A||_inf ||x||_inf + ||b||_inf) for device b, x."""
+    eta = _f64()
+    _check(lib().gmres_backward_error(h, _ptr(b), _ptr(x), ctypes.byref(eta)),
+           "gmres_backward_error")
+    return eta.value
 
 
 def gmres_orth_norms(h, count):

@@ -85,7 +85,7 @@ def test_batch_rejects_cross_system_columns(gpulib):
 @pytest.mark.parametrize("prec", ["fp64", "mixed", "mixed_fp16"])
 @pytest.mark.parametrize("ortho", ["mgs", "cgsr"])
 def test_batch_cluster_path(prec, ortho, gpulib):
-    """Systems of >= 16384 rows go to thread-block clusters (reductions over
+    """Systems of >= 8192 rows go to thread-block clusters (reductions over
     distributed shared memory) while the small ones run one block each, in
     a concurrent launch; both kinds must converge and match the oracle."""
     systems = [(I.convdiff2d(130, 130, pe=20.0), None), (I.convdiff2d(128, 160, pe=5.0), None)]
@@ -131,3 +131,26 @@ def test_batch_autotune(gpulib):
     assert st0 == st1 == G.OK
     assert np.array_equal(x0, x1)
     assert [r.iters for r in r0] == [r.iters for r in r1]
+
+
+def test_batch_cluster_threshold(gpulib):
+    """Moving the cluster threshold moves systems between the one-block and
+    the cluster launch; the results stay converged either way."""
+    systems = [(I.convdiff2d(130, 130, pe=20.0), None)]
+    systems += I.batched_convdiff2d(count=3, nmin=40, nmax=2000, seed=12)
+    out = [(A, I.rhs_ones_noise(A, 1e-3, 400 + k) if b is None else b)
+           for k, (A, b) in enumerate(systems)]
+    sys_ptr, rp, ci, va, b = G.pack_batch(out)
+    h = G.gmres_batch_create(len(out), sys_ptr, rp, ci, va)
+    for rows, launches in ((0, 1), (1, 1), (16384, 2)):
+        G.gmres_batch_set_cluster_rows(h, rows)
+        x = np.zeros(len(b))
+        st, res, info = G.gmres_batch_solve(h, b, x, 30, 1e-10, G.ORTHO_MGS, G.MIXED, 20000,
+                                            nsys=len(out))
+        assert st == G.OK and info.kernel_launches[G.K_BLOCK] == launches, rows
+        for i, (A, bi) in enumerate(out):
+            xi = x[sys_ptr[i]:sys_ptr[i + 1]]
+            assert O.residual_norm(A, bi, xi) / np.linalg.norm(bi) <= 1e-10
+    with pytest.raises(G.GmresError):
+        G.gmres_batch_set_cluster_rows(h, -1)
+    G.gmres_batch_destroy(h)

@@ -272,6 +272,45 @@ def test_limited_takes_fewer_iterations_than_mixed(gpulib, stream):
     assert w64 - wlim == 101 * ldv * 4
 
 
+def test_precision_changes_on_one_handle(gpulib, stream):
+    """Solves of different working precisions in a row on one handle (grid
+    path, n not a multiple of the padding): the padding rows of the work
+    vectors are cleared when the working type changes, so every solve still
+    reaches the binary64 target."""
+    A = I.convdiff2d(40, pe=10.0)
+    b = I.rhs_ones_noise(A, 1e-3, 5)
+    n = len(b)
+    s = G.Solver(A, stream=stream)
+    s.set_opts(path=G.PATH_GRID)
+    for prec in ("fp64", "mixed", "mixed_limited", "mixed_bf16", "fp64", "mixed_fp16"):
+        x, st, info = s.solve(b, np.zeros(n), m=30, ortho="cgsr", prec=prec)
+        assert st == G.OK, prec
+        assert O.residual_norm(A, b, x) / np.linalg.norm(b) <= 1e-10, prec
+    s.close()
+
+
+def test_backward_error(gpulib, stream):
+    """The normwise backward error the paper reports (infinity-norm form)
+    against numpy's, on the solution of a mixed solve and on x = 0 (where it
+    is ||b|| / ||b|| = 1), also with split storage."""
+    A = I.convdiff2d(40, pe=10.0)
+    b = I.rhs_ones_noise(A, 1e-3, 5)
+    n = len(b)
+    D = I.csr_to_dense(A)
+    for flags in (0, G.CREATE_SPLIT):
+        s = G.Solver(A, flags=flags, stream=stream)
+        db = dev(b)
+        dx = torch.zeros(n, dtype=torch.float64, device="cuda")
+        assert G.gmres_backward_error(s.h, db, dx) == 1.0
+        s.solve(db, dx, m=30, ortho="cgsr", prec="mixed")
+        eta = G.gmres_backward_error(s.h, db, dx)
+        s.close()
+        x = dx.cpu().numpy()
+        want = np.abs(b - D @ x).max() / (np.abs(D).sum(axis=1).max() * np.abs(x).max()
+                                          + np.abs(b).max())
+        assert 0 < eta <= 1e-10 and abs(eta - want) <= 1e-3 * want, (eta, want)
+
+
 _KAPPA = {}
 
 
