@@ -57,6 +57,9 @@ def parse():
                    help="form v_{j+1} inside the next SpMV instead of in its own kernel")
     p.add_argument("--cluster-rows", type=int, default=None,
                    help="batched: systems of at least this many rows use 8-block clusters")
+    p.add_argument("--trsv-kernel", type=int, default=None,
+                   help="ILU(0) triangular solves: 1 per-row flags, 2 level barrier "
+                        "(library default: chosen by rows per level)")
     p.add_argument("--spmv-lanes", type=int, default=0,
                    help="lanes per CSR row (0: autotuned)")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -215,6 +218,8 @@ def bench_ours(args):
         solver.set_opts(block_cluster=args.block_cluster)
     if args.fuse_normalize:
         solver.set_opts(normalize_fused=1)
+    if args.trsv_kernel is not None:
+        solver.set_opts(trsv_kernel=args.trsv_kernel)
     learned = spec.get("precond") == "learned"
     spai_params = None
     if learned:
@@ -363,6 +368,9 @@ def bench_ours(args):
             "workload": args.workload, "description": spec.get("desc"),
             "n": n, "nnz": nnz, "m": m, "ortho": ortho, "precision": prec, "tol": 1e-10,
             "precond": {"learned": "learned SpAI", "ilu": "ILU(0), left"}.get(spec.get("precond")),
+            "trsv_kernel": ({0: "auto", 1: "per-row flags", 2: "level barrier"}[
+                int(G.gmres_get_opts(solver.h).trsv_kernel)]
+                if spec.get("precond") == "ilu" else None),
             "rhs": "b = A 1 + N(0, sigma^2), sigma = 1e-3, x0 = 0", "seed": SEED,
             "l2": "inputs larger than L2" if nnz * 12 > 129e6
                   else "inputs L2-resident (no flush; small-system workload)",

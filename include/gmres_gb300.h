@@ -153,6 +153,13 @@ typedef struct gmres_opts {
                              next step's SpMV (same values, one pass less, but
                              a division per gathered entry: measured slower on
                              the 3-D stencil); 0 (default): its own kernel    */
+    int32_t trsv_kernel;  /* ILU(0) triangular solves: 2 (and 0, the default)
+                             = one cooperative launch per triangle that
+                             solves level by level with a grid barrier
+                             between levels; 1 = one warp per row, rows
+                             claimed in level order, waits on per-row ready
+                             flags (measured slower on 2-D and 3-D stencils
+                             and on a 2M-row power-law matrix)               */
 } gmres_opts;
 
 /* Kernel classes reported in gmres_info (index into kernel_ms / kernel_bytes). */

@@ -1004,7 +1004,7 @@ gmres_status validate_opts(const gmres_opts *o) {
         (o->orth_norm != GMRES_ORTH_OFF && !(o->orth_threshold > 0)) ||
         o->repeat_first < -1 || o->repeat_first > 1 || o->precond < 0 || o->precond > 2 ||
         o->ilu_binary32 < 0 || o->ilu_binary32 > 1 || o->normalize_fused < 0 ||
-        o->normalize_fused > 1)
+        o->normalize_fused > 1 || o->trsv_kernel < 0 || o->trsv_kernel > 2)
         return GMRES_ERR_ARG;
     return GMRES_OK;
 }
@@ -1032,6 +1032,7 @@ void gmres_default_opts(gmres_opts *o) {
     o->orth_threshold = 1.0;
     o->orth_iters = 10;
     o->normalize_fused = 0;
+    o->trsv_kernel = 0;
 }
 
 const char *gmres_status_str(gmres_status s) {

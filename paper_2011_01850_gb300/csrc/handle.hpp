@@ -93,8 +93,10 @@ struct gmres_handle {
     // diagonal positions, ready flags of the two triangles + claim counters
     DevBuf ilu64, ilu32, ilu_dpos, ilu_flags, t2;
     DevBuf ilu_order;            // rows in level order: L's n entries, then U's
+    DevBuf ilu_lptr;             // level starts in ilu_order: L's levels + 1, then U's
     int ilu_ok = 0;
     int ilu_levels = 0;
+    int ilu_ulevels = 0;
     unsigned ilu_epoch = 1;
     unsigned mgs_round = 0;      // next exchange round number (0: flags not set up)
     int64_t chunk = 0;     // rows per block

@@ -13,7 +13,9 @@
 // for bit.  A binary32 copy serves the binary32 restart cycle.
 //
 // Triangular solves.  L y = z (unit lower) and U x = y run as one persistent
-// launch each, without level barriers: each warp claims the next row of the
+// launch each, in one of two forms.  The level form walks the level schedule
+// with a grid barrier between levels (k_trsv_levels, below).  The flag form
+// has no level barriers: each warp claims the next row of the
 // triangle's level schedule from a counter (every row a claimed row depends
 // on sits in an earlier level, so a running warp claimed it earlier, and a
 // whole level is in flight at once); its lanes wait on the dependencies'
@@ -48,6 +50,9 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
 }
 __device__ __forceinline__ void st_release_u32(unsigned *p, unsigned v) {
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void red_release_add_u32(unsigned *p, unsigned v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
 // Factor the rows rows[0..count) (one level) in place; err[0] = 1 on a zero
@@ -165,6 +170,147 @@ __global__ void __launch_bounds__(256) k_trsv(int n, const int *rowptr, const in
     }
 }
 
+// The same triangle as one cooperative launch that walks the level schedule:
+// every row of level l depends only on rows of earlier levels, so the
+// threads solve the rows of a level independently and the grid passes a
+// barrier between levels.  The barrier is split: a block arrives as soon as
+// its rows of level l are stored, then loads the structure of its rows of
+// level l + 1 (row index, entry range, right-hand side, the first TRSV_PF
+// factor entries and their columns; none of it depends on the level being
+// solved), and only then waits.  After the wait only the solution values of
+// the dependencies remain to be read.  Warps take consecutive 32-row runs of
+// a level, interleaved over the blocks so that every SM gets a share of a
+// narrow level.  Each row subtracts its terms in column order with
+// separately rounded products, as the oracle does.  The barrier counter
+// grows by gridDim.x per level: a block arrives with one release reduction
+// (its stores, ordered before it by the block barrier, are visible before
+// the count), and thread 0 polls the count with acquire loads.  A wait that
+// runs past `spin` polls (or sees another block's report) reports a timeout
+// in *err and the block returns.
+constexpr int TRSV_LV_THREADS = 1024;
+constexpr int TRSV_PF = 4;
+
+template <class T, class AT>
+struct RowAhead {
+    int i;  // row, -1 when the thread has none at this level
+    int b, e;
+    T rhs;
+    AT diag;
+    int col[TRSV_PF];
+    AT val[TRSV_PF];
+};
+
+template <class T, class AT, bool LOWER>
+__device__ __forceinline__ void trsv_load_row(RowAhead<T, AT> &r, int pos, int hi,
+                                              const int *order, const int *rowptr,
+                                              const int *colind, const int *dpos, const AT *lu,
+                                              const T *in) {
+    r.i = -1;
+    if (pos >= hi)
+        return;
+    const int i = order[pos];
+    r.i = i;
+    const int d = dpos[i];
+    r.b = LOWER ? rowptr[i] : d + 1;
+    r.e = LOWER ? d : rowptr[i + 1];
+    r.rhs = in[i];
+    r.diag = LOWER ? AT(1) : lu[d];
+#pragma unroll
+    for (int k = 0; k < TRSV_PF; ++k) {
+        if (r.b + k < r.e) {
+            r.col[k] = colind[r.b + k];
+            r.val[k] = lu[r.b + k];
+        }
+    }
+}
+
+template <class T, class AT, bool LOWER>
+__device__ __forceinline__ void trsv_solve_row(const RowAhead<T, AT> &r, const int *colind,
+                                               const AT *lu, T *out) {
+    T acc = r.rhs;
+#pragma unroll
+    for (int k = 0; k < TRSV_PF; ++k)
+        if (r.b + k < r.e)
+            acc = sub_rn(acc, mul_rn((T)r.val[k], __ldcg(out + r.col[k])));
+    for (int p = r.b + TRSV_PF; p < r.e; ++p)
+        acc = sub_rn(acc, mul_rn((T)lu[p], __ldcg(out + colind[p])));
+    if (!LOWER)
+        acc = acc / (T)r.diag;
+    out[r.i] = acc;
+}
+
+template <class T, class AT, bool LOWER>
+__global__ void __launch_bounds__(TRSV_LV_THREADS, 1)
+    k_trsv_levels(int nlev, const int *lptr, const int *order, const int *rowptr,
+                  const int *colind, const int *dpos, const AT *lu, const T *in, T *out,
+                  unsigned *bar, long long spin, int *err) {
+    __shared__ int s_stop;
+    const int first = (blockIdx.x + gridDim.x * (threadIdx.x >> 5)) * 32 + (threadIdx.x & 31);
+    const int stride = gridDim.x * blockDim.x;
+    if (threadIdx.x == 0)
+        s_stop = 0;
+    RowAhead<T, AT> r;
+    trsv_load_row<T, AT, LOWER>(r, lptr[0] + first, lptr[1], order, rowptr, colind, dpos, lu,
+                                in);
+    for (int l = 0; l < nlev; ++l) {
+        const int lo = lptr[l], hi = lptr[l + 1];
+        if (r.i >= 0)
+            trsv_solve_row<T, AT, LOWER>(r, colind, lu, out);
+        for (int pos = lo + first + stride; pos < hi; pos += stride) {
+            RowAhead<T, AT> q;
+            trsv_load_row<T, AT, LOWER>(q, pos, hi, order, rowptr, colind, dpos, lu, in);
+            trsv_solve_row<T, AT, LOWER>(q, colind, lu, out);
+        }
+        if (l + 1 == nlev)
+            break;
+        __syncthreads();
+        if (threadIdx.x == 0)
+            red_release_add_u32(bar, 1u);
+        trsv_load_row<T, AT, LOWER>(r, hi + first, lptr[l + 2], order, rowptr, colind, dpos, lu,
+                                    in);
+        if (threadIdx.x == 0) {
+            const unsigned target = (unsigned)(l + 1) * gridDim.x;
+            long long it = 0;
+            while (ld_acquire_u32(bar) < target) {
+                if (*(volatile int *)err != 0 || ++it > spin) {
+                    atomicExch(err, 1);
+                    s_stop = 1;
+                    break;
+                }
+            }
+        }
+        __syncthreads();
+        if (s_stop)
+            return;
+    }
+}
+
+template <class T, class AT, bool LOWER>
+cudaError_t launch_trsv_levels(gmres_handle *h, const AT *lu, const T *in, T *out,
+                               unsigned *bar, long long spin, int *err) {
+    static int per_sm = -1;
+    if (per_sm < 0) {
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &per_sm, k_trsv_levels<T, AT, LOWER>, TRSV_LV_THREADS, 0);
+        if (e != cudaSuccess)
+            return e;
+    }
+    if (per_sm < 1)
+        return cudaErrorCooperativeLaunchTooLarge;
+    cudaError_t e = cudaMemsetAsync(bar, 0, sizeof(unsigned), h->stream);
+    if (e != cudaSuccess)
+        return e;
+    int nlev = LOWER ? h->ilu_levels : h->ilu_ulevels;
+    const int *lptr = h->ilu_lptr.as<int>() + (LOWER ? 0 : h->ilu_levels + 1);
+    const int *order = h->ilu_order.as<int>() + (LOWER ? 0 : h->n);
+    const int *rowptr = h->rowptr.as<int>(), *colind = h->colind.as<int>(),
+              *dpos = h->ilu_dpos.as<int>();
+    void *args[] = {&nlev, &lptr, &order, &rowptr, &colind, &dpos, &lu, &in, &out,
+                    &bar, &spin, &err};
+    return cudaLaunchCooperativeKernel((const void *)k_trsv_levels<T, AT, LOWER>, dim3(h->nsm),
+                                       dim3(TRSV_LV_THREADS), args, 0, h->stream);
+}
+
 template <class T, class AT, bool LOWER>
 cudaError_t launch_trsv(gmres_handle *h, const AT *lu, const T *in, T *out, unsigned *flags,
                         unsigned epoch, unsigned *counter, long long spin, int *err) {
@@ -243,15 +389,21 @@ gmres_status ilu_factor(gmres_handle *h) {
         ulevel[i] = lv;
         nulev = std::max(nulev, lv + 1);
     }
+    std::vector<int32_t> uptr(nulev + 1, 0);
+    for (int i = 0; i < n; ++i)
+        uptr[ulevel[i] + 1]++;
+    for (int l = 0; l < nulev; ++l)
+        uptr[l + 1] += uptr[l];
     {
-        std::vector<int32_t> uptr(nulev + 1, 0);
+        std::vector<int32_t> pos(uptr.begin(), uptr.end() - 1);
         for (int i = 0; i < n; ++i)
-            uptr[ulevel[i] + 1]++;
-        for (int l = 0; l < nulev; ++l)
-            uptr[l + 1] += uptr[l];
-        for (int i = 0; i < n; ++i)
-            uorder[uptr[ulevel[i]]++] = i;
+            uorder[pos[ulevel[i]]++] = i;
     }
+    CK(h->ilu_lptr.ensure(sizeof(int32_t) * (size_t)(nlev + nulev + 2)));
+    CK(cudaMemcpyAsync(h->ilu_lptr.p, lptr.data(), sizeof(int32_t) * (nlev + 1),
+                       cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(h->ilu_lptr.as<int32_t>() + nlev + 1, uptr.data(),
+                       sizeof(int32_t) * (nulev + 1), cudaMemcpyHostToDevice, h->stream));
     CK(h->ilu_order.ensure(sizeof(int32_t) * 2 * (size_t)n));
     CK(cudaMemcpyAsync(h->ilu_order.p, order.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice,
                        h->stream));
@@ -288,9 +440,12 @@ gmres_status ilu_factor(gmres_handle *h) {
     CK(cudaStreamSynchronize(h->stream));
     h->ilu_epoch = 1;
     h->ilu_levels = nlev;
+    h->ilu_ulevels = nulev;
     h->ilu_ok = bad ? 0 : 1;
     return bad ? GMRES_ERR_BREAKDOWN : GMRES_OK;
 }
+
+bool trsv_uses_levels(const gmres_handle *h) { return h->opts.trsv_kernel != 1; }
 
 template <class T, class AT>
 cudaError_t ilu_apply(gmres_handle *h, const AT *lu, const T *z, T *tmp, T *out, int *err) {
@@ -310,6 +465,12 @@ cudaError_t ilu_apply(gmres_handle *h, const AT *lu, const T *z, T *tmp, T *out,
     // a legitimate wait lasts at most the dependency chain (a few hundred
     // rows of latency); 2^22 polls is seconds, far beyond it
     const long long spin = h->opts.spin_limit > 0 ? h->opts.spin_limit : (1LL << 22);
+    if (trsv_uses_levels(h)) {
+        cudaError_t e = launch_trsv_levels<T, AT, true>(h, lu, z, tmp, ctr, spin, err);
+        if (e != cudaSuccess)
+            return e;
+        return launch_trsv_levels<T, AT, false>(h, lu, tmp, out, ctr + 1, spin, err);
+    }
     cudaError_t e = launch_trsv<T, AT, true>(h, lu, z, tmp, lflags, e0, ctr, spin, err);
     if (e != cudaSuccess)
         return e;

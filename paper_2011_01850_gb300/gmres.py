@@ -63,6 +63,7 @@ class Opts(ctypes.Structure):
         ("orth_threshold", ctypes.c_double),
         ("orth_iters", ctypes.c_int32),
         ("normalize_fused", ctypes.c_int32),
+        ("trsv_kernel", ctypes.c_int32),
     ]
 
 

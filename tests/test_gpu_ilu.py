@@ -40,8 +40,14 @@ def test_ilu_factors_bitwise(case, gpulib):
     assert np.array_equal(lu, O.ilu0(A)[2])
 
 
+TRSV = [(1, "flags"), (2, "levels")]
+
+
+@pytest.mark.parametrize("trsv", TRSV, ids=[t[1] for t in TRSV])
 @pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
-def test_ilu_apply(case, gpulib):
+def test_ilu_apply(case, trsv, gpulib):
+    """Both triangular-solve kernels (per-row ready flags; grid barrier
+    between levels) give the oracle's M^-1 z bit for bit in binary64."""
     A = case[1]()
     n = len(A[0]) - 1
     LU = O.ilu0(A)
@@ -49,6 +55,7 @@ def test_ilu_apply(case, gpulib):
     want = O.ilu_apply(LU, z)
     s = G.Solver(A)
     G.gmres_ilu0(s.h)
+    s.set_opts(trsv_kernel=trsv[0])
     out = torch.zeros(n, device="cuda", dtype=torch.float64)
     G.gmres_ilu_apply(s.h, dev(z), out, G.FP64)
     out32 = torch.zeros(n, device="cuda", dtype=torch.float32)
@@ -80,15 +87,17 @@ def test_ilu_cycle_parity(prec, ortho, gpulib):
     assert np.abs(g["u"] - o["u"]).max() / np.abs(o["u"]).max() <= tol
 
 
+@pytest.mark.parametrize("trsv", TRSV, ids=[t[1] for t in TRSV])
 @pytest.mark.parametrize("prec", ["fp64", "fp64_ilu32", "mixed", "mixed_limited"])
-def test_ilu_solve(prec, gpulib):
+def test_ilu_solve(prec, trsv, gpulib):
     A = I.convdiff3d(20, eps=(0.1, 0.1, 0.1), seed=2)
     b = I.rhs_ones_noise(A, 1e-3, 6)
     n = len(b)
     s = G.Solver(A)
     _, _, plain = s.solve(b, np.zeros(n), m=40, ortho="cgsr", prec="mixed")
     G.gmres_ilu0(s.h)
-    s.set_opts(precond=G.PRECOND_ILU0, ilu_binary32=int(prec == "fp64_ilu32"))
+    s.set_opts(precond=G.PRECOND_ILU0, ilu_binary32=int(prec == "fp64_ilu32"),
+               trsv_kernel=trsv[0])
     p = "fp64" if prec.startswith("fp64") else prec
     x, st, info = s.solve(b, np.zeros(n), m=40, ortho="cgsr", prec=p)
     s.close()
@@ -103,6 +112,36 @@ def test_ilu_solve(prec, gpulib):
     assert info["iters"] < plain["iters"]
 
 
+def test_ilu_levels_large_and_short_waits(gpulib):
+    """Both triangular-solve kernels on a 3-D stencil wide enough that a
+    level spans many warps (48^3: 142 levels of up to 1 700 rows); with a
+    one-poll wait limit each either finishes or reports a timeout, and the
+    handle keeps working afterwards."""
+    A = I.convdiff3d(48, eps=(0.1, 0.1, 0.1), seed=5)
+    n = len(A[0]) - 1
+    z = np.random.default_rng(9).standard_normal(n)
+    want = O.ilu_apply(O.ilu0(A), z)
+    s = G.Solver(A)
+    G.gmres_ilu0(s.h)
+    out = torch.zeros(n, device="cuda", dtype=torch.float64)
+    for k in (1, 2, 0):
+        s.set_opts(trsv_kernel=k)
+        out.zero_()
+        G.gmres_ilu_apply(s.h, dev(z), out, G.FP64)
+        assert np.array_equal(out.cpu().numpy(), want), k
+    for k in (1, 2):
+        s.set_opts(trsv_kernel=k, spin_limit=1)
+        try:
+            G.gmres_ilu_apply(s.h, dev(z), out, G.FP64)
+        except G.GmresError as e:
+            assert e.status == G.ERR_TIMEOUT
+        s.set_opts(spin_limit=0)
+        out.zero_()
+        G.gmres_ilu_apply(s.h, dev(z), out, G.FP64)
+        assert np.array_equal(out.cpu().numpy(), want), k
+    s.close()
+
+
 def test_ilu_refusals_and_timeout(gpulib):
     A = I.convdiff2d(20, pe=10.0)
     b = I.rhs_ones_noise(A, 1e-3, 1)
@@ -113,14 +152,14 @@ def test_ilu_refusals_and_timeout(gpulib):
         s.solve(b, np.zeros(n), m=20, prec="mixed")
     assert e.value.status == G.ERR_ARG
     G.gmres_ilu0(s.h)
-    # a spin limit of one poll: the triangular solves give up at once and
-    # report a timeout; the handle stays usable
-    s.set_opts(spin_limit=1)
+    # a spin limit of one poll: the flag-driven triangular solves give up at
+    # once and report a timeout; the handle stays usable
+    s.set_opts(spin_limit=1, trsv_kernel=1)
     out = torch.zeros(n, device="cuda", dtype=torch.float64)
     with pytest.raises(G.GmresError) as e:
         G.gmres_ilu_apply(s.h, dev(b), out, G.FP64)
     assert e.value.status == G.ERR_TIMEOUT
-    s.set_opts(spin_limit=0)
+    s.set_opts(spin_limit=0, trsv_kernel=0)
     x, st, info = s.solve(b, np.zeros(n), m=20, prec="mixed")
     assert st == G.OK
     s.close()
