@@ -58,8 +58,8 @@ def parse():
     p.add_argument("--cluster-rows", type=int, default=None,
                    help="batched: systems of at least this many rows use 8-block clusters")
     p.add_argument("--trsv-kernel", type=int, default=None,
-                   help="ILU(0) triangular solves: 1 per-row flags, 2 level barrier "
-                        "(library default: chosen by rows per level)")
+                   help="ILU(0) triangular solves: 1 per-row flags, 2 level barrier, "
+                        "3 barrier-free (library default: 3 or 2 per triangle)")
     p.add_argument("--spmv-lanes", type=int, default=0,
                    help="lanes per CSR row (0: autotuned)")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -368,7 +368,7 @@ def bench_ours(args):
             "workload": args.workload, "description": spec.get("desc"),
             "n": n, "nnz": nnz, "m": m, "ortho": ortho, "precision": prec, "tol": 1e-10,
             "precond": {"learned": "learned SpAI", "ilu": "ILU(0), left"}.get(spec.get("precond")),
-            "trsv_kernel": ({0: "auto", 1: "per-row flags", 2: "level barrier"}[
+            "trsv_kernel": ({0: "auto", 1: "per-row flags", 2: "level barrier", 3: "barrier-free"}[
                 int(G.gmres_get_opts(solver.h).trsv_kernel)]
                 if spec.get("precond") == "ilu" else None),
             "rhs": "b = A 1 + N(0, sigma^2), sigma = 1e-3, x0 = 0", "seed": SEED,
@@ -408,6 +408,16 @@ def bench_ours(args):
     }
     if "fp64" in compare:
         out["speedup_vs_fp64"] = compare["fp64"]["speedup_of_headline"]
+    if dom == "precond" and spec.get("precond") == "ilu" and klaunch[dom]:
+        # the triangular solves pass their dependency levels one after another:
+        # bound by the latency of a level, not by bytes
+        lo, up = G.gmres_ilu_levels(solver.h)
+        per_launch_us = kms[dom] * 1e3 / klaunch[dom]
+        out["roofline"].update({
+            "bound": "latency", "kernel": "level-scheduled triangular solves (L, U)",
+            "levels_per_launch": (lo + up) / 2,
+            "us_per_level": round(per_launch_us / ((lo + up) / 2), 3),
+            "note": "achieved/frac: algorithmic bytes over time against HBM, for context"})
     solver.close()
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(A, b, spec, iters, restarts, m)

@@ -153,13 +153,17 @@ typedef struct gmres_opts {
                              next step's SpMV (same values, one pass less, but
                              a division per gathered entry: measured slower on
                              the 3-D stencil); 0 (default): its own kernel    */
-    int32_t trsv_kernel;  /* ILU(0) triangular solves: 2 (and 0, the default)
-                             = one cooperative launch per triangle that
-                             solves level by level with a grid barrier
-                             between levels; 1 = one warp per row, rows
-                             claimed in level order, waits on per-row ready
-                             flags (measured slower on 2-D and 3-D stencils
-                             and on a 2M-row power-law matrix)               */
+    int32_t trsv_kernel;  /* ILU(0) triangular solves, one launch per
+                             triangle: 3 = cooperative, no barrier: the
+                             solution entries start as an all-ones NaN
+                             pattern and each warp polls its rows'
+                             dependencies' entries, level after level;
+                             2 = cooperative, a grid barrier between levels;
+                             1 = one warp per row, rows claimed in level
+                             order, per-row ready flags.  0 (default): per
+                             triangle, 3 when every row has at most four
+                             entries in it and every level fits the grid,
+                             else 2                                          */
 } gmres_opts;
 
 /* Kernel classes reported in gmres_info (index into kernel_ms / kernel_bytes). */
@@ -414,8 +418,8 @@ gmres_status gmres_memory_bytes(gmres_t h, int32_t m, gmres_precision prec, int6
  * the pattern), kept in binary64 and binary32.  Select it with opts.precond
  * = 2: every solve then applies M^-1 = (L U)^-1 on the left (Alg. 1:
  * r = M^-1 z, w = M^-1 A v_j; the convergence test stays on ||b - A x||), on
- * the grid path, with sync-free triangular solves (ready flags, bounded
- * waits).  gmres_set_values drops the factors.  Errors: GMRES_ERR_ARG (rows
+ * the grid path, with level-scheduled triangular solves (opts.trsv_kernel;
+ * bounded waits).  gmres_set_values drops the factors.  Errors: GMRES_ERR_ARG (rows
  * not sorted, a missing diagonal entry, split storage), GMRES_ERR_BREAKDOWN
  * (a zero or non-finite pivot), GMRES_ERR_OOM, GMRES_ERR_CUDA. */
 gmres_status gmres_ilu0(gmres_t h);
@@ -424,6 +428,13 @@ gmres_status gmres_ilu0(gmres_t h);
  * A's pattern: L's strictly lower entries, U's upper entries with the
  * diagonal).  GMRES_ERR_ARG before gmres_ilu0. */
 gmres_status gmres_ilu_factors(gmres_t h, double *lu);
+
+/* Dependency levels of the two triangles of gmres_ilu0's factors: *lower
+ * for L y = z (row i waits for the rows k < i of its pattern), *upper for
+ * U x = y (row i waits for the j > i).  Each triangular solve passes its
+ * levels in sequence, so its time is about levels x the per-level latency.
+ * GMRES_ERR_ARG before gmres_ilu0 or for a null pointer. */
+gmres_status gmres_ilu_levels(gmres_t h, int32_t *lower, int32_t *upper);
 
 /* out = (L U)^-1 z with the factors of gmres_ilu0: z, out device vectors of
  * n binary64 (GMRES_FP64) or binary32 (otherwise) values, binary64 or

@@ -1004,7 +1004,7 @@ gmres_status validate_opts(const gmres_opts *o) {
         (o->orth_norm != GMRES_ORTH_OFF && !(o->orth_threshold > 0)) ||
         o->repeat_first < -1 || o->repeat_first > 1 || o->precond < 0 || o->precond > 2 ||
         o->ilu_binary32 < 0 || o->ilu_binary32 > 1 || o->normalize_fused < 0 ||
-        o->normalize_fused > 1 || o->trsv_kernel < 0 || o->trsv_kernel > 2)
+        o->normalize_fused > 1 || o->trsv_kernel < 0 || o->trsv_kernel > 3)
         return GMRES_ERR_ARG;
     return GMRES_OK;
 }
@@ -1627,6 +1627,14 @@ gmres_status gmres_ilu0(gmres_t h) {
     if (h->nnz == 0)
         return GMRES_ERR_ARG;
     return ilu_factor(h);
+}
+
+gmres_status gmres_ilu_levels(gmres_t h, int32_t *lower, int32_t *upper) {
+    if (!h || !lower || !upper || !h->ilu_ok)
+        return GMRES_ERR_ARG;
+    *lower = h->ilu_levels;
+    *upper = h->ilu_ulevels;
+    return GMRES_OK;
 }
 
 gmres_status gmres_ilu_factors(gmres_t h, double *lu) {

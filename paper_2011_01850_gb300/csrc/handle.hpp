@@ -97,6 +97,7 @@ struct gmres_handle {
     int ilu_ok = 0;
     int ilu_levels = 0;
     int ilu_ulevels = 0;
+    bool ilu_wave_ok[2] = {false, false};  // L, U suit the barrier-free solve
     unsigned ilu_epoch = 1;
     unsigned mgs_round = 0;      // next exchange round number (0: flags not set up)
     int64_t chunk = 0;     // rows per block

@@ -13,9 +13,10 @@
 // for bit.  A binary32 copy serves the binary32 restart cycle.
 //
 // Triangular solves.  L y = z (unit lower) and U x = y run as one persistent
-// launch each, in one of two forms.  The level form walks the level schedule
-// with a grid barrier between levels (k_trsv_levels, below).  The flag form
-// has no level barriers: each warp claims the next row of the
+// launch each, in one of three forms.  The barrier-free form polls the
+// dependencies' solution entries themselves (k_trsv_wave); the level form
+// walks the level schedule with a grid barrier between levels
+// (k_trsv_levels).  The flag form: each warp claims the next row of the
 // triangle's level schedule from a counter (every row a claimed row depends
 // on sits in an earlier level, so a running warp claimed it earlier, and a
 // whole level is in flight at once); its lanes wait on the dependencies'
@@ -311,6 +312,190 @@ cudaError_t launch_trsv_levels(gmres_handle *h, const AT *lu, const T *in, T *ou
                                        dim3(TRSV_LV_THREADS), args, 0, h->stream);
 }
 
+// The same triangle without a barrier: the solution vector is its own
+// ready flag.  Before the launch every entry of `out` is set to the all-ones
+// bit pattern (a NaN that the solve never stores: a computed value with that
+// pattern is stored as the canonical NaN instead); a row polls its
+// dependencies' entries until none holds the pattern.  Values are single
+// aligned words, stored and polled with relaxed gpu-scope accesses.  Every
+// warp walks all levels in step: at each level it takes its 32-row runs
+// (interleaved over the blocks, as in k_trsv_levels), and its lanes poll
+// together until every lane's dependencies are in, so the warp never
+// diverges across a wait.  Every dependency sits in an earlier level, which
+// each warp finishes before it starts a later one, so with all blocks
+// resident (cooperative launch) every wait ends; a wait that runs past `spin`
+// polls, or sees another warp's report, reports a timeout in *err.
+template <class T>
+struct WordOf;
+template <>
+struct WordOf<float> {
+    using U = unsigned;
+    static constexpr U none = 0xffffffffu;
+    static constexpr U qnan = 0x7fc00000u;
+};
+template <>
+struct WordOf<double> {
+    using U = unsigned long long;
+    static constexpr U none = ~0ull;
+    static constexpr U qnan = 0x7ff8000000000000ull;
+};
+
+__device__ __forceinline__ unsigned ld_relaxed_w(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned long long ld_relaxed_w(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed_w(unsigned *p, unsigned v) {
+    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void st_relaxed_w(unsigned long long *p, unsigned long long v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ float word_value(unsigned u) { return __uint_as_float(u); }
+__device__ __forceinline__ double word_value(unsigned long long u) {
+    return __longlong_as_double((long long)u);
+}
+__device__ __forceinline__ unsigned value_word(float v) { return __float_as_uint(v); }
+__device__ __forceinline__ unsigned long long value_word(double v) {
+    return (unsigned long long)__double_as_longlong(v);
+}
+
+// The whole warp polls until every lane's first `cnt` (<= TRSV_PF)
+// dependencies hold values (lanes without a row pass cnt = 0).  All lanes
+// leave together; false (for every lane) on a timeout.
+template <class T, class U>
+__device__ __forceinline__ bool wave_wait_warp(const U *ob, const int *col, int cnt, T *x,
+                                               long long spin, int *err) {
+    unsigned pending = 0;
+#pragma unroll
+    for (int k = 0; k < TRSV_PF; ++k)
+        if (k < cnt)
+            pending |= 1u << k;
+    long long it = 0;
+    for (;;) {
+        U w[TRSV_PF];
+#pragma unroll
+        for (int k = 0; k < TRSV_PF; ++k)
+            if (pending & (1u << k))
+                w[k] = ld_relaxed_w(ob + col[k]);
+#pragma unroll
+        for (int k = 0; k < TRSV_PF; ++k)
+            if ((pending & (1u << k)) && w[k] != WordOf<T>::none) {
+                x[k] = word_value(w[k]);
+                pending &= ~(1u << k);
+            }
+        if (__all_sync(0xffffffffu, pending == 0))
+            return true;
+        const int bad = __shfl_sync(0xffffffffu, *(volatile int *)err, 0);
+        if (bad != 0 || ++it > spin) {
+            if ((threadIdx.x & 31) == 0)
+                atomicExch(err, 1);
+            return false;
+        }
+    }
+}
+
+// Solves the row of r (if any) with the whole warp taking part in the waits.
+template <class T, class AT, bool LOWER>
+__device__ __forceinline__ bool wave_solve_warp(const RowAhead<T, AT> &r, const int *colind,
+                                                const AT *lu, T *out, long long spin, int *err) {
+    using U = typename WordOf<T>::U;
+    U *ob = reinterpret_cast<U *>(out);
+    const int len = r.i >= 0 ? r.e - r.b : 0;
+    const int cnt = len < TRSV_PF ? len : TRSV_PF;
+    T x[TRSV_PF];
+    if (!wave_wait_warp<T, U>(ob, r.col, cnt, x, spin, err))
+        return false;
+    T acc = r.rhs;
+#pragma unroll
+    for (int k = 0; k < TRSV_PF; ++k)
+        if (k < cnt)
+            acc = sub_rn(acc, mul_rn((T)r.val[k], x[k]));
+    // entries past the first TRSV_PF: one at a time, the warp in step
+    const int more = __reduce_max_sync(0xffffffffu, len > TRSV_PF ? len - TRSV_PF : 0);
+    for (int q = 0; q < more; ++q) {
+        const bool mine = TRSV_PF + q < len;
+        const int j = mine ? colind[r.b + TRSV_PF + q] : 0;
+        T xj = 0;
+        if (!wave_wait_warp<T, U>(ob, &j, mine ? 1 : 0, &xj, spin, err))
+            return false;
+        if (mine)
+            acc = sub_rn(acc, mul_rn((T)lu[r.b + TRSV_PF + q], xj));
+    }
+    if (r.i >= 0) {
+        if (!LOWER)
+            acc = acc / (T)r.diag;
+        U word = value_word(acc);
+        if (word == WordOf<T>::none)
+            word = WordOf<T>::qnan;
+        st_relaxed_w(ob + r.i, word);
+    }
+    return true;
+}
+
+constexpr int TRSV_WAVE_THREADS = 512;
+
+template <class T, class AT, bool LOWER>
+__global__ void __launch_bounds__(TRSV_WAVE_THREADS, 1)
+    k_trsv_wave(int nlev, const int *lptr, const int *order, const int *rowptr,
+                const int *colind, const int *dpos, const AT *lu, const T *in, T *out,
+                long long spin, int *err) {
+    const int lane = threadIdx.x & 31;
+    const int wbase = (blockIdx.x + gridDim.x * (threadIdx.x >> 5)) * 32;  // warp-uniform
+    const int stride = gridDim.x * blockDim.x;
+    RowAhead<T, AT> r;
+    int lo = __ldg(lptr), hi = __ldg(lptr + 1);
+    trsv_load_row<T, AT, LOWER>(r, lo + wbase + lane, hi, order, rowptr, colind, dpos, lu, in);
+    for (int l = 0; l < nlev; ++l) {
+        const int hi2 = l + 1 < nlev ? __ldg(lptr + l + 2) : hi;
+        RowAhead<T, AT> nx;
+        trsv_load_row<T, AT, LOWER>(nx, hi + wbase + lane, hi2, order, rowptr, colind, dpos, lu,
+                                    in);
+        if (lo + wbase < hi && !wave_solve_warp<T, AT, LOWER>(r, colind, lu, out, spin, err))
+            return;
+        for (int base = lo + wbase + stride; base < hi; base += stride) {
+            RowAhead<T, AT> q;
+            trsv_load_row<T, AT, LOWER>(q, base + lane, hi, order, rowptr, colind, dpos, lu, in);
+            if (!wave_solve_warp<T, AT, LOWER>(q, colind, lu, out, spin, err))
+                return;
+        }
+        r = nx;
+        lo = hi;
+        hi = hi2;
+    }
+}
+
+template <class T, class AT, bool LOWER>
+cudaError_t launch_trsv_wave(gmres_handle *h, const AT *lu, const T *in, T *out, long long spin,
+                             int *err) {
+    static int per_sm = -1;
+    if (per_sm < 0) {
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &per_sm, k_trsv_wave<T, AT, LOWER>, TRSV_WAVE_THREADS, 0);
+        if (e != cudaSuccess)
+            return e;
+    }
+    if (per_sm < 1)
+        return cudaErrorCooperativeLaunchTooLarge;
+    // every entry starts as the all-ones pattern (not yet solved)
+    cudaError_t e = cudaMemsetAsync(out, 0xff, sizeof(T) * (size_t)h->n, h->stream);
+    if (e != cudaSuccess)
+        return e;
+    int nlev = LOWER ? h->ilu_levels : h->ilu_ulevels;
+    const int *lptr = h->ilu_lptr.as<int>() + (LOWER ? 0 : h->ilu_levels + 1);
+    const int *order = h->ilu_order.as<int>() + (LOWER ? 0 : h->n);
+    const int *rowptr = h->rowptr.as<int>(), *colind = h->colind.as<int>(),
+              *dpos = h->ilu_dpos.as<int>();
+    void *args[] = {&nlev, &lptr, &order, &rowptr, &colind, &dpos, &lu, &in, &out, &spin, &err};
+    return cudaLaunchCooperativeKernel((const void *)k_trsv_wave<T, AT, LOWER>, dim3(h->nsm),
+                                       dim3(TRSV_WAVE_THREADS), args, 0, h->stream);
+}
+
 template <class T, class AT, bool LOWER>
 cudaError_t launch_trsv(gmres_handle *h, const AT *lu, const T *in, T *out, unsigned *flags,
                         unsigned epoch, unsigned *counter, long long spin, int *err) {
@@ -332,6 +517,16 @@ cudaError_t launch_trsv(gmres_handle *h, const AT *lu, const T *in, T *out, unsi
                                                        order, lu, in, out, flags, epoch, counter,
                                                        spin, err);
     return cudaGetLastError();
+}
+
+template <class T, class AT, bool LOWER>
+cudaError_t launch_triangle(gmres_handle *h, const AT *lu, const T *in, T *out, unsigned *flags,
+                            unsigned epoch, unsigned *ctr, long long spin, int *err) {
+    switch (gmres::trsv_kind(h, LOWER)) {
+    case 3: return launch_trsv_wave<T, AT, LOWER>(h, lu, in, out, spin, err);
+    case 2: return launch_trsv_levels<T, AT, LOWER>(h, lu, in, out, ctr, spin, err);
+    default: return launch_trsv<T, AT, LOWER>(h, lu, in, out, flags, epoch, ctr, spin, err);
+    }
 }
 
 }  // namespace
@@ -441,11 +636,32 @@ gmres_status ilu_factor(gmres_handle *h) {
     h->ilu_epoch = 1;
     h->ilu_levels = nlev;
     h->ilu_ulevels = nulev;
+    // the barrier-free solve suits triangles whose rows all fit the entries
+    // loaded ahead (longer rows wait on one entry at a time) and whose
+    // levels fit the grid in one pass
+    {
+        int lmax = 0, umax = 0, lwidth = 0, uwidth = 0;
+        for (int i = 0; i < n; ++i) {
+            lmax = std::max(lmax, dpos[i] - rp[i]);
+            umax = std::max(umax, rp[i + 1] - dpos[i] - 1);
+        }
+        for (int l = 0; l < nlev; ++l)
+            lwidth = std::max(lwidth, lptr[l + 1] - lptr[l]);
+        for (int l = 0; l < nulev; ++l)
+            uwidth = std::max(uwidth, uptr[l + 1] - uptr[l]);
+        const int slots = h->nsm * TRSV_WAVE_THREADS;
+        h->ilu_wave_ok[0] = lmax <= TRSV_PF && lwidth <= slots;
+        h->ilu_wave_ok[1] = umax <= TRSV_PF && uwidth <= slots;
+    }
     h->ilu_ok = bad ? 0 : 1;
     return bad ? GMRES_ERR_BREAKDOWN : GMRES_OK;
 }
 
-bool trsv_uses_levels(const gmres_handle *h) { return h->opts.trsv_kernel != 1; }
+int trsv_kind(const gmres_handle *h, bool lower) {
+    if (h->opts.trsv_kernel != 0)
+        return h->opts.trsv_kernel;
+    return (lower ? h->ilu_wave_ok[0] : h->ilu_wave_ok[1]) ? 3 : 2;
+}
 
 template <class T, class AT>
 cudaError_t ilu_apply(gmres_handle *h, const AT *lu, const T *z, T *tmp, T *out, int *err) {
@@ -465,16 +681,12 @@ cudaError_t ilu_apply(gmres_handle *h, const AT *lu, const T *z, T *tmp, T *out,
     // a legitimate wait lasts at most the dependency chain (a few hundred
     // rows of latency); 2^22 polls is seconds, far beyond it
     const long long spin = h->opts.spin_limit > 0 ? h->opts.spin_limit : (1LL << 22);
-    if (trsv_uses_levels(h)) {
-        cudaError_t e = launch_trsv_levels<T, AT, true>(h, lu, z, tmp, ctr, spin, err);
-        if (e != cudaSuccess)
-            return e;
-        return launch_trsv_levels<T, AT, false>(h, lu, tmp, out, ctr + 1, spin, err);
-    }
-    cudaError_t e = launch_trsv<T, AT, true>(h, lu, z, tmp, lflags, e0, ctr, spin, err);
+    // the lower solve has read z before the upper solve starts writing out
+    // (they may be the same vector)
+    cudaError_t e = launch_triangle<T, AT, true>(h, lu, z, tmp, lflags, e0, ctr, spin, err);
     if (e != cudaSuccess)
         return e;
-    return launch_trsv<T, AT, false>(h, lu, tmp, out, uflags, e0, ctr + 1, spin, err);
+    return launch_triangle<T, AT, false>(h, lu, tmp, out, uflags, e0, ctr + 1, spin, err);
 }
 
 template cudaError_t ilu_apply<double, double>(gmres_handle *, const double *, const double *,

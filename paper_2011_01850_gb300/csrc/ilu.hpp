@@ -17,9 +17,10 @@ gmres_status ilu_factor(gmres_handle *h);
 
 // out = (L U)^-1 z on the device: L y = z into tmp, then U out = tmp (T
 // arithmetic, factors of type AT); a wait that runs out sets *err.
-// Whether ilu_apply runs the level-barrier triangular solves (opts.trsv_kernel
-// 0 or 2) rather than the flag-driven ones (1).
-bool trsv_uses_levels(const gmres_handle *h);
+// Kernel of one triangular solve: opts.trsv_kernel when set, else 3 (no
+// barrier) for a triangle whose rows hold at most four entries and whose
+// levels fit the grid, 2 (level barrier) otherwise.
+int trsv_kind(const gmres_handle *h, bool lower);
 
 template <class T, class AT>
 cudaError_t ilu_apply(gmres_handle *h, const AT *lu, const T *z, T *tmp, T *out, int *err);

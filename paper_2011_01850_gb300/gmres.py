@@ -121,6 +121,7 @@ SIGNATURES = {
     "gmres_ilu0": (_st, [_vp]),
     "gmres_ilu_apply": (_st, [_vp, _vp, _vp, _i32]),
     "gmres_ilu_factors": (_st, [_vp, _vp]),
+    "gmres_ilu_levels": (_st, [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
     "gmres_batch_autotune": (_st, [_vp, _vp, _i32, _i32, _i32, _i32, ctypes.POINTER(_i32)]),
     "gmres_batch_set_cluster_rows": (_st, [_vp, _i32]),
     "gmres_batch_create": (_st, [ctypes.POINTER(_vp), _i32, _vp, _vp, _vp, _vp, _vp]),
@@ -303,6 +304,13 @@ def gmres_batch_autotune(h, rhs, m, ortho, prec, iters):
 def gmres_ilu0(h):
     """ILU(0) factors of the handle's matrix (select with precond=2)."""
     return _check(lib().gmres_ilu0(h), "gmres_ilu0")
+
+
+def gmres_ilu_levels(h):
+    """(levels of L, levels of U) of the ILU(0) factors."""
+    lo, up = _i32(), _i32()
+    _check(lib().gmres_ilu_levels(h, ctypes.byref(lo), ctypes.byref(up)), "gmres_ilu_levels")
+    return lo.value, up.value
 
 
 def gmres_ilu_factors(h, nnz):

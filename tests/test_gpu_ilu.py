@@ -40,7 +40,7 @@ def test_ilu_factors_bitwise(case, gpulib):
     assert np.array_equal(lu, O.ilu0(A)[2])
 
 
-TRSV = [(1, "flags"), (2, "levels")]
+TRSV = [(1, "flags"), (2, "levels"), (3, "wave")]
 
 
 @pytest.mark.parametrize("trsv", TRSV, ids=[t[1] for t in TRSV])
@@ -112,6 +112,27 @@ def test_ilu_solve(prec, trsv, gpulib):
     assert info["iters"] < plain["iters"]
 
 
+def test_ilu_level_counts(gpulib):
+    """An N^3 7-point grid in natural order has 3N - 2 dependency levels in
+    each triangle (level of (x, y, z) = x + y + z); a 2-D N x M grid has
+    N + M - 1; a diagonal matrix has one."""
+    for A, want in ((I.convdiff3d(11, eps=(0.1, 0.1, 0.1), seed=1), 31),
+                    (I.convdiff2d(9, 13, pe=10.0), 21)):
+        s = G.Solver(A)
+        with pytest.raises(G.GmresError):
+            G.gmres_ilu_levels(s.h)
+        G.gmres_ilu0(s.h)
+        assert G.gmres_ilu_levels(s.h) == (want, want)
+        s.close()
+    n = 50
+    D = (np.arange(n + 1, dtype=np.int32), np.arange(n, dtype=np.int32),
+         np.linspace(1.0, 2.0, n))
+    s = G.Solver(D)
+    G.gmres_ilu0(s.h)
+    assert G.gmres_ilu_levels(s.h) == (1, 1)
+    s.close()
+
+
 def test_ilu_levels_large_and_short_waits(gpulib):
     """Both triangular-solve kernels on a 3-D stencil wide enough that a
     level spans many warps (48^3: 142 levels of up to 1 700 rows); with a
@@ -124,12 +145,12 @@ def test_ilu_levels_large_and_short_waits(gpulib):
     s = G.Solver(A)
     G.gmres_ilu0(s.h)
     out = torch.zeros(n, device="cuda", dtype=torch.float64)
-    for k in (1, 2, 0):
+    for k in (1, 2, 3, 0):
         s.set_opts(trsv_kernel=k)
         out.zero_()
         G.gmres_ilu_apply(s.h, dev(z), out, G.FP64)
         assert np.array_equal(out.cpu().numpy(), want), k
-    for k in (1, 2):
+    for k in (1, 2, 3):
         s.set_opts(trsv_kernel=k, spin_limit=1)
         try:
             G.gmres_ilu_apply(s.h, dev(z), out, G.FP64)
