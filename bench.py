@@ -60,6 +60,8 @@ def parse():
     p.add_argument("--trsv-kernel", type=int, default=None,
                    help="ILU(0) triangular solves: 1 per-row flags, 2 level barrier, "
                         "3 barrier-free (library default: 3 or 2 per triangle)")
+    p.add_argument("--batch-ortho", default="mgs", choices=["mgs", "cgsr"],
+                   help="batched workload: orthogonalisation of the timed solves")
     p.add_argument("--spmv-lanes", type=int, default=0,
                    help="lanes per CSR row (0: autotuned)")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -447,13 +449,14 @@ def bench_batched(args, world, rank, local):
     dx = torch.zeros(len(b), device="cuda", dtype=torch.float64)
     m = 30
     # SpMV lanes per row from the library's autotuner (capped solves, untimed)
-    lanes = {p_: G.gmres_batch_autotune(h, db, m, G.ORTHO_MGS, G.PRECISIONS[p_], 2 * m)
+    bortho = {"mgs": G.ORTHO_MGS, "cgsr": G.ORTHO_CGSR}[args.batch_ortho]
+    lanes = {p_: G.gmres_batch_autotune(h, db, m, bortho, G.PRECISIONS[p_], 2 * m)
              for p_ in ("fp64", "mixed")}
 
     def step(prec, collect):
         # the tuned choice for this precision (lanes = 0 would reuse the last one tuned)
         dx.zero_()
-        st, res, info = G.gmres_batch_solve(h, db, dx, m, 1e-10, G.ORTHO_MGS,
+        st, res, info = G.gmres_batch_solve(h, db, dx, m, 1e-10, bortho,
                                             G.PRECISIONS[prec], 100000, lanes=lanes[prec],
                                             nsys=nsys)
         if st != G.OK:
@@ -505,7 +508,7 @@ def bench_batched(args, world, rank, local):
         t0 = time.perf_counter()
         for _ in range(args.steps):
             xh[:] = 0
-            st, res, info = G.gmres_batch_solve(h, b, xh, m, 1e-10, G.ORTHO_MGS, G.MIXED,
+            st, res, info = G.gmres_batch_solve(h, b, xh, m, 1e-10, bortho, G.MIXED,
                                                 100000, nsys=nsys)
             assert st == G.OK
         e2e = {"value": round((time.perf_counter() - t0) * 1e3 / args.steps, 3), "unit": "ms",
@@ -521,7 +524,7 @@ def bench_batched(args, world, rank, local):
         "warmup": args.warmup, "ms_per_step": round(ms_step, 3), "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "batched2048", "systems": nsys, "rows": int(len(b)),
-                   "nnz": int(len(ci)), "m": m, "ortho": "mgs", "precision": "mixed",
+                   "nnz": int(len(ci)), "m": m, "ortho": args.batch_ortho, "precision": "mixed",
                    "tol": 1e-10,
                    "launch": "one-block and 8-block-cluster persistent launches, concurrent",
                    "spmv_lanes": lanes, "l2": "inputs larger than L2"},
