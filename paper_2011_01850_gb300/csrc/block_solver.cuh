@@ -282,19 +282,34 @@ __device__ void team_solve_one(const BlockSys<T, VT> &S, const BlockParams &P, B
                 w0 += S.w[i] * S.w[i];
             T wnorm0 = wsqrt(team_sum1<T, CS>(w0, red, slot, bc, &buft));
             if (P.ortho == 0) {
-                // MGS: h_i = w . v_i, w <- w - h_i v_i, one column at a time
+                // MGS: h_i = w . v_i, w <- w - h_i v_i, one column at a time.
+                // Every thread owns the rows rb + tid + k nth, so the update
+                // of column i and the dot product of column i + 1 share one
+                // pass over the rows: each row is updated, then multiplied,
+                // the same operations in the same order as two passes, with
+                // one pass of latency per column instead of two.
+                T d = 0;
+                for (int r = rb + tid; r < re; r += nth)
+                    d += S.w[r] * Basis<VT>::ld(S.V + r, S.vinv);
                 for (int i = 0; i <= c; ++i) {
-                    const VT *vi = S.V + (size_t)i * S.ldv;
-                    T d = 0;
-                    for (int r = rb + tid; r < re; r += nth)
-                        d += S.w[r] * Basis<VT>::ld(vi + r, S.vinv);
-                    T hi = team_sum1<T, CS>(d, red, slot, bc, &buft);
-                    for (int r = rb + tid; r < re; r += nth)
-                        S.w[r] = S.w[r] - hi * Basis<VT>::ld(vi + r, S.vinv);
+                    const T hi = team_sum1<T, CS>(d, red, slot, bc, &buft);
                     if (tid == 0)
                         hc[i] = hi;
-                    __syncthreads();
+                    const VT *vi = S.V + (size_t)i * S.ldv;
+                    d = 0;
+                    if (i < c) {
+                        const VT *vn = vi + S.ldv;
+                        for (int r = rb + tid; r < re; r += nth) {
+                            const T wr = S.w[r] - hi * Basis<VT>::ld(vi + r, S.vinv);
+                            S.w[r] = wr;
+                            d += wr * Basis<VT>::ld(vn + r, S.vinv);
+                        }
+                    } else {
+                        for (int r = rb + tid; r < re; r += nth)
+                            S.w[r] = S.w[r] - hi * Basis<VT>::ld(vi + r, S.vinv);
+                    }
                 }
+                __syncthreads();
             } else {
                 // CGSR: two classical passes, column = sum of both
                 for (int pass = 0; pass < 2; ++pass) {
