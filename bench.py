@@ -55,6 +55,8 @@ def parse():
                    help="block path: 1 block or an 8-block cluster per system (library default)")
     p.add_argument("--fuse-normalize", action="store_true",
                    help="form v_{j+1} inside the next SpMV instead of in its own kernel")
+    p.add_argument("--cluster-threads", type=int, default=None,
+                   help="batched: threads per block of the large systems' clusters")
     p.add_argument("--cluster-rows", type=int, default=None,
                    help="batched: systems of at least this many rows use 8-block clusters")
     p.add_argument("--trsv-kernel", type=int, default=None,
@@ -445,6 +447,8 @@ def bench_batched(args, world, rank, local):
     h = G.gmres_batch_create(nsys, sys_ptr, rp, ci, va, stream=stream)
     if args.cluster_rows is not None:
         G.gmres_batch_set_cluster_rows(h, args.cluster_rows)
+    if args.cluster_threads is not None:
+        G.gmres_batch_set_cluster_threads(h, args.cluster_threads)
     db = torch.tensor(b, device="cuda", dtype=torch.float64)
     dx = torch.zeros(len(b), device="cuda", dtype=torch.float64)
     m = 30

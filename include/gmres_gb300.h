@@ -363,6 +363,15 @@ gmres_status gmres_batch_solve(gmres_batch_t b, const double *rhs, double *x, in
  * GMRES_ERR_ARG for min_rows < 0. */
 gmres_status gmres_batch_set_cluster_rows(gmres_batch_t b, int32_t min_rows);
 
+/* Threads per block of the clusters that solve the large systems (128, 256,
+ * 512 or 1024; the one-block systems always use 256).  More threads give a
+ * cluster fewer rows per thread, so a shorter chain of memory latencies per
+ * inner iteration, and fewer clusters fit the GPU at once.  Default 256
+ * (2048 uneven 2-D systems: 2.30 s, against 2.50 s at 512 and 3.09 s at
+ * 1024: the batch is bound by throughput, not by its slowest system).
+ * GMRES_ERR_ARG for any other value. */
+gmres_status gmres_batch_set_cluster_threads(gmres_batch_t b, int32_t threads);
+
 /* SpMV tile autotuner of the batched solver: times a capped solve (iters
  * inner iterations per system, from x0 = 0, on scratch memory; the batch's
  * x is not touched) with 1, 2, 4, 8 and 16 lanes per CSR row and keeps the

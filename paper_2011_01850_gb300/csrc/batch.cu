@@ -26,6 +26,17 @@
 using namespace gmres;
 using namespace gmres_host;
 
+// Systems of at least this many rows are solved by a cluster of CLUSTER_CTAS
+// thread blocks (distributed-shared-memory reductions); smaller ones by one
+// block.  Both launches run concurrently, each over its own work queue.
+constexpr int CLUSTER_MIN_ROWS = 8192;
+constexpr int CLUSTER_CTAS = 8;
+// Threads per block of the cluster launch (the one-block launch uses 256).
+// More threads give the large systems' clusters fewer rows per thread (a
+// shorter latency chain per inner iteration) but fewer clusters at once;
+// measured on 2048 uneven systems, 256 is fastest.
+constexpr int CLUSTER_THREADS = 256;
+
 struct gmres_batch {
     int nsys = 0;
     int64_t nrows = 0, nnz = 0;
@@ -38,17 +49,13 @@ struct gmres_batch {
     std::vector<int> order;         // largest system first
     int nlarge = 0;                 // systems solved by clusters (the first nlarge of order)
     int tuned_lanes = 0;            // lanes per row chosen by gmres_batch_autotune (0: none)
+    int cluster_threads = CLUSTER_THREADS;  // threads per block of the cluster launch
     cudaStream_t aux = nullptr;     // stream of the cluster launch
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     DevBuf rowptr, colind, vals64, vals32;
     DevBuf V, w, r, xb, bb, sys, res, ord, queue;
 };
 
-// Systems of at least this many rows are solved by a cluster of CLUSTER_CTAS
-// thread blocks (distributed-shared-memory reductions); smaller ones by one
-// block.  Both launches run concurrently, each over its own work queue.
-constexpr int CLUSTER_MIN_ROWS = 8192;
-constexpr int CLUSTER_CTAS = 8;
 
 // The systems of at least min_rows rows (0: none) go to clusters: they are
 // the first nlarge entries of the largest-first order.
@@ -144,7 +151,7 @@ gmres_status batch_run(gmres_batch *B, const double *db, double *dx, int m, doub
     cudaLaunchAttribute attr[1];
     int ncl = 0;
     if (B->nlarge > 0) {
-        cfg.blockDim = dim3(threads);
+        cfg.blockDim = dim3(B->cluster_threads);
         cfg.dynamicSmemBytes = smem;
         cfg.stream = B->aux;
         attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -469,6 +476,13 @@ gmres_status gmres_batch_set_cluster_rows(gmres_batch_t B, int32_t min_rows) {
     if (!B || min_rows < 0)
         return GMRES_ERR_ARG;
     set_nlarge(B, min_rows);
+    return GMRES_OK;
+}
+
+gmres_status gmres_batch_set_cluster_threads(gmres_batch_t B, int32_t threads) {
+    if (!B || (threads != 128 && threads != 256 && threads != 512 && threads != 1024))
+        return GMRES_ERR_ARG;
+    B->cluster_threads = threads;
     return GMRES_OK;
 }
 

@@ -124,6 +124,7 @@ SIGNATURES = {
     "gmres_ilu_levels": (_st, [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
     "gmres_batch_autotune": (_st, [_vp, _vp, _i32, _i32, _i32, _i32, ctypes.POINTER(_i32)]),
     "gmres_batch_set_cluster_rows": (_st, [_vp, _i32]),
+    "gmres_batch_set_cluster_threads": (_st, [_vp, _i32]),
     "gmres_batch_create": (_st, [ctypes.POINTER(_vp), _i32, _vp, _vp, _vp, _vp, _vp]),
     "gmres_batch_destroy": (None, [_vp]),
     "gmres_batch_solve": (_st, [_vp, _vp, _vp, _i32, _f64, _i32, _i32, _i32, _i32, _vp,
@@ -290,6 +291,11 @@ def gmres_batch_set_cluster_rows(h, min_rows):
     """Systems of at least min_rows rows go to 8-block clusters (0: none)."""
     return _check(lib().gmres_batch_set_cluster_rows(h, int(min_rows)),
                   "gmres_batch_set_cluster_rows")
+
+def gmres_batch_set_cluster_threads(h, threads):
+    """Threads per block of the clusters that solve the large systems."""
+    return _check(lib().gmres_batch_set_cluster_threads(h, int(threads)),
+                  "gmres_batch_set_cluster_threads")
 
 
 def gmres_batch_autotune(h, rhs, m, ortho, prec, iters):

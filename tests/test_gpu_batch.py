@@ -154,3 +154,31 @@ def test_batch_cluster_threshold(gpulib):
     with pytest.raises(G.GmresError):
         G.gmres_batch_set_cluster_rows(h, -1)
     G.gmres_batch_destroy(h)
+
+
+@pytest.mark.parametrize("threads", [128, 512, 1024])
+def test_batch_cluster_threads(threads, gpulib):
+    """The large systems' clusters run with any block size the setting
+    allows (the rows are split over more or fewer threads); every system
+    still converges to the binary64 target, in a number of iterations close
+    to the oracle's."""
+    systems = [(I.convdiff2d(110, 97, pe=30.0), None), (I.convdiff2d(90, 120, pe=5.0), None)]
+    systems += I.batched_convdiff2d(count=4, nmin=100, nmax=3000, seed=13)
+    out = [(A, I.rhs_ones_noise(A, 1e-3, 500 + k) if b is None else b)
+           for k, (A, b) in enumerate(systems)]
+    sys_ptr, rp, ci, va, b = G.pack_batch(out)
+    h = G.gmres_batch_create(len(out), sys_ptr, rp, ci, va)
+    G.gmres_batch_set_cluster_threads(h, threads)
+    x = np.zeros(len(b))
+    st, res, info = G.gmres_batch_solve(h, b, x, 30, 1e-10, G.ORTHO_MGS, G.MIXED, 20000,
+                                        nsys=len(out))
+    assert st == G.OK and info.kernel_launches[G.K_BLOCK] == 2
+    for i, (A, bi) in enumerate(out):
+        xi = x[sys_ptr[i]:sys_ptr[i + 1]]
+        assert O.residual_norm(A, bi, xi) / np.linalg.norm(bi) <= 1e-10
+    _, oi = O.gmres(out[0][0], out[0][1], m=30, ortho=O.MGS, prec=O.MIXED)
+    assert abs(res[0].iters - oi["iters"]) <= max(3, 0.1 * oi["iters"])
+    for bad in (0, 100, 2048):
+        with pytest.raises(G.GmresError):
+            G.gmres_batch_set_cluster_threads(h, bad)
+    G.gmres_batch_destroy(h)
