@@ -337,7 +337,12 @@ __global__ void __launch_bounds__(ROWS_THREADS)
         } else if (SPLIT) {
             // update, split by vectors: every warp sums its vectors over the
             // whole slice (2 KB runs), the partials meet in shared memory and
-            // warp wid forms row group wid as ((p0 + p1) + p2) + p3
+            // warp wid forms row group wid as ((p0 + p1) + p2) + p3.  The
+            // thread's rows of w are loaded first (only this block touches
+            // the slice), so their latency hides under the basis loads.
+            const int64_t r = s0 + wid * RW + lane * RPL;
+            T w[RPL];
+            ld_w<T, RPL>(c.w + r, w);
             T tp[4][RPL];
             rows_project_split<T, VT, RPL, ACC>(c, ncols, hs, s0, wid, lane, tp, pol_keep);
 #pragma unroll
@@ -346,9 +351,6 @@ __global__ void __launch_bounds__(ROWS_THREADS)
                 for (int q = 0; q < RPL; ++q)
                     tsm[wid * SR + g * RW + lane * RPL + q] = tp[g][q];
             __syncthreads();
-            const int64_t r = s0 + wid * RW + lane * RPL;
-            T w[RPL];
-            ld_w<T, RPL>(c.w + r, w);
 #pragma unroll
             for (int q = 0; q < RPL; ++q) {
                 const int o = wid * RW + lane * RPL + q;
@@ -463,8 +465,14 @@ __global__ void __launch_bounds__(PB_THREADS)
     int64_t sl1 = sl0 + slices_per_block;
     if (sl1 > nslices)
         sl1 = nslices;
+    // w of a slice is read one slice ahead (only this block touches its
+    // slices), so the update below does not wait for it
+    float wcur = (threadIdx.x < PB_ROWS && sl0 < sl1) ? c.w[sl0 * PB_ROWS + threadIdx.x] : 0.f;
     for (int64_t sl = sl0; sl < sl1; ++sl) {
         const int64_t s0 = sl * PB_ROWS;
+        const float wnext = (threadIdx.x < PB_ROWS && sl + 1 < sl1)
+                                ? c.w[s0 + PB_ROWS + threadIdx.x]
+                                : 0.f;
         float v[KC][4];
 #pragma unroll
         for (int k = 0; k < KC; ++k) {
@@ -493,10 +501,11 @@ __global__ void __launch_bounds__(PB_THREADS)
 #pragma unroll
             for (int w = 1; w < PB_WARPS; ++w)
                 t += tsm[w * PB_ROWS + r];
-            const float wn = c.w[s0 + r] - t;
+            const float wn = wcur - t;
             c.w[s0 + r] = wn;
             wsl[r] = wn;
         }
+        wcur = wnext;
         __syncthreads();
         const float4 wv = *reinterpret_cast<const float4 *>(wsl + lane * 4);
 #pragma unroll
