@@ -187,9 +187,9 @@ COMPARE = {
 }
 SPAI_PARAMS = os.path.join(ROOT, "paper_2011_01850_gb300", "data", "spai_aniso64.npy")
 # DRAM bytes per algorithmic byte of the CGSR passes (binary32 basis), from
-# one ncu capture of a mid-cycle step (51 vectors) at 96^3: 564.2 MB of DRAM
+# one ncu capture of a mid-cycle step (51 vectors) at 96^3: 563.3 MB of DRAM
 # traffic for 559.2 MB algorithmic; scaled to the timed launches.
-CGSR_ROWS_TRAFFIC_RATIO = 1.009
+CGSR_ROWS_TRAFFIC_RATIO = 1.007
 
 
 def bench_ours(args):
