@@ -967,6 +967,19 @@ gmres_status solve_block(gmres_handle *h, const double *b, double *x, int m, dou
     info->bnorm = R.bnorm;
     info->launches += 1;
     info->kernel_launches[GMRES_K_BLOCK] += 1;
+    {
+        // algorithmic bytes of the solve (SpMV + orthogonalisation per inner
+        // step, binary64 residual per cycle), counted as the batched solver does
+        const double n = (double)h->n, nz = (double)h->nnz;
+        const double sv = sizeof(VT), st = sizeof(T);
+        const double cycles = R.restarts, it = R.iters;
+        const double avgc = cycles > 0 ? (it / cycles + 1) / 2 : 0;  // mean basis size
+        const double orth = ortho == GMRES_ORTHO_CGSR ? 3 * avgc * n * sv + 5 * n * st
+                                                      : avgc * n * sv + 2 * n * st;
+        info->kernel_bytes[GMRES_K_BLOCK] +=
+            it * (nz * (st + 4) + 4 * n + n * sv + n * st + orth + n * st + n * sv) +
+            (cycles + 1) * (12 * nz + 4 * n + 24 * n);
+    }
     return (gmres_status)R.status;
 }
 

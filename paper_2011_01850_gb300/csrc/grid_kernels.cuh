@@ -791,6 +791,7 @@ __global__ void __launch_bounds__(256) k_mgs_last(GridCtx<T, VT> c, int ncols) {
 
 // v_{col} = w / h_{j+1,j} (Alg. 1 "v_{j+1} <- w / h_{j+1,j}"), rounded to the
 // basis type.  Skipped when the cycle has ended.
+constexpr int NORM_UNROLL = 8;
 template <class T, class VT>
 __global__ void __launch_bounds__(256) k_normalize(GridCtx<T, VT> c, int col, int force) {
     // force: also on the step that ended the cycle (the loss-of-orthogonality
@@ -802,13 +803,26 @@ __global__ void __launch_bounds__(256) k_normalize(GridCtx<T, VT> c, int col, in
     int64_t rb, re;
     block_rows(c, rb, re);
     VT *dst = c.V + (size_t)col * c.ldv;
-    for (int64_t r = rb + 4 * threadIdx.x; r < re; r += 4 * blockDim.x) {
-        T v[4];
-        ldv4(c.w + r, v);
+    // NORM_UNROLL groups of 4 rows per thread: all their loads are issued
+    // before the first division, so enough bytes are in flight per SM to
+    // stream at HBM speed with two blocks per SM
+    constexpr int U = NORM_UNROLL;
+    const int64_t step = 4 * (int64_t)blockDim.x;
+    for (int64_t r0 = rb + 4 * threadIdx.x; r0 < re; r0 += U * step) {
+        T v[U][4];
 #pragma unroll
-        for (int k = 0; k < 4; ++k)
-            v[k] = v[k] / h;
-        stb4<T, VT>(dst + r, v, c.vscale);
+        for (int u = 0; u < U; ++u)
+            if (r0 + u * step < re)
+                ldv4(c.w + r0 + u * step, v[u]);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (r0 + u * step < re) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    v[u][k] = v[u][k] / h;
+                stb4<T, VT>(dst + r0 + u * step, v[u], c.vscale);
+            }
+        }
     }
 }
 
