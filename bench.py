@@ -62,6 +62,10 @@ def parse():
     p.add_argument("--trsv-kernel", type=int, default=None,
                    help="ILU(0) triangular solves: 1 per-row flags, 2 level barrier, "
                         "3 barrier-free (library default: 3 or 2 per triangle)")
+    p.add_argument("--batch-count", type=int, default=2048,
+                   help="batched workload: number of systems (profiling a smaller batch)")
+    p.add_argument("--batch-rows", type=int, nargs=2, default=[500, 50000],
+                   metavar=("MIN", "MAX"), help="batched workload: range of system sizes")
     p.add_argument("--batch-ortho", default="mgs", choices=["mgs", "cgsr"],
                    help="batched workload: orthogonalisation of the timed solves")
     p.add_argument("--spmv-lanes", type=int, default=0,
@@ -440,7 +444,8 @@ def bench_batched(args, world, rank, local):
     from paper_2011_01850_gb300 import gmres as G
     from paper_2011_01850_gb300 import inputs as I
 
-    systems = I.batched_convdiff2d(count=2048, nmin=500, nmax=50000, seed=batched_seed(rank))
+    systems = I.batched_convdiff2d(count=args.batch_count, nmin=args.batch_rows[0],
+                                   nmax=args.batch_rows[1], seed=batched_seed(rank))
     sys_ptr, rp, ci, va, b = G.pack_batch(systems)
     nsys = len(systems)
     stream = torch.cuda.current_stream()
@@ -454,8 +459,11 @@ def bench_batched(args, world, rank, local):
     m = 30
     # SpMV lanes per row from the library's autotuner (capped solves, untimed)
     bortho = {"mgs": G.ORTHO_MGS, "cgsr": G.ORTHO_CGSR}[args.batch_ortho]
-    lanes = {p_: G.gmres_batch_autotune(h, db, m, bortho, G.PRECISIONS[p_], 2 * m)
-             for p_ in ("fp64", "mixed")}
+    if args.spmv_lanes:
+        lanes = {"fp64": args.spmv_lanes, "mixed": args.spmv_lanes}
+    else:
+        lanes = {p_: G.gmres_batch_autotune(h, db, m, bortho, G.PRECISIONS[p_], 2 * m)
+                 for p_ in ("fp64", "mixed")}
 
     def step(prec, collect):
         # the tuned choice for this precision (lanes = 0 would reuse the last one tuned)
@@ -513,7 +521,7 @@ def bench_batched(args, world, rank, local):
         for _ in range(args.steps):
             xh[:] = 0
             st, res, info = G.gmres_batch_solve(h, b, xh, m, 1e-10, bortho, G.MIXED,
-                                                100000, nsys=nsys)
+                                                100000, lanes=lanes["mixed"], nsys=nsys)
             assert st == G.OK
         e2e = {"value": round((time.perf_counter() - t0) * 1e3 / args.steps, 3), "unit": "ms",
                "h2d_bytes_per_step": 16 * len(b), "d2h_bytes_per_step": 8 * len(b)}
@@ -527,7 +535,8 @@ def bench_batched(args, world, rank, local):
         "value": round(ms_step, 3), "unit": "ms", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_step, 3), "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "batched2048", "systems": nsys, "rows": int(len(b)),
+        "config": {"workload": "batched2048", "systems": nsys,
+                   "system_rows": list(args.batch_rows), "rows": int(len(b)),
                    "nnz": int(len(ci)), "m": m, "ortho": args.batch_ortho, "precision": "mixed",
                    "tol": 1e-10,
                    "launch": "one-block and 8-block-cluster persistent launches, concurrent",
