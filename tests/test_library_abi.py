@@ -65,3 +65,39 @@ def test_host_only_calls(so):
 def test_built_for_sm103a_only():
     # the build passes exactly one -gencode, for sm_103a
     assert B.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_header_is_plain_c_and_links_from_c(so, tmp_path):
+    """The C-ABI is usable from C: the header compiles as C99 with warnings
+    as errors, and a C program linked against the library calls its
+    host-only entry points (status strings, default options, version)."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("gcc not found")
+    src = tmp_path / "use_abi.c"
+    src.write_text(r'''
+#include <stdio.h>
+#include <string.h>
+#include "gmres_gb300.h"
+int main(void) {
+    gmres_opts o;
+    gmres_default_opts(&o);
+    if (o.inner_factor != 0.5 || o.repeat_first != -1 || o.trsv_kernel != 0) return 2;
+    if (strcmp(gmres_status_str(GMRES_OK), "converged") != 0) return 3;
+    if (strstr(gmres_version(), "sm_103a") == NULL) return 4;
+    printf("%s\n", gmres_status_str(GMRES_ERR_ARG));
+    return 0;
+}
+''')
+    lib = B.build()
+    exe = tmp_path / "use_abi"
+    cmd = [gcc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror",
+           "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe),
+           lib, "-Wl,-rpath," + os.path.dirname(lib)]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, (r.returncode, r.stderr)
+    assert r.stdout.strip() == "invalid argument"
