@@ -64,3 +64,24 @@ def test_our_arm_line(gpulib):
     assert isinstance(c["reasons"], list)
     assert d["gpu_launches"] > 0
     assert d["relres"] <= 1e-10
+
+
+def test_reference_arm_under_torchrun():
+    """Launched as the driver launches it for N > 1 (torchrun, 127.0.0.1):
+    rank 0 alone runs the oracle and prints the one line; the other rank
+    exits 0 without work."""
+    import socket
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    r = subprocess.run([sys.executable, "-m", "torch.distributed.run", "--nnodes=1",
+                        "--nproc-per-node", "2", "--master-addr", "127.0.0.1",
+                        "--master-port", str(port), os.path.join(ROOT, "bench.py"),
+                        "--impl", "reference", "--workload", "convdiff3d_24", "--steps", "1",
+                        "--warmup", "0", "--gpus", "2"],
+                       cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1, r.stdout[-2000:]
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
