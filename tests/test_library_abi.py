@@ -101,3 +101,16 @@ int main(void) {
     r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
     assert r.returncode == 0, (r.returncode, r.stderr)
     assert r.stdout.strip() == "invalid argument"
+
+
+def test_no_library_no_fallback(monkeypatch, tmp_path):
+    """Without the compiled library every entry point raises: there is no
+    CPU fallback behind the binding."""
+    monkeypatch.setattr(G, "LIB_PATH", str(tmp_path / "absent.so"))
+    monkeypatch.setattr(G, "_lib", None)
+    with pytest.raises(RuntimeError, match="no fallback"):
+        G.lib()
+    import numpy as np
+    A = (np.array([0, 1], np.int32), np.array([0], np.int32), np.array([2.0]))
+    with pytest.raises(RuntimeError, match="no fallback"):
+        G.Solver(A)
