@@ -126,6 +126,9 @@ def _bind(L):
                                        ctypes.POINTER(ctypes.c_int32),
                                        ctypes.POINTER(ctypes.c_int32)]
     L.orc_arnoldi_cycle_ex.restype = ctypes.c_int
+    L.orc_arnoldi_step.argtypes = [ctypes.c_int32, _i32p, _i32p, _f64p, _f64p, ctypes.c_int32,
+                                   ctypes.c_int32, ctypes.c_int32, _f64p, _f64p]
+    L.orc_arnoldi_step.restype = ctypes.c_int
     L.orc_s_norm2.argtypes = [ctypes.c_int32, _f64p, ctypes.c_int32, ctypes.c_int32]
     L.orc_s_norm2.restype = ctypes.c_double
     L.orc_high_part.argtypes = [ctypes.c_double]
@@ -285,6 +288,22 @@ def arnoldi_cycle(A, r0, m, ortho=CGSR, prec=FP64, kmax=None, tau=0.0, inner_abs
     jj = j.value
     return dict(V=V, Hbar=Hb.T.copy(), H=H.T.copy(), s=s, cs=cs, sn=sn, y=y, u=u, arn=arn, j=jj,
                 breakdown=bool(bd.value), orth=orth)
+
+
+def arnoldi_step(A, V, ortho=CGSR, prec=FP64):
+    """One inner iteration from the basis V (rows = stored basis vectors):
+    returns (h, vnext) with h = (h_{1..j,j}, h_{j+1,j}) and vnext = w / h_{j+1,j}
+    in the working precision, before storage rounding."""
+    rp, ci, va = _csr(A)
+    n = len(rp) - 1
+    V = np.ascontiguousarray(V, dtype=np.float64).reshape(-1, n)
+    j = V.shape[0]
+    h = np.zeros(j + 1)
+    vnext = np.zeros(n)
+    rc = _L().orc_arnoldi_step(n, rp, ci, va, V, j, ortho, prec, h, vnext)
+    if rc:
+        raise ValueError("orc_arnoldi_step failed: %d" % rc)
+    return h, vnext
 
 
 def ilu0(A):

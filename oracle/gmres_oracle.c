@@ -410,6 +410,52 @@ int orc_arnoldi_cycle(int32_t n, const int32_t *rowptr, const int32_t *colind, c
                                 arn, NULL, jout, breakdown);
 }
 
+int orc_arnoldi_step(int32_t n, const int32_t *rowptr, const int32_t *colind,
+                     const double *vals, const double *V, int32_t ncols, int32_t ortho,
+                     int32_t prec, double *h, double *vnext)
+{
+    if (n <= 0 || ncols < 1 || (ortho != ORC_MGS && ortho != ORC_CGSR) || prec < ORC_FP64 ||
+        prec > ORC_MIXED_LIMITED || prec == ORC_ALL_FP32 || !V || !h || !vnext ||
+        !csr_ok(n, rowptr, colind))
+        return -1;
+    const int is_f32 = (prec != ORC_FP64 && prec != ORC_MIXED_LIMITED);
+    const int32_t nnz = rowptr[n];
+    const size_t nv = (size_t)ncols * n;
+    int rc;
+    if (is_f32) {
+        float *a = (float *)malloc(sizeof(float) * (size_t)(nnz + 1));
+        float *Vf = (float *)malloc(sizeof(float) * (nv + 1));
+        float *hf = (float *)malloc(sizeof(float) * (size_t)(ncols + 1));
+        float *vf = (float *)malloc(sizeof(float) * (size_t)n);
+        if (!a || !Vf || !hf || !vf) {
+            free(a); free(Vf); free(hf); free(vf);
+            return -2;
+        }
+        for (int32_t k = 0; k < nnz; ++k)
+            a[k] = (float)vals[k];
+        for (size_t i = 0; i < nv; ++i)
+            Vf[i] = (float)V[i];
+        rc = step_f32(n, rowptr, colind, a, Vf, ncols, ortho, hf, vf);
+        if (rc == 0) {
+            for (int32_t i = 0; i <= ncols; ++i)
+                h[i] = hf[i];
+            for (int32_t r = 0; r < n; ++r)
+                vnext[r] = vf[r];
+        }
+        free(a); free(Vf); free(hf); free(vf);
+    } else {
+        /* limited mixed: the Krylov step's copy of A stored in binary32 */
+        double *a = (double *)malloc(sizeof(double) * (size_t)(nnz + 1));
+        if (!a)
+            return -2;
+        for (int32_t k = 0; k < nnz; ++k)
+            a[k] = prec == ORC_MIXED_LIMITED ? (double)(float)vals[k] : vals[k];
+        rc = step_f64(n, rowptr, colind, a, V, ncols, ortho, h, vnext);
+        free(a);
+    }
+    return rc;
+}
+
 /* Negative control (ORC_ALL_FP32): z = b - A x formed in binary32 from
  * binary32 copies of A, b and x; returns ||z|| in binary32. */
 static float residual_f32(int32_t n, const int32_t *rowptr, const int32_t *colind,

@@ -152,6 +152,17 @@ int orc_arnoldi_cycle(int32_t n, const int32_t *rowptr, const int32_t *colind, c
                       double *V, double *Hbar, double *Hrot, double *s, double *cs, double *sn,
                       double *y, double *u, double *arn, int32_t *jout, int32_t *breakdown);
 
+/* One inner iteration of Alg. 1 from the given basis V (ncols columns,
+ * column-major, values as the basis stores them): w = A v_ncols, MGS or CGSR
+ * against V, h_{j+1,j} = ||w||, all in the working precision prec selects
+ * (binary32 values and arithmetic for the mixed precisions; binary64
+ * arithmetic with A rounded to binary32 for ORC_MIXED_LIMITED).  Outputs:
+ * h (ncols+1: h_{1..j,j}, then h_{j+1,j}) and vnext (n: w / h_{j+1,j} in the
+ * working precision, before the basis rounds it).  No Givens rotation. */
+int orc_arnoldi_step(int32_t n, const int32_t *rowptr, const int32_t *colind,
+                     const double *vals, const double *V, int32_t ncols, int32_t ortho,
+                     int32_t prec, double *h, double *vnext);
+
 /* orc_arnoldi_cycle with every restart criterion of orc_restart; orth
  * (length m, may be NULL) receives ||S_k|| after each inner iteration (0
  * where the test is off or the cycle broke down). */

@@ -205,6 +205,34 @@ def pin_mgs_equals_cgsr():
     assert d <= 1e-10, d
 
 
+def pin_arnoldi_step():
+    """One inner iteration from a given basis (the replay the full-size GPU
+    tests use): in binary64, h_{1..j,j} = V_j^T A v_j (dense numpy), h_{j+1,j}
+    = ||A v_j - V_j h||, and v_{j+1} is a unit vector orthogonal to V_j, for
+    MGS and CGSR; fed its own cycle's basis, the step reproduces that cycle's
+    Hessenberg column and next basis vector in every precision."""
+    A, b = _cd_small()
+    D = _dense(A)
+    for ortho in (O.MGS, O.CGSR):
+        c = O.arnoldi_cycle(A, b, m=12, ortho=ortho, prec=O.FP64)
+        for j in (1, 5, 12):
+            V = c["V"][:j]
+            h, vn = O.arnoldi_step(A, V, ortho=ortho, prec=O.FP64)
+            w = D @ V[-1]
+            hx = V @ w
+            assert np.allclose(h[:j], hx, rtol=0, atol=1e-13 * np.linalg.norm(w)), (ortho, j)
+            assert abs(h[j] - np.linalg.norm(w - V.T @ hx)) <= 1e-12 * np.linalg.norm(w)
+            assert abs(np.linalg.norm(vn) - 1.0) <= 1e-13
+            assert np.abs(V @ vn).max() <= 1e-12, (ortho, j)
+        for prec in (O.MIXED, O.MIXED_FP16, O.MIXED_LIMITED):
+            c = O.arnoldi_cycle(A, b, m=12, ortho=ortho, prec=prec)
+            for j in (3, 12):
+                h, vn = O.arnoldi_step(A, c["V"][:j], ortho=ortho, prec=prec)
+                assert np.array_equal(h, c["Hbar"][: j + 1, j - 1]), (ortho, prec, j)
+                if j < c["j"]:
+                    assert np.array_equal(O.round_basis(vn, prec, len(b)), c["V"][j])
+
+
 def pin_givens_least_squares():
     """The rotated problem solves min ||beta e1 - Hbar y|| (checked against
     numpy lstsq), |s_{j+1}| equals that minimum, and it never increases."""
@@ -733,5 +761,5 @@ ALL_PINS = [
     pin_spai_grad_m_fd, pin_spai_grad_params_fd, pin_spai_special_cases, pin_spai_optimum,
     pin_spai_feature_invariants, pin_adam_first_step, pin_stall_restart, pin_s_matrix,
     pin_orthogonality_loss_restart, pin_limited_mixed, pin_split_bytes, pin_ilu0,
-    pin_ilu_left_gmres,
+    pin_ilu_left_gmres, pin_arnoldi_step,
 ]

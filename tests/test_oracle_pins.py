@@ -84,6 +84,8 @@ MUTATIONS = [
     ("cycle_impl.inc", "for (int32_t p = rowptr[i]; p < rowptr[i + 1] && colind[p] < i; ++p)\n            acc -= lu[p] * out[colind[p]];",
      "for (int32_t p = rowptr[i]; p < rowptr[i + 1] && colind[p] <= i; ++p)\n            acc -= lu[p] * out[colind[p]];",
      "forward substitution takes in the diagonal"),
+    ("cycle_impl.inc", "FN(spmv)(n, rowptr, colind, a, V + (size_t)(ncols - 1) * n, w);",
+     "FN(spmv)(n, rowptr, colind, a, V, w);", "replayed step multiplies v_1, not v_j"),
     ("spai_oracle.c", "atr[colind[k]] += vals[k] * r[i];", "atr[i] += vals[k] * r[colind[k]];",
      "A instead of A^T in the preconditioner gradient"),
     ("spai_oracle.c", "d2[o] = z2[o] > 0 ? dgk * params[P_W3 + o] : 0;",
