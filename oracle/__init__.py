@@ -103,6 +103,36 @@ def build(force: bool = False, src_dir: str = _HERE, out_path: str = _LIB_PATH) 
     return out_path
 
 
+_OMP_PATH = os.path.join(_HERE, "liboracle_omp.so")
+_omp = None
+
+
+def build_omp(force: bool = False) -> str:
+    """The CPU-baseline timing build: the same sources with -O3 -fopenmp, so
+    the loops over rows and vector entries run on every host core (the
+    parity build above stays single-threaded and is the one tests use)."""
+    srcs = _sources_present()
+    newest = max(os.path.getmtime(f) for f in srcs)
+    if force or not os.path.exists(_OMP_PATH) or os.path.getmtime(_OMP_PATH) < newest:
+        c_files = [f for f in srcs if f.endswith(".c")]
+        tmp = _OMP_PATH + ".tmp%d" % os.getpid()
+        cmd = ["gcc", "-std=c11", "-O3", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared",
+               "-o", tmp] + c_files + ["-lm"]
+        subprocess.run(cmd, check=True, cwd=_HERE)
+        os.replace(tmp, _OMP_PATH)
+    return _OMP_PATH
+
+
+def lib_omp():
+    """The OpenMP timing build, loaded (built on first use)."""
+    global _omp
+    with _lock:
+        if _omp is None:
+            build_omp()
+            _omp = _bind(ctypes.CDLL(_OMP_PATH))
+        return _omp
+
+
 def _bind(L):
     L.orc_spmv.argtypes = [ctypes.c_int32, _i32p, _i32p, _f64p, _f64p, _f64p, ctypes.c_int32]
     L.orc_spmv.restype = ctypes.c_int
@@ -137,6 +167,8 @@ def _bind(L):
     L.orc_ilu0.restype = ctypes.c_int
     L.orc_ilu_apply.argtypes = [ctypes.c_int32, _i32p, _i32p, _f64p, _f64p, _f64p]
     L.orc_ilu_apply.restype = ctypes.c_int
+    L.orc_threads.argtypes = [ctypes.c_int32]
+    L.orc_threads.restype = ctypes.c_int
     L.orc_gmres.argtypes = [ctypes.c_int32, _i32p, _i32p, _f64p, _f64p, _f64p,
                             ctypes.POINTER(Opts), vp, vp, vp, ctypes.POINTER(Info), vp, vp]
     L.orc_gmres.restype = ctypes.c_int
@@ -327,6 +359,12 @@ def ilu_apply(LU, z):
     if rc:
         raise ValueError("orc_ilu_apply failed: %d" % rc)
     return out
+
+
+def threads(want=0):
+    """Threads of the active build's row and vector loops (1 for the parity
+    build); want > 0 sets them first (OpenMP timing build)."""
+    return _L().orc_threads(int(want))
 
 
 def high_part(v):

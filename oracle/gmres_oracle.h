@@ -194,6 +194,10 @@ int orc_ilu_apply(int32_t n, const int32_t *rowptr, const int32_t *colind, const
  * 32 bits cleared: sign, exponent and the top 20 fraction bits). */
 double orc_high_part(double v);
 
+/* Threads the loops over rows and vector entries use: 1 in the parity build;
+ * in the OpenMP timing build, want > 0 sets the count first.  Returns it. */
+int orc_threads(int32_t want);
+
 /* Restarted GMRES(m) (Alg. 1).  x holds x_0 on entry and the result on exit.
  * arn_hist (length maxiter) receives |s_{j+1}| of every inner iteration;
  * cyc_hist (length maxiter+1) receives ||b - A x_k|| / ||b|| at the top of every
