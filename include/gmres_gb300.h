@@ -267,6 +267,20 @@ gmres_status gmres_arnoldi(gmres_t h, const double *r0, int32_t m, int32_t kmax,
                            double *V, double *Hbar, double *H, double *s, double *cs, double *sn,
                            double *y, double *u, double *arn, int32_t *jout, int32_t *breakdown);
 
+/* One inner iteration of Algorithm 1 from a caller-given basis, for parity
+ * checks at sizes where a whole cycle drifts with the summation order: the
+ * first ncols basis vectors are taken from V (host, binary64, ncols x n,
+ * vector i at V + i*n, values as the precision's basis stores them: they are
+ * rounded to the storage type on upload), then the iteration a solve runs
+ * for column j = ncols: w = A v_j, MGS or CGSR against V_j (the kernels
+ * gmres_opts selects), h_{j+1,j} = ||w|| and v_{j+1} = w / h_{j+1,j}.
+ * Host outputs: hcol (ncols + 1: h_{1..j,j}, then h_{j+1,j}), vnext (n, may be
+ * NULL: v_{j+1} as stored, widened).  1 <= ncols <= 128.  Errors:
+ * GMRES_ERR_ARG (also with a preconditioner or split storage),
+ * GMRES_ERR_BREAKDOWN when h_{j+1,j} vanished (vnext not formed). */
+gmres_status gmres_arnoldi_step(gmres_t h, const double *V, int32_t ncols, gmres_ortho ortho,
+                                gmres_precision prec, double *hcol, double *vnext);
+
 /* Time every SpMV variant (lanes per row 1..32) on this matrix in binary32
  * and binary64 and keep the fastest for later solves (the tile autotuner).
  * lanes32 / lanes64 (may be NULL) receive the choices. */
@@ -386,15 +400,18 @@ gmres_status gmres_batch_autotune(gmres_batch_t b, const double *rhs, int32_t m,
 /* ---------------------------------------------------------------------------
  * Solve without allocating device memory.  The paper has no counterpart; this
  * is for callers that cannot allocate at the point of the solve: cudaMalloc /
- * cudaFree may synchronise the whole device, are not allowed while a stream
- * is being captured into a CUDA graph, and some frameworks own the entire
- * device budget through their own allocator.
+ * cudaFree may synchronise the whole device, and some frameworks own the
+ * entire device budget through their own allocator.
  *
  * gmres_solve_noalloc runs the single-block whole-solve kernel (the block path
  * of gmres_solve) on the caller's DEVICE arrays: CSR rowptr (n+1), colind and
  * vals (nnz, binary64), b and x (n, binary64; x = x_0 on entry, the result on
  * exit).  m, tol, ortho, prec, maxiter, info: as for gmres_solve; stream is a
- * cudaStream_t.  The caller guarantees a valid CSR matrix (not checked).
+ * cudaStream_t.  Every system runs on one thread block here, also binary64
+ * systems of 2048 rows and more, which gmres_solve would give a cluster of 8
+ * blocks (so iteration counts may differ from gmres_solve's for those).
+ * rowptr[0] must be 0 and rowptr[n] must equal nnz (both read back and
+ * checked: GMRES_ERR_ARG); the rest of the CSR structure is not checked.
  * All workspace (Krylov basis, work vectors, binary32 values, result record)
  * comes from one file-scope device array of GMRES_NOALLOC_SCRATCH_BYTES that
  * every GPU loading the library holds until the process exits; a system whose
@@ -402,9 +419,11 @@ gmres_status gmres_batch_autotune(gmres_batch_t b, const double *rhs, int32_t m,
  * GMRES_ERR_ARG and a message on stderr.  No call allocates: neither
  * cudaMalloc, cudaFree nor any allocating library routine.  The first call on
  * a device looks up the array's device address (cudaGetSymbolAddress) with
- * that device current; make that first call before any stream capture.  All
- * calls share the array and each overwrites it: calls that overlap on the GPU
- * race and must be serialised by the caller.  Host pointers: GMRES_ERR_ARG.
+ * that device current; make that first call before any stream capture.  Every
+ * call waits for its stream to finish before it returns (it reads the result
+ * record back to the host).  All calls share the array and each overwrites
+ * it: calls that overlap on the GPU race and must be serialised by the
+ * caller.  Host pointers: GMRES_ERR_ARG.
  * ------------------------------------------------------------------------- */
 #define GMRES_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
 

@@ -1523,6 +1523,60 @@ gmres_status arnoldi_impl(gmres_handle *h, const double *r0, int m, int kmax, gm
     return GMRES_OK;
 }
 
+// One inner iteration from a caller-given basis (gmres_arnoldi_step): the
+// basis is loaded into the workspace, the control block says "cycle running,
+// column ncols-1", and the same enqueue_step_core a solve uses runs once.
+template <class T, class VT>
+gmres_status arnoldi_step_impl(gmres_handle *h, const double *V, int ncols, gmres_ortho ortho,
+                               gmres_precision prec, double *hcol, double *vnext) {
+    const int m = ncols;  // the basis holds m + 1 = ncols + 1 vectors
+    gmres_status st = ensure_workspace(h, m, prec);
+    if (st != GMRES_OK)
+        return st;
+    GridCtx<T, VT> c = make_ctx<T, VT>(h, m);
+    c.tol_abs = -1.0;
+    c.tau = 0.0;
+    c.inner_abs = -1.0;
+    c.stall_factor = 0.0;
+    c.kmax = m + 1;  // the Givens step must not end the cycle
+    Acct acct;
+    CK(cudaMemsetAsync(h->small.p, 0, h->small.bytes, h->stream));
+    Ctl k0;
+    memset(&k0, 0, sizeof(k0));
+    k0.active = 1;
+    k0.j = ncols - 1;
+    k0.beta = 1.0;
+    k0.arn = 1.0;
+    CK(cudaMemcpyAsync(h->ctl.p, &k0, sizeof(Ctl), cudaMemcpyHostToDevice, h->stream));
+    const size_t vbytes = (size_t)h->n * (ncols + 1) * sizeof(double);
+    CK(h->z.ensure(vbytes));
+    CK(cudaMemcpyAsync(h->z.p, V, (size_t)h->n * ncols * sizeof(double), cudaMemcpyHostToDevice,
+                       h->stream));
+    k_import_basis<T, VT><<<h->nsm * 4, 256, 0, h->stream>>>(c, ncols, h->z.as<double>());
+    CKL();
+    st = enqueue_step_core(h, c, ncols - 1, ortho, acct);
+    if (st != GMRES_OK)
+        return st;
+    st = read_ctl(h);
+    if (st != GMRES_OK)
+        return st;
+    std::vector<T> tmp;
+    SmallPtrs<T> sp = small_ptrs<T>(h);
+    export_small(sp.Hb + (size_t)(ncols - 1) * (m + 1), hcol, (size_t)ncols + 1, h->stream, tmp);
+    if (vnext) {
+        k_export_basis<T, VT><<<h->nsm * 4, 256, 0, h->stream>>>(c, ncols + 1, h->z.as<double>());
+        CKL();
+        CK(cudaMemcpyAsync(vnext, h->z.as<double>() + (size_t)ncols * h->n,
+                           (size_t)h->n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+    }
+    if (h->hctl->nonfinite)
+        return GMRES_ERR_NONFINITE;
+    if (h->hctl->breakdown)
+        return GMRES_ERR_BREAKDOWN;
+    return GMRES_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1557,6 +1611,32 @@ gmres_status gmres_arnoldi(gmres_t h, const double *r0, int32_t m, int32_t kmax,
     default:
         return arnoldi_impl<float, __half>(h, r0, m, kmax, ortho, prec, tau, inner_abs, V, Hbar,
                                            H, s, cs, sn, y, u, arn, jout, breakdown);
+    }
+}
+
+gmres_status gmres_arnoldi_step(gmres_t h, const double *V, int32_t ncols, gmres_ortho ortho,
+                                gmres_precision prec, double *hcol, double *vnext) {
+    if (!h || !V || !hcol || ncols < 1 || ncols > MMAX ||
+        (ortho != GMRES_ORTHO_MGS && ortho != GMRES_ORTHO_CGSR) || prec < GMRES_FP64 ||
+        prec > GMRES_MIXED_LIMITED || h->split || h->opts.precond != 0 ||
+        h->opts.normalize_fused)
+        return GMRES_ERR_ARG;
+    h->timer.on = false;
+    switch (prec) {
+    case GMRES_FP64:
+        return arnoldi_step_impl<double, double>(h, V, ncols, ortho, prec, hcol, vnext);
+    case GMRES_MIXED:
+        return arnoldi_step_impl<float, float>(h, V, ncols, ortho, prec, hcol, vnext);
+    case GMRES_MIXED_BF16:
+        return arnoldi_step_impl<float, __nv_bfloat16>(h, V, ncols, ortho, prec, hcol, vnext);
+    case GMRES_MIXED_LIMITED: {
+        h->limited = true;
+        gmres_status st = arnoldi_step_impl<double, float>(h, V, ncols, ortho, prec, hcol, vnext);
+        h->limited = false;
+        return st;
+    }
+    default:
+        return arnoldi_step_impl<float, __half>(h, V, ncols, ortho, prec, hcol, vnext);
     }
 }
 

@@ -937,4 +937,17 @@ __global__ void k_export_basis(GridCtx<T, VT> c, int ncols, double *out) {
     }
 }
 
+// Basis columns [0, ncols) from a binary64 host-side copy (column i at
+// src + i * n), rounded to the storage type; padding rows stay zero.  Used by
+// the one-step replay entry point, whose inputs are basis values as stored.
+template <class T, class VT>
+__global__ void k_import_basis(GridCtx<T, VT> c, int ncols, const double *src) {
+    const int64_t total = (int64_t)ncols * c.n;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        int64_t col = idx / c.n, row = idx % c.n;
+        Basis<VT>::st(c.V + col * c.ldv + row, (T)src[idx], c.vscale);
+    }
+}
+
 }  // namespace gmres

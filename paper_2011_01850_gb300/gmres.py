@@ -113,6 +113,7 @@ SIGNATURES = {
     "gmres_residual": (_st, [_vp, _vp, _vp, _vp, ctypes.POINTER(_f64)]),
     "gmres_arnoldi": (_st, [_vp, _vp, _i32, _i32, _i32, _i32, _f64, _f64] + [_vp] * 9
                       + [ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
+    "gmres_arnoldi_step": (_st, [_vp, _vp, _i32, _i32, _i32, _vp, _vp]),
     "gmres_autotune": (_st, [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
     "gmres_memory_bytes": (_st, [_vp, _i32, _i32, ctypes.POINTER(ctypes.c_int64),
                                  ctypes.POINTER(ctypes.c_int64)]),
@@ -278,6 +279,19 @@ def gmres_arnoldi(h, r0, m, kmax, ortho, prec, tau=0.0, inner_abs=0.0, n=None):
     _check(st, "gmres_arnoldi")
     return dict(V=V, Hbar=Hb.T.copy(), H=H.T.copy(), s=s, cs=cs, sn=sn, y=y, u=u, arn=arn,
                 j=j.value, breakdown=bool(bd.value))
+
+
+def gmres_arnoldi_step(h, V, ortho, prec, want_v=True):
+    """One inner iteration from the basis V (rows = basis vectors, host
+    binary64): returns (hcol, vnext) with hcol = (h_{1..j,j}, h_{j+1,j})."""
+    V = np.ascontiguousarray(V, dtype=np.float64)
+    ncols, n = V.shape
+    hcol = np.zeros(ncols + 1)
+    vnext = np.zeros(n) if want_v else None
+    st = lib().gmres_arnoldi_step(h, _ptr(V), int(ncols), int(ortho), int(prec), _ptr(hcol),
+                                  _ptr(vnext))
+    _check(st, "gmres_arnoldi_step")
+    return hcol, vnext
 
 
 def gmres_autotune(h):

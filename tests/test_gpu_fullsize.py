@@ -2,13 +2,18 @@
 
 160^3 convection-diffusion (n = 4 096 000, nnz = 28 518 400), mixed CGSR
 GMRES(100) in the launch configuration bench.py times (autotuned SpMV lanes,
-grid path).  The oracle cannot solve this size in test time, so the checks are
-the ones that hold at any size: the binary64 relative residual of the returned
-x, recomputed by the oracle, is <= 1e-10; the mixed solve reaches the same
-residual class as the binary64 solve; and the SpMV kernels match the oracle on
-sampled rows (full binary64/binary32 oracle SpMV, rows sampled for the
-element-wise gamma_k comparison).
+grid path).  The oracle needs about 20 minutes per solve at this size, so its
+results are stored (oracle/golden_fullsize.py writes tests/golden/
+convdiff3d_160_schedule.json and convdiff3d_160_x.npz; oracle/cond.py the
+condition-number estimate): the GPU solve must run the oracle's restart
+schedule, its x must agree with the oracle's binary64 x at 65 536 seeded rows
+(to 1e-8 when both are solved tightly), its binary64 relative residual,
+recomputed by the oracle, must be <= 1e-10, and the SpMV kernels match the
+oracle on sampled rows (gamma_k bounds).
 """
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -20,6 +25,8 @@ pytestmark = pytest.mark.gpu
 
 if torch.cuda.is_available():
     from paper_2011_01850_gb300 import gmres as G
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 
 
 @pytest.fixture(scope="module")
@@ -49,22 +56,68 @@ def test_fullsize_spmv_sampled_rows(full, gpulib):
     s.close()
 
 
-@pytest.mark.parametrize("prec", ["mixed", "fp64"])
-def test_fullsize_solve_residual(full, prec, gpulib):
+def _golden():
+    with open(os.path.join(GOLDEN, "convdiff3d_160_schedule.json")) as f:
+        sched = json.load(f)
+    z = np.load(os.path.join(GOLDEN, "convdiff3d_160_x.npz"))
+    meta = json.loads(str(z["meta"]))
+    with open(os.path.join(GOLDEN, "convdiff3d_kappa.json")) as f:
+        kappa = json.load(f)["kappa_160"]
+    return sched, z["idx"], z["x"], meta, kappa
+
+
+def _solve(full, prec, tol):
     A, b, spec = full
     n = len(A[0]) - 1
     s = G.Solver(A, stream=torch.cuda.current_stream())
     G.gmres_autotune(s.h)
     db = torch.tensor(b, device="cuda", dtype=torch.float64)
     dx = torch.zeros(n, device="cuda", dtype=torch.float64)
-    _, st, info = s.solve(db, dx, m=spec["m"], tol=1e-10, ortho=spec["ortho"], prec=prec,
+    _, st, info = s.solve(db, dx, m=spec["m"], tol=tol, ortho=spec["ortho"], prec=prec,
                           maxiter=100000)
     s.close()
+    return dx.cpu().numpy(), st, info
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_fullsize_solve_residual(full, prec, gpulib):
+    """The benchmarked solve: relative residual <= 1e-10 recomputed by the
+    oracle; the mixed solve runs the oracle's restart schedule (stored by
+    oracle/golden_fullsize.py: 1300 inner iterations in 13 cycles, the first
+    one 100 long); the solution agrees with the oracle's binary64 solution
+    (solved to 1e-13, stored at 65 536 seeded rows) within the forward-error
+    bound kappa_2 (rel_gpu + rel_oracle), kappa_2 ~ 1.05e4 extrapolated from
+    smaller grids of the family (oracle/cond.py)."""
+    A, b, spec = full
+    x, st, info = _solve(full, prec, 1e-10)
     assert st == G.OK, info
     assert info["path"] == G.PATH_GRID
-    x = dx.cpu().numpy()
     rel = O.residual_norm(A, b, x) / np.linalg.norm(b)
     assert rel <= 1e-10, rel
     assert abs(rel - info["relres"]) <= 1e-6 * rel
-    # the solution of b = A 1 + noise is close to 1 (noise 1e-3 per entry)
-    assert np.abs(x - 1.0).max() < 0.5
+    sched, idx, xo, meta, kappa = _golden()
+    if prec == "mixed":
+        assert (info["iters"], info["restarts"], info["first_len"]) == (
+            sched["iters"], sched["restarts"], sched["first_len"]), (info, sched)
+    # ||x - x_o||_inf <= ||x - x_o||_2 <= kappa (rel + rel_o) ||x_o||_2, and the
+    # stored entries are close to 1: divide by their smallest magnitude
+    err = np.abs(x[idx] - xo) / np.abs(xo)
+    bound = kappa * (rel + meta["relres"]) * meta["xnorm"] / np.abs(xo).min()
+    assert err.max() <= bound, (err.max(), bound)
+    print(prec, "max entry-wise error vs oracle:", err.max(), "bound:", bound)
+
+
+def test_fullsize_solution_to_1e8(full, gpulib):
+    """North-star accuracy at full size: solved to a relative residual of
+    1e-13, the mixed solver's x agrees with the oracle's binary64 x to 1e-8
+    relative in every stored entry (kappa_2 * 2e-13 ~ 2e-9 allows it)."""
+    A, b, spec = full
+    x, st, info = _solve(full, "mixed", 1e-13)
+    assert st == G.OK, info
+    rel = O.residual_norm(A, b, x) / np.linalg.norm(b)
+    assert rel <= 1e-13, rel
+    sched, idx, xo, meta, kappa = _golden()
+    assert kappa * (rel + meta["relres"]) < 1e-8
+    err = np.abs(x[idx] - xo) / np.abs(xo)
+    assert err.max() <= 1e-8, err.max()
+    print("tol 1e-13: iters", info["iters"], "max entry-wise error vs oracle:", err.max())
