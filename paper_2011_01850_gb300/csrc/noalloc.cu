@@ -2,8 +2,7 @@
 //
 // Some callers cannot allocate device memory at the point where they need a
 // solve: cudaMalloc and cudaFree may synchronise the whole device (stalling
-// every other stream of a time-stepping code), they are not allowed while a
-// stream is being captured into a CUDA graph, and some frameworks own the
+// every other stream of a time-stepping code), and some frameworks own the
 // entire device budget through their own allocator.  gmres_solve_noalloc
 // serves them: it runs the single-block whole-solve kernel of the block path
 // on the caller's device arrays, and takes every byte of workspace -- the
@@ -12,7 +11,9 @@
 // That array exists on every GPU that loads the library, for the life of the
 // process.  All calls share it, so calls that overlap on the GPU (different
 // streams, different host threads) race on it and must be serialised by the
-// caller; each call overwrites what the previous one left there.
+// caller; each call overwrites what the previous one left there.  Every call
+// waits for its stream to finish before it returns: it reads rowptr's end
+// points and the result record back to the host.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -194,6 +195,24 @@ extern "C" gmres_status gmres_solve_noalloc(int32_t n, const int32_t *rowptr,
         !on_device(b) || !on_device(x))
         return GMRES_ERR_ARG;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    // rowptr[0] and rowptr[n] against the stated nonzero count: the kernels
+    // read rowptr[n] entries of colind and vals, and the binary32 copy in the
+    // scratch holds nnz of them (two 4-byte reads; the call synchronises its
+    // stream at the end anyway)
+    int32_t ends[2] = {-1, -1};
+    if (cudaMemcpyAsync(&ends[0], rowptr, sizeof(int32_t), cudaMemcpyDeviceToHost, s) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(&ends[1], rowptr + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaGetLastError();
+        return GMRES_ERR_CUDA;
+    }
+    if (ends[0] != 0 || (int64_t)ends[1] != nnz) {
+        fprintf(stderr, "gmres_solve_noalloc: rowptr[0] = %d, rowptr[n] = %d, nnz = %lld\n",
+                ends[0], ends[1], (long long)nnz);
+        return GMRES_ERR_ARG;
+    }
     gmres_status st;
     switch (prec) {
     case GMRES_FP64:
