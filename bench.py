@@ -8,8 +8,9 @@ CGSR on the 3-D 7-point upwind convection-diffusion stencil, 160^3 grid
 b = A 1 + N(0, sigma^2) noise with sigma = 1e-3, x0 = 0, tol 1e-10; the FP64 GMRES(100) CGSR solve
 of the same system is timed beside it.  One step = one full solve to 1e-10.
 
-Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle on
-bounded samples of the same workload instead.
+Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle (its
+OpenMP build, every host core) on whole restart cycles of the same workload
+instead, scaled to the oracle's own schedule.
 """
 from __future__ import annotations
 
@@ -30,10 +31,10 @@ sys.path.insert(0, ROOT)
 WORKLOAD = "convdiff3d_160"
 SEED = 20110185
 # Inner iterations and restart cycles of the oracle's own full solves of the
-# workloads (python -m oracle.schedule <workload> <precision>; the 160^3
-# mixed CGSR GMRES(100) solve took 1085 s on one x86 core); used to scale the
-# oracle's per-cycle samples to a full solve.  The GPU solves take the same
-# schedules.
+# workloads (python -m oracle.golden_fullsize schedule stores the 160^3 one in
+# tests/golden/convdiff3d_160_schedule.json, which takes precedence; the solve
+# took 1121 s on one x86 core); used to scale the oracle's measured restart
+# cycle to a full solve.  The GPU solves take the same schedules.
 SCHEDULE = {"convdiff3d_160": {"mixed": {"iters": 1300, "restarts": 13}}}
 
 
@@ -428,7 +429,7 @@ def bench_ours(args):
             "note": "achieved/frac: algorithmic bytes over time against HBM, for context"})
     solver.close()
     if rank == 0 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(A, b, spec, iters, restarts, m)
+        out["cpu_baseline"] = cpu_baseline(args.workload, A, b, spec, iters, restarts, m)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
@@ -558,78 +559,131 @@ def bench_batched(args, world, rank, local):
         dist.destroy_process_group()
 
 
-def oracle_sample(A, b, spec, ks=(2, 8, 16)):
-    """Time the oracle's restart cycle for three inner-iteration counts on the
-    full workload and fit T(k) = c + a k + b k(k+1)/2 (iteration j costs
-    a + b j: one SpMV plus passes over j basis vectors); also time one
-    binary64 residual.  Returns (t_res, c, a, b, seconds spent)."""
+def host_cpu():
+    """(cores, CPU model) of this host."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if not model:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for line in f:
+                    if line.lower().startswith("model name"):
+                        model = line.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    import platform
+    return os.cpu_count() or 1, model or platform.machine()
+
+
+def oracle_schedule(name, prec):
+    """The oracle's own restart schedule of a workload: stored by
+    oracle/golden_fullsize.py where it exists, else the table above."""
+    path = os.path.join(ROOT, "tests", "golden", name + "_schedule.json")
+    try:
+        with open(path) as f:
+            g = json.load(f)
+        if g.get("prec") == prec:
+            return {"iters": g["iters"], "restarts": g["restarts"]}
+    except (OSError, ValueError, KeyError):
+        pass
+    return SCHEDULE.get(name, {}).get(prec)
+
+
+def oracle_cycle_sample(A, b, spec, kmax):
+    """Time, with the oracle's OpenMP build on every host core, one binary64
+    residual and one restart cycle of kmax inner iterations on the full
+    workload (the cycle starts from b, as the first one of a solve does).
+    Returns (t_residual, t_cycle, threads)."""
     import oracle as O
     prec = {"fp64": O.FP64, "mixed": O.MIXED, "mixed_bf16": O.MIXED_BF16,
             "mixed_fp16": O.MIXED_FP16}[spec["prec"]]
     ortho = O.CGSR if spec["ortho"] == "cgsr" else O.MGS
-    m = spec["m"]
-    t0 = time.perf_counter()
-    O.residual_norm(A, b, np.zeros_like(b))
-    t_res = time.perf_counter() - t0
-    ts = []
-    # a preconditioned workload costs one more SpMV per step: time the oracle
-    # with an M on A's pattern computed by the oracle itself (Jacobi values)
     M = ilu = None
-    if spec.get("precond") == "ilu":
-        ilu = O.ilu0(A)  # the oracle's own factors (their time is not counted)
-    elif spec.get("precond"):
-        M = (A[0], A[1], O.spai_values(A, O.spai_jacobi_params()))
-    for k in ks:
+    with O.use(O.lib_omp()):
+        threads = O.threads(os.cpu_count() or 1)
+        if spec.get("precond") == "ilu":
+            ilu = O.ilu0(A)  # the oracle's own factors (their time is not counted)
+        elif spec.get("precond"):
+            M = (A[0], A[1], O.spai_values(A, O.spai_jacobi_params()))
         t0 = time.perf_counter()
-        O.arnoldi_cycle(A, b, m, ortho=ortho, prec=prec, kmax=k, export_basis=False, M=M,
-                        ilu=ilu)
-        ts.append(time.perf_counter() - t0)
-    M = np.array([[1.0, k, k * (k + 1) / 2.0] for k in ks])
-    c, a, bco = np.linalg.lstsq(M, np.array(ts), rcond=None)[0]
-    return t_res, max(c, 0.0), max(a, 0.0), max(bco, 0.0), sum(ts) + t_res
+        O.residual_norm(A, b, np.zeros_like(b))
+        t_res = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        O.arnoldi_cycle(A, b, spec["m"], ortho=ortho, prec=prec, kmax=kmax,
+                        export_basis=False, M=M, ilu=ilu)
+        t_cyc = time.perf_counter() - t0
+    return t_res, t_cyc, threads
 
 
-def estimate_solve_s(t_res, c, a, bco, iters, restarts, m):
-    """Oracle time for a solve with the given schedule (cycles of up to m)."""
-    total = (restarts + 1) * t_res
-    left = iters
-    for _ in range(restarts):
-        L = min(m, left)
-        left -= L
-        total += c + a * L + bco * L * (L + 1) / 2
-    return total
+def scale_to_schedule(t_res, t_cyc, kmax, iters, restarts):
+    """Solve time for a schedule of `restarts` cycles and `iters` inner
+    iterations from a measured cycle of kmax iterations: every cycle of kmax
+    iterations costs the measured time (exact when the schedule's cycles all
+    have that length, as the 160^3 workload's 13 cycles of 100 do); a shorter
+    last cycle costs its share of the orthogonalisation work, which grows
+    like L (L + 1) / 2 inner products."""
+    full, rem = divmod(iters, kmax)
+    t = full * t_cyc + (restarts + 1) * t_res
+    if rem:
+        t += t_cyc * (rem * (rem + 1)) / (kmax * (kmax + 1))
+    return t
 
 
-def cpu_baseline(A, b, spec, iters, restarts, m):
-    t_res, c, a, bco, spent = oracle_sample(A, b, spec)
-    est = estimate_solve_s(t_res, c, a, bco, iters, restarts, m)
-    return {"value": round(est * 1e3, 1), "unit": "ms", "cores": 1, "kind": "oracle",
-            "sample": "oracle (single thread) restart cycles of 2, 8 and 16 inner iterations "
-                      "and one binary64 residual on the full workload (%.1f s of CPU); cycle "
-                      "cost c + a k + b k(k+1)/2 fitted and applied to the measured schedule "
-                      "(%d iterations in %d cycles of m=%d)" % (spent, iters, restarts, m)}
+def cpu_baseline(name, A, b, spec, iters, restarts, m):
+    """The oracle timed on the host cores, scaled to the oracle's own schedule
+    for the workload (or to the GPU's, where no oracle schedule is stored)."""
+    sched = oracle_schedule(name, spec["prec"]) or {"iters": iters, "restarts": restarts}
+    t_res, t_cyc, threads = oracle_cycle_sample(A, b, spec, m)
+    est = scale_to_schedule(t_res, t_cyc, m, sched["iters"], sched["restarts"])
+    cores, model = host_cpu()
+    return {"value": round(est * 1e3, 1), "unit": "ms", "cores": threads, "kind": "oracle",
+            "cpu": model, "host_cores": cores,
+            "cycle_s": round(t_cyc, 3), "residual_s": round(t_res, 4),
+            "sample": "the oracle's OpenMP build (-O3 -fopenmp, loops over rows and vector "
+                      "entries on %d threads) timed on one whole restart cycle of %d inner "
+                      "iterations (%.1f s) and one binary64 residual (%.3f s) of the full "
+                      "workload, scaled to the oracle's schedule of %d iterations in %d "
+                      "cycles" % (threads, m, t_cyc, t_res, sched["iters"], sched["restarts"])}
 
 
 def bench_reference(args):
+    """The reference arm: the oracle as it stands (OpenMP timing build, every
+    host core), rank 0 only.  Warm-up steps time a 2-iteration cycle (thread
+    start-up, page-in); every timed step times one whole restart cycle of m
+    inner iterations and one residual of the full workload, scaled to the
+    oracle's own schedule for it."""
     world, rank, local = dist_setup(args)
     if rank != 0:
         return
-    import oracle as O  # noqa: F401
     A, b, spec = make_workload(args.workload)
     m = spec["m"]
-    sched = SCHEDULE.get(args.workload, {}).get(spec["prec"]) or {"iters": None}
-    iters = sched.get("iters") if isinstance(sched, dict) else None
-    restarts = sched.get("restarts") if isinstance(sched, dict) else None
-    vals = []
-    spent = 0.0
+    sched = oracle_schedule(args.workload, spec["prec"]) or {"iters": m, "restarts": 1}
+    vals, cycles, residuals = [], [], []
+    threads = 1
     for i in range(args.warmup + args.steps):
-        t_res, c, a, bco, s = oracle_sample(A, b, spec, ks=(2, 8, 16))
-        spent += s
-        if i >= args.warmup:
-            it = iters or 1
-            rs = restarts or 1
-            vals.append(estimate_solve_s(t_res, c, a, bco, it, rs, m) * 1e3)
+        if i < args.warmup:
+            oracle_cycle_sample(A, b, spec, 2)
+            continue
+        t_res, t_cyc, threads = oracle_cycle_sample(A, b, spec, m)
+        cycles.append(t_cyc)
+        residuals.append(t_res)
+        vals.append(scale_to_schedule(t_res, t_cyc, m, sched["iters"], sched["restarts"]) * 1e3)
     v = statistics.mean(vals)
+    cores, model = host_cpu()
+    sample = ("per step: one whole restart cycle of %d inner iterations (mean %.2f s) and one "
+              "binary64 residual (mean %.3f s) of the full workload with the oracle's OpenMP "
+              "build on %d threads, scaled to the oracle's schedule of %d iterations in %d "
+              "cycles; warm-up steps: a 2-iteration cycle"
+              % (m, statistics.mean(cycles), statistics.mean(residuals), threads,
+                 sched["iters"], sched["restarts"]))
     out = {
         "impl": "reference",
         "metric": "time-to-1e-10 residual and HBM GB/s: mixed vs FP64 GMRES(m), one GB300",
@@ -639,10 +693,8 @@ def bench_reference(args):
         "dtype": "f32" if spec["prec"] != "fp64" else "f64", "data": "synthetic",
         "config": {"workload": args.workload, "m": m, "ortho": spec["ortho"],
                    "precision": spec["prec"], "tol": 1e-10, "seed": SEED},
-        "cpu_baseline": {"value": round(v, 1), "unit": "ms", "cores": 1, "kind": "oracle",
-                         "sample": "per step: oracle restart cycles of 2, 8 and 16 inner "
-                                   "iterations plus one residual on the full workload, "
-                                   "scaled to %s iterations / %s cycles" % (iters, restarts)},
+        "cpu_baseline": {"value": round(v, 1), "unit": "ms", "cores": threads, "kind": "oracle",
+                         "cpu": model, "host_cores": cores, "sample": sample},
         "e2e": {"value": round(v, 1), "unit": "ms", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
