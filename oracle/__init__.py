@@ -27,6 +27,12 @@ _lib = None
 MGS, CGSR = 0, 1
 ORTH_OFF, ORTH_SPECTRAL, ORTH_FROBENIUS = 0, 1, 2
 FP64, MIXED, MIXED_BF16, MIXED_FP16, ALL_FP32, MIXED_LIMITED = 0, 1, 2, 3, 4, 5
+# per-variable precision switches (gmres_oracle.h, Sec. 4.1): bit set = that
+# variable stored in binary32, the rest of the binary64 solver unchanged
+PV_A_KRYLOV, PV_M, PV_V, PV_W, PV_H, PV_GIVENS, PV_Z = 1, 2, 4, 8, 16, 32, 64
+PV_A_RESID, PV_B, PV_X, PV_AX = 128, 256, 512, 1024
+PV_CORRECTION = PV_A_KRYLOV | PV_M | PV_V | PV_W | PV_H | PV_GIVENS | PV_Z
+PV_REFINEMENT = PV_A_RESID | PV_B | PV_X | PV_AX
 
 _i32p = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
 _f64p = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
@@ -52,6 +58,7 @@ class Opts(ctypes.Structure):
         ("split_bytes", ctypes.c_int32),
         ("left_precond", ctypes.c_int32),
         ("ilu32", ctypes.c_int32),
+        ("pv_mask", ctypes.c_int32),
     ]
 
 
@@ -69,6 +76,7 @@ class Restart(ctypes.Structure):
         ("split_bytes", ctypes.c_int32),
         ("left_precond", ctypes.c_int32),
         ("ilu32", ctypes.c_int32),
+        ("pv_mask", ctypes.c_int32),
     ]
 
 
@@ -269,7 +277,7 @@ def round_basis(v, prec, n):
 def arnoldi_cycle(A, r0, m, ortho=CGSR, prec=FP64, kmax=None, tau=0.0, inner_abs=0.0, M=None,
                   export_basis=True, stall_factor=0.0, stall_window=0, orth_norm=ORTH_OFF,
                   orth_threshold=1.0, orth_iters=10, split_bytes=False, ilu=None,
-                  ilu32=False):
+                  ilu32=False, pv_mask=0):
     """One restart cycle from residual r0; returns a dict of its quantities.
 
     V is (m+1, n) (row i = basis vector i), Hbar/H are (m+1, m), the first ``j``
@@ -296,6 +304,7 @@ def arnoldi_cycle(A, r0, m, ortho=CGSR, prec=FP64, kmax=None, tau=0.0, inner_abs
     rs.stall_window = stall_window if stall_window > 0 else (m + 19) // 20
     rs.orth_norm, rs.orth_threshold, rs.orth_iters = orth_norm, orth_threshold, orth_iters
     rs.split_bytes = int(bool(split_bytes))
+    rs.pv_mask = int(pv_mask)
     if ilu is not None:
         if M is not None:
             raise ValueError("one preconditioner at a time")
@@ -391,14 +400,15 @@ def default_tau(prec):
 def gmres(A, b, x0=None, m=30, tol=1e-10, ortho=CGSR, prec=FP64, maxiter=10000, tau=None,
           repeat_first=None, inner_factor=0.5, M=None, history=False, stall_factor=0.0,
           stall_window=0, orth_norm=ORTH_OFF, orth_threshold=1.0, orth_iters=10,
-          split_bytes=False, ilu=None, ilu32=False):
+          split_bytes=False, ilu=None, ilu32=False, pv_mask=0):
     """Restarted GMRES(m) (Algorithm 1).  Returns (x, info dict).
 
     Restart strategies (Sec. 3): repeat_first (first), tau (second),
     stall_factor/stall_window (third; window 0 = ceil(0.05 m)), orth_norm /
     orth_threshold / orth_iters (fourth, loss of orthogonality via ||S_k||).
     split_bytes: A stored as high/low 32-bit halves, the Krylov step reading
-    the high-order half (Sec. 4)."""
+    the high-order half (Sec. 4).  pv_mask: PV_* bits, the per-variable
+    precision study of Sec. 4.1 (with prec=FP64)."""
     rp, ci, va = _csr(A)
     n = len(rp) - 1
     b = np.ascontiguousarray(b, dtype=np.float64)
@@ -412,6 +422,7 @@ def gmres(A, b, x0=None, m=30, tol=1e-10, ortho=CGSR, prec=FP64, maxiter=10000, 
     o.stall_factor, o.stall_window = stall_factor, stall_window
     o.orth_norm, o.orth_threshold, o.orth_iters = orth_norm, orth_threshold, orth_iters
     o.split_bytes = int(bool(split_bytes))
+    o.pv_mask = int(pv_mask)
     if ilu is not None:
         if M is not None:
             raise ValueError("one preconditioner at a time")

@@ -168,6 +168,15 @@ double orc_s_norm2(int32_t k, const double *S, int32_t ld, int32_t iters)
  * The restart cycle in binary64 and in binary32.
  * ------------------------------------------------------------------------- */
 
+/* A value written to a variable of the per-variable study (Sec. 4.1): rounded
+ * to binary32 when its bit is in mask, else unchanged.  PV(x, bit) applies it
+ * with the mask `pv` in scope, in the cycle's working type R. */
+static double pv32(double v, int32_t mask, int32_t bit)
+{
+    return (mask & bit) ? (double)(float)v : v;
+}
+#define PV(x, bit) ((R)pv32((double)(x), pv, (bit)))
+
 #define R double
 #define FN(name) name##_f64
 #define SQRT_R(x) sqrt(x)
@@ -337,16 +346,17 @@ static int run_cycle(int32_t n, const int32_t *rowptr, const int32_t *colind, co
     } else {
         /* limited mixed: A for the next Krylov vector and M stored in
          * binary32, used in binary64 arithmetic (the basis is rounded by
-         * orc_store) */
+         * orc_store); the same for the per-variable switches of A and M */
         double *a = (double *)c.a, *pm = (double *)c.pm;
         for (int32_t k = 0; k < nnz; ++k)
-            a[k] = !limited ? vals[k]
+            a[k] = !limited ? pv32(vals[k], rs->pv_mask, ORC_PV_A_KRYLOV)
                             : (rs->split_bytes ? orc_high_part(vals[k]) : (double)(float)vals[k]);
         memcpy(c.r0, r0, sizeof(double) * (size_t)n);
         /* M in binary32 for limited mixed and for the binary32 ILU factors */
         for (int32_t k = 0; k < pnnz; ++k)
             pm[k] = (limited || (rs->left_precond && rs->ilu32)) ? (double)(float)pm_vals[k]
-                                                                   : pm_vals[k];
+                                                                   : pv32(pm_vals[k], rs->pv_mask,
+                                                                          ORC_PV_M);
         rc = cycle_f64(n, rowptr, colind, (double *)c.a, (double *)c.r0, m, kmax, ortho, prec,
                        rs, pm_rowptr, pm_colind, pm_vals ? (double *)c.pm : NULL,
                        (double *)c.V, (double *)c.Hb, (double *)c.H, (double *)c.s,
@@ -369,7 +379,7 @@ static int run_cycle(int32_t n, const int32_t *rowptr, const int32_t *colind, co
 
 static int restart_ok(const orc_restart *rs)
 {
-    return rs && rs->tau >= 0 && rs->inner_abs >= 0 && rs->stall_factor >= 0 &&
+    return rs && (rs->pv_mask & ~ORC_PV_ALL) == 0 && rs->tau >= 0 && rs->inner_abs >= 0 && rs->stall_factor >= 0 &&
            (rs->stall_factor == 0 || rs->stall_window >= 1) && rs->orth_norm >= ORC_ORTH_OFF &&
            rs->orth_norm <= ORC_ORTH_FROBENIUS &&
            (rs->orth_norm != ORC_ORTH_SPECTRAL || rs->orth_iters >= 1);
@@ -385,7 +395,7 @@ int orc_arnoldi_cycle_ex(int32_t n, const int32_t *rowptr, const int32_t *colind
 {
     if (n <= 0 || m < 1 || kmax < 1 || kmax > m || (ortho != ORC_MGS && ortho != ORC_CGSR) ||
         prec < ORC_FP64 || prec > ORC_MIXED_LIMITED || !csr_ok(n, rowptr, colind) ||
-        !restart_ok(rs))
+        !restart_ok(rs) || (rs->pv_mask && prec != ORC_FP64))
         return -1;
     if (pm_vals && !csr_ok(n, pm_rowptr, pm_colind))
         return -1;
@@ -491,6 +501,27 @@ static float residual_f32(int32_t n, const int32_t *rowptr, const int32_t *colin
     return sqrtf(ss);
 }
 
+/* The residual of the per-variable study: z = b - A x with A and b as stored
+ * (a, bs: binary32 values under ORC_PV_A_RESID / ORC_PV_B) and the product
+ * A x stored in binary32 under ORC_PV_AX before the subtraction; binary64
+ * arithmetic.  Returns ||z||_2. */
+static double residual_pv(int32_t n, const int32_t *rowptr, const int32_t *colind,
+                          const double *a, const double *bs, const double *x, double *z,
+                          int32_t pv)
+{
+    double ss = 0;
+    for (int32_t i = 0; i < n; ++i) {
+        double acc = 0;
+        for (int32_t k = rowptr[i]; k < rowptr[i + 1]; ++k)
+            acc += a[k] * x[colind[k]];
+        acc = pv32(acc, pv, ORC_PV_AX);
+        double zi = bs[i] - acc;
+        z[i] = zi;
+        ss += zi * zi;
+    }
+    return sqrt(ss);
+}
+
 int orc_gmres(int32_t n, const int32_t *rowptr, const int32_t *colind, const double *vals,
               const double *b, double *x, const orc_opts *o,
               const int32_t *pm_rowptr, const int32_t *pm_colind, const double *pm_vals,
@@ -501,12 +532,15 @@ int orc_gmres(int32_t n, const int32_t *rowptr, const int32_t *colind, const dou
         o->prec > ORC_MIXED_LIMITED || !csr_ok(n, rowptr, colind) || !b || !x ||
         o->stall_factor < 0 || o->stall_window < 0 || o->orth_norm < ORC_ORTH_OFF ||
         o->orth_norm > ORC_ORTH_FROBENIUS ||
-        (o->orth_norm == ORC_ORTH_SPECTRAL && o->orth_iters < 1))
+        (o->orth_norm == ORC_ORTH_SPECTRAL && o->orth_iters < 1) ||
+        (o->pv_mask & ~ORC_PV_ALL) || (o->pv_mask && o->prec != ORC_FP64))
         return -1;
     if (pm_vals && !csr_ok(n, pm_rowptr, pm_colind))
         return -1;
 
     const int32_t m = o->m;
+    /* refinement variables of the per-variable study stored in binary32 */
+    const int32_t pvr = o->pv_mask & (ORC_PV_A_RESID | ORC_PV_B | ORC_PV_X | ORC_PV_AX);
     orc_info inf;
     memset(&inf, 0, sizeof(inf));
     inf.bnorm = nrm2_f64(n, b);
@@ -541,8 +575,24 @@ int orc_gmres(int32_t n, const int32_t *rowptr, const int32_t *colind, const dou
             }
         }
     }
-    if (!z || !u || !arn || (o->prec == ORC_ALL_FP32 && (!a32 || !b32 || !x32 || !z32))) {
+    double *ar = NULL, *br = NULL;
+    if (pvr) {
+        int32_t nnz = rowptr[n];
+        ar = (double *)malloc(sizeof(double) * (size_t)(nnz + 1));
+        br = (double *)malloc(sizeof(double) * (size_t)n);
+        if (ar && br) {
+            for (int32_t k = 0; k < nnz; ++k)
+                ar[k] = pv32(vals[k], pvr, ORC_PV_A_RESID);
+            for (int32_t i = 0; i < n; ++i) {
+                br[i] = pv32(b[i], pvr, ORC_PV_B);
+                x[i] = pv32(x[i], pvr, ORC_PV_X);
+            }
+        }
+    }
+    if (!z || !u || !arn || (o->prec == ORC_ALL_FP32 && (!a32 || !b32 || !x32 || !z32)) ||
+        (pvr && (!ar || !br))) {
         free(z); free(u); free(arn); free(a32); free(b32); free(x32); free(z32);
+        free(ar); free(br);
         return -2;
     }
 
@@ -557,6 +607,7 @@ int orc_gmres(int32_t n, const int32_t *rowptr, const int32_t *colind, const dou
     rs.split_bytes = o->split_bytes;
     rs.left_precond = o->left_precond;
     rs.ilu32 = o->ilu32;
+    rs.pv_mask = o->pv_mask;
     int32_t cycle_len = m;
     int rc = 0;
     for (;;) {
@@ -570,10 +621,12 @@ int orc_gmres(int32_t n, const int32_t *rowptr, const int32_t *colind, const dou
             for (int32_t i = 0; i < n; ++i)
                 z[i] = z32[i];
             rn = rn32;
+        } else if (pvr) {
+            rn = residual_pv(n, rowptr, colind, ar, br, x, z, pvr);
         } else {
             rn = orc_residual(n, rowptr, colind, vals, b, x, z);
         }
-        double true_rel = (o->prec == ORC_ALL_FP32)
+        double true_rel = (o->prec == ORC_ALL_FP32 || pvr)
                               ? orc_residual(n, rowptr, colind, vals, b, x, NULL) / inf.bnorm
                               : rn / inf.bnorm;
         if (cyc_hist)
@@ -608,8 +661,10 @@ int orc_gmres(int32_t n, const int32_t *rowptr, const int32_t *colind, const dou
                 x32[i] = x32[i] + (float)u[i];
         } else {
             #pragma omp parallel for schedule(static)
-            for (int32_t i = 0; i < n; ++i)
+            for (int32_t i = 0; i < n; ++i) {
                 x[i] = x[i] + u[i];
+                x[i] = pv32(x[i], pvr, ORC_PV_X);
+            }
         }
         if (arn_hist)
             for (int32_t i = 0; i < j; ++i)
@@ -628,5 +683,6 @@ int orc_gmres(int32_t n, const int32_t *rowptr, const int32_t *colind, const dou
     if (info)
         *info = inf;
     free(z); free(u); free(arn); free(a32); free(b32); free(x32); free(z32);
+    free(ar); free(br);
     return rc;
 }

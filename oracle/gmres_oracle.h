@@ -48,6 +48,32 @@ enum { ORC_MGS = 0, ORC_CGSR = 1 };
 enum { ORC_FP64 = 0, ORC_MIXED = 1, ORC_MIXED_BF16 = 2, ORC_MIXED_FP16 = 3, ORC_ALL_FP32 = 4,
        ORC_MIXED_LIMITED = 5 };
 
+/* Per-variable precision switches (Sec. 4.1, the study that stores one
+ * variable at a time in binary32 while the rest of the solver stays binary64):
+ * with prec = ORC_FP64, every value written to a variable whose bit is set is
+ * rounded to binary32; arithmetic stays binary64.  The paper's "correction
+ * variables" (inside the restart cycle) and "refinement variables" (the
+ * residual and the update):
+ *   correction  ORC_PV_A_KRYLOV  A as used to compute the next Krylov vector
+ *               ORC_PV_M         the preconditioner
+ *               ORC_PV_V         the Krylov basis
+ *               ORC_PV_W         the Krylov vector being orthogonalised (w)
+ *               ORC_PV_H         the Hessenberg matrix (projection
+ *                                coefficients, h_{j+1,j}, rotated entries)
+ *               ORC_PV_GIVENS    the least-squares vectors: rotations
+ *                                (alpha, beta), right-hand side s, solution y
+ *               ORC_PV_Z         the non-preconditioned residual z as the
+ *                                cycle receives it
+ *   refinement  ORC_PV_A_RESID   A as used for the residual
+ *               ORC_PV_B         the right-hand side b
+ *               ORC_PV_X         the solution x (the update x += u rounds)
+ *               ORC_PV_AX        the vector A x from which z = b - A x is formed */
+enum {
+    ORC_PV_A_KRYLOV = 1, ORC_PV_M = 2, ORC_PV_V = 4, ORC_PV_W = 8, ORC_PV_H = 16,
+    ORC_PV_GIVENS = 32, ORC_PV_Z = 64, ORC_PV_A_RESID = 128, ORC_PV_B = 256, ORC_PV_X = 512,
+    ORC_PV_AX = 1024, ORC_PV_ALL = 2047
+};
+
 typedef struct {
     int32_t m;            /* maximum inner iterations per restart cycle         */
     int32_t ortho;        /* ORC_MGS or ORC_CGSR                                 */
@@ -79,6 +105,7 @@ typedef struct {
                              preconditioner M, applied as w = A M v_j)        */
     int32_t ilu32;        /* with left_precond in ORC_FP64: the factors stored in
                              binary32 (the paper's FP32-ILU variant, Sec. 4.2) */
+    int32_t pv_mask;      /* ORC_PV_* bits (prec must be ORC_FP64); 0 = none   */
 } orc_opts;
 
 enum { ORC_ORTH_OFF = 0, ORC_ORTH_SPECTRAL = 1, ORC_ORTH_FROBENIUS = 2 };
@@ -99,6 +126,7 @@ typedef struct {
     int32_t split_bytes;  /* as in orc_opts */
     int32_t left_precond; /* as in orc_opts */
     int32_t ilu32;        /* as in orc_opts */
+    int32_t pv_mask;      /* as in orc_opts (the correction variables act here) */
 } orc_restart;
 
 typedef struct {

@@ -233,6 +233,90 @@ def pin_arnoldi_step():
                     assert np.array_equal(O.round_basis(vn, prec, len(b)), c["V"][j])
 
 
+def _f32_exact(a):
+    a = np.asarray(a, dtype=np.float64)
+    return np.array_equal(a.astype(np.float32).astype(np.float64), a)
+
+
+def pin_pv_storage():
+    """Per-variable precision study (Sec. 4.1): a switch stores exactly its
+    variable in binary32.  In one binary64 cycle, the basis switch makes every
+    stored basis entry a binary32 value, the Hessenberg switch every entry of
+    the unrotated and rotated Hessenberg matrices, the least-squares switch
+    the rotations, s and y -- and the other quantities stay genuinely
+    binary64.  The A, M and z switches equal the plain binary64 cycle run on
+    binary32-rounded A, M and r0 (their definitions), bit for bit; the w
+    switch moves the cycle by binary32 roundings only."""
+    A, b = _cd_small()
+    rp, ci, va = A
+    M = (rp, ci, O.spai_values(A, O.spai_jacobi_params()))
+    r32 = lambda v: np.asarray(v).astype(np.float32).astype(np.float64)
+    for ortho in (O.MGS, O.CGSR):
+        base = O.arnoldi_cycle(A, b, m=12, ortho=ortho, prec=O.FP64)
+        j = base["j"]
+        assert not _f32_exact(base["V"][:j]) and not _f32_exact(base["Hbar"][:, :j])
+        c = O.arnoldi_cycle(A, b, m=12, ortho=ortho, prec=O.FP64, pv_mask=O.PV_V)
+        assert _f32_exact(c["V"][: j + 1]) and not _f32_exact(c["Hbar"][:, :j])
+        c = O.arnoldi_cycle(A, b, m=12, ortho=ortho, prec=O.FP64, pv_mask=O.PV_H)
+        assert _f32_exact(c["Hbar"][:, :j]) and _f32_exact(c["H"][:, :j])
+        assert not _f32_exact(c["V"][:j]) and not _f32_exact(c["cs"][:j])
+        c = O.arnoldi_cycle(A, b, m=12, ortho=ortho, prec=O.FP64, pv_mask=O.PV_GIVENS)
+        for k in ("cs", "sn", "y"):
+            assert _f32_exact(c[k][:j]), k
+        assert _f32_exact(c["s"][: j + 1]) and not _f32_exact(c["H"][:, :j])
+        c = O.arnoldi_cycle(A, b, m=12, ortho=ortho, prec=O.FP64, pv_mask=O.PV_A_KRYLOV)
+        d = O.arnoldi_cycle((rp, ci, r32(va)), b, m=12, ortho=ortho, prec=O.FP64)
+        assert np.array_equal(c["Hbar"], d["Hbar"]) and np.array_equal(c["u"], d["u"])
+        c = O.arnoldi_cycle(A, b, m=12, ortho=ortho, prec=O.FP64, pv_mask=O.PV_Z)
+        d = O.arnoldi_cycle(A, r32(b), m=12, ortho=ortho, prec=O.FP64)
+        assert np.array_equal(c["Hbar"], d["Hbar"]) and np.array_equal(c["u"], d["u"])
+        c = O.arnoldi_cycle(A, b, m=12, ortho=ortho, prec=O.FP64, M=M, pv_mask=O.PV_M)
+        d = O.arnoldi_cycle(A, b, m=12, ortho=ortho, prec=O.FP64, M=(rp, ci, r32(M[2])))
+        assert np.array_equal(c["Hbar"], d["Hbar"]) and np.array_equal(c["u"], d["u"])
+        c = O.arnoldi_cycle(A, b, m=12, ortho=ortho, prec=O.FP64, pv_mask=O.PV_W)
+        dh = np.abs(c["Hbar"] - base["Hbar"]).max() / np.abs(base["Hbar"]).max()
+        assert 0 < dh <= 1e-5, dh
+
+
+def pin_pv_limited_is_three_switches():
+    """The paper's limited mixed solver (Sec. 4.1) is, by its definition, the
+    binary64 solver with A for the Krylov step, M and the basis stored in
+    binary32: the per-variable switches for those three variables give it bit
+    for bit, with and without a preconditioner, for MGS and CGSR."""
+    A = I.convdiff2d(20, pe=10.0)
+    b = I.rhs_ones_noise(A, 1e-3, 2)
+    M = (A[0], A[1], O.spai_values(A, O.spai_jacobi_params()))
+    for ortho in (O.MGS, O.CGSR):
+        for Mx in (None, M):
+            xl, il = O.gmres(A, b, m=20, tol=1e-11, ortho=ortho, prec=O.MIXED_LIMITED,
+                             tau=0.0, repeat_first=False, M=Mx, history=True)
+            xp, ip = O.gmres(A, b, m=20, tol=1e-11, ortho=ortho, prec=O.FP64, M=Mx,
+                             pv_mask=O.PV_A_KRYLOV | O.PV_M | O.PV_V, history=True)
+            assert np.array_equal(xl, xp) and np.array_equal(il["arnoldi"], ip["arnoldi"])
+
+
+def pin_pv_refinement_vs_correction():
+    """Sec. 4.1 and Sec. 2: with any one correction variable (A for the Krylov
+    step, w, the basis, the Hessenberg matrix, the least-squares vectors, the
+    cycle's copy of z) in binary32 the restarted solver still reaches a
+    binary64 relative residual of 1e-12; with any one refinement variable (A
+    for the residual, b, x, the product A x) in binary32 its true residual
+    cannot fall below about the binary32 unit roundoff: it stays above
+    u32 / 10 whatever the iteration count."""
+    A = I.convdiff2d(30, pe=10.0)
+    b = I.rhs_ones_noise(A, 1e-3, 9)
+    u32 = 2.0 ** -24
+    for ortho in (O.MGS, O.CGSR):
+        for bit in (O.PV_A_KRYLOV, O.PV_W, O.PV_V, O.PV_H, O.PV_GIVENS, O.PV_Z):
+            _, i = O.gmres(A, b, m=30, tol=1e-12, ortho=ortho, prec=O.FP64, maxiter=2000,
+                           pv_mask=bit)
+            assert i["converged"] and i["relres"] <= 1e-12, (ortho, bit, i)
+        for bit in (O.PV_A_RESID, O.PV_B, O.PV_X, O.PV_AX):
+            _, i = O.gmres(A, b, m=30, tol=1e-12, ortho=ortho, prec=O.FP64, maxiter=1500,
+                           pv_mask=bit, history=True)
+            assert not i["converged"] and min(i["cycle_relres"]) > u32 / 10, (ortho, bit, i)
+
+
 def pin_givens_least_squares():
     """The rotated problem solves min ||beta e1 - Hbar y|| (checked against
     numpy lstsq), |s_{j+1}| equals that minimum, and it never increases."""
@@ -761,5 +845,6 @@ ALL_PINS = [
     pin_spai_grad_m_fd, pin_spai_grad_params_fd, pin_spai_special_cases, pin_spai_optimum,
     pin_spai_feature_invariants, pin_adam_first_step, pin_stall_restart, pin_s_matrix,
     pin_orthogonality_loss_restart, pin_limited_mixed, pin_split_bytes, pin_ilu0,
-    pin_ilu_left_gmres, pin_arnoldi_step,
+    pin_ilu_left_gmres, pin_arnoldi_step, pin_pv_storage, pin_pv_limited_is_three_switches,
+    pin_pv_refinement_vs_correction,
 ]

@@ -39,14 +39,14 @@ MUTATIONS = [
      "acc -= H[(size_t)i * ld + l] * y[l];", "transposed triangle in back substitution"),
     ("cycle_impl.inc", "for (int32_t l = i + 1; l < j; ++l)",
      "for (int32_t l = i + 2; l < j; ++l)", "dropped term in back substitution"),
-    ("cycle_impl.inc", "V[(size_t)(c + 1) * n + r] = (R)orc_store(w[r] / hnext, prec, n);",
-     "V[(size_t)(c + 1) * n + r] = (R)orc_store(w[r], prec, n);", "v_{j+1} not normalised"),
-    ("cycle_impl.inc", "V[r] = (R)orc_store(rr[r] / beta, prec, n);",
-     "V[r] = (R)orc_store(rr[r], prec, n);", "v_1 not normalised"),
+    ("cycle_impl.inc", "V[(size_t)(c + 1) * n + r] = (R)orc_store(w[r] / hnext, vprec, n);",
+     "V[(size_t)(c + 1) * n + r] = (R)orc_store(w[r], vprec, n);", "v_{j+1} not normalised"),
+    ("cycle_impl.inc", "V[r] = (R)orc_store(rr[r] / beta, vprec, n);",
+     "V[r] = (R)orc_store(rr[r], vprec, n);", "v_1 not normalised"),
     ("cycle_impl.inc", "for (int32_t i = 0; i < j; ++i) {\n        const R *v = V + (size_t)i * n;",
      "for (int32_t i = 0; i + 1 < j; ++i) {\n        const R *v = V + (size_t)i * n;",
      "MGS skips the last projection"),
-    ("cycle_impl.inc", "FN(cgs_pass)(n, j, V, w, g2);\n", "",
+    ("cycle_impl.inc", "FN(cgs_pass)(n, j, V, w, g2, pv);\n", "",
      "CGSR without its second pass"),
     ("cycle_impl.inc", "Hb[(size_t)c * ld + c + 1] = hnext;", "Hb[(size_t)c * ld + c + 1] = wnorm0;",
      "subdiagonal from the wrong norm"),
@@ -69,7 +69,7 @@ MUTATIONS = [
      "ah[j - rs->stall_window] < arnres", "stall factor dropped"),
     ("gmres_oracle.c", "acc += S[(size_t)l * ld + i] * yv[i];",
      "acc += S[(size_t)i * ld + l] * yv[i];", "power method multiplies by S, not S^T"),
-    ("gmres_oracle.c", "a[k] = !limited ? vals[k]", "a[k] = 1 ? vals[k]",
+    ("gmres_oracle.c", "a[k] = !limited ? pv32(", "a[k] = 1 ? pv32(",
      "limited mode keeps A in binary64"),
     ("gmres_oracle.c", "u &= 0xFFFFFFFF00000000ull;", "u &= 0xFFFFFFFFF0000000ull;",
      "high part keeps four low-order bits"),
@@ -79,13 +79,21 @@ MUTATIONS = [
      "ILU(0) without the division by the pivot"),
     ("ilu_oracle.c", "lu[q] = lu[q] - lu[p] * lu[kj];", "lu[q] = lu[q] + lu[p] * lu[kj];",
      "ILU(0) update sign"),
-    ("cycle_impl.inc", "FN(ilu_apply)(n, pm_rowptr, pm_colind, pm, r0, rl);\n        rr = rl;",
-     "rr = r0;", "left preconditioner not applied to the residual"),
+    ("cycle_impl.inc", "FN(ilu_apply)(n, pm_rowptr, pm_colind, pm, rr, rl);\n        rr = rl;",
+     "", "left preconditioner not applied to the residual"),
     ("cycle_impl.inc", "for (int32_t p = rowptr[i]; p < rowptr[i + 1] && colind[p] < i; ++p)\n            acc -= lu[p] * out[colind[p]];",
      "for (int32_t p = rowptr[i]; p < rowptr[i + 1] && colind[p] <= i; ++p)\n            acc -= lu[p] * out[colind[p]];",
      "forward substitution takes in the diagonal"),
     ("cycle_impl.inc", "FN(spmv)(n, rowptr, colind, a, V + (size_t)(ncols - 1) * n, w);",
      "FN(spmv)(n, rowptr, colind, a, V, w);", "replayed step multiplies v_1, not v_j"),
+    ("gmres_oracle.c", "x[i] = x[i] + u[i];\n                x[i] = pv32(x[i], pvr, ORC_PV_X);",
+     "x[i] = x[i] + u[i];", "solution switch not applied to the update"),
+    ("cycle_impl.inc", "hij = PV(hij, ORC_PV_H);", "hij = PV(hij, ORC_PV_W);",
+     "MGS coefficient rounded under the w switch"),
+    ("cycle_impl.inc", "const int32_t vprec = (pv & ORC_PV_V) ? ORC_MIXED : prec;",
+     "const int32_t vprec = prec;", "basis switch ignored"),
+    ("gmres_oracle.c", "ar[k] = pv32(vals[k], pvr, ORC_PV_A_RESID);", "ar[k] = vals[k];",
+     "residual keeps binary64 A under its switch"),
     ("spai_oracle.c", "atr[colind[k]] += vals[k] * r[i];", "atr[i] += vals[k] * r[colind[k]];",
      "A instead of A^T in the preconditioner gradient"),
     ("spai_oracle.c", "d2[o] = z2[o] > 0 ? dgk * params[P_W3 + o] : 0;",
