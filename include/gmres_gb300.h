@@ -96,6 +96,31 @@ typedef enum {
 #define GMRES_ORTH_SPECTRAL 1  /* power method on S^T S                        */
 #define GMRES_ORTH_FROBENIUS 2 /* ||S||_F, an upper bound of ||S||_2          */
 
+/* Per-variable precision switches (gmres_opts.pv_mask; Sec. 4.1, the study
+ * that stores one solver variable at a time in binary32 while the rest of the
+ * binary64 solver is unchanged): with GMRES_FP64 on the grid path, every value
+ * written to a variable whose bit is set is rounded to binary32 (round to
+ * nearest even); arithmetic stays binary64.  The paper's "correction
+ * variables" (the restart cycle) ... */
+#define GMRES_PV_A_KRYLOV 1   /* A as used to compute the next Krylov vector */
+#define GMRES_PV_M 2          /* the preconditioner M                        */
+#define GMRES_PV_V 4          /* the Krylov basis                            */
+#define GMRES_PV_W 8          /* the Krylov vector being orthogonalised, w   */
+#define GMRES_PV_H 16         /* the Hessenberg matrix: projection
+                                 coefficients, h_{j+1,j}, rotated entries    */
+#define GMRES_PV_GIVENS 32    /* the least-squares vectors: rotations, the
+                                 rotated right-hand side s, the solution y   */
+#define GMRES_PV_Z 64         /* the non-preconditioned residual z as the
+                                 cycle receives it                           */
+/* ... and its "refinement variables" (the residual and the update): */
+#define GMRES_PV_A_RESID 128  /* A as used for the residual z = b - A x      */
+#define GMRES_PV_B 256        /* the right-hand side b                       */
+#define GMRES_PV_X 512        /* the solution x (the update x += u rounds)   */
+#define GMRES_PV_AX 1024      /* the product A x from which z is formed      */
+/* With a refinement switch the solver tests its own (perturbed) residual; it
+ * then reports the binary64 residual of the returned x in gmres_info.relres
+ * and returns GMRES_OK only if that residual met tol (else GMRES_MAXITER). */
+
 /* Solver options (gmres_default_opts gives the defaults). */
 typedef struct gmres_opts {
     double tau;           /* restart when |s_{j+1}| <= tau * beta (Sec. 3, second
@@ -164,6 +189,10 @@ typedef struct gmres_opts {
                              triangle, 3 when every row has at most four
                              entries in it and every level fits the grid,
                              else 2                                          */
+    int32_t pv_mask;      /* GMRES_PV_* bits (default 0): the per-variable
+                             precision study; GMRES_FP64 on the grid path only
+                             (not with split storage or cgs_kernel 1), else
+                             gmres_solve returns GMRES_ERR_ARG                */
 } gmres_opts;
 
 /* Kernel classes reported in gmres_info (index into kernel_ms / kernel_bytes). */

@@ -355,7 +355,7 @@ __global__ void __launch_bounds__(ROWS_THREADS)
             for (int q = 0; q < RPL; ++q) {
                 const int o = wid * RW + lane * RPL + q;
                 const T t = ((tsm[o] + tsm[SR + o]) + tsm[2 * SR + o]) + tsm[3 * SR + o];
-                w[q] = w[q] - t;
+                w[q] = pv_round(w[q] - t, c.pv, PV_W);
                 if (MODE == 2)
                     nsq += w[q] * w[q];
                 if (MODE == 1)
@@ -378,7 +378,7 @@ __global__ void __launch_bounds__(ROWS_THREADS)
             rows_project<T, VT, RPL>(c, ncols, hs, r, t, pol_keep);
 #pragma unroll
             for (int q = 0; q < RPL; ++q) {
-                w[q] = w[q] - t[q];
+                w[q] = pv_round(w[q] - t[q], c.pv, PV_W);
                 if (MODE == 2)
                     nsq += w[q] * w[q];
             }
@@ -423,10 +423,10 @@ __global__ void __launch_bounds__(ROWS_THREADS)
     __shared__ T snorm;
     reduce_columns(part + MMAX + 1, gridDim.x, 1, &snorm);
     for (int i = threadIdx.x; i < ncols; i += blockDim.x)
-        c.h1[i] = ldcg(c.h1 + i) + ldcg(c.h2 + i);
+        c.h1[i] = pv_round(ldcg(c.h1 + i) + ldcg(c.h2 + i), c.pv, PV_H);
     __threadfence();
     __syncthreads();
-    givens_step(c, ncols - 1, c.h1, wsqrt(snorm));
+    givens_step(c, ncols - 1, c.h1, pv_round(wsqrt(snorm), c.pv, PV_H));
 }
 
 // Pass B with the slice held in registers (binary32 basis): w <- w - V h1,
@@ -524,10 +524,12 @@ __global__ void __launch_bounds__(PB_THREADS)
 
 // out[col] = sum over the blocks of part[b][col], col < ncols, and, when
 // `extra` >= 0, ctl->wnorm0 = sqrt(sum of part[b][MMAX+1]) (the ||A v_j||
-// reference of pass A).  One block per column, fixed-order tree.
+// reference of pass A).  One block per column, fixed-order tree.  pv: the
+// per-variable switches (PV_H stores the projection coefficients in binary32).
 template <class T>
 __global__ void __launch_bounds__(256) k_reduce_cols(const T *part, int nblocks, int ncols,
-                                                     T *out, Ctl *ctl, int with_norm) {
+                                                     T *out, Ctl *ctl, int with_norm,
+                                                     unsigned pv = 0) {
     // with_norm 2: the Gram column of MODE 3 (runs under its condition)
     if (with_norm == 2 ? !(ctl->j == ncols && !ctl->breakdown && !ctl->nonfinite)
                        : !ctl->active)
@@ -541,7 +543,7 @@ __global__ void __launch_bounds__(256) k_reduce_cols(const T *part, int nblocks,
     a = block_sum1(a, sred);
     if (threadIdx.x == 0) {
         if (col < ncols)
-            out[col] = a;
+            out[col] = pv_round(a, pv, PV_H);
         else if (with_norm)
             ctl->wnorm0 = (double)wsqrt(a);
     }

@@ -35,6 +35,11 @@ using namespace gmres_host;
 
 namespace {
 constexpr int kThreads = 256;
+static_assert(GMRES_PV_A_KRYLOV == PV_A_KRYLOV && GMRES_PV_M == PV_M && GMRES_PV_V == PV_V &&
+                  GMRES_PV_W == PV_W && GMRES_PV_H == PV_H && GMRES_PV_GIVENS == PV_GIVENS &&
+                  GMRES_PV_Z == PV_Z && GMRES_PV_A_RESID == PV_A_RESID && GMRES_PV_B == PV_B &&
+                  GMRES_PV_X == PV_X && GMRES_PV_AX == PV_AX,
+              "per-variable switch bits of the C-ABI and the kernels");
 }  // namespace
 
 namespace {
@@ -218,12 +223,21 @@ GridCtx<T, VT> make_ctx(gmres_handle *h, int m) {
         c.aform = 1;
     }
     c.left = ilu_on(h) ? 1 : 0;
+    // per-variable precision study (binary64 solves only): A for the Krylov
+    // step and M read from their binary32 copies in binary64 arithmetic, A
+    // for the residual from the binary32 copy; the rest rounds in the kernels
+    c.pv = (std::is_same<T, double>::value && !h->limited) ? (unsigned)h->opts.pv_mask : 0u;
+    c.a_res32 = h->vals32.as<float>();
+    if ((c.pv & PV_A_KRYLOV) && !h->split) {
+        c.a_lim = h->vals32.as<float>();
+        c.aform = 1;
+    }
     if (spai_on(h)) {
         c.prowptr = c.rowptr;
         c.pcolind = c.colind;
         c.pvals = std::is_same<T, double>::value ? reinterpret_cast<const T *>(h->pvals64.p)
                                                  : reinterpret_cast<const T *>(h->pvals32.p);
-        if (h->limited)
+        if (h->limited || (c.pv & PV_M))
             c.pvals_lim = h->pvals32.as<float>();
     }
     return c;
@@ -371,7 +385,7 @@ template <class T, class VT>
 cudaError_t apply_ilu(gmres_handle *h, const T *z, T *tmp, T *out) {
     int *err = &h->ctl.as<Ctl>()->timeout;
     if constexpr (std::is_same<T, double>::value) {
-        if (!h->limited && !h->opts.ilu_binary32)
+        if (!h->limited && !h->opts.ilu_binary32 && !(h->opts.pv_mask & PV_M))
             return ilu_apply<double, double>(h, h->ilu64.as<double>(), z, tmp, out, err);
         return ilu_apply<double, float>(h, h->ilu32.as<float>(), z, tmp, out, err);
     } else {
@@ -397,7 +411,7 @@ gmres_status left_start(gmres_handle *h, GridCtx<T, VT> &c, Acct &acct) {
 template <class T, class VT>
 bool fused_normalize(const gmres_handle *h, const GridCtx<T, VT> &c, bool coop_mgs) {
     return h->opts.normalize_fused && !c.left && !c.pvals &&
-           h->opts.orth_norm == GMRES_ORTH_OFF && !coop_mgs;
+           h->opts.orth_norm == GMRES_ORTH_OFF && !coop_mgs && !c.pv;
 }
 
 template <class T, class VT>
@@ -444,7 +458,8 @@ gmres_status enqueue_cgs_rows(gmres_handle *h, GridCtx<T, VT> &c, int ncols, Acc
     const int pf = h->opts.l2_prefetch;
     k_cgs_rows<T, VT, 0, SPLIT><<<gsz[0], ROWS_THREADS, 0, h->stream>>>(c, ncols, c.part, kpb[0],
                                                                         pf);
-    k_reduce_cols<T><<<ncols + 1, 256, 0, h->stream>>>(c.part, gsz[0], ncols, c.h1, c.ctl, 1);
+    k_reduce_cols<T><<<ncols + 1, 256, 0, h->stream>>>(c.part, gsz[0], ncols, c.h1, c.ctl, 1,
+                                                       c.pv);
     if constexpr (std::is_same<T, float>::value && std::is_same<VT, float>::value) {
         if (h->opts.cgs_kernel != 3) {
             // pass B with the slice in registers; KC vectors per warp
@@ -465,16 +480,19 @@ gmres_status enqueue_cgs_rows(gmres_handle *h, GridCtx<T, VT> &c, int ncols, Acc
             const int64_t kb = (nsl_b + cap - 1) / cap;
             const int gb = (int)((nsl_b + kb - 1) / kb);
             kfn<<<gb, PB_THREADS, 0, h->stream>>>(c, ncols, c.part, kb);
-            k_reduce_cols<T><<<ncols, 256, 0, h->stream>>>(c.part, gb, ncols, c.h2, c.ctl, 0);
+            k_reduce_cols<T><<<ncols, 256, 0, h->stream>>>(c.part, gb, ncols, c.h2, c.ctl, 0,
+                                                           c.pv);
         } else {
             k_cgs_rows<T, VT, 1, SPLIT><<<gsz[1], ROWS_THREADS, 0, h->stream>>>(c, ncols, c.part,
                                                                                 kpb[1], pf);
-            k_reduce_cols<T><<<ncols, 256, 0, h->stream>>>(c.part, gsz[1], ncols, c.h2, c.ctl, 0);
+            k_reduce_cols<T><<<ncols, 256, 0, h->stream>>>(c.part, gsz[1], ncols, c.h2, c.ctl, 0,
+                                                           c.pv);
         }
     } else {
         k_cgs_rows<T, VT, 1, SPLIT><<<gsz[1], ROWS_THREADS, 0, h->stream>>>(c, ncols, c.part,
                                                                             kpb[1], pf);
-        k_reduce_cols<T><<<ncols, 256, 0, h->stream>>>(c.part, gsz[1], ncols, c.h2, c.ctl, 0);
+        k_reduce_cols<T><<<ncols, 256, 0, h->stream>>>(c.part, gsz[1], ncols, c.h2, c.ctl, 0,
+                                                       c.pv);
     }
     k_cgs_rows<T, VT, 2, SPLIT><<<gsz[2], ROWS_THREADS, 0, h->stream>>>(c, ncols, c.part, kpb[2],
                                                                         pf);
@@ -511,12 +529,19 @@ gmres_status enqueue_step_core(gmres_handle *h, GridCtx<T, VT> &c, int col, gmre
         CK((launch_spmv_norm<T, VT>(h, c, col, c.t, L)));
         std::swap(c.w, c.t);
     } else if (c.left) {
-        // t = A v_j, w = M^-1 t (left preconditioning, Alg. 1)
-        CK((launch_spmv_step<T, VT, VT>(h, c, vj, c.t, L)));
+        // t = A v_j, w = M^-1 t (left preconditioning, Alg. 1); under the
+        // per-variable w switch w, not t, is the stored Krylov vector
+        GridCtx<T, VT> ct = c;
+        ct.pv = c.pv & ~(unsigned)PV_W;
+        CK((launch_spmv_step<T, VT, VT>(h, ct, vj, c.t, L)));
         h->timer.end(GMRES_K_SPMV, e);
         acct.launches[GMRES_K_SPMV]++;
         e = h->timer.begin();
         CK((apply_ilu<T, VT>(h, c.t, h->t2.as<T>(), c.w)));
+        if (c.pv & PV_W) {
+            k_round32<T><<<h->grid, kThreads, 0, h->stream>>>(h->n, c.w, c.ctl);
+            CKL();
+        }
         h->timer.end(GMRES_K_PRECOND, e);
         acct.launches[GMRES_K_PRECOND] += 2;
         e = h->timer.begin();
@@ -529,6 +554,7 @@ gmres_status enqueue_step_core(gmres_handle *h, GridCtx<T, VT> &c, int col, gmre
         cp.a = c.pvals;
         cp.a_lim = c.pvals_lim;
         cp.aform = c.pvals_lim ? 1 : 0;
+        cp.pv = c.pv & ~(unsigned)PV_W;  // t = M v_j is not the Krylov vector w
         CK((launch_spmv_step<T, VT, VT>(h, cp, vj, c.t, L)));
         acct.launches[GMRES_K_PRECOND]++;
         h->timer.end(GMRES_K_PRECOND, e);
@@ -743,6 +769,11 @@ gmres_status solve_grid(gmres_handle *h, const double *b, double *x, int m, doub
     }
     c.tol_abs = tol * bnorm;
     c.inner_abs = h->opts.inner_factor * tol * bnorm;
+    if (c.pv & PV_X) {
+        // the solution as the study stores it from the start
+        k_round32<double><<<h->grid, kThreads, 0, h->stream>>>(h->n, x, nullptr);
+        CKL();
+    }
     cudaEvent_t e = h->timer.begin();
     CK(launch_residual(h, c, b, x, nullptr, 1));
     h->timer.end(GMRES_K_RESIDUAL, e);
@@ -812,7 +843,7 @@ gmres_status solve_grid(gmres_handle *h, const double *b, double *x, int m, doub
                 CK((launch_spmv_plain<T, float>(h, lanes_for<T, VT>(h), c.pvals_lim, c.t, c.w)));
             else
                 CK(launch_spmv_plain<T>(h, lanes_for<T, VT>(h), c.pvals, c.t, c.w));
-            k_axpy_x<T><<<h->grid, kThreads, 0, h->stream>>>(h->n, c.w, x, c.ctl);
+            k_axpy_x<T><<<h->grid, kThreads, 0, h->stream>>>(h->n, c.w, x, c.ctl, c.pv);
             CKL();
             acct.launches[GMRES_K_UPDATE] += 2;
         }
@@ -872,6 +903,23 @@ gmres_status solve_grid(gmres_handle *h, const double *b, double *x, int m, doub
             break;
         }
         prev_rn = rn;
+    }
+    if (c.pv & (PV_A_RESID | PV_B | PV_X | PV_AX)) {
+        // the solver tested its own residual (A, b, x or A x stored in
+        // binary32); report the binary64 residual of the x it returns, and
+        // count the solve as converged only if that met tol
+        GridCtx<T, VT> ct = c;
+        ct.pv = 0;
+        CK(cudaMemsetAsync(h->ctl.p, 0, sizeof(Ctl), h->stream));
+        CK(launch_residual(h, ct, b, x, nullptr, 0));
+        acct.launches[GMRES_K_RESIDUAL]++;
+        st = read_ctl(h);
+        if (st != GMRES_OK)
+            return st;
+        info->relres = h->hctl->rnorm / bnorm;
+        info->converged = h->hctl->converged;
+        if (result == GMRES_OK && !info->converged)
+            result = GMRES_MAXITER;
     }
     h->timer.harvest(info->kernel_ms);
     for (int k = 0; k < GMRES_K_COUNT; ++k) {
@@ -988,8 +1036,8 @@ gmres_status solve_dispatch_path(gmres_handle *h, const double *b, double *x, in
                                  gmres_ortho ortho, gmres_precision prec, int maxiter,
                                  gmres_info *info) {
     int path = h->opts.path;
-    const bool grid_only =
-        h->opts.orth_norm != GMRES_ORTH_OFF || h->limited || h->split || ilu_on(h);
+    const bool grid_only = h->opts.orth_norm != GMRES_ORTH_OFF || h->limited || h->split ||
+                           ilu_on(h) || h->opts.pv_mask != 0;
     if (path == GMRES_PATH_AUTO)
         path = (h->n <= 16384 && !spai_on(h) && !grid_only)
                    ? GMRES_PATH_BLOCK
@@ -1017,7 +1065,8 @@ gmres_status validate_opts(const gmres_opts *o) {
         (o->orth_norm != GMRES_ORTH_OFF && !(o->orth_threshold > 0)) ||
         o->repeat_first < -1 || o->repeat_first > 1 || o->precond < 0 || o->precond > 2 ||
         o->ilu_binary32 < 0 || o->ilu_binary32 > 1 || o->normalize_fused < 0 ||
-        o->normalize_fused > 1 || o->trsv_kernel < 0 || o->trsv_kernel > 3)
+        o->normalize_fused > 1 || o->trsv_kernel < 0 || o->trsv_kernel > 3 ||
+        o->pv_mask < 0 || o->pv_mask > (int32_t)PV_ALL)
         return GMRES_ERR_ARG;
     return GMRES_OK;
 }
@@ -1314,9 +1363,19 @@ gmres_status gmres_solve(gmres_t h, const double *b, double *x, int32_t m, doubl
         dx = h->xb.as<double>();
     }
     gmres_status st;
-    switch (prec) {
+    if (h->opts.pv_mask != 0 &&
+        (prec != GMRES_FP64 || h->split || h->opts.cgs_kernel == 1 ||
+         h->opts.path == GMRES_PATH_BLOCK)) {
+        st = GMRES_ERR_ARG;  // the per-variable study: binary64 solves on the grid path
+    } else switch (prec) {
     case GMRES_FP64:
-        st = solve_dispatch_path<double, double>(h, db, dx, m, tol, ortho, prec, maxiter, info);
+        // the basis switch stores V as binary32 values
+        if (h->opts.pv_mask & PV_V)
+            st = solve_dispatch_path<double, float>(h, db, dx, m, tol, ortho, prec, maxiter,
+                                                    info);
+        else
+            st = solve_dispatch_path<double, double>(h, db, dx, m, tol, ortho, prec, maxiter,
+                                                     info);
         break;
     case GMRES_MIXED:
         st = solve_dispatch_path<float, float>(h, db, dx, m, tol, ortho, prec, maxiter, info);
@@ -1366,6 +1425,7 @@ gmres_status gmres_residual(gmres_t h, const double *b, const double *x, double 
         return st;
     GridCtx<double, double> c = make_ctx<double, double>(h, 1);
     c.tol_abs = -1.0;
+    c.pv = 0;  // plain binary64, whatever the per-variable switches
     CK(launch_residual(h, c, b, x, z, 0));
     st = read_ctl(h);
     if (st != GMRES_OK)
@@ -1383,6 +1443,7 @@ gmres_status gmres_backward_error(gmres_t h, const double *b, const double *x, d
         return st;
     GridCtx<double, double> c = make_ctx<double, double>(h, 1);
     c.tol_abs = -1.0;
+    c.pv = 0;  // plain binary64, whatever the per-variable switches
     double *z = h->z.as<double>();
     CK(launch_residual(h, c, b, x, z, 0));
     ScopedBuf mx;
@@ -1434,6 +1495,8 @@ gmres_status arnoldi_impl(gmres_handle *h, const double *r0, int m, int kmax, gm
     c.tau = tau;
     c.inner_abs = inner_abs;
     c.kmax = kmax;
+    // one cycle from r0: only the per-variable switches inside the cycle act
+    c.pv &= ~(unsigned)(PV_A_RESID | PV_B | PV_X | PV_AX);
     Acct acct;
     CK(cudaMemsetAsync(h->ctl.p, 0, sizeof(Ctl), h->stream));
     // small arrays start at zero so unused entries export as zero
@@ -1590,8 +1653,13 @@ gmres_status gmres_arnoldi(gmres_t h, const double *r0, int32_t m, int32_t kmax,
         prec > GMRES_MIXED_LIMITED)
         return GMRES_ERR_ARG;
     h->timer.on = false;
+    if (h->opts.pv_mask != 0 && (prec != GMRES_FP64 || h->split || h->opts.cgs_kernel == 1))
+        return GMRES_ERR_ARG;
     switch (prec) {
     case GMRES_FP64:
+        if (h->opts.pv_mask & PV_V)
+            return arnoldi_impl<double, float>(h, r0, m, kmax, ortho, prec, tau, inner_abs, V,
+                                               Hbar, H, s, cs, sn, y, u, arn, jout, breakdown);
         return arnoldi_impl<double, double>(h, r0, m, kmax, ortho, prec, tau, inner_abs, V, Hbar,
                                             H, s, cs, sn, y, u, arn, jout, breakdown);
     case GMRES_MIXED:
@@ -1619,7 +1687,7 @@ gmres_status gmres_arnoldi_step(gmres_t h, const double *V, int32_t ncols, gmres
     if (!h || !V || !hcol || ncols < 1 || ncols > MMAX ||
         (ortho != GMRES_ORTHO_MGS && ortho != GMRES_ORTHO_CGSR) || prec < GMRES_FP64 ||
         prec > GMRES_MIXED_LIMITED || h->split || h->opts.precond != 0 ||
-        h->opts.normalize_fused)
+        h->opts.normalize_fused || h->opts.pv_mask != 0)
         return GMRES_ERR_ARG;
     h->timer.on = false;
     switch (prec) {

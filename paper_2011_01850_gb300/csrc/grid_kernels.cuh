@@ -19,6 +19,21 @@ namespace gmres {
 
 constexpr int PSTRIDE = MMAX + 8;  // partial-sum slots per block
 
+// Per-variable precision study (Sec. 4.1): a set bit stores that variable in
+// binary32 -- every value written to it is rounded -- while the binary64
+// solver's arithmetic is unchanged (GridCtx::pv, binary64 solves only).
+enum : unsigned {
+    PV_A_KRYLOV = 1u, PV_M = 2u, PV_V = 4u, PV_W = 8u, PV_H = 16u, PV_GIVENS = 32u,
+    PV_Z = 64u, PV_A_RESID = 128u, PV_B = 256u, PV_X = 512u, PV_AX = 1024u, PV_ALL = 2047u
+};
+
+// A value written to a variable of the study: rounded to binary32 when its
+// bit is set (a no-op for binary32 working values).
+template <class T>
+__device__ __forceinline__ T pv_round(T v, unsigned mask, unsigned bit) {
+    return (mask & bit) ? (T)(float)v : v;
+}
+
 template <class T, class VT>
 struct GridCtx {
     int n, m, ld;        // rows, restart length, Hessenberg leading dim (m+1)
@@ -63,6 +78,10 @@ struct GridCtx {
     double *ahist;
     double stall_factor;
     int stall_w;
+    // per-variable precision switches (PV_* bits) and A's binary32 copy for
+    // the residual under PV_A_RESID
+    unsigned pv;
+    const float *a_res32;
 };
 
 // 4 consecutive basis entries starting at p (16-byte aligned for fp32 /
@@ -288,7 +307,7 @@ __global__ void __launch_bounds__(256) k_spmv_step(GridCtx<T, VT> c, const XT *x
         int row = (int)(base + gi);
         T v = step_row<T, VT, XT, L>(c, x, row, gl);
         if (row < c.n && gl == 0)
-            y[row] = v;
+            y[row] = pv_round(v, c.pv, PV_W);
     }
 }
 
@@ -373,16 +392,21 @@ __global__ void __launch_bounds__(256) k_residual(GridCtx<T, VT> c, const double
     int bad = 0;
     for (int64_t base = warp * G; base < c.n; base += nwarps * G) {
         int row = (int)(base + gi);
-        double ax = c.ahi ? csr_row_v<double, ValHiLo, double, L>(c.rowptr, c.colind,
-                                                                  ValHiLo{c.ahi, c.alo}, x, 1.f,
-                                                                  row, c.n, gl)
-                          : csr_row<double, double, double, L>(c.rowptr, c.colind, c.a64, x, 1.f,
-                                                               row, c.n, gl);
+        double ax;
+        if (c.ahi)
+            ax = csr_row_v<double, ValHiLo, double, L>(c.rowptr, c.colind, ValHiLo{c.ahi, c.alo},
+                                                       x, 1.f, row, c.n, gl);
+        else if (c.pv & PV_A_RESID)
+            ax = csr_row<double, float, double, L>(c.rowptr, c.colind, c.a_res32, x, 1.f, row,
+                                                   c.n, gl);
+        else
+            ax = csr_row<double, double, double, L>(c.rowptr, c.colind, c.a64, x, 1.f, row, c.n,
+                                                    gl);
         if (row < c.n && gl == 0) {
-            double zi = b[row] - ax;
+            const double zi = pv_round(b[row], c.pv, PV_B) - pv_round(ax, c.pv, PV_AX);
             if (z)
                 z[row] = zi;
-            T ri = (T)zi;
+            T ri = pv_round((T)zi, c.pv, PV_Z);
             c.r[row] = ri;
             ss += zi * zi;
             sst += ri * ri;
@@ -523,8 +547,8 @@ __device__ void givens_step(GridCtx<T, VT> &c, int col, const T *hc_global, T hn
         Ctl *k = c.ctl;
         for (int i = 0; i < col; ++i) {
             T hi = sh[i], hi1 = sh[i + 1];
-            sh[i] = scs[i] * hi + ssn[i] * hi1;
-            sh[i + 1] = -ssn[i] * hi + scs[i] * hi1;
+            sh[i] = pv_round(scs[i] * hi + ssn[i] * hi1, c.pv, PV_H);
+            sh[i + 1] = pv_round(-ssn[i] * hi + scs[i] * hi1, c.pv, PV_H);
         }
         T hjj = sh[col], hj1 = sh[col + 1];
         T rho = wsqrt(hjj * hjj + hj1 * hj1);
@@ -536,14 +560,16 @@ __device__ void givens_step(GridCtx<T, VT> &c, int col, const T *hc_global, T hn
             al = hjj / rho;
             be = hj1 / rho;
         }
+        al = pv_round(al, c.pv, PV_GIVENS);
+        be = pv_round(be, c.pv, PV_GIVENS);
         c.cs[col] = al;
         c.sn[col] = be;
         T sj = c.s[col];
-        c.s[col] = al * sj;
-        T snew = -be * sj;
+        c.s[col] = pv_round(al * sj, c.pv, PV_GIVENS);
+        T snew = pv_round(-be * sj, c.pv, PV_GIVENS);
         c.s[col + 1] = snew;
-        sh[col] = al * hjj + be * hj1;
-        sh[col + 1] = -be * hjj + al * hj1;
+        sh[col] = pv_round(al * hjj + be * hj1, c.pv, PV_H);
+        sh[col + 1] = pv_round(-be * hjj + al * hj1, c.pv, PV_H);
         double arn = fabs((double)snew);
         double wn0 = k->wnorm0;
         int bd = (double)hnext <= (double)c.brk * wn0;
@@ -699,10 +725,10 @@ __global__ void __launch_bounds__(256) k_cgs_update_norm(GridCtx<T, VT> c, int n
     reduce_columns(c.part, gridDim.x, 1, &stot);
     // Hessenberg column = h1 + h2 (sum of the two classical passes)
     for (int i = threadIdx.x; i < ncols; i += blockDim.x)
-        c.h1[i] = ldcg(c.h1 + i) + ldcg(c.h2 + i);
+        c.h1[i] = pv_round(ldcg(c.h1 + i) + ldcg(c.h2 + i), c.pv, PV_H);
     __threadfence();
     __syncthreads();
-    T hnext = wsqrt(stot);
+    T hnext = pv_round(wsqrt(stot), c.pv, PV_H);
     givens_step(c, ncols - 1, c.h1, hnext);
 }
 
@@ -728,7 +754,7 @@ __global__ void __launch_bounds__(256) k_mgs_step(GridCtx<T, VT> c, int i) {
             ld4<T, VT>(c.V + (size_t)(i - 1) * c.ldv + r, c.vinv, vp);
 #pragma unroll
             for (int k = 0; k < 4; ++k)
-                wv[k] = wv[k] - hp * vp[k];
+                wv[k] = pv_round(wv[k] - hp * vp[k], c.pv, PV_W);
             st4(c.w + r, wv);
         } else {
 #pragma unroll
@@ -751,7 +777,7 @@ __global__ void __launch_bounds__(256) k_mgs_step(GridCtx<T, VT> c, int i) {
     reduce_columns(c.part, gridDim.x, 2, red);
     __syncthreads();
     if (threadIdx.x == 0) {
-        c.h1[i] = red[0];
+        c.h1[i] = pv_round(red[0], c.pv, PV_H);
         if (i == 0)
             c.ctl->wnorm0 = (double)wsqrt(red[1]);
     }
@@ -773,7 +799,7 @@ __global__ void __launch_bounds__(256) k_mgs_last(GridCtx<T, VT> c, int ncols) {
         ld4<T, VT>(c.V + (size_t)i * c.ldv + r, c.vinv, vp);
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            wv[k] = wv[k] - hp * vp[k];
+            wv[k] = pv_round(wv[k] - hp * vp[k], c.pv, PV_W);
             nsq += wv[k] * wv[k];
         }
         st4(c.w + r, wv);
@@ -786,7 +812,7 @@ __global__ void __launch_bounds__(256) k_mgs_last(GridCtx<T, VT> c, int ncols) {
     __shared__ T stot;
     reduce_columns(c.part, gridDim.x, 1, &stot);
     __syncthreads();
-    givens_step(c, ncols - 1, c.h1, wsqrt(stot));
+    givens_step(c, ncols - 1, c.h1, pv_round(wsqrt(stot), c.pv, PV_H));
 }
 
 // v_{col} = w / h_{j+1,j} (Alg. 1 "v_{j+1} <- w / h_{j+1,j}"), rounded to the
@@ -848,7 +874,7 @@ __global__ void k_backsolve(GridCtx<T, VT> c) {
             for (int l = i + 1; l < j; ++l)
                 acc -= Hs[l * j + i] * ys[l];
             T piv = Hs[i * j + i];
-            ys[i] = (piv == T(0)) ? T(0) : acc / piv;
+            ys[i] = pv_round((piv == T(0)) ? T(0) : acc / piv, c.pv, PV_GIVENS);
         }
     }
     __syncthreads();
@@ -885,19 +911,33 @@ __global__ void __launch_bounds__(256) k_update(GridCtx<T, VT> c, double *x, int
 #pragma unroll
             for (int k = 0; k < 4; ++k)
                 if (r + k < c.n)
-                    x[r + k] += (double)u[k];
+                    x[r + k] = pv_round(x[r + k] + (double)u[k], c.pv, PV_X);
         }
     }
 }
 
 // x += (double) u for a full-length working vector u (after u = M t).
+// pv: the per-variable switches (PV_X stores x in binary32).
 template <class T>
-__global__ void __launch_bounds__(256) k_axpy_x(int n, const T *u, double *x, const Ctl *ctl) {
+__global__ void __launch_bounds__(256) k_axpy_x(int n, const T *u, double *x, const Ctl *ctl,
+                                                unsigned pv) {
     if (ctl->last_j == 0 || ctl->nonfinite)
         return;
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n;
          r += (int64_t)gridDim.x * blockDim.x)
-        x[r] += (double)u[r];
+        x[r] = pv_round(x[r] + (double)u[r], pv, PV_X);
+}
+
+// v <- fl32(v) entry by entry (per-variable study: the initial x under PV_X,
+// w after a left preconditioner under PV_W).  Skipped when the cycle has
+// ended if ctl is given.
+template <class T>
+__global__ void __launch_bounds__(256) k_round32(int64_t n, T *v, const Ctl *ctl) {
+    if (ctl && !ctl->active)
+        return;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n;
+         r += (int64_t)gridDim.x * blockDim.x)
+        v[r] = (T)(float)v[r];
 }
 
 // ||b||_2 in binary64 into ctl->bnorm (two-stage, deterministic).

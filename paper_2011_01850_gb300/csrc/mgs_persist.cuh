@@ -199,7 +199,7 @@ __global__ void __launch_bounds__(MGSP_THREADS, 1)
         T tot[2];
         if (!exchange_round<T, 2>(slots, 0, round0, acc, tot, err, spin, sx))
             return;
-        hprev = tot[0];
+        hprev = pv_round(tot[0], c.pv, PV_H);
         wn0sq = tot[1];
     }
     if (tid == 0)
@@ -215,7 +215,7 @@ __global__ void __launch_bounds__(MGSP_THREADS, 1)
             ld4<T, VT>(vi + q, c.vinv, b);
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                T wv = ws[q + k] - hprev * a[k];
+                T wv = pv_round(ws[q + k] - hprev * a[k], c.pv, PV_W);
                 ws[q + k] = wv;
                 d += wv * b[k];
             }
@@ -223,7 +223,7 @@ __global__ void __launch_bounds__(MGSP_THREADS, 1)
         T dv[1] = {block_sum1(d, sred)}, hv[1];
         if (!exchange_round<T, 1>(slots, i & 1, round0 + (unsigned)i, dv, hv, err, spin, sx))
             return;
-        hprev = hv[0];
+        hprev = pv_round(hv[0], c.pv, PV_H);
         if (tid == 0)
             hcol[i] = hprev;
     }
@@ -237,7 +237,7 @@ __global__ void __launch_bounds__(MGSP_THREADS, 1)
             ld4<T, VT>(vp + q, c.vinv, a);
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                T wv = ws[q + k] - hprev * a[k];
+                T wv = pv_round(ws[q + k] - hprev * a[k], c.pv, PV_W);
                 ws[q + k] = wv;
                 nsq += wv * wv;
             }
@@ -246,7 +246,7 @@ __global__ void __launch_bounds__(MGSP_THREADS, 1)
         if (!exchange_round<T, 1>(slots, ncols & 1, round0 + (unsigned)ncols, nv, tv, err,
                                   spin, sx))
             return;
-        hnext = wsqrt(tv[0]);
+        hnext = pv_round(wsqrt(tv[0]), c.pv, PV_H);
     }
     // v_{j+1} = w / h_{j+1,j} into basis column ncols (unused if the cycle ends)
     if (hnext > T(0)) {

@@ -26,6 +26,9 @@ CREATE_DEVICE_PTRS, CREATE_TRANSPOSE, CREATE_SPLIT = 1, 2, 4
 PATH_AUTO, PATH_GRID, PATH_BLOCK = 0, 1, 2
 PRECOND_NONE, PRECOND_SPAI, PRECOND_ILU0 = 0, 1, 2
 ORTH_OFF, ORTH_SPECTRAL, ORTH_FROBENIUS = 0, 1, 2
+# per-variable precision switches (gmres_opts.pv_mask)
+PV_A_KRYLOV, PV_M, PV_V, PV_W, PV_H, PV_GIVENS, PV_Z = 1, 2, 4, 8, 16, 32, 64
+PV_A_RESID, PV_B, PV_X, PV_AX = 128, 256, 512, 1024
 K_RESIDUAL, K_SPMV, K_ORTHO, K_NORMALIZE, K_UPDATE, K_PRECOND, K_BLOCK = range(7)
 K_COUNT = 8
 KERNEL_CLASS_NAMES = ["residual", "spmv", "ortho", "normalize", "update", "precond", "block"]
@@ -64,6 +67,7 @@ class Opts(ctypes.Structure):
         ("orth_iters", ctypes.c_int32),
         ("normalize_fused", ctypes.c_int32),
         ("trsv_kernel", ctypes.c_int32),
+        ("pv_mask", ctypes.c_int32),
     ]
 
 
