@@ -180,7 +180,8 @@ def make_workload(name):
 # Comparisons timed beside the headline mode of each workload:
 # (label, precision, ortho, preconditioner)
 COMPARE = {
-    "convdiff3d_160": [("fp64", "fp64", "cgsr", None)],
+    "convdiff3d_160": [("fp64", "fp64", "cgsr", None), ("mixed_fp16", "mixed_fp16", "cgsr", None),
+                       ("mixed_bf16", "mixed_bf16", "cgsr", None)],
     "convdiff3d_96_ilu": [("unpreconditioned", "mixed", "cgsr", "none"),
                           ("fp64_ilu0", "fp64", "cgsr", "ilu")],
     "convdiff3d_96": [("fp64", "fp64", "cgsr", None)],
@@ -296,6 +297,23 @@ def bench_ours(args):
     # the paper's accuracy measure on the last timed solution (outside the
     # timed region)
     bwd_err = G.gmres_backward_error(solver.h, db, dx)
+    # error against the oracle's binary64 solution where it is stored
+    # (tests/golden/<workload>_x.npz, written by oracle/golden_fullsize.py)
+    gold = None
+    gpath = os.path.join(ROOT, "tests", "golden", args.workload + "_x.npz")
+    if os.path.exists(gpath):
+        z = np.load(gpath)
+        gold = (torch.tensor(z["idx"].astype(np.int64), device="cuda"),
+                torch.tensor(z["x"], device="cuda", dtype=torch.float64))
+
+    def x_error():
+        if gold is None:
+            return None
+        d = (dx[gold[0]] - gold[1]).abs() / gold[1].abs()
+        return {"max": float(d.max()), "rms": float(torch.sqrt((d * d).mean())),
+                "samples": int(d.numel())}
+
+    headline_err = x_error()
 
     # end to end through the public API with host buffers (H2D of b and x0,
     # D2H of x inside every step)
@@ -332,8 +350,9 @@ def bench_ours(args):
             torch.cuda.synchronize()
             cms = e0.elapsed_time(e1) / args.compare_steps
             compare[label] = {"ms": round(cms, 3), "iters": got[0]["iters"],
-                              "restarts": got[0]["restarts"],
-                              "speedup_of_headline": round(cms / ms_step, 3)}
+                              "restarts": got[0]["restarts"], "relres": got[0]["relres"],
+                              "speedup_of_headline": round(cms / ms_step, 3),
+                              "err_vs_oracle": x_error()}
         set_pre(main_pre)
         if "setup_ms" in ilu_state:
             compare["ilu_factor_ms"] = ilu_state["setup_ms"]
@@ -413,6 +432,7 @@ def bench_ours(args):
         "clocks": clk,
         "e2e": e2e,
         "relres": infos[0]["relres"],
+        "err_vs_oracle": headline_err,
         "backward_error": bwd_err,
     }
     if "fp64" in compare:

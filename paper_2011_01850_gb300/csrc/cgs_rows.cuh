@@ -267,7 +267,10 @@ __device__ __forceinline__ void rows_dots(const GridCtx<T, VT> &c, int ncols, in
     }
 }
 
-template <class T, class VT, int MODE, bool SPLIT = true>
+// PVS: the per-variable study's instantiation (every updated entry of w under
+// PV_W, the Hessenberg column and h_{j+1,j} under PV_H stored in binary32), so
+// the default passes carry none of it.
+template <class T, class VT, int MODE, bool SPLIT = true, bool PVS = false>
 __global__ void __launch_bounds__(ROWS_THREADS)
     k_cgs_rows(GridCtx<T, VT> c, int ncols, T *part, int64_t slices_per_block, int pf) {
     // MODE 3 follows the step that appended basis column ncols, also when
@@ -355,7 +358,9 @@ __global__ void __launch_bounds__(ROWS_THREADS)
             for (int q = 0; q < RPL; ++q) {
                 const int o = wid * RW + lane * RPL + q;
                 const T t = ((tsm[o] + tsm[SR + o]) + tsm[2 * SR + o]) + tsm[3 * SR + o];
-                w[q] = pv_round(w[q] - t, c.pv, PV_W);
+                w[q] = w[q] - t;
+                if (PVS)
+                    w[q] = pv_round(w[q], c.pv, PV_W);
                 if (MODE == 2)
                     nsq += w[q] * w[q];
                 if (MODE == 1)
@@ -378,7 +383,9 @@ __global__ void __launch_bounds__(ROWS_THREADS)
             rows_project<T, VT, RPL>(c, ncols, hs, r, t, pol_keep);
 #pragma unroll
             for (int q = 0; q < RPL; ++q) {
-                w[q] = pv_round(w[q] - t[q], c.pv, PV_W);
+                w[q] = w[q] - t[q];
+                if (PVS)
+                    w[q] = pv_round(w[q], c.pv, PV_W);
                 if (MODE == 2)
                     nsq += w[q] * w[q];
             }
@@ -422,11 +429,14 @@ __global__ void __launch_bounds__(ROWS_THREADS)
         return;
     __shared__ T snorm;
     reduce_columns(part + MMAX + 1, gridDim.x, 1, &snorm);
-    for (int i = threadIdx.x; i < ncols; i += blockDim.x)
-        c.h1[i] = pv_round(ldcg(c.h1 + i) + ldcg(c.h2 + i), c.pv, PV_H);
+    for (int i = threadIdx.x; i < ncols; i += blockDim.x) {
+        const T hsum = ldcg(c.h1 + i) + ldcg(c.h2 + i);
+        c.h1[i] = PVS ? pv_round(hsum, c.pv, PV_H) : hsum;
+    }
     __threadfence();
     __syncthreads();
-    givens_step(c, ncols - 1, c.h1, pv_round(wsqrt(snorm), c.pv, PV_H));
+    const T hn = wsqrt(snorm);
+    givens_step<PVS>(c, ncols - 1, c.h1, PVS ? pv_round(hn, c.pv, PV_H) : hn);
 }
 
 // Pass B with the slice held in registers (binary32 basis): w <- w - V h1,
@@ -542,8 +552,11 @@ __global__ void __launch_bounds__(256) k_reduce_cols(const T *part, int nblocks,
         a += part[(size_t)b * PSTRIDE + slot];
     a = block_sum1(a, sred);
     if (threadIdx.x == 0) {
-        if (col < ncols)
-            out[col] = pv_round(a, pv, PV_H);
+        if (col < ncols) {
+            if (pv & PV_H)
+                a = (T)(float)a;  // the per-variable study's Hessenberg switch
+            out[col] = a;
+        }
         else if (with_norm)
             ctl->wnorm0 = (double)wsqrt(a);
     }

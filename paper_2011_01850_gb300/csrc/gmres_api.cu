@@ -264,6 +264,20 @@ template <class T, class VT>
 cudaError_t launch_residual(gmres_handle *h, const GridCtx<T, VT> &c, const double *b,
                             const double *x, double *z, int setup) {
     dim3 g(h->grid), bl(kThreads);
+    if constexpr (std::is_same<T, double>::value) {
+        // the per-variable study's residual: its own instantiations
+        if (c.pv & (PV_A_RESID | PV_B | PV_AX | PV_Z)) {
+            switch (h->lanes64) {
+            case 1: k_residual<T, VT, 1, true><<<g, bl, 0, h->stream>>>(c, b, x, z, setup); break;
+            case 2: k_residual<T, VT, 2, true><<<g, bl, 0, h->stream>>>(c, b, x, z, setup); break;
+            case 4: k_residual<T, VT, 4, true><<<g, bl, 0, h->stream>>>(c, b, x, z, setup); break;
+            case 8: k_residual<T, VT, 8, true><<<g, bl, 0, h->stream>>>(c, b, x, z, setup); break;
+            case 16: k_residual<T, VT, 16, true><<<g, bl, 0, h->stream>>>(c, b, x, z, setup); break;
+            default: k_residual<T, VT, 32, true><<<g, bl, 0, h->stream>>>(c, b, x, z, setup); break;
+            }
+            return cudaGetLastError();
+        }
+    }
     switch (h->lanes64) {
     case 1: k_residual<T, VT, 1><<<g, bl, 0, h->stream>>>(c, b, x, z, setup); break;
     case 2: k_residual<T, VT, 2><<<g, bl, 0, h->stream>>>(c, b, x, z, setup); break;
@@ -489,13 +503,31 @@ gmres_status enqueue_cgs_rows(gmres_handle *h, GridCtx<T, VT> &c, int ncols, Acc
                                                            c.pv);
         }
     } else {
-        k_cgs_rows<T, VT, 1, SPLIT><<<gsz[1], ROWS_THREADS, 0, h->stream>>>(c, ncols, c.part,
-                                                                            kpb[1], pf);
+        if constexpr (std::is_same<T, double>::value) {
+            if (c.pv & PV_ORTHO)  // the per-variable study's instantiation
+                k_cgs_rows<T, VT, 1, SPLIT, true><<<gsz[1], ROWS_THREADS, 0, h->stream>>>(
+                    c, ncols, c.part, kpb[1], pf);
+            else
+                k_cgs_rows<T, VT, 1, SPLIT><<<gsz[1], ROWS_THREADS, 0, h->stream>>>(
+                    c, ncols, c.part, kpb[1], pf);
+        } else {
+            k_cgs_rows<T, VT, 1, SPLIT><<<gsz[1], ROWS_THREADS, 0, h->stream>>>(c, ncols, c.part,
+                                                                                kpb[1], pf);
+        }
         k_reduce_cols<T><<<ncols, 256, 0, h->stream>>>(c.part, gsz[1], ncols, c.h2, c.ctl, 0,
                                                        c.pv);
     }
-    k_cgs_rows<T, VT, 2, SPLIT><<<gsz[2], ROWS_THREADS, 0, h->stream>>>(c, ncols, c.part, kpb[2],
-                                                                        pf);
+    if constexpr (std::is_same<T, double>::value) {
+        if (c.pv & PV_ORTHO)
+            k_cgs_rows<T, VT, 2, SPLIT, true><<<gsz[2], ROWS_THREADS, 0, h->stream>>>(
+                c, ncols, c.part, kpb[2], pf);
+        else
+            k_cgs_rows<T, VT, 2, SPLIT><<<gsz[2], ROWS_THREADS, 0, h->stream>>>(c, ncols, c.part,
+                                                                                kpb[2], pf);
+    } else {
+        k_cgs_rows<T, VT, 2, SPLIT><<<gsz[2], ROWS_THREADS, 0, h->stream>>>(c, ncols, c.part,
+                                                                            kpb[2], pf);
+    }
     acct.launches[GMRES_K_ORTHO] += 5;
     CKL();
     h->timer.end(GMRES_K_ORTHO, e);
@@ -531,9 +563,7 @@ gmres_status enqueue_step_core(gmres_handle *h, GridCtx<T, VT> &c, int col, gmre
     } else if (c.left) {
         // t = A v_j, w = M^-1 t (left preconditioning, Alg. 1); under the
         // per-variable w switch w, not t, is the stored Krylov vector
-        GridCtx<T, VT> ct = c;
-        ct.pv = c.pv & ~(unsigned)PV_W;
-        CK((launch_spmv_step<T, VT, VT>(h, ct, vj, c.t, L)));
+        CK((launch_spmv_step<T, VT, VT>(h, c, vj, c.t, L)));
         h->timer.end(GMRES_K_SPMV, e);
         acct.launches[GMRES_K_SPMV]++;
         e = h->timer.begin();
@@ -554,7 +584,6 @@ gmres_status enqueue_step_core(gmres_handle *h, GridCtx<T, VT> &c, int col, gmre
         cp.a = c.pvals;
         cp.a_lim = c.pvals_lim;
         cp.aform = c.pvals_lim ? 1 : 0;
-        cp.pv = c.pv & ~(unsigned)PV_W;  // t = M v_j is not the Krylov vector w
         CK((launch_spmv_step<T, VT, VT>(h, cp, vj, c.t, L)));
         acct.launches[GMRES_K_PRECOND]++;
         h->timer.end(GMRES_K_PRECOND, e);
@@ -562,6 +591,11 @@ gmres_status enqueue_step_core(gmres_handle *h, GridCtx<T, VT> &c, int col, gmre
         CK((launch_spmv_step<T, VT, T>(h, c, c.t, c.w, L)));
     } else {
         CK((launch_spmv_step<T, VT, VT>(h, c, vj, c.w, L)));
+    }
+    if (!c.left && (c.pv & PV_W)) {
+        // the per-variable study's w switch: w = A v_j stored in binary32
+        k_round32<T><<<h->grid, kThreads, 0, h->stream>>>(h->n, c.w, c.ctl);
+        CKL();
     }
     h->timer.end(GMRES_K_SPMV, e);
     acct.launches[GMRES_K_SPMV]++;
@@ -620,16 +654,30 @@ gmres_status enqueue_step_core(gmres_handle *h, GridCtx<T, VT> &c, int col, gmre
         GridCtx<T, VT> cc = c;
         int nc = ncols;
         void *args[] = {&cc, &nc, &chunk, &spin, &slots, &round0};
-        CK(cudaLaunchCooperativeKernel((const void *)k_mgs_persist<T, VT>, dim3(h->nsm),
-                                       dim3(MGSP_THREADS), args,
+        const void *kfn = (const void *)k_mgs_persist<T, VT>;
+        if constexpr (std::is_same<T, double>::value) {
+            if (c.pv & PV_ORTHO) {  // the per-variable study's instantiation
+                kfn = (const void *)k_mgs_persist<T, VT, true>;
+                CK(cudaFuncSetAttribute(k_mgs_persist<T, VT, true>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)((size_t)chunk * sizeof(T) + 16)));
+            }
+        }
+        CK(cudaLaunchCooperativeKernel(kfn, dim3(h->nsm), dim3(MGSP_THREADS), args,
                                        (size_t)chunk * sizeof(T) + 16, h->stream));
         acct.launches[GMRES_K_ORTHO] += 1;
         h->timer.end(GMRES_K_ORTHO, e);
         return GMRES_OK;
     } else {
-        for (int i = 0; i < ncols; ++i)
-            k_mgs_step<T, VT><<<g, b, 0, h->stream>>>(c, i);
-        k_mgs_last<T, VT><<<g, b, 0, h->stream>>>(c, ncols);
+        if (c.pv & PV_ORTHO) {  // the per-variable study's instantiations
+            for (int i = 0; i < ncols; ++i)
+                k_mgs_step<T, VT, true><<<g, b, 0, h->stream>>>(c, i);
+            k_mgs_last<T, VT, true><<<g, b, 0, h->stream>>>(c, ncols);
+        } else {
+            for (int i = 0; i < ncols; ++i)
+                k_mgs_step<T, VT><<<g, b, 0, h->stream>>>(c, i);
+            k_mgs_last<T, VT><<<g, b, 0, h->stream>>>(c, ncols);
+        }
         acct.launches[GMRES_K_ORTHO] += ncols + 1;
     }
     CKL();
@@ -834,7 +882,10 @@ gmres_status solve_grid(gmres_handle *h, const double *b, double *x, int m, doub
         k_backsolve<T, VT><<<1, 32, sm, h->stream>>>(c);
         CKL();
         const bool pre = c.pvals != nullptr;
-        k_update<T, VT><<<h->grid, kThreads, 0, h->stream>>>(c, x, pre ? 1 : 0);
+        if (c.pv & PV_X)  // the per-variable study's instantiation
+            k_update<T, VT, true><<<h->grid, kThreads, 0, h->stream>>>(c, x, pre ? 1 : 0);
+        else
+            k_update<T, VT><<<h->grid, kThreads, 0, h->stream>>>(c, x, pre ? 1 : 0);
         CKL();
         acct.launches[GMRES_K_UPDATE] += 2;
         if (pre) {

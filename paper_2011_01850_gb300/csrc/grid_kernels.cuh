@@ -24,7 +24,9 @@ constexpr int PSTRIDE = MMAX + 8;  // partial-sum slots per block
 // solver's arithmetic is unchanged (GridCtx::pv, binary64 solves only).
 enum : unsigned {
     PV_A_KRYLOV = 1u, PV_M = 2u, PV_V = 4u, PV_W = 8u, PV_H = 16u, PV_GIVENS = 32u,
-    PV_Z = 64u, PV_A_RESID = 128u, PV_B = 256u, PV_X = 512u, PV_AX = 1024u, PV_ALL = 2047u
+    PV_Z = 64u, PV_A_RESID = 128u, PV_B = 256u, PV_X = 512u, PV_AX = 1024u, PV_ALL = 2047u,
+    // the switches the orthogonalisation kernels and the Givens step apply
+    PV_ORTHO = PV_W | PV_H | PV_GIVENS
 };
 
 // A value written to a variable of the study: rounded to binary32 when its
@@ -307,7 +309,7 @@ __global__ void __launch_bounds__(256) k_spmv_step(GridCtx<T, VT> c, const XT *x
         int row = (int)(base + gi);
         T v = step_row<T, VT, XT, L>(c, x, row, gl);
         if (row < c.n && gl == 0)
-            y[row] = pv_round(v, c.pv, PV_W);
+            y[row] = v;
     }
 }
 
@@ -377,7 +379,10 @@ __global__ void __launch_bounds__(256) k_spmv_plain(int n, const int *rowptr, co
 // the working-precision copy r = fl(z) and ||r|| in the working precision.
 // The last block sets up the cycle: beta, s = beta e_1, active flag.
 // ---------------------------------------------------------------------------
-template <class T, class VT, int L>
+// PVR: the per-variable study's residual (A, b, A x or the cycle's copy of z
+// stored in binary32 as GridCtx::pv says); a separate instantiation, so the
+// default residual carries none of it.
+template <class T, class VT, int L, bool PVR = false>
 __global__ void __launch_bounds__(256) k_residual(GridCtx<T, VT> c, const double *b,
                                                   const double *x, double *z, int setup) {
     __shared__ double sd[32];
@@ -396,17 +401,18 @@ __global__ void __launch_bounds__(256) k_residual(GridCtx<T, VT> c, const double
         if (c.ahi)
             ax = csr_row_v<double, ValHiLo, double, L>(c.rowptr, c.colind, ValHiLo{c.ahi, c.alo},
                                                        x, 1.f, row, c.n, gl);
-        else if (c.pv & PV_A_RESID)
+        else if (PVR && (c.pv & PV_A_RESID))
             ax = csr_row<double, float, double, L>(c.rowptr, c.colind, c.a_res32, x, 1.f, row,
                                                    c.n, gl);
         else
             ax = csr_row<double, double, double, L>(c.rowptr, c.colind, c.a64, x, 1.f, row, c.n,
                                                     gl);
         if (row < c.n && gl == 0) {
-            const double zi = pv_round(b[row], c.pv, PV_B) - pv_round(ax, c.pv, PV_AX);
+            const double zi = PVR ? pv_round(b[row], c.pv, PV_B) - pv_round(ax, c.pv, PV_AX)
+                                  : b[row] - ax;
             if (z)
                 z[row] = zi;
-            T ri = pv_round((T)zi, c.pv, PV_Z);
+            T ri = PVR ? pv_round((T)zi, c.pv, PV_Z) : (T)zi;
             c.r[row] = ri;
             ss += zi * zi;
             sst += ri * ri;
@@ -526,8 +532,12 @@ __global__ void __launch_bounds__(256) k_pnorm(GridCtx<T, VT> c) {
 // of the final orthogonalisation kernel; col is the 0-based column index,
 // hc[0..col] the projections, hnext = h_{j+1,j}.
 // ---------------------------------------------------------------------------
-template <class T, class VT>
+// PVS: the per-variable study's instantiation (the rotated Hessenberg entries
+// under PV_H, the rotations and s under PV_GIVENS stored in binary32); the
+// default one carries none of it.
+template <bool PVS = false, class T, class VT>
 __device__ void givens_step(GridCtx<T, VT> &c, int col, const T *hc_global, T hnext) {
+    auto st32 = [&](T v, unsigned bit) { return PVS ? pv_round(v, c.pv, bit) : v; };
     __shared__ T sh[MMAX + 2], scs[MMAX], ssn[MMAX];
     for (int i = threadIdx.x; i <= col; i += blockDim.x)
         sh[i] = ldcg(hc_global + i);
@@ -547,8 +557,8 @@ __device__ void givens_step(GridCtx<T, VT> &c, int col, const T *hc_global, T hn
         Ctl *k = c.ctl;
         for (int i = 0; i < col; ++i) {
             T hi = sh[i], hi1 = sh[i + 1];
-            sh[i] = pv_round(scs[i] * hi + ssn[i] * hi1, c.pv, PV_H);
-            sh[i + 1] = pv_round(-ssn[i] * hi + scs[i] * hi1, c.pv, PV_H);
+            sh[i] = st32(scs[i] * hi + ssn[i] * hi1, PV_H);
+            sh[i + 1] = st32(-ssn[i] * hi + scs[i] * hi1, PV_H);
         }
         T hjj = sh[col], hj1 = sh[col + 1];
         T rho = wsqrt(hjj * hjj + hj1 * hj1);
@@ -560,16 +570,16 @@ __device__ void givens_step(GridCtx<T, VT> &c, int col, const T *hc_global, T hn
             al = hjj / rho;
             be = hj1 / rho;
         }
-        al = pv_round(al, c.pv, PV_GIVENS);
-        be = pv_round(be, c.pv, PV_GIVENS);
+        al = st32(al, PV_GIVENS);
+        be = st32(be, PV_GIVENS);
         c.cs[col] = al;
         c.sn[col] = be;
         T sj = c.s[col];
-        c.s[col] = pv_round(al * sj, c.pv, PV_GIVENS);
-        T snew = pv_round(-be * sj, c.pv, PV_GIVENS);
+        c.s[col] = st32(al * sj, PV_GIVENS);
+        T snew = st32(-be * sj, PV_GIVENS);
         c.s[col + 1] = snew;
-        sh[col] = pv_round(al * hjj + be * hj1, c.pv, PV_H);
-        sh[col + 1] = pv_round(-be * hjj + al * hj1, c.pv, PV_H);
+        sh[col] = st32(al * hjj + be * hj1, PV_H);
+        sh[col + 1] = st32(-be * hjj + al * hj1, PV_H);
         double arn = fabs((double)snew);
         double wn0 = k->wnorm0;
         int bd = (double)hnext <= (double)c.brk * wn0;
@@ -593,151 +603,11 @@ __device__ void givens_step(GridCtx<T, VT> &c, int col, const T *hc_global, T hn
 }
 
 // ---------------------------------------------------------------------------
-// CGSR passes (procedure CGSR, done twice).  ncols = j basis vectors.
-//   k_cgs_dot          h1 = V^T w; also ||w||^2 (= ||A v_j||^2, breakdown ref)
-//   k_cgs_update_dot   w <- w - V h1, then h2 = V^T w
-//   k_cgs_update_norm  w <- w - V h2, ||w||^2 -> h_{j+1,j}; Hessenberg column
-//                      h1 + h2; Givens step
-// ---------------------------------------------------------------------------
-template <class T, class VT>
-__device__ __forceinline__ void cgs_block_dots(GridCtx<T, VT> &c, int ncols, int64_t rb, int64_t re,
-                                               T *out_part) {
-    __shared__ T sred[8 * 32];
-    for (int c0 = 0; c0 < ncols; c0 += 8) {
-        T acc[8];
-#pragma unroll
-        for (int k = 0; k < 8; ++k)
-            acc[k] = 0;
-        for (int64_t r = rb + 4 * threadIdx.x; r < re; r += 4 * blockDim.x) {
-            T wv[4];
-            ldv4(c.w + r, wv);
-#pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                if (c0 + k < ncols) {
-                    T v[4];
-                    ld4<T, VT>(c.V + (size_t)(c0 + k) * c.ldv + r, c.vinv, v);
-                    acc[k] += v[0] * wv[0] + v[1] * wv[1] + v[2] * wv[2] + v[3] * wv[3];
-                }
-            }
-        }
-        block_sum<T, 8>(acc, sred);
-        if (threadIdx.x == 0) {
-#pragma unroll
-            for (int k = 0; k < 8; ++k)
-                if (c0 + k < ncols)
-                    out_part[c0 + k] = acc[k];
-        }
-    }
-}
-
-template <class T, class VT>
-__global__ void __launch_bounds__(256) k_cgs_dot(GridCtx<T, VT> c, int ncols) {
-    if (!c.ctl->active)
-        return;
-    __shared__ T sred[32];
-    int64_t rb, re;
-    block_rows(c, rb, re);
-    T *mypart = c.part + (size_t)blockIdx.x * PSTRIDE;
-    cgs_block_dots(c, ncols, rb, re, mypart);
-    // ||w||^2 for the breakdown reference
-    T nsq = 0;
-    for (int64_t r = rb + 4 * threadIdx.x; r < re; r += 4 * blockDim.x) {
-        T wv[4];
-        ldv4(c.w + r, wv);
-        nsq += wv[0] * wv[0] + wv[1] * wv[1] + wv[2] * wv[2] + wv[3] * wv[3];
-    }
-    nsq = block_sum1(nsq, sred);
-    if (threadIdx.x == 0)
-        mypart[MMAX + 1] = nsq;
-    if (!arrive_last(&c.ctl->counter[1]))
-        return;
-    reduce_columns(c.part, gridDim.x, ncols, c.h1);
-    __shared__ T snsq;
-    reduce_columns(c.part + MMAX + 1, gridDim.x, 1, &snsq);
-    __syncthreads();
-    if (threadIdx.x == 0)
-        c.ctl->wnorm0 = (double)wsqrt(snsq);  // ||A v_j||, read by the Givens step
-}
-
-template <class T, class VT>
-__device__ __forceinline__ T cgs_update_rows(GridCtx<T, VT> &c, int ncols, const T *hs, int64_t rb,
-                                             int64_t re) {
-    T nsq = 0;
-    for (int64_t r = rb + 4 * threadIdx.x; r < re; r += 4 * blockDim.x) {
-        T t[4] = {0, 0, 0, 0};
-        for (int i = 0; i < ncols; ++i) {
-            T v[4];
-            ld4<T, VT>(c.V + (size_t)i * c.ldv + r, c.vinv, v);
-            T hi = hs[i];
-#pragma unroll
-            for (int k = 0; k < 4; ++k)
-                t[k] += v[k] * hi;
-        }
-        T wv[4];
-        ldv4(c.w + r, wv);
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            wv[k] = wv[k] - t[k];
-            nsq += wv[k] * wv[k];
-        }
-        st4(c.w + r, wv);
-    }
-    return nsq;
-}
-
-template <class T, class VT>
-__global__ void __launch_bounds__(256) k_cgs_update_dot(GridCtx<T, VT> c, int ncols) {
-    if (!c.ctl->active)
-        return;
-    __shared__ T hs[MMAX + 1];
-    for (int i = threadIdx.x; i < ncols; i += blockDim.x)
-        hs[i] = c.h1[i];
-    __syncthreads();
-    int64_t rb, re;
-    block_rows(c, rb, re);
-    cgs_update_rows(c, ncols, hs, rb, re);
-    __syncthreads();
-    T *mypart = c.part + (size_t)blockIdx.x * PSTRIDE;
-    cgs_block_dots(c, ncols, rb, re, mypart);
-    if (!arrive_last(&c.ctl->counter[2]))
-        return;
-    reduce_columns(c.part, gridDim.x, ncols, c.h2);
-}
-
-template <class T, class VT>
-__global__ void __launch_bounds__(256) k_cgs_update_norm(GridCtx<T, VT> c, int ncols) {
-    if (!c.ctl->active)
-        return;
-    __shared__ T hs[MMAX + 1];
-    __shared__ T sred[32];
-    for (int i = threadIdx.x; i < ncols; i += blockDim.x)
-        hs[i] = c.h2[i];
-    __syncthreads();
-    int64_t rb, re;
-    block_rows(c, rb, re);
-    T nsq = cgs_update_rows(c, ncols, hs, rb, re);
-    nsq = block_sum1(nsq, sred);
-    if (threadIdx.x == 0)
-        c.part[(size_t)blockIdx.x * PSTRIDE] = nsq;
-    if (!arrive_last(&c.ctl->counter[3]))
-        return;
-    __shared__ T stot;
-    reduce_columns(c.part, gridDim.x, 1, &stot);
-    // Hessenberg column = h1 + h2 (sum of the two classical passes)
-    for (int i = threadIdx.x; i < ncols; i += blockDim.x)
-        c.h1[i] = pv_round(ldcg(c.h1 + i) + ldcg(c.h2 + i), c.pv, PV_H);
-    __threadfence();
-    __syncthreads();
-    T hnext = pv_round(wsqrt(stot), c.pv, PV_H);
-    givens_step(c, ncols - 1, c.h1, hnext);
-}
-
-// ---------------------------------------------------------------------------
 // MGS chain (procedure MGS): step i applies the previous projection
 // w <- w - h_{i-1} v_{i-1} and forms h_i = w . v_i in the same pass; the final
 // step applies the last projection, takes ||w|| and runs the Givens step.
 // ---------------------------------------------------------------------------
-template <class T, class VT>
+template <class T, class VT, bool PVS = false>
 __global__ void __launch_bounds__(256) k_mgs_step(GridCtx<T, VT> c, int i) {
     if (!c.ctl->active)
         return;
@@ -745,6 +615,7 @@ __global__ void __launch_bounds__(256) k_mgs_step(GridCtx<T, VT> c, int i) {
     int64_t rb, re;
     block_rows(c, rb, re);
     const T hp = (i > 0) ? c.h1[i - 1] : T(0);
+    const bool rw = PVS && (c.pv & PV_W);  // per-variable w switch
     T acc[2] = {0, 0};  // [0] = w . v_i, [1] = ||w||^2 (i == 0 only)
     for (int64_t r = rb + 4 * threadIdx.x; r < re; r += 4 * blockDim.x) {
         T wv[4], vi[4];
@@ -754,7 +625,12 @@ __global__ void __launch_bounds__(256) k_mgs_step(GridCtx<T, VT> c, int i) {
             ld4<T, VT>(c.V + (size_t)(i - 1) * c.ldv + r, c.vinv, vp);
 #pragma unroll
             for (int k = 0; k < 4; ++k)
-                wv[k] = pv_round(wv[k] - hp * vp[k], c.pv, PV_W);
+                wv[k] = wv[k] - hp * vp[k];
+            if (rw) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    wv[k] = (T)(float)wv[k];
+            }
             st4(c.w + r, wv);
         } else {
 #pragma unroll
@@ -777,13 +653,13 @@ __global__ void __launch_bounds__(256) k_mgs_step(GridCtx<T, VT> c, int i) {
     reduce_columns(c.part, gridDim.x, 2, red);
     __syncthreads();
     if (threadIdx.x == 0) {
-        c.h1[i] = pv_round(red[0], c.pv, PV_H);
+        c.h1[i] = PVS ? pv_round(red[0], c.pv, PV_H) : red[0];
         if (i == 0)
             c.ctl->wnorm0 = (double)wsqrt(red[1]);
     }
 }
 
-template <class T, class VT>
+template <class T, class VT, bool PVS = false>
 __global__ void __launch_bounds__(256) k_mgs_last(GridCtx<T, VT> c, int ncols) {
     if (!c.ctl->active)
         return;
@@ -792,6 +668,7 @@ __global__ void __launch_bounds__(256) k_mgs_last(GridCtx<T, VT> c, int ncols) {
     block_rows(c, rb, re);
     const int i = ncols - 1;
     const T hp = c.h1[i];
+    const bool rw = PVS && (c.pv & PV_W);  // per-variable w switch
     T nsq = 0;
     for (int64_t r = rb + 4 * threadIdx.x; r < re; r += 4 * blockDim.x) {
         T wv[4], vp[4];
@@ -799,7 +676,9 @@ __global__ void __launch_bounds__(256) k_mgs_last(GridCtx<T, VT> c, int ncols) {
         ld4<T, VT>(c.V + (size_t)i * c.ldv + r, c.vinv, vp);
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            wv[k] = pv_round(wv[k] - hp * vp[k], c.pv, PV_W);
+            wv[k] = wv[k] - hp * vp[k];
+            if (rw)
+                wv[k] = (T)(float)wv[k];
             nsq += wv[k] * wv[k];
         }
         st4(c.w + r, wv);
@@ -812,7 +691,8 @@ __global__ void __launch_bounds__(256) k_mgs_last(GridCtx<T, VT> c, int ncols) {
     __shared__ T stot;
     reduce_columns(c.part, gridDim.x, 1, &stot);
     __syncthreads();
-    givens_step(c, ncols - 1, c.h1, pv_round(wsqrt(stot), c.pv, PV_H));
+    const T hn = wsqrt(stot);
+    givens_step<PVS>(c, ncols - 1, c.h1, PVS ? pv_round(hn, c.pv, PV_H) : hn);
 }
 
 // v_{col} = w / h_{j+1,j} (Alg. 1 "v_{j+1} <- w / h_{j+1,j}"), rounded to the
@@ -874,7 +754,10 @@ __global__ void k_backsolve(GridCtx<T, VT> c) {
             for (int l = i + 1; l < j; ++l)
                 acc -= Hs[l * j + i] * ys[l];
             T piv = Hs[i * j + i];
-            ys[i] = pv_round((piv == T(0)) ? T(0) : acc / piv, c.pv, PV_GIVENS);
+            T yi = (piv == T(0)) ? T(0) : acc / piv;
+            if (c.pv & PV_GIVENS)
+                yi = (T)(float)yi;  // the per-variable study's least-squares switch
+            ys[i] = yi;
         }
     }
     __syncthreads();
@@ -885,7 +768,9 @@ __global__ void k_backsolve(GridCtx<T, VT> c) {
 // u = V_j y in the working precision, then x += (double) u (Alg. 1 "x_{k+1}
 // <- x_k + u_k", binary64 addition, Sec. 2).  With a right preconditioner the
 // kernel writes t = V_j y instead and the update is applied after t -> M t.
-template <class T, class VT>
+// PVS: the per-variable study's instantiation (x stored in binary32 under
+// PV_X).
+template <class T, class VT, bool PVS = false>
 __global__ void __launch_bounds__(256) k_update(GridCtx<T, VT> c, double *x, int to_t) {
     __shared__ T ys[MMAX];
     const int j = c.ctl->last_j;
@@ -896,6 +781,7 @@ __global__ void __launch_bounds__(256) k_update(GridCtx<T, VT> c, double *x, int
     __syncthreads();
     int64_t rb, re;
     block_rows(c, rb, re);
+    const bool rx = PVS && (c.pv & PV_X);
     for (int64_t r = rb + 4 * threadIdx.x; r < re; r += 4 * blockDim.x) {
         T u[4] = {0, 0, 0, 0};
         for (int i = 0; i < j; ++i) {
@@ -910,8 +796,12 @@ __global__ void __launch_bounds__(256) k_update(GridCtx<T, VT> c, double *x, int
         } else {
 #pragma unroll
             for (int k = 0; k < 4; ++k)
-                if (r + k < c.n)
-                    x[r + k] = pv_round(x[r + k] + (double)u[k], c.pv, PV_X);
+                if (r + k < c.n) {
+                    double xn = x[r + k] + (double)u[k];
+                    if (rx)
+                        xn = (double)(float)xn;  // per-variable x switch
+                    x[r + k] = xn;
+                }
         }
     }
 }

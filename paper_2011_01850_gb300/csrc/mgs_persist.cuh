@@ -155,7 +155,10 @@ __device__ __forceinline__ bool exchange_round(unsigned long long *slots, int p,
     return ok;
 }
 
-template <class T, class VT>
+// PVS: the per-variable study's instantiation (every updated entry of w under
+// PV_W, the coefficients and h_{j+1,j} under PV_H stored in binary32); the
+// default loops carry none of it.
+template <class T, class VT, bool PVS = false>
 __global__ void __launch_bounds__(MGSP_THREADS, 1)
     k_mgs_persist(GridCtx<T, VT> c, int ncols, int64_t chunk, long long spin,
                   unsigned long long *slots, unsigned round0) {
@@ -199,7 +202,7 @@ __global__ void __launch_bounds__(MGSP_THREADS, 1)
         T tot[2];
         if (!exchange_round<T, 2>(slots, 0, round0, acc, tot, err, spin, sx))
             return;
-        hprev = pv_round(tot[0], c.pv, PV_H);
+        hprev = PVS ? pv_round(tot[0], c.pv, PV_H) : tot[0];
         wn0sq = tot[1];
     }
     if (tid == 0)
@@ -215,7 +218,9 @@ __global__ void __launch_bounds__(MGSP_THREADS, 1)
             ld4<T, VT>(vi + q, c.vinv, b);
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                T wv = pv_round(ws[q + k] - hprev * a[k], c.pv, PV_W);
+                T wv = ws[q + k] - hprev * a[k];
+                if (PVS)
+                    wv = pv_round(wv, c.pv, PV_W);
                 ws[q + k] = wv;
                 d += wv * b[k];
             }
@@ -223,7 +228,7 @@ __global__ void __launch_bounds__(MGSP_THREADS, 1)
         T dv[1] = {block_sum1(d, sred)}, hv[1];
         if (!exchange_round<T, 1>(slots, i & 1, round0 + (unsigned)i, dv, hv, err, spin, sx))
             return;
-        hprev = pv_round(hv[0], c.pv, PV_H);
+        hprev = PVS ? pv_round(hv[0], c.pv, PV_H) : hv[0];
         if (tid == 0)
             hcol[i] = hprev;
     }
@@ -237,7 +242,9 @@ __global__ void __launch_bounds__(MGSP_THREADS, 1)
             ld4<T, VT>(vp + q, c.vinv, a);
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                T wv = pv_round(ws[q + k] - hprev * a[k], c.pv, PV_W);
+                T wv = ws[q + k] - hprev * a[k];
+                if (PVS)
+                    wv = pv_round(wv, c.pv, PV_W);
                 ws[q + k] = wv;
                 nsq += wv * wv;
             }
@@ -246,7 +253,9 @@ __global__ void __launch_bounds__(MGSP_THREADS, 1)
         if (!exchange_round<T, 1>(slots, ncols & 1, round0 + (unsigned)ncols, nv, tv, err,
                                   spin, sx))
             return;
-        hnext = pv_round(wsqrt(tv[0]), c.pv, PV_H);
+        hnext = wsqrt(tv[0]);
+        if (PVS)
+            hnext = pv_round(hnext, c.pv, PV_H);
     }
     // v_{j+1} = w / h_{j+1,j} into basis column ncols (unused if the cycle ends)
     if (hnext > T(0)) {
@@ -266,7 +275,7 @@ __global__ void __launch_bounds__(MGSP_THREADS, 1)
             c.ctl->wnorm0 = (double)wsqrt(wn0sq);
         __threadfence();
         __syncthreads();
-        givens_step(c, ncols - 1, c.h1, hnext);
+        givens_step<PVS>(c, ncols - 1, c.h1, hnext);
     }
 }
 

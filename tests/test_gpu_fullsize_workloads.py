@@ -9,7 +9,13 @@
 * The 2048-system batch (sizes log-uniform in [500, 50000], seed of the
   benchmark's first rank): every system's solution has an oracle-recomputed
   relative residual <= 1e-10, and the residual each system reports agrees.
+* The power-law 2M matrix with bfloat16 and binary16 bases (MGS GMRES(50)) and
+  the anisotropic 128^3 matrix with the learned preconditioner (CGSR
+  GMRES(50), fallback on and off): oracle-recomputed residual <= 1e-10; the
+  learned preconditioner needs fewer iterations than none.
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -83,3 +89,80 @@ def test_fullsize_batched_2048(gpulib):
         rel = O.residual_norm(A, bi, xi) / np.linalg.norm(bi)
         assert rel <= 1e-10, (i, rel)
         assert res[i].converged == 1 and abs(res[i].relres - rel) <= 1e-3 * rel + 1e-14, i
+
+
+def _resid_bound(A, b, x):
+    """Two binary64 evaluations of ||b - A x|| / ||b|| differ by at most
+    2 gamma_{k+1} || |A||x| + |b| || / ||b|| (k entries per row)."""
+    rp, ci, va = A
+    n = len(b)
+    k = int(np.diff(rp).max()) + 1
+    ax = np.zeros(n)
+    np.add.at(ax, np.repeat(np.arange(n), np.diff(rp)), np.abs(va) * np.abs(x[ci]))
+    u = 2.0 ** -53
+    return 2 * k * u / (1 - k * u) * np.linalg.norm(ax + np.abs(b)) / np.linalg.norm(b)
+
+
+def _full_solve(A, b, spec, prec, precond=None, params=None, fallback=1):
+    n = len(b)
+    s = G.Solver(A, stream=torch.cuda.current_stream())
+    G.gmres_autotune(s.h)
+    if precond == "spai":
+        G.gmres_spai_set(s.h, params)
+        s.set_opts(precond=G.PRECOND_SPAI, fallback=fallback)
+    db = torch.tensor(b, device="cuda", dtype=torch.float64)
+    dx = torch.zeros(n, device="cuda", dtype=torch.float64)
+    _, st, info = s.solve(db, dx, m=spec["m"], tol=1e-10, ortho=spec["ortho"], prec=prec,
+                          maxiter=100000)
+    s.close()
+    return dx.cpu().numpy(), st, info
+
+
+@pytest.fixture(scope="module")
+def powerlaw2m():
+    return I.workload("powerlaw_2m", seed=SEED)
+
+
+@pytest.mark.parametrize("prec", ["mixed_bf16", "mixed_fp16"])
+def test_fullsize_powerlaw_16bit_basis(powerlaw2m, prec, gpulib):
+    """Random power-law 2 000 000-row matrix (rows 3-200, mean 16), mixed
+    MGS GMRES(50) with the Krylov basis stored in bfloat16 / binary16: the
+    binary64 relative residual of x, recomputed by the oracle, is <= 1e-10 and
+    agrees with the reported one within the rounding of two evaluations."""
+    A, b, spec = powerlaw2m
+    x, st, info = _full_solve(A, b, spec, prec)
+    assert st == G.OK, info
+    assert info["path"] == G.PATH_GRID
+    rel = O.residual_norm(A, b, x) / np.linalg.norm(b)
+    assert rel <= 1e-10, rel
+    assert abs(rel - info["relres"]) <= _resid_bound(A, b, x), (rel, info["relres"])
+    print(prec, "iters", info["iters"], "restarts", info["restarts"], "relres", rel)
+
+
+@pytest.fixture(scope="module")
+def aniso128():
+    A, b, spec = I.workload("aniso3d_128", seed=SEED)
+    params = np.load(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                                  "paper_2011_01850_gb300", "data", "spai_aniso64.npy"))
+    return A, b, spec, params.astype(np.float32)
+
+
+def test_fullsize_aniso_learned_preconditioner(aniso128, gpulib):
+    """Held-out 128^3 anisotropic (1:10:100) convection-diffusion, mixed CGSR
+    GMRES(50) with the committed learned SpAI right preconditioner, with and
+    without the stagnation fallback: both reach an oracle-recomputed binary64
+    relative residual <= 1e-10 without falling back, in fewer inner iterations
+    than the unpreconditioned mixed solve."""
+    A, b, spec, params = aniso128
+    _, st0, info0 = _full_solve(A, b, spec, "mixed")
+    assert st0 == G.OK
+    for fallback in (1, 0):
+        x, st, info = _full_solve(A, b, spec, "mixed", precond="spai", params=params,
+                                  fallback=fallback)
+        assert st == G.OK, (fallback, info)
+        assert not info["fell_back"]
+        rel = O.residual_norm(A, b, x) / np.linalg.norm(b)
+        assert rel <= 1e-10, (fallback, rel)
+        assert abs(rel - info["relres"]) <= _resid_bound(A, b, x)
+        assert info["iters"] < info0["iters"], (info["iters"], info0["iters"])
+    print("learned", info["iters"], "unpreconditioned", info0["iters"])
