@@ -152,8 +152,12 @@ typedef struct gmres_opts {
                              rows with the update split by rows, 3 = as 0 but
                              the second pass re-reads each slice from L2      */
     int32_t mgs_kernel;   /* MGS: 0 = one cooperative kernel per inner step with
-                             w in shared memory (default; used when w's row
-                             chunk fits), 1 = one kernel per basis vector       */
+                             w in shared memory and the block's basis rows
+                             staged there one vector ahead by bulk copies
+                             (default; without the staging when the rows do
+                             not fit, one kernel per basis vector when w does
+                             not fit either), 1 = one kernel per basis vector,
+                             2 = the cooperative kernel without the staging */
     int32_t l2_prefetch;  /* register-streaming CGSR: each block prefetches the
                              basis rows of the slice this many slices ahead of
                              the one it is reading into L2 (bulk prefetch);

@@ -154,7 +154,9 @@ gmres_status ensure_workspace(gmres_handle *h, int m, gmres_precision prec) {
     CK(h->bb.ensure(ldv * 8));
     CK(h->small.ensure((size_t)(2 * (MMAX + 1) * MMAX + 6 * (MMAX + 2)) * 8));
     CK(h->part.ensure((size_t)std::max(h->grid, h->nsm * h->rows_blocks_per_sm) * PSTRIDE * 8));
-    CK(h->part64.ensure((size_t)h->grid * 4 * 8));
+    // binary64 partials: the reduction kernels (grid blocks) and the
+    // residual, which runs on the SpMV's grid (8 blocks per SM)
+    CK(h->part64.ensure((size_t)std::max(h->grid, h->nsm * 8) * 4 * 8));
     if (ilu_on(h))
         CK(h->t2.ensure(ldv * 8));
     if (ilu_on(h))
@@ -260,10 +262,12 @@ cudaError_t launch_spmv_step(gmres_handle *h, const GridCtx<T, VT> &c, const XT 
     return cudaGetLastError();
 }
 
+// z = b - A x gathers x like the SpMV, so it gets the SpMV's grid (more warps
+// in flight per SM than the reduction kernels' two blocks).
 template <class T, class VT>
 cudaError_t launch_residual(gmres_handle *h, const GridCtx<T, VT> &c, const double *b,
                             const double *x, double *z, int setup) {
-    dim3 g(h->grid), bl(kThreads);
+    dim3 g(h->nsm * 8), bl(kThreads);
     if constexpr (std::is_same<T, double>::value) {
         // the per-variable study's residual: its own instantiations
         if (c.pv & (PV_A_RESID | PV_B | PV_AX | PV_Z)) {
@@ -371,7 +375,9 @@ bool mgs_persist_ok(gmres_handle *h) {
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, h->device);
     if (h->nsm > MGSP_MAXGRID)
         coop = 0;  // one warp reads every block's exchange slots
-    const int64_t chunk = round_up((h->ldv + h->nsm - 1) / h->nsm, 4);
+    // rows per block: a multiple of 8 (the staged kernel's bulk copies move
+    // whole 16-byte units), the same for both kernels so they sum alike
+    const int64_t chunk = round_up((h->ldv + h->nsm - 1) / h->nsm, 8);
     const size_t smem = (size_t)chunk * sizeof(T) + 16;
     int optin = 0;
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
@@ -388,6 +394,41 @@ bool mgs_persist_ok(gmres_handle *h) {
     }
     cudaGetLastError();
     h->mgs_chunk = chunk;
+    h->mgs_ok_cache[key] = ok;
+    return ok;
+}
+
+// Whether the staged cooperative MGS kernel can run: the persistent kernel's
+// conditions, plus w's row chunk and three basis row chunks in shared memory.
+template <class T, class VT>
+bool mgs_staged_ok(gmres_handle *h) {
+    if (!mgs_persist_ok<T, VT>(h))
+        return false;
+    const void *key = (const void *)k_mgs_staged<T, VT>;
+    auto it = h->mgs_ok_cache.find(key);
+    if (it != h->mgs_ok_cache.end())
+        return it->second;
+    const int64_t chunk = round_up((h->ldv + h->nsm - 1) / h->nsm, 8);
+    const size_t smem = MGSS_HEAD + (size_t)chunk * (sizeof(T) + 3 * sizeof(VT));
+    int optin = 0;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
+    bool ok = true;
+    auto prep = [&](auto fn) {
+        cudaFuncAttributes fa;
+        int per_sm = 0;
+        ok = ok && cudaFuncGetAttributes(&fa, fn) == cudaSuccess &&
+             smem + fa.sharedSizeBytes <= (size_t)optin &&
+             cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) ==
+                 cudaSuccess &&
+             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, MGSP_THREADS, smem) ==
+                 cudaSuccess &&
+             per_sm >= 1;
+    };
+    prep(k_mgs_staged<T, VT>);
+    if constexpr (std::is_same<T, double>::value)
+        prep(k_mgs_staged<T, VT, true>);
+    cudaGetLastError();
+    h->mgss_chunk = chunk;
     h->mgs_ok_cache[key] = ok;
     return ok;
 }
@@ -554,7 +595,7 @@ gmres_status enqueue_step_core(gmres_handle *h, GridCtx<T, VT> &c, int col, gmre
     // the previous step's normalisation moves into this step's SpMV unless a
     // preconditioner, the orthogonality test or the cooperative MGS kernel
     // (which writes v_{j+1} itself) is in use
-    const bool coop_mgs = ortho == GMRES_ORTHO_MGS && h->opts.mgs_kernel == 0 &&
+    const bool coop_mgs = ortho == GMRES_ORTHO_MGS && h->opts.mgs_kernel != 1 &&
                           mgs_persist_ok<T, VT>(h);
     const bool fused = fused_normalize(h, c, coop_mgs);
     if (fused && col > 0) {
@@ -636,9 +677,12 @@ gmres_status enqueue_step_core(gmres_handle *h, GridCtx<T, VT> &c, int col, gmre
         k_cgs_tile<T, VT, 1><<<gt, CGS_THREADS, sm, h->stream>>>(c, ncols, TR, spin);
         k_cgs_tile<T, VT, 2><<<gt, CGS_THREADS, sm, h->stream>>>(c, ncols, TR, spin);
         acct.launches[GMRES_K_ORTHO] += 3;
-    } else if (h->opts.mgs_kernel == 0 && mgs_persist_ok<T, VT>(h)) {
-        // one cooperative kernel: w stays in shared memory, v_{j+1} written
-        int64_t chunk = h->mgs_chunk;
+    } else if (h->opts.mgs_kernel != 1 && mgs_persist_ok<T, VT>(h)) {
+        // one cooperative kernel: w stays in shared memory, v_{j+1} written;
+        // by default with the block's basis rows staged in shared memory one
+        // vector ahead (when they fit)
+        const bool staged = h->opts.mgs_kernel == 0 && mgs_staged_ok<T, VT>(h);
+        int64_t chunk = staged ? h->mgss_chunk : h->mgs_chunk;
         long long spin = h->opts.spin_limit > 0 ? h->opts.spin_limit : (1LL << 24);
         // exchange slots: 2 parities x 4 words per block, round numbers
         // never reused (cleared before they wrap)
@@ -654,17 +698,24 @@ gmres_status enqueue_step_core(gmres_handle *h, GridCtx<T, VT> &c, int col, gmre
         GridCtx<T, VT> cc = c;
         int nc = ncols;
         void *args[] = {&cc, &nc, &chunk, &spin, &slots, &round0};
-        const void *kfn = (const void *)k_mgs_persist<T, VT>;
+        const void *kfn = staged ? (const void *)k_mgs_staged<T, VT>
+                                 : (const void *)k_mgs_persist<T, VT>;
+        size_t smem = staged ? MGSS_HEAD + (size_t)chunk * (sizeof(T) + 3 * sizeof(VT))
+                             : (size_t)chunk * sizeof(T) + 16;
         if constexpr (std::is_same<T, double>::value) {
-            if (c.pv & PV_ORTHO) {  // the per-variable study's instantiation
-                kfn = (const void *)k_mgs_persist<T, VT, true>;
-                CK(cudaFuncSetAttribute(k_mgs_persist<T, VT, true>,
-                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)((size_t)chunk * sizeof(T) + 16)));
+            if (c.pv & PV_ORTHO) {  // the per-variable study's instantiations
+                if (staged) {
+                    kfn = (const void *)k_mgs_staged<T, VT, true>;
+                } else {
+                    kfn = (const void *)k_mgs_persist<T, VT, true>;
+                    CK(cudaFuncSetAttribute(k_mgs_persist<T, VT, true>,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)smem));
+                }
             }
         }
-        CK(cudaLaunchCooperativeKernel(kfn, dim3(h->nsm), dim3(MGSP_THREADS), args,
-                                       (size_t)chunk * sizeof(T) + 16, h->stream));
+        CK(cudaLaunchCooperativeKernel(kfn, dim3(h->nsm), dim3(MGSP_THREADS), args, smem,
+                                       h->stream));
         acct.launches[GMRES_K_ORTHO] += 1;
         h->timer.end(GMRES_K_ORTHO, e);
         return GMRES_OK;
@@ -747,7 +798,7 @@ void account_cycle(gmres_handle *h, int j, gmres_ortho ortho, Acct &acct) {
     // row pointers, diagonal positions) plus its vectors and ready flags
     const double sL = (sizeof(T) == 8 && !h->limited && !h->opts.ilu_binary32) ? 8.0 : 4.0;
     const double ilu_bytes = nnz * (sL + 4) + 2.0 * (n + 1) * 4 + n * 4 + 4.0 * n * sT + 8.0 * n;
-    const bool coop = ortho == GMRES_ORTHO_MGS && h->opts.mgs_kernel == 0 &&
+    const bool coop = ortho == GMRES_ORTHO_MGS && h->opts.mgs_kernel != 1 &&
                       mgs_persist_ok<T, VT>(h);
     const bool fused = h->opts.normalize_fused && !pre && !ilu &&
                        h->opts.orth_norm == GMRES_ORTH_OFF && !coop;
@@ -1108,7 +1159,7 @@ gmres_status validate_opts(const gmres_opts *o) {
     if (!(o->inner_factor >= 0) || o->path < 0 || o->path > 2 || o->spin_limit < 0 ||
         (o->spmv_lanes != 0 && (o->spmv_lanes < 1 || o->spmv_lanes > 32 ||
                                 (o->spmv_lanes & (o->spmv_lanes - 1)))) ||
-        o->cgs_kernel < 0 || o->cgs_kernel > 3 || o->mgs_kernel < 0 || o->mgs_kernel > 1 ||
+        o->cgs_kernel < 0 || o->cgs_kernel > 3 || o->mgs_kernel < 0 || o->mgs_kernel > 2 ||
         o->l2_prefetch < 0 || o->l2_prefetch > 4 || !(o->stall_factor >= 0) ||
         (o->block_cluster != 0 && o->block_cluster != 1 && o->block_cluster != TEAM_SINGLE_CTAS) ||
         o->stall_window < 0 || o->stall_window > MMAX || o->orth_norm < GMRES_ORTH_OFF ||

@@ -229,22 +229,32 @@ __device__ __forceinline__ T csr_row_g(const int *__restrict__ rowptr,
     if (row < n) {
         int beg = __ldg(rowptr + row), end = __ldg(rowptr + row + 1);
         int k = beg + gl;
-        // four independent gathers in flight per lane; the sum keeps the
+        // four independent gathers in flight per lane, also on the last,
+        // partial group of a row (its missing entries are predicated off, so
+        // a short row's entries are all requested at once); the sum keeps the
         // sequential order of k
-        for (; k + 3 * L < end; k += 4 * L) {
-            const int c0 = __ldg(colind + k), c1 = __ldg(colind + k + L);
-            const int c2 = __ldg(colind + k + 2 * L), c3 = __ldg(colind + k + 3 * L);
-            const T a0 = (T)a(k), a1 = (T)a(k + L);
-            const T a2 = (T)a(k + 2 * L), a3 = (T)a(k + 3 * L);
-            const T x0 = xv(c0), x1 = xv(c1);
-            const T x2 = xv(c2), x3 = xv(c3);
+        for (; k < end; k += 4 * L) {
+            const bool p1 = k + L < end, p2 = k + 2 * L < end, p3 = k + 3 * L < end;
+            const int c0 = __ldg(colind + k);
+            const int c1 = p1 ? __ldg(colind + k + L) : c0;
+            const int c2 = p2 ? __ldg(colind + k + 2 * L) : c0;
+            const int c3 = p3 ? __ldg(colind + k + 3 * L) : c0;
+            const T a0 = (T)a(k);
+            const T a1 = p1 ? (T)a(k + L) : T(0);
+            const T a2 = p2 ? (T)a(k + 2 * L) : T(0);
+            const T a3 = p3 ? (T)a(k + 3 * L) : T(0);
+            const T x0 = xv(c0);
+            const T x1 = p1 ? xv(c1) : T(0);
+            const T x2 = p2 ? xv(c2) : T(0);
+            const T x3 = p3 ? xv(c3) : T(0);
             acc += a0 * x0;
-            acc += a1 * x1;
-            acc += a2 * x2;
-            acc += a3 * x3;
+            if (p1)
+                acc += a1 * x1;
+            if (p2)
+                acc += a2 * x2;
+            if (p3)
+                acc += a3 * x3;
         }
-        for (; k < end; k += L)
-            acc += (T)a(k) * xv(__ldg(colind + k));
     }
 #pragma unroll
     for (int off = L / 2; off > 0; off >>= 1)

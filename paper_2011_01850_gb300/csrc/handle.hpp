@@ -83,6 +83,7 @@ struct gmres_handle {
     int grid = 0;          // blocks of the reduction kernels
     int rows_blocks_per_sm = 4;  // blocks per SM of the register-streaming CGSR kernels
     int64_t mgs_chunk = 0;       // rows per block of the cooperative MGS kernel
+    int64_t mgss_chunk = 0;      // rows per block of the staged cooperative MGS kernel
     std::map<const void *, bool> mgs_ok_cache;  // cooperative MGS feasible, per kernel
     DevBuf mgs_seq;              // exchange slots of the cooperative MGS kernel
     DevBuf mon;                  // restart-test histories and the U, S matrices

@@ -21,6 +21,7 @@
 #pragma once
 
 #include "grid_kernels.cuh"
+#include "tma.cuh"
 
 namespace gmres {
 
@@ -236,6 +237,201 @@ __global__ void __launch_bounds__(MGSP_THREADS, 1)
     T hnext;
     {
         const VT *vp = c.V + (size_t)(ncols - 1) * c.ldv + rb;
+        T nsq = 0;
+        for (int64_t q = 4 * tid; q < len; q += 4 * nth) {
+            T a[4];
+            ld4<T, VT>(vp + q, c.vinv, a);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                T wv = ws[q + k] - hprev * a[k];
+                if (PVS)
+                    wv = pv_round(wv, c.pv, PV_W);
+                ws[q + k] = wv;
+                nsq += wv * wv;
+            }
+        }
+        T nv[1] = {block_sum1(nsq, sred)}, tv[1];
+        if (!exchange_round<T, 1>(slots, ncols & 1, round0 + (unsigned)ncols, nv, tv, err,
+                                  spin, sx))
+            return;
+        hnext = wsqrt(tv[0]);
+        if (PVS)
+            hnext = pv_round(hnext, c.pv, PV_H);
+    }
+    // v_{j+1} = w / h_{j+1,j} into basis column ncols (unused if the cycle ends)
+    if (hnext > T(0)) {
+        VT *dst = c.V + (size_t)ncols * c.ldv + rb;
+        for (int64_t q = 4 * tid; q < len; q += 4 * nth) {
+            T v[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                v[k] = ws[q + k] / hnext;
+            stb4<T, VT>(dst + q, v, c.vscale);
+        }
+    }
+    if (blockIdx.x == 0) {
+        for (int i = tid; i < ncols; i += nth)
+            c.h1[i] = hcol[i];
+        if (tid == 0)
+            c.ctl->wnorm0 = (double)wsqrt(wn0sq);
+        __threadfence();
+        __syncthreads();
+        givens_step<PVS>(c, ncols - 1, c.h1, hnext);
+    }
+}
+
+// The same MGS step with the block's rows of the basis staged in shared
+// memory: a ring of three row-chunk buffers filled by bulk copies one basis
+// vector ahead, so the copy of v_{i+1} is in flight while the block sweeps
+// with v_{i-1}, v_i and waits in exchange round i; every sweep then reads
+// shared memory only (w stays there too).  Same arithmetic, same order as
+// k_mgs_persist, so the two give the same results bit for bit.  Needs
+// chunk (sizeof(T) + 3 sizeof(VT)) + MGSS_HEAD bytes of shared memory, chunk a
+// multiple of 8 (bulk copies of whole 16-byte units from 16-byte aligned
+// rows).  A bulk copy that does not complete within `spin` probes is a
+// timeout: the block reports it, waits (bounded) for its other copies in
+// flight and returns, like every other block at its next exchange round.
+constexpr int MGSS_HEAD = 64;  // three mbarriers, padded to keep the data 16-byte aligned
+
+template <class T, class VT, bool PVS = false>
+__global__ void __launch_bounds__(MGSP_THREADS, 1)
+    k_mgs_staged(GridCtx<T, VT> c, int ncols, int64_t chunk, long long spin,
+                 unsigned long long *slots, unsigned round0) {
+    if (!c.ctl->active)
+        return;
+    extern __shared__ __align__(128) unsigned char mgss_smem[];
+    uint64_t *bars = reinterpret_cast<uint64_t *>(mgss_smem);
+    T *ws = reinterpret_cast<T *>(mgss_smem + MGSS_HEAD);
+    VT *vbuf = reinterpret_cast<VT *>(mgss_smem + MGSS_HEAD + (size_t)chunk * sizeof(T));
+    __shared__ T sred[2 * 32];
+    __shared__ T sx[3];
+    __shared__ T hcol[MMAX + 2];
+    __shared__ int s_fail;
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const int64_t rb = (int64_t)blockIdx.x * chunk;
+    int64_t re = rb + chunk;
+    if (re > c.ldv)
+        re = c.ldv;
+    const int64_t len = re > rb ? re - rb : 0;
+    const uint32_t vbytes = (uint32_t)(len * (int64_t)sizeof(VT));
+    int *err = &c.ctl->timeout;
+    if (tid == 0) {
+        for (int k = 0; k < 3; ++k)
+            mbar_init(&bars[k], 1);
+        mbar_init_fence();
+        s_fail = 0;
+    }
+    __syncthreads();
+    // basis column `col` into ring buffer col % 3 (thread 0)
+    int issued = 0, waited = 0;  // columns issued / waited for (same in every thread)
+    auto issue = [&](int col) {
+        if (len > 0 && tid == 0) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_arrive_expect_tx(&bars[col % 3], vbytes);
+            bulk_g2s(vbuf + (size_t)(col % 3) * chunk, c.V + (size_t)col * c.ldv + rb, vbytes,
+                     &bars[col % 3]);
+        }
+        ++issued;
+    };
+    // wait for column `col`; false (in every thread) on a timeout
+    auto wait = [&](int col) -> bool {
+        bool ok = true;
+        if (len > 0)
+            ok = mbar_wait(&bars[col % 3], (uint32_t)((col / 3) & 1), spin);
+        if (!ok)
+            s_fail = 1;
+        ++waited;
+        __syncthreads();
+        return s_fail == 0;
+    };
+    // on the way out: let every copy still in flight land (bounded) before
+    // the block's shared memory is released
+    auto drain = [&]() {
+        for (int col = waited; col < issued; ++col)
+            if (len > 0)
+                mbar_wait(&bars[col % 3], (uint32_t)((col / 3) & 1), spin);
+    };
+    auto fail = [&]() {
+        if (tid == 0)
+            atomicExch(err, 1);
+        drain();
+    };
+    auto vb = [&](int col) -> const VT * { return vbuf + (size_t)(col % 3) * chunk; };
+
+    issue(0);
+    if (ncols > 1)
+        issue(1);
+    for (int64_t q = 4 * tid; q < len; q += 4 * nth) {
+        T v[4];
+        ldv4(c.w + rb + q, v);
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            ws[q + k] = v[k];
+    }
+    if (!wait(0)) {
+        fail();
+        return;
+    }
+    // h_0 = w . v_0 and ||w||^2 (breakdown reference)
+    T hprev, wn0sq;
+    {
+        T acc[2] = {0, 0};
+        for (int64_t q = 4 * tid; q < len; q += 4 * nth) {
+            T v[4];
+            ld4<T, VT>(vb(0) + q, c.vinv, v);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                acc[0] += ws[q + k] * v[k];
+                acc[1] += ws[q + k] * ws[q + k];
+            }
+        }
+        block_sum<T, 2>(acc, sred);
+        T tot[2];
+        if (!exchange_round<T, 2>(slots, 0, round0, acc, tot, err, spin, sx)) {
+            drain();
+            return;
+        }
+        hprev = PVS ? pv_round(tot[0], c.pv, PV_H) : tot[0];
+        wn0sq = tot[1];
+    }
+    if (tid == 0)
+        hcol[0] = hprev;
+    for (int i = 1; i < ncols; ++i) {
+        if (i + 1 < ncols)
+            issue(i + 1);  // its buffer last held v_{i-2}, read before round i-1 ended
+        if (!wait(i)) {
+            fail();
+            return;
+        }
+        const VT *vp = vb(i - 1);
+        const VT *vi = vb(i);
+        T d = 0;
+        for (int64_t q = 4 * tid; q < len; q += 4 * nth) {
+            T a[4], b[4];
+            ld4<T, VT>(vp + q, c.vinv, a);
+            ld4<T, VT>(vi + q, c.vinv, b);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                T wv = ws[q + k] - hprev * a[k];
+                if (PVS)
+                    wv = pv_round(wv, c.pv, PV_W);
+                ws[q + k] = wv;
+                d += wv * b[k];
+            }
+        }
+        T dv[1] = {block_sum1(d, sred)}, hv[1];
+        if (!exchange_round<T, 1>(slots, i & 1, round0 + (unsigned)i, dv, hv, err, spin, sx)) {
+            drain();
+            return;
+        }
+        hprev = PVS ? pv_round(hv[0], c.pv, PV_H) : hv[0];
+        if (tid == 0)
+            hcol[i] = hprev;
+    }
+    // last projection and ||w||^2
+    T hnext;
+    {
+        const VT *vp = vb(ncols - 1);
         T nsq = 0;
         for (int64_t q = 4 * tid; q < len; q += 4 * nth) {
             T a[4];

@@ -442,6 +442,29 @@ def test_mgs_cooperative_matches_per_column(gpulib, stream):
     assert i0["kernel_launches"]["ortho"] < i1["kernel_launches"]["ortho"]
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "mixed_bf16", "mixed_fp16"])
+@pytest.mark.parametrize("n", [60000, 2_000_000])
+def test_mgs_staged_equals_unstaged(prec, n, gpulib, stream):
+    """The cooperative MGS kernel with the basis rows staged in shared memory
+    by bulk copies (mgs_kernel 0) does the unstaged kernel's arithmetic in
+    the same order (mgs_kernel 2): one restart cycle gives the same Hessenberg
+    matrix, basis and correction bit for bit, at a size where every block
+    holds a short row chunk and at the power-law workload's 2 M rows (binary64
+    there too large to stage: both run unstaged, still equal)."""
+    A = I.powerlaw_random(n, seed=21)
+    b = I.rhs_ones_noise(A, 1e-3, 3)
+    res = []
+    for kern in (0, 2):
+        s = G.Solver(A, stream=stream)
+        s.set_opts(path=G.PATH_GRID, mgs_kernel=kern)
+        res.append(G.gmres_arnoldi(s.h, dev(b), 50, 50, G.ORTHO_MGS, G.PRECISIONS[prec], n=n))
+        s.close()
+    g0, g2 = res
+    assert g0["j"] == g2["j"] == 50
+    for k in ("Hbar", "H", "s", "y", "u", "V"):
+        assert np.array_equal(g0[k], g2[k]), k
+
+
 @pytest.mark.parametrize("prec", ["fp64", "mixed", "mixed_fp16"])
 def test_cgsr_kernel_families_agree(prec, gpulib, stream):
     """The CGSR kernel families (rows with the update split by basis vectors
