@@ -128,13 +128,36 @@ gmres_status batch_run(gmres_batch *B, const double *db, double *dx, int m, doub
                   : (B->tuned_lanes > 0 ? B->tuned_lanes : pow2_lanes(B->avg_row / 2.0));
     using KFn = void (*)(const BlockSys<T, VT> *, BlockParams, BlockResult *);
     KFn kfn = nullptr, kcl = nullptr;
+    // 256-thread launches: the instantiations bounded for several resident
+    // blocks per SM; other cluster widths: the plain bound
+    const bool c256 = B->cluster_threads == 256;
     switch (L) {
-    case 1: kfn = &k_block_solve<T, VT, 1>; kcl = &k_team_solve<T, VT, 1, CLUSTER_CTAS>; break;
-    case 2: kfn = &k_block_solve<T, VT, 2>; kcl = &k_team_solve<T, VT, 2, CLUSTER_CTAS>; break;
-    case 4: kfn = &k_block_solve<T, VT, 4>; kcl = &k_team_solve<T, VT, 4, CLUSTER_CTAS>; break;
-    case 8: kfn = &k_block_solve<T, VT, 8>; kcl = &k_team_solve<T, VT, 8, CLUSTER_CTAS>; break;
-    case 16: kfn = &k_block_solve<T, VT, 16>; kcl = &k_team_solve<T, VT, 16, CLUSTER_CTAS>; break;
-    default: kfn = &k_block_solve<T, VT, 32>; kcl = &k_team_solve<T, VT, 32, CLUSTER_CTAS>; break;
+    case 1:
+        kfn = &k_block_solve<T, VT, 1, 256>;
+        kcl = c256 ? &k_team_solve<T, VT, 1, CLUSTER_CTAS, 256> : &k_team_solve<T, VT, 1, CLUSTER_CTAS>;
+        break;
+    case 2:
+        kfn = &k_block_solve<T, VT, 2, 256>;
+        kcl = c256 ? &k_team_solve<T, VT, 2, CLUSTER_CTAS, 256> : &k_team_solve<T, VT, 2, CLUSTER_CTAS>;
+        break;
+    case 4:
+        kfn = &k_block_solve<T, VT, 4, 256>;
+        kcl = c256 ? &k_team_solve<T, VT, 4, CLUSTER_CTAS, 256> : &k_team_solve<T, VT, 4, CLUSTER_CTAS>;
+        break;
+    case 8:
+        kfn = &k_block_solve<T, VT, 8, 256>;
+        kcl = c256 ? &k_team_solve<T, VT, 8, CLUSTER_CTAS, 256> : &k_team_solve<T, VT, 8, CLUSTER_CTAS>;
+        break;
+    case 16:
+        kfn = &k_block_solve<T, VT, 16, 256>;
+        kcl = c256 ? &k_team_solve<T, VT, 16, CLUSTER_CTAS, 256>
+                   : &k_team_solve<T, VT, 16, CLUSTER_CTAS>;
+        break;
+    default:
+        kfn = &k_block_solve<T, VT, 32, 256>;
+        kcl = c256 ? &k_team_solve<T, VT, 32, CLUSTER_CTAS, 256>
+                   : &k_team_solve<T, VT, 32, CLUSTER_CTAS>;
+        break;
     }
     const size_t smem = block_smem_bytes<T>(m);
     CK(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

@@ -451,11 +451,24 @@ __device__ void block_solve_one(const BlockSys<T, VT> &S, const BlockParams &P, 
     team_solve_one<T, VT, L, 1>(S, P, res, smem_raw);
 }
 
+// Launch bounds of the whole-solve kernels.  Launches of up to 1024 threads
+// (single systems) use the plain bound; the batched solver's 256-thread
+// launches ask for several resident blocks per SM, which caps the registers
+// per thread: occupancy is what hides the latency of these block-wide
+// reductions.  Measured on 2048 uneven 2-D systems, GMRES(30) MGS: binary32
+// 2.25 s with 64 registers (4 blocks per SM), 1.98 s with 40 (6), 2.06 s with
+// 51 (5), 2.01 s with 32 (8, spilling), 2.96 s with 80 (3) and 3.88 s
+// unbounded (~125, 2); binary64 best with 5 blocks (3.12 s against 3.28 s).
+template <class T, int MAXT>
+struct SolveMinBlocks {
+    static constexpr int value = MAXT > 256 ? 1 : (sizeof(T) == 4 ? 6 : 5);
+};
+
 // Persistent grid over a work queue of systems (largest first); one team
 // (block or cluster) per system.
-template <class T, class VT, int L, int CS>
-__global__ void __launch_bounds__(1024) k_team_solve(const BlockSys<T, VT> *sys, BlockParams P,
-                                                     BlockResult *res) {
+template <class T, class VT, int L, int CS, int MAXT = 1024>
+__global__ void __launch_bounds__(MAXT, SolveMinBlocks<T, MAXT>::value)
+    k_team_solve(const BlockSys<T, VT> *sys, BlockParams P, BlockResult *res) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_idx;
     for (;;) {
@@ -479,9 +492,9 @@ __global__ void __launch_bounds__(1024) k_team_solve(const BlockSys<T, VT> *sys,
     }
 }
 
-template <class T, class VT, int L>
-__global__ void __launch_bounds__(1024) k_block_solve(const BlockSys<T, VT> *sys, BlockParams P,
-                                                      BlockResult *res) {
+template <class T, class VT, int L, int MAXT = 1024>
+__global__ void __launch_bounds__(MAXT, SolveMinBlocks<T, MAXT>::value)
+    k_block_solve(const BlockSys<T, VT> *sys, BlockParams P, BlockResult *res) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_idx;
     for (;;) {
