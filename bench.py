@@ -437,6 +437,37 @@ def bench_ours(args):
     }
     if "fp64" in compare:
         out["speedup_vs_fp64"] = compare["fp64"]["speedup_of_headline"]
+    if learned:
+        # inference of the learned preconditioner (features cached, the MLP on
+        # every nonzero, M's values): once per matrix, outside the timed solves
+        set_pre("learned")
+        torch.cuda.synchronize()
+        tinf = []
+        for _ in range(5):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            G.gmres_spai_set(solver.h, spai_params)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            tinf.append(e0.elapsed_time(e1))
+        inf_ms = statistics.median(tinf)
+        # 8 -> 64 -> 64 -> 1 network: 4672 multiply-adds per nonzero
+        fwd_flop = 2.0 * 4672 * nnz
+        # FP32 FMA peak from the unit counts: SMs x 128 FP32 lanes x 2 flop x
+        # the maximum SM clock (MEASURED_PEAKS.json's, else 2070 MHz)
+        sms = torch.cuda.get_device_properties(local).multi_processor_count
+        try:
+            with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+                mhz = float(json.load(f).get("sm_max_mhz", 2070.0))
+        except (OSError, ValueError):
+            mhz = 2070.0
+        fp32_peak = sms * 128 * 2 * mhz * 1e6 / 1e12
+        out["spai"] = {"inference_ms": round(inf_ms, 3), "forward_gflop": round(fwd_flop / 1e9, 1),
+                       "achieved_tflops": round(fwd_flop / (inf_ms * 1e-3) / 1e12, 2),
+                       "fp32_peak_tflops": round(fp32_peak, 1),
+                       "frac": round(fwd_flop / (inf_ms * 1e-3) / 1e12 / fp32_peak, 3),
+                       "solve_plus_inference_ms": round(ms_step + inf_ms, 3)}
     if dom == "precond" and spec.get("precond") == "ilu" and klaunch[dom]:
         # the triangular solves pass their dependency levels one after another:
         # bound by the latency of a level, not by bytes

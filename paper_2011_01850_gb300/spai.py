@@ -136,10 +136,28 @@ if __name__ == "__main__":  # pragma: no cover - offline training entry point
     ap.add_argument("--N", type=int, default=64)
     ap.add_argument("--count", type=int, default=2000)
     ap.add_argument("--out", default=None)
+    ap.add_argument("--record", default=None,
+                    help="write the run's settings, wall time and loss history (JSON)")
     args = ap.parse_args()
     t0 = time.time()
     p, hist = train(N=args.N, count=args.count, log=print)
-    print(json.dumps({"seconds": time.time() - t0, "first_loss": hist[0],
+    secs = time.time() - t0
+    print(json.dumps({"seconds": secs, "first_loss": hist[0],
                       "last_loss": float(np.mean(hist[-20:]))}))
     if args.out:
         np.save(args.out, p)
+    if args.record:
+        import sys
+        rec = {"command": "python -m paper_2011_01850_gb300.spai " + " ".join(sys.argv[1:]),
+               "seconds": round(secs, 1), "matrices": args.count, "grid": args.N,
+               "family": "3-D 7-point upwind convection-diffusion, v ~ U[-1,1]^3 per node, "
+                         "diffusion 0.1 (1, r1, r2), r1, r2 log-uniform in [1, 100]",
+               "adam": {"lr": 3e-3, "beta1": 0.9, "beta2": 0.999, "eps": 1e-8},
+               "init": "Jacobi parameters + N(0, 0.02^2), seed 0",
+               "probes": "8 Rademacher probes per step (counter-based, seed 1000003 s + step); "
+                         "every 10th matrix also the residuals of unpreconditioned mixed "
+                         "CGSR GMRES(30) after 5 and 15 inner iterations (unit RMS)",
+               "steps": len(hist), "loss": [float(v) for v in hist]}
+        with open(args.record, "w") as f:
+            json.dump(rec, f)
+            f.write("\n")
