@@ -247,6 +247,19 @@ GridCtx<T, VT> make_ctx(gmres_handle *h, int m) {
 
 int spmv_grid(gmres_handle *h) { return h->nsm * 8; }
 
+// v_1 and the update x += V_j y run 8 blocks per SM, like the SpMV, with the
+// row chunk to match: more bytes in flight per SM than the reduction
+// kernels' 2 (the update at 160^3: 7.1 -> 6.4 ms per solve; the
+// normalisation gained nothing, a ~10 us kernel bound by its ramp, and keeps
+// the 2-block grid).
+template <class T, class VT>
+GridCtx<T, VT> stream_ctx(const gmres_handle *h, const GridCtx<T, VT> &c, int *grid) {
+    GridCtx<T, VT> s = c;
+    *grid = h->nsm * 8;
+    s.chunk = round_up((h->ldv + *grid - 1) / *grid, 4);
+    return s;
+}
+
 // Launch helpers templated on the lanes-per-row count.
 template <class T, class VT, class XT>
 cudaError_t launch_spmv_step(gmres_handle *h, const GridCtx<T, VT> &c, const XT *x, T *y, int L) {
@@ -917,7 +930,11 @@ gmres_status solve_grid(gmres_handle *h, const double *b, double *x, int m, doub
         if (h->opts.orth_norm != GMRES_ORTH_OFF)
             CK(cudaMemsetAsync(mon_hist(h), 0, (MMAX + 2) * sizeof(double), h->stream));
         e = h->timer.begin();
-        k_init<T, VT><<<h->grid, kThreads, 0, h->stream>>>(c);
+        {
+            int gi = 0;
+            const GridCtx<T, VT> ci = stream_ctx(h, c, &gi);
+            k_init<T, VT><<<gi, kThreads, 0, h->stream>>>(ci);
+        }
         CKL();
         h->timer.end(GMRES_K_NORMALIZE, e);
         acct.launches[GMRES_K_NORMALIZE]++;
@@ -933,10 +950,12 @@ gmres_status solve_grid(gmres_handle *h, const double *b, double *x, int m, doub
         k_backsolve<T, VT><<<1, 32, sm, h->stream>>>(c);
         CKL();
         const bool pre = c.pvals != nullptr;
+        int gu = 0;
+        const GridCtx<T, VT> cu = stream_ctx(h, c, &gu);
         if (c.pv & PV_X)  // the per-variable study's instantiation
-            k_update<T, VT, true><<<h->grid, kThreads, 0, h->stream>>>(c, x, pre ? 1 : 0);
+            k_update<T, VT, true><<<gu, kThreads, 0, h->stream>>>(cu, x, pre ? 1 : 0);
         else
-            k_update<T, VT><<<h->grid, kThreads, 0, h->stream>>>(c, x, pre ? 1 : 0);
+            k_update<T, VT><<<gu, kThreads, 0, h->stream>>>(cu, x, pre ? 1 : 0);
         CKL();
         acct.launches[GMRES_K_UPDATE] += 2;
         if (pre) {
