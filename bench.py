@@ -47,15 +47,13 @@ def parse():
     p.add_argument("--workload", default=WORKLOAD)
     p.add_argument("--compare-steps", "--fp64-steps", dest="compare_steps", type=int, default=1)
     p.add_argument("--spai-params", default=None)
-    p.add_argument("--cgs-kernel", type=int, default=0,
-                   help="CGSR kernel family: 0 register-streaming rows, 1 TMA tiles, "
-                        "2 rows with the per-row-group update")
+    p.add_argument("--cgs-kernel", type=int, default=0, choices=[0, 2],
+                   help="CGSR kernel family: 0 register-streaming rows (update split by "
+                        "basis vectors), 2 the same with the update split by rows")
     p.add_argument("--l2-prefetch", type=int, default=None,
                    help="CGSR rows kernels: slices prefetched ahead into L2 (library default)")
     p.add_argument("--block-cluster", type=int, default=None,
                    help="block path: 1 block or an 8-block cluster per system (library default)")
-    p.add_argument("--fuse-normalize", action="store_true",
-                   help="form v_{j+1} inside the next SpMV instead of in its own kernel")
     p.add_argument("--cluster-threads", type=int, default=None,
                    help="batched: threads per block of the large systems' clusters")
     p.add_argument("--cluster-rows", type=int, default=None,
@@ -226,8 +224,6 @@ def bench_ours(args):
         solver.set_opts(l2_prefetch=args.l2_prefetch)
     if args.block_cluster is not None:
         solver.set_opts(block_cluster=args.block_cluster)
-    if args.fuse_normalize:
-        solver.set_opts(normalize_fused=1)
     if args.trsv_kernel is not None:
         solver.set_opts(trsv_kernel=args.trsv_kernel)
     learned = spec.get("precond") == "learned"
@@ -372,9 +368,8 @@ def bench_ours(args):
     tot_kms = sum(kms.values())
     iters = infos[0]["iters"]
     restarts = infos[0]["restarts"]
-    kernel_names = {"ortho": ("CGSR passes (k_cgs_tile x3)" if args.cgs_kernel == 1
-                              else "CGSR passes (k_cgs_rows x2 + k_cgs_passb_reg + "
-                                   "k_reduce_cols x2)" if args.cgs_kernel == 0 and prec == "mixed"
+    kernel_names = {"ortho": ("CGSR passes (k_cgs_rows x2 + k_cgs_passb_reg + "
+                              "k_reduce_cols x2)" if prec == "mixed"
                               else "CGSR passes (k_cgs_rows x3 + k_reduce_cols x2)")
                     if ortho == "cgsr" else "MGS step (k_mgs_persist, cooperative)",
                     "block": "single-block solver (k_block_solve)",
@@ -404,12 +399,10 @@ def bench_ours(args):
                   else "inputs L2-resident (no flush; small-system workload)",
             "parallelism": "replicas" if world > 1 else "single GPU",
             "spmv_lanes": {"f32": lanes32, "f64": lanes64},
-            "cgs_kernel": ["register-streaming rows, pass B slice in registers", "TMA tiles",
-                           "register-streaming rows, per-row-group update",
-                           "register-streaming rows, pass B re-read from L2"][args.cgs_kernel],
+            "cgs_kernel": {0: "register-streaming rows, pass B slice in registers",
+                           2: "register-streaming rows, per-row-group update"}[args.cgs_kernel],
             "l2_prefetch": int(G.gmres_get_opts(solver.h).l2_prefetch),
             "block_cluster": int(G.gmres_get_opts(solver.h).block_cluster),
-            "normalize_fused": int(G.gmres_get_opts(solver.h).normalize_fused),
         },
         "iters": iters, "restarts": restarts,
         "compare": compare,

@@ -148,9 +148,9 @@ typedef struct gmres_opts {
                              (default; the updates split by basis vectors, and
                              with a binary32 basis the second pass keeps each
                              slice in registers between update and dot
-                             products), 1 = TMA-fed shared-memory tiles, 2 =
-                             rows with the update split by rows, 3 = as 0 but
-                             the second pass re-reads each slice from L2      */
+                             products), 2 = the same passes with the update
+                             split by rows (another summation order); 1 and 3
+                             are retired (GMRES_ERR_ARG)                      */
     int32_t mgs_kernel;   /* MGS: 0 = one cooperative kernel per inner step with
                              w in shared memory and the block's basis rows
                              staged there one vector ahead by bulk copies
@@ -161,7 +161,7 @@ typedef struct gmres_opts {
     int32_t l2_prefetch;  /* register-streaming CGSR: each block prefetches the
                              basis rows of the slice this many slices ahead of
                              the one it is reading into L2 (bulk prefetch);
-                             0 = off, 1..4                                      */
+                             0 = off (default), 1..4                          */
     int32_t block_cluster;/* block path: thread blocks per system, 1 (one block)
                              or 8 (a cluster with distributed-shared-memory
                              reductions); 0 = automatic (8 for binary64 from
@@ -178,10 +178,6 @@ typedef struct gmres_opts {
                              grid path only (GMRES_PATH_AUTO picks it)          */
     double orth_threshold;/* end the cycle once ||S_k|| >= this (default 1.0)  */
     int32_t orth_iters;   /* power-method iterations (default 10, as Sec. 4.1) */
-    int32_t normalize_fused; /* 1: v_{j+1} = w / h_{j+1,j} is formed inside the
-                             next step's SpMV (same values, one pass less, but
-                             a division per gathered entry: measured slower on
-                             the 3-D stencil); 0 (default): its own kernel    */
     int32_t trsv_kernel;  /* ILU(0) triangular solves, one launch per
                              triangle: 3 = cooperative, no barrier: the
                              solution entries start as an all-ones NaN
@@ -195,8 +191,8 @@ typedef struct gmres_opts {
                              else 2                                          */
     int32_t pv_mask;      /* GMRES_PV_* bits (default 0): the per-variable
                              precision study; GMRES_FP64 on the grid path only
-                             (not with split storage or cgs_kernel 1), else
-                             gmres_solve returns GMRES_ERR_ARG                */
+                             (not with split storage), else gmres_solve
+                             returns GMRES_ERR_ARG                            */
 } gmres_opts;
 
 /* Kernel classes reported in gmres_info (index into kernel_ms / kernel_bytes). */

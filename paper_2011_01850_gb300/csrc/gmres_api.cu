@@ -21,7 +21,6 @@
 #include "../../include/gmres_gb300.h"
 #include "block_solver.cuh"
 #include "cgs_rows.cuh"
-#include "cgs_tile.cuh"
 #include "mgs_persist.cuh"
 #include "grid_kernels.cuh"
 #include "orth_monitor.cuh"
@@ -475,32 +474,11 @@ gmres_status left_start(gmres_handle *h, GridCtx<T, VT> &c, Acct &acct) {
     return GMRES_OK;
 }
 
-// Whether v_{j+1} = w / h is formed inside the next step's SpMV.
-template <class T, class VT>
-bool fused_normalize(const gmres_handle *h, const GridCtx<T, VT> &c, bool coop_mgs) {
-    return h->opts.normalize_fused && !c.left && !c.pvals &&
-           h->opts.orth_norm == GMRES_ORTH_OFF && !coop_mgs && !c.pv;
-}
-
-template <class T, class VT>
-cudaError_t launch_spmv_norm(gmres_handle *h, const GridCtx<T, VT> &c, int col, T *y, int L) {
-    dim3 g(spmv_grid(h)), b(kThreads);
-    switch (L) {
-    case 1: k_spmv_norm<T, VT, 1><<<g, b, 0, h->stream>>>(c, col, y); break;
-    case 2: k_spmv_norm<T, VT, 2><<<g, b, 0, h->stream>>>(c, col, y); break;
-    case 4: k_spmv_norm<T, VT, 4><<<g, b, 0, h->stream>>>(c, col, y); break;
-    case 8: k_spmv_norm<T, VT, 8><<<g, b, 0, h->stream>>>(c, col, y); break;
-    case 16: k_spmv_norm<T, VT, 16><<<g, b, 0, h->stream>>>(c, col, y); break;
-    default: k_spmv_norm<T, VT, 32><<<g, b, 0, h->stream>>>(c, col, y); break;
-    }
-    return cudaGetLastError();
-}
-
 // The three register-streaming CGSR passes (and the two column reductions)
 // for an inner step with ncols basis vectors, then v_{j+1}.
 template <class T, class VT, bool SPLIT>
 gmres_status enqueue_cgs_rows(gmres_handle *h, GridCtx<T, VT> &c, int ncols, Acct &acct,
-                              cudaEvent_t e, bool fused) {
+                              cudaEvent_t e) {
     // one resident wave per kernel: grid = SMs x resident blocks per SM
     static int per_sm[3] = {0, 0, 0};
     if (per_sm[0] == 0) {
@@ -523,70 +501,54 @@ gmres_status enqueue_cgs_rows(gmres_handle *h, GridCtx<T, VT> &c, int ncols, Acc
         kpb[k] = (nsl + cap - 1) / cap;
         gsz[k] = (int)((nsl + kpb[k] - 1) / kpb[k]);
     }
+    // the per-variable study's instantiations (binary64 solves only)
+    bool pvs = false;
+    if constexpr (std::is_same<T, double>::value)
+        pvs = (c.pv & PV_ORTHO) != 0;
     const int pf = h->opts.l2_prefetch;
     k_cgs_rows<T, VT, 0, SPLIT><<<gsz[0], ROWS_THREADS, 0, h->stream>>>(c, ncols, c.part, kpb[0],
                                                                         pf);
     k_reduce_cols<T><<<ncols + 1, 256, 0, h->stream>>>(c.part, gsz[0], ncols, c.h1, c.ctl, 1,
                                                        c.pv);
     if constexpr (std::is_same<T, float>::value && std::is_same<VT, float>::value) {
-        if (h->opts.cgs_kernel != 3) {
-            // pass B with the slice in registers; KC vectors per warp
-            const int kc = (ncols + PB_WARPS - 1) / PB_WARPS;
-            void (*kfn)(GridCtx<float, float>, int, float *, int64_t) =
-                kc <= 2 ? k_cgs_passb_reg<2>
-                        : kc <= 4 ? k_cgs_passb_reg<4>
-                                  : kc <= 8 ? k_cgs_passb_reg<8>
-                                            : kc <= 12 ? k_cgs_passb_reg<12> : k_cgs_passb_reg<17>;
-            static std::map<const void *, int> pb_per_sm;
-            int &bps = pb_per_sm[(const void *)kfn];
-            if (bps == 0) {
-                CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kfn, PB_THREADS, 0));
-                bps = std::max(1, bps);
-            }
-            const int64_t nsl_b = h->ldv / PB_ROWS;
-            const int64_t cap = (int64_t)h->nsm * bps;
-            const int64_t kb = (nsl_b + cap - 1) / cap;
-            const int gb = (int)((nsl_b + kb - 1) / kb);
-            kfn<<<gb, PB_THREADS, 0, h->stream>>>(c, ncols, c.part, kb);
-            k_reduce_cols<T><<<ncols, 256, 0, h->stream>>>(c.part, gb, ncols, c.h2, c.ctl, 0,
-                                                           c.pv);
-        } else {
-            k_cgs_rows<T, VT, 1, SPLIT><<<gsz[1], ROWS_THREADS, 0, h->stream>>>(c, ncols, c.part,
-                                                                                kpb[1], pf);
-            k_reduce_cols<T><<<ncols, 256, 0, h->stream>>>(c.part, gsz[1], ncols, c.h2, c.ctl, 0,
-                                                           c.pv);
+        // pass B with the slice in registers; KC vectors per warp
+        const int kc = (ncols + PB_WARPS - 1) / PB_WARPS;
+        void (*kfn)(GridCtx<float, float>, int, float *, int64_t) =
+            kc <= 2 ? k_cgs_passb_reg<2>
+                    : kc <= 4 ? k_cgs_passb_reg<4>
+                              : kc <= 8 ? k_cgs_passb_reg<8>
+                                        : kc <= 12 ? k_cgs_passb_reg<12> : k_cgs_passb_reg<17>;
+        static std::map<const void *, int> pb_per_sm;
+        int &bps = pb_per_sm[(const void *)kfn];
+        if (bps == 0) {
+            CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kfn, PB_THREADS, 0));
+            bps = std::max(1, bps);
         }
+        const int64_t nsl_b = h->ldv / PB_ROWS;
+        const int64_t cap = (int64_t)h->nsm * bps;
+        const int64_t kb = (nsl_b + cap - 1) / cap;
+        const int gb = (int)((nsl_b + kb - 1) / kb);
+        kfn<<<gb, PB_THREADS, 0, h->stream>>>(c, ncols, c.part, kb);
+        k_reduce_cols<T><<<ncols, 256, 0, h->stream>>>(c.part, gb, ncols, c.h2, c.ctl, 0, c.pv);
     } else {
-        if constexpr (std::is_same<T, double>::value) {
-            if (c.pv & PV_ORTHO)  // the per-variable study's instantiation
-                k_cgs_rows<T, VT, 1, SPLIT, true><<<gsz[1], ROWS_THREADS, 0, h->stream>>>(
-                    c, ncols, c.part, kpb[1], pf);
-            else
-                k_cgs_rows<T, VT, 1, SPLIT><<<gsz[1], ROWS_THREADS, 0, h->stream>>>(
-                    c, ncols, c.part, kpb[1], pf);
-        } else {
+        if (pvs)
+            k_cgs_rows<T, VT, 1, SPLIT, true><<<gsz[1], ROWS_THREADS, 0, h->stream>>>(
+                c, ncols, c.part, kpb[1], pf);
+        else
             k_cgs_rows<T, VT, 1, SPLIT><<<gsz[1], ROWS_THREADS, 0, h->stream>>>(c, ncols, c.part,
                                                                                 kpb[1], pf);
-        }
         k_reduce_cols<T><<<ncols, 256, 0, h->stream>>>(c.part, gsz[1], ncols, c.h2, c.ctl, 0,
                                                        c.pv);
     }
-    if constexpr (std::is_same<T, double>::value) {
-        if (c.pv & PV_ORTHO)
-            k_cgs_rows<T, VT, 2, SPLIT, true><<<gsz[2], ROWS_THREADS, 0, h->stream>>>(
-                c, ncols, c.part, kpb[2], pf);
-        else
-            k_cgs_rows<T, VT, 2, SPLIT><<<gsz[2], ROWS_THREADS, 0, h->stream>>>(c, ncols, c.part,
-                                                                                kpb[2], pf);
-    } else {
+    if (pvs)
+        k_cgs_rows<T, VT, 2, SPLIT, true><<<gsz[2], ROWS_THREADS, 0, h->stream>>>(c, ncols, c.part,
+                                                                                  kpb[2], pf);
+    else
         k_cgs_rows<T, VT, 2, SPLIT><<<gsz[2], ROWS_THREADS, 0, h->stream>>>(c, ncols, c.part,
                                                                             kpb[2], pf);
-    }
     acct.launches[GMRES_K_ORTHO] += 5;
     CKL();
     h->timer.end(GMRES_K_ORTHO, e);
-    if (fused)
-        return GMRES_OK;  // the next step's SpMV forms v_{j+1}
     e = h->timer.begin();
     dim3 g(h->grid), b(kThreads);
     k_normalize<T, VT><<<g, b, 0, h->stream>>>(c, ncols, h->opts.orth_norm != GMRES_ORTH_OFF);
@@ -605,16 +567,7 @@ gmres_status enqueue_step_core(gmres_handle *h, GridCtx<T, VT> &c, int col, gmre
     const int L = lanes_for<T, VT>(h);
     const VT *vj = c.V + (size_t)col * c.ldv;
     cudaEvent_t e = h->timer.begin();
-    // the previous step's normalisation moves into this step's SpMV unless a
-    // preconditioner, the orthogonality test or the cooperative MGS kernel
-    // (which writes v_{j+1} itself) is in use
-    const bool coop_mgs = ortho == GMRES_ORTHO_MGS && h->opts.mgs_kernel != 1 &&
-                          mgs_persist_ok<T, VT>(h);
-    const bool fused = fused_normalize(h, c, coop_mgs);
-    if (fused && col > 0) {
-        CK((launch_spmv_norm<T, VT>(h, c, col, c.t, L)));
-        std::swap(c.w, c.t);
-    } else if (c.left) {
+    if (c.left) {
         // t = A v_j, w = M^-1 t (left preconditioning, Alg. 1); under the
         // per-variable w switch w, not t, is the stored Krylov vector
         CK((launch_spmv_step<T, VT, VT>(h, c, vj, c.t, L)));
@@ -656,41 +609,12 @@ gmres_status enqueue_step_core(gmres_handle *h, GridCtx<T, VT> &c, int col, gmre
     const int ncols = col + 1;
     dim3 g(h->grid), b(kThreads);
     e = h->timer.begin();
-    if (ortho == GMRES_ORTHO_CGSR && h->opts.cgs_kernel != 1) {
-        if (h->opts.cgs_kernel == 2)
-            return enqueue_cgs_rows<T, VT, false>(h, c, ncols, acct, e, fused);
-        return enqueue_cgs_rows<T, VT, true>(h, c, ncols, acct, e, fused);
-    }
     if (ortho == GMRES_ORTHO_CGSR) {
-        const int TR = cgs_choose_tr<VT>(ncols);
-        const size_t sm = cgs_smem_bytes<T, VT>(ncols, TR);
-        const long long spin = h->opts.spin_limit > 0 ? h->opts.spin_limit : (1LL << 26);
-        // dynamic shared memory may use the opt-in limit minus the kernel's
-        // static shared memory
-        static int dyn_max = 0;
-        if (dyn_max == 0) {
-            int optin = 0;
-            CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
-            void (*fns[3])(GridCtx<T, VT>, int, int, long long) = {
-                k_cgs_tile<T, VT, 0>, k_cgs_tile<T, VT, 1>, k_cgs_tile<T, VT, 2>};
-            int lim = optin;
-            for (auto fn : fns) {
-                cudaFuncAttributes fa;
-                CK(cudaFuncGetAttributes(&fa, fn));
-                lim = std::min(lim, optin - (int)fa.sharedSizeBytes);
-            }
-            for (auto fn : fns)
-                CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-            dyn_max = lim;
-        }
-        if ((int64_t)sm > dyn_max)
-            return GMRES_ERR_ARG;
-        dim3 gt(h->nsm);
-        k_cgs_tile<T, VT, 0><<<gt, CGS_THREADS, sm, h->stream>>>(c, ncols, TR, spin);
-        k_cgs_tile<T, VT, 1><<<gt, CGS_THREADS, sm, h->stream>>>(c, ncols, TR, spin);
-        k_cgs_tile<T, VT, 2><<<gt, CGS_THREADS, sm, h->stream>>>(c, ncols, TR, spin);
-        acct.launches[GMRES_K_ORTHO] += 3;
-    } else if (h->opts.mgs_kernel != 1 && mgs_persist_ok<T, VT>(h)) {
+        if (h->opts.cgs_kernel == 2)
+            return enqueue_cgs_rows<T, VT, false>(h, c, ncols, acct, e);
+        return enqueue_cgs_rows<T, VT, true>(h, c, ncols, acct, e);
+    }
+    if (h->opts.mgs_kernel != 1 && mgs_persist_ok<T, VT>(h)) {
         // one cooperative kernel: w stays in shared memory, v_{j+1} written;
         // by default with the block's basis rows staged in shared memory one
         // vector ahead (when they fit)
@@ -746,8 +670,6 @@ gmres_status enqueue_step_core(gmres_handle *h, GridCtx<T, VT> &c, int col, gmre
     }
     CKL();
     h->timer.end(GMRES_K_ORTHO, e);
-    if (fused)
-        return GMRES_OK;  // the next step's SpMV forms v_{j+1}
     e = h->timer.begin();
     k_normalize<T, VT><<<g, b, 0, h->stream>>>(c, col + 1, h->opts.orth_norm != GMRES_ORTH_OFF);
     CKL();
@@ -811,10 +733,6 @@ void account_cycle(gmres_handle *h, int j, gmres_ortho ortho, Acct &acct) {
     // row pointers, diagonal positions) plus its vectors and ready flags
     const double sL = (sizeof(T) == 8 && !h->limited && !h->opts.ilu_binary32) ? 8.0 : 4.0;
     const double ilu_bytes = nnz * (sL + 4) + 2.0 * (n + 1) * 4 + n * 4 + 4.0 * n * sT + 8.0 * n;
-    const bool coop = ortho == GMRES_ORTHO_MGS && h->opts.mgs_kernel != 1 &&
-                      mgs_persist_ok<T, VT>(h);
-    const bool fused = h->opts.normalize_fused && !pre && !ilu &&
-                       h->opts.orth_norm == GMRES_ORTH_OFF && !coop;
     for (int it = 0; it < j; ++it) {
         const double c = it + 1;
         acct.bytes[GMRES_K_SPMV] += nnz * (sA + 4) + (n + 1) * 4 + n * (pre ? sT : sV) + n * sT;
@@ -828,9 +746,7 @@ void account_cycle(gmres_handle *h, int j, gmres_ortho ortho, Acct &acct) {
             acct.bytes[GMRES_K_ORTHO] += c * n * sV + 2 * n * sT;
         if (h->opts.orth_norm != GMRES_ORTH_OFF)
             acct.bytes[GMRES_K_ORTHO] += (c + 1) * n * sV;  // u = V^T v_{j+1}
-        if (fused && it > 0)
-            acct.bytes[GMRES_K_SPMV] += n * sT;  // x read as w (sT, not sV) + v written (sV)
-        else if (!fused && it + 1 < j)
+        if (it + 1 < j)
             acct.bytes[GMRES_K_NORMALIZE] += n * sT + n * sV;
     }
     acct.bytes[GMRES_K_NORMALIZE] += n * sT + n * sV;  // v_1 = r / beta
@@ -1179,14 +1095,14 @@ gmres_status validate_opts(const gmres_opts *o) {
         (o->spmv_lanes != 0 && (o->spmv_lanes < 1 || o->spmv_lanes > 32 ||
                                 (o->spmv_lanes & (o->spmv_lanes - 1)))) ||
         o->cgs_kernel < 0 || o->cgs_kernel > 3 || o->mgs_kernel < 0 || o->mgs_kernel > 2 ||
-        o->l2_prefetch < 0 || o->l2_prefetch > 4 || !(o->stall_factor >= 0) ||
+        o->cgs_kernel == 1 || o->cgs_kernel == 3 || o->l2_prefetch < 0 || o->l2_prefetch > 4 ||
+        !(o->stall_factor >= 0) ||
         (o->block_cluster != 0 && o->block_cluster != 1 && o->block_cluster != TEAM_SINGLE_CTAS) ||
         o->stall_window < 0 || o->stall_window > MMAX || o->orth_norm < GMRES_ORTH_OFF ||
         o->orth_norm > GMRES_ORTH_FROBENIUS || o->orth_iters < 0 ||
         (o->orth_norm != GMRES_ORTH_OFF && !(o->orth_threshold > 0)) ||
         o->repeat_first < -1 || o->repeat_first > 1 || o->precond < 0 || o->precond > 2 ||
-        o->ilu_binary32 < 0 || o->ilu_binary32 > 1 || o->normalize_fused < 0 ||
-        o->normalize_fused > 1 || o->trsv_kernel < 0 || o->trsv_kernel > 3 ||
+        o->ilu_binary32 < 0 || o->ilu_binary32 > 1 || o->trsv_kernel < 0 || o->trsv_kernel > 3 ||
         o->pv_mask < 0 || o->pv_mask > (int32_t)PV_ALL)
         return GMRES_ERR_ARG;
     return GMRES_OK;
@@ -1214,7 +1130,6 @@ void gmres_default_opts(gmres_opts *o) {
     o->orth_norm = GMRES_ORTH_OFF;
     o->orth_threshold = 1.0;
     o->orth_iters = 10;
-    o->normalize_fused = 0;
     o->trsv_kernel = 0;
 }
 
@@ -1287,7 +1202,7 @@ gmres_status gmres_create(gmres_t *out, int32_t n, const int32_t *rowptr, const 
     gmres_default_opts(&h->opts);
     h->n = n;
     h->nnz = nnz;
-    h->ldv = round_up(n, CGS_TR_MAX);  // every CGSR tile height divides it
+    h->ldv = round_up(n, LDV_ALIGN);  // every row slice of the streaming kernels divides it
     h->stream = reinterpret_cast<cudaStream_t>(stream);
     h->timer.st = h->stream;
     auto fail = [&](gmres_status s) {
@@ -1485,7 +1400,7 @@ gmres_status gmres_solve(gmres_t h, const double *b, double *x, int32_t m, doubl
     }
     gmres_status st;
     if (h->opts.pv_mask != 0 &&
-        (prec != GMRES_FP64 || h->split || h->opts.cgs_kernel == 1 ||
+        (prec != GMRES_FP64 || h->split ||
          h->opts.path == GMRES_PATH_BLOCK)) {
         st = GMRES_ERR_ARG;  // the per-variable study: binary64 solves on the grid path
     } else switch (prec) {
@@ -1774,7 +1689,7 @@ gmres_status gmres_arnoldi(gmres_t h, const double *r0, int32_t m, int32_t kmax,
         prec > GMRES_MIXED_LIMITED)
         return GMRES_ERR_ARG;
     h->timer.on = false;
-    if (h->opts.pv_mask != 0 && (prec != GMRES_FP64 || h->split || h->opts.cgs_kernel == 1))
+    if (h->opts.pv_mask != 0 && (prec != GMRES_FP64 || h->split))
         return GMRES_ERR_ARG;
     switch (prec) {
     case GMRES_FP64:
@@ -1808,7 +1723,7 @@ gmres_status gmres_arnoldi_step(gmres_t h, const double *V, int32_t ncols, gmres
     if (!h || !V || !hcol || ncols < 1 || ncols > MMAX ||
         (ortho != GMRES_ORTHO_MGS && ortho != GMRES_ORTHO_CGSR) || prec < GMRES_FP64 ||
         prec > GMRES_MIXED_LIMITED || h->split || h->opts.precond != 0 ||
-        h->opts.normalize_fused || h->opts.pv_mask != 0)
+        h->opts.pv_mask != 0)
         return GMRES_ERR_ARG;
     h->timer.on = false;
     switch (prec) {

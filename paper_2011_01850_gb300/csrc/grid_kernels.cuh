@@ -19,6 +19,11 @@ namespace gmres {
 
 constexpr int PSTRIDE = MMAX + 8;  // partial-sum slots per block
 
+// Leading dimension of the basis and the work vectors: n rounded up to this,
+// a multiple of every row slice the streaming kernels take (512 or 1024 rows
+// in the CGSR passes, 128 in pass B), so none of them needs a tail check.
+constexpr int LDV_ALIGN = 2048;
+
 // Per-variable precision study (Sec. 4.1): a set bit stores that variable in
 // binary32 -- every value written to it is rounded -- while the binary64
 // solver's arithmetic is unchanged (GridCtx::pv, binary64 solves only).
@@ -200,24 +205,13 @@ struct ValHiLo {
 };
 
 // The vector a row gathers from: a stored vector of type XT (scaled for
-// binary16), or the next basis vector v = w / h formed on the fly from the
-// orthogonalised w, rounded through the basis format exactly as storing and
-// reloading it would.
+// binary16).
 template <class T, class XT>
 struct XPlain {
     const XT *x;
     float xinv;
     __device__ __forceinline__ T operator()(int col) const {
         return (T)Basis<XT>::ld(x + col, xinv);
-    }
-};
-template <class T, class VT>
-struct XNorm {
-    const T *w;
-    T h;
-    float scale, inv;
-    __device__ __forceinline__ T operator()(int col) const {
-        return (T)Basis<VT>::rt(w[col] / h, scale, inv);
     }
 };
 
@@ -320,34 +314,6 @@ __global__ void __launch_bounds__(256) k_spmv_step(GridCtx<T, VT> c, const XT *x
         T v = step_row<T, VT, XT, L>(c, x, row, gl);
         if (row < c.n && gl == 0)
             y[row] = v;
-    }
-}
-
-// The normalisation of the previous step fused into this step's SpMV:
-// v_col = w / h_{col,col-1} is written into the basis (rounded to its
-// format) by the owner of each row, and y = A v_col gathers the same
-// rounded values computed from w, so the result equals a separate
-// normalisation followed by the SpMV, without the extra pass over w and V.
-// y must not alias w (the host swaps the two work vectors afterwards).
-template <class T, class VT, int L>
-__global__ void __launch_bounds__(256) k_spmv_norm(GridCtx<T, VT> c, int col, T *y) {
-    if (!c.ctl->active)
-        return;
-    const T h = (T)c.ctl->hnext;
-    const XNorm<T, VT> xv{c.w, h, c.vscale, c.vinv};
-    VT *dst = c.V + (size_t)col * c.ldv;
-    const int G = 32 / L;
-    const int lane = threadIdx.x & 31;
-    const int gl = lane % L, gi = lane / L;
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t base = warp * G; base < c.n; base += nwarps * G) {
-        int row = (int)(base + gi);
-        T v = step_row_g<T, VT, XNorm<T, VT>, L>(c, xv, row, gl);
-        if (row < c.n && gl == 0) {
-            y[row] = v;
-            Basis<VT>::st(dst + row, c.w[row] / h, c.vscale);
-        }
     }
 }
 

@@ -322,6 +322,11 @@ __global__ void __launch_bounds__(MGSP_THREADS, 1)
         s_fail = 0;
     }
     __syncthreads();
+    // a bulk copy completes unless the GPU faults: its waits get their own
+    // generous bound, independent of `spin` (the bound of the exchange waits,
+    // which may be set low to force a timeout), so that a block never leaves
+    // while a copy of its own is still writing its shared memory
+    const long long climit = spin > (1LL << 22) ? spin : (1LL << 22);
     // basis column `col` into ring buffer col % 3 (thread 0)
     int issued = 0, waited = 0;  // columns issued / waited for (same in every thread)
     auto issue = [&](int col) {
@@ -337,7 +342,7 @@ __global__ void __launch_bounds__(MGSP_THREADS, 1)
     auto wait = [&](int col) -> bool {
         bool ok = true;
         if (len > 0)
-            ok = mbar_wait(&bars[col % 3], (uint32_t)((col / 3) & 1), spin);
+            ok = mbar_wait(&bars[col % 3], (uint32_t)((col / 3) & 1), climit);
         if (!ok)
             s_fail = 1;
         ++waited;
@@ -349,7 +354,7 @@ __global__ void __launch_bounds__(MGSP_THREADS, 1)
     auto drain = [&]() {
         for (int col = waited; col < issued; ++col)
             if (len > 0)
-                mbar_wait(&bars[col % 3], (uint32_t)((col / 3) & 1), spin);
+                mbar_wait(&bars[col % 3], (uint32_t)((col / 3) & 1), climit);
     };
     auto fail = [&]() {
         if (tid == 0)

@@ -65,7 +65,6 @@ class Opts(ctypes.Structure):
         ("orth_norm", ctypes.c_int32),
         ("orth_threshold", ctypes.c_double),
         ("orth_iters", ctypes.c_int32),
-        ("normalize_fused", ctypes.c_int32),
         ("trsv_kernel", ctypes.c_int32),
         ("pv_mask", ctypes.c_int32),
     ]

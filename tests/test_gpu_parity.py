@@ -468,15 +468,15 @@ def test_mgs_staged_equals_unstaged(prec, n, gpulib, stream):
 @pytest.mark.parametrize("prec", ["fp64", "mixed", "mixed_fp16"])
 def test_cgsr_kernel_families_agree(prec, gpulib, stream):
     """The CGSR kernel families (rows with the update split by basis vectors
-    and pass B's slice in registers, TMA-fed tiles, rows with the update
-    split by rows, rows with pass B re-reading from L2) sum in different
-    orders; binary64 takes the same schedule with solutions equal
-    to 1e-11, and every family reaches the binary64 target."""
+    and pass B's slice in registers; rows with the update split by rows) sum
+    in different orders; binary64 takes the same schedule with solutions
+    equal to 1e-11, and both reach the binary64 target.  The retired
+    families are rejected."""
     A = I.convdiff3d(26, eps=(0.1, 0.1, 0.1), seed=3)  # n = 17576: several slices per block
     b = I.rhs_ones_noise(A, 1e-3, 5)
     n = len(A[0]) - 1
     out = {}
-    for kern in (0, 1, 2, 3):
+    for kern in (0, 2):
         s = G.Solver(A, stream=stream)
         s.set_opts(path=G.PATH_GRID, cgs_kernel=kern)
         x, st, info = s.solve(b, np.zeros(n), m=40, ortho="cgsr", prec=prec)
@@ -484,8 +484,13 @@ def test_cgsr_kernel_families_agree(prec, gpulib, stream):
         assert st == G.OK
         assert O.residual_norm(A, b, x) / np.linalg.norm(b) <= 1e-10
         out[kern] = (x, info)
+    s = G.Solver(A, stream=stream)
+    for kern in (1, 3):
+        with pytest.raises(G.GmresError):
+            s.set_opts(cgs_kernel=kern)
+    s.close()
     if prec == "fp64":
-        for kern in (1, 2, 3):
+        for kern in (2,):
             assert out[kern][1]["iters"] == out[0][1]["iters"]
             assert out[kern][1]["restarts"] == out[0][1]["restarts"]
             assert np.linalg.norm(out[kern][0] - out[0][0]) / np.linalg.norm(out[0][0]) <= 1e-11
