@@ -46,7 +46,12 @@ __device__ __forceinline__ void fence_acq_rel_gpu() {
 }
 
 // One round of the grid-wide exchange that replaces "barrier, then sum the
-// per-block partials".  Every block owns 4 words per parity p in `slots`.
+// per-block partials".  It takes every thread's NV partials in v, sums them
+// over the block (warp butterflies, then warp 0 over the warp sums) and
+// exchanges the block sums; the round costs two block barriers.  `bad` is a
+// thread's own failure (a copy wait that gave up): if any thread of the block
+// has one, the block records a timeout in *err, publishes nothing and returns
+// false.  Every block owns 4 words per parity p in `slots`.
 // Thread 0 publishes the block's NV partials: for binary32 each word holds
 // (round << 32 | value bits), so one 64-bit store publishes a value together
 // with its round; for binary64 the values go first and a release store of
@@ -64,31 +69,53 @@ __device__ __forceinline__ void fence_acq_rel_gpu() {
 // *err.
 template <class T, int NV>
 __device__ __forceinline__ bool exchange_round(unsigned long long *slots, int p, unsigned round,
-                                               const T (&mine)[NV], T (&out)[NV], int *err,
-                                               long long limit, T *sbuf) {
+                                               T (&v)[NV], T (&out)[NV], int *err,
+                                               long long limit, T *sred, T *sbuf, bool bad) {
     constexpr bool F32 = sizeof(T) == 4;
     const int G = (int)gridDim.x;
-    if (threadIdx.x == 0) {
-        unsigned long long *my = slots + ((size_t)blockIdx.x * 2 + p) * 4;
-        if constexpr (F32) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
 #pragma unroll
-            for (int v = 0; v < NV; ++v)
-                st_relaxed_u64(my + v, ((unsigned long long)round << 32) |
-                                           (unsigned long long)__float_as_uint((float)mine[v]));
-        } else {
+    for (int k = 0; k < NV; ++k)
+        v[k] = warp_sum(v[k]);
+    if (lane == 0) {
 #pragma unroll
-            for (int v = 0; v < NV; ++v)
-                st_relaxed_u64(my + v, (unsigned long long)__double_as_longlong((double)mine[v]));
-            st_release_u64(my + 3, (unsigned long long)round);
-        }
+        for (int k = 0; k < NV; ++k)
+            sred[k * 32 + wid] = v[k];
+    }
+    if (__syncthreads_or(bad)) {
+        if (threadIdx.x == 0)
+            atomicExch(err, 1);
+        return false;
     }
     if (threadIdx.x < 32) {
-        const int lane = threadIdx.x;
+        T mine[NV];
+#pragma unroll
+        for (int k = 0; k < NV; ++k)
+            mine[k] = warp_sum(lane < nw ? sred[k * 32 + lane] : T(0));
+        if (lane == 0) {
+            unsigned long long *my = slots + ((size_t)blockIdx.x * 2 + p) * 4;
+            if constexpr (F32) {
+#pragma unroll
+                for (int k = 0; k < NV; ++k)
+                    st_relaxed_u64(my + k, ((unsigned long long)round << 32) |
+                                               (unsigned long long)__float_as_uint((float)mine[k]));
+            } else {
+#pragma unroll
+                for (int k = 0; k < NV; ++k)
+                    st_relaxed_u64(my + k,
+                                   (unsigned long long)__double_as_longlong((double)mine[k]));
+                st_release_u64(my + 3, (unsigned long long)round);
+            }
+        }
         unsigned long long w[MGSP_QMAX][NV];
         bool ok = true;
         long long it = 0;
         for (;;) {
             bool ready = true;
+            // the timeout word is loaded with the slots, not after them, so
+            // a poll costs one round trip to L2
+            const int e = *(volatile int *)err;
 #pragma unroll
             for (int q = 0; q < MGSP_QMAX; ++q) {
                 const int b = lane + 32 * q;
@@ -96,9 +123,9 @@ __device__ __forceinline__ bool exchange_round(unsigned long long *slots, int p,
                     const unsigned long long *ws = slots + ((size_t)b * 2 + p) * 4;
                     if constexpr (F32) {
 #pragma unroll
-                        for (int v = 0; v < NV; ++v) {
-                            w[q][v] = ld_relaxed_u64(ws + v);
-                            ready = ready && (unsigned)(w[q][v] >> 32) == round;
+                        for (int k = 0; k < NV; ++k) {
+                            w[q][k] = ld_relaxed_u64(ws + k);
+                            ready = ready && (unsigned)(w[q][k] >> 32) == round;
                         }
                     } else {
                         ready = ready && (unsigned)ld_relaxed_u64(ws + 3) == round;
@@ -107,7 +134,7 @@ __device__ __forceinline__ bool exchange_round(unsigned long long *slots, int p,
             }
             if (__all_sync(0xffffffffu, ready))
                 break;
-            if (*(volatile int *)err != 0 || ++it > limit) {
+            if (e != 0 || ++it > limit) {
                 ok = false;
                 break;
             }
@@ -115,8 +142,8 @@ __device__ __forceinline__ bool exchange_round(unsigned long long *slots, int p,
         ok = __all_sync(0xffffffffu, ok);
         T acc[NV];
 #pragma unroll
-        for (int v = 0; v < NV; ++v)
-            acc[v] = 0;
+        for (int k = 0; k < NV; ++k)
+            acc[k] = 0;
         if (ok) {
             if constexpr (!F32)
                 fence_acq_rel_gpu();
@@ -125,35 +152,33 @@ __device__ __forceinline__ bool exchange_round(unsigned long long *slots, int p,
                 const int b = lane + 32 * q;
                 if (b < G) {
 #pragma unroll
-                    for (int v = 0; v < NV; ++v) {
+                    for (int k = 0; k < NV; ++k) {
                         if constexpr (F32)
-                            acc[v] += (T)__uint_as_float((unsigned)(w[q][v] & 0xffffffffull));
+                            acc[k] += (T)__uint_as_float((unsigned)(w[q][k] & 0xffffffffull));
                         else
-                            acc[v] += (T)__longlong_as_double((long long)ld_relaxed_u64(
-                                slots + ((size_t)b * 2 + p) * 4 + v));
+                            acc[k] += (T)__longlong_as_double((long long)ld_relaxed_u64(
+                                slots + ((size_t)b * 2 + p) * 4 + k));
                     }
                 }
             }
         }
 #pragma unroll
-        for (int v = 0; v < NV; ++v)
-            acc[v] = warp_sum(acc[v]);
+        for (int k = 0; k < NV; ++k)
+            acc[k] = warp_sum(acc[k]);
         if (lane == 0) {
             if (!ok)
                 atomicExch(err, 1);
 #pragma unroll
-            for (int v = 0; v < NV; ++v)
-                sbuf[v] = acc[v];
+            for (int k = 0; k < NV; ++k)
+                sbuf[k] = acc[k];
             sbuf[NV] = ok ? T(1) : T(0);
         }
     }
     __syncthreads();
 #pragma unroll
-    for (int v = 0; v < NV; ++v)
-        out[v] = sbuf[v];
-    const bool ok = sbuf[NV] != T(0);
-    __syncthreads();
-    return ok;
+    for (int k = 0; k < NV; ++k)
+        out[k] = sbuf[k];
+    return sbuf[NV] != T(0);
 }
 
 // PVS: the per-variable study's instantiation (every updated entry of w under
@@ -199,9 +224,8 @@ __global__ void __launch_bounds__(MGSP_THREADS, 1)
                 acc[1] += ws[q + k] * ws[q + k];
             }
         }
-        block_sum<T, 2>(acc, sred);
         T tot[2];
-        if (!exchange_round<T, 2>(slots, 0, round0, acc, tot, err, spin, sx))
+        if (!exchange_round<T, 2>(slots, 0, round0, acc, tot, err, spin, sred, sx, false))
             return;
         hprev = PVS ? pv_round(tot[0], c.pv, PV_H) : tot[0];
         wn0sq = tot[1];
@@ -226,8 +250,9 @@ __global__ void __launch_bounds__(MGSP_THREADS, 1)
                 d += wv * b[k];
             }
         }
-        T dv[1] = {block_sum1(d, sred)}, hv[1];
-        if (!exchange_round<T, 1>(slots, i & 1, round0 + (unsigned)i, dv, hv, err, spin, sx))
+        T dv[1] = {d}, hv[1];
+        if (!exchange_round<T, 1>(slots, i & 1, round0 + (unsigned)i, dv, hv, err, spin, sred,
+                                  sx, false))
             return;
         hprev = PVS ? pv_round(hv[0], c.pv, PV_H) : hv[0];
         if (tid == 0)
@@ -250,9 +275,9 @@ __global__ void __launch_bounds__(MGSP_THREADS, 1)
                 nsq += wv * wv;
             }
         }
-        T nv[1] = {block_sum1(nsq, sred)}, tv[1];
+        T nv[1] = {nsq}, tv[1];
         if (!exchange_round<T, 1>(slots, ncols & 1, round0 + (unsigned)ncols, nv, tv, err,
-                                  spin, sx))
+                                  spin, sred, sx, false))
             return;
         hnext = wsqrt(tv[0]);
         if (PVS)
@@ -306,7 +331,6 @@ __global__ void __launch_bounds__(MGSP_THREADS, 1)
     __shared__ T sred[2 * 32];
     __shared__ T sx[3];
     __shared__ T hcol[MMAX + 2];
-    __shared__ int s_fail;
     const int tid = threadIdx.x, nth = blockDim.x;
     const int64_t rb = (int64_t)blockIdx.x * chunk;
     int64_t re = rb + chunk;
@@ -319,7 +343,6 @@ __global__ void __launch_bounds__(MGSP_THREADS, 1)
         for (int k = 0; k < 3; ++k)
             mbar_init(&bars[k], 1);
         mbar_init_fence();
-        s_fail = 0;
     }
     __syncthreads();
     // a bulk copy completes unless the GPU faults: its waits get their own
@@ -338,16 +361,15 @@ __global__ void __launch_bounds__(MGSP_THREADS, 1)
         }
         ++issued;
     };
-    // wait for column `col`; false (in every thread) on a timeout
+    // wait for column `col`; false in this thread on a timeout.  No barrier:
+    // a thread whose wait gave up still sweeps its (in-bounds) rows, and the
+    // block learns of it at the next exchange round, which then fails
     auto wait = [&](int col) -> bool {
         bool ok = true;
         if (len > 0)
             ok = mbar_wait(&bars[col % 3], (uint32_t)((col / 3) & 1), climit);
-        if (!ok)
-            s_fail = 1;
         ++waited;
-        __syncthreads();
-        return s_fail == 0;
+        return ok;
     };
     // on the way out: let every copy still in flight land (bounded) before
     // the block's shared memory is released
@@ -355,11 +377,6 @@ __global__ void __launch_bounds__(MGSP_THREADS, 1)
         for (int col = waited; col < issued; ++col)
             if (len > 0)
                 mbar_wait(&bars[col % 3], (uint32_t)((col / 3) & 1), climit);
-    };
-    auto fail = [&]() {
-        if (tid == 0)
-            atomicExch(err, 1);
-        drain();
     };
     auto vb = [&](int col) -> const VT * { return vbuf + (size_t)(col % 3) * chunk; };
 
@@ -373,10 +390,7 @@ __global__ void __launch_bounds__(MGSP_THREADS, 1)
         for (int k = 0; k < 4; ++k)
             ws[q + k] = v[k];
     }
-    if (!wait(0)) {
-        fail();
-        return;
-    }
+    const bool got0 = wait(0);
     // h_0 = w . v_0 and ||w||^2 (breakdown reference)
     T hprev, wn0sq;
     {
@@ -390,9 +404,8 @@ __global__ void __launch_bounds__(MGSP_THREADS, 1)
                 acc[1] += ws[q + k] * ws[q + k];
             }
         }
-        block_sum<T, 2>(acc, sred);
         T tot[2];
-        if (!exchange_round<T, 2>(slots, 0, round0, acc, tot, err, spin, sx)) {
+        if (!exchange_round<T, 2>(slots, 0, round0, acc, tot, err, spin, sred, sx, !got0)) {
             drain();
             return;
         }
@@ -404,10 +417,7 @@ __global__ void __launch_bounds__(MGSP_THREADS, 1)
     for (int i = 1; i < ncols; ++i) {
         if (i + 1 < ncols)
             issue(i + 1);  // its buffer last held v_{i-2}, read before round i-1 ended
-        if (!wait(i)) {
-            fail();
-            return;
-        }
+        const bool got = wait(i);
         const VT *vp = vb(i - 1);
         const VT *vi = vb(i);
         T d = 0;
@@ -424,8 +434,9 @@ __global__ void __launch_bounds__(MGSP_THREADS, 1)
                 d += wv * b[k];
             }
         }
-        T dv[1] = {block_sum1(d, sred)}, hv[1];
-        if (!exchange_round<T, 1>(slots, i & 1, round0 + (unsigned)i, dv, hv, err, spin, sx)) {
+        T dv[1] = {d}, hv[1];
+        if (!exchange_round<T, 1>(slots, i & 1, round0 + (unsigned)i, dv, hv, err, spin, sred,
+                                  sx, !got)) {
             drain();
             return;
         }
@@ -450,9 +461,9 @@ __global__ void __launch_bounds__(MGSP_THREADS, 1)
                 nsq += wv * wv;
             }
         }
-        T nv[1] = {block_sum1(nsq, sred)}, tv[1];
+        T nv[1] = {nsq}, tv[1];
         if (!exchange_round<T, 1>(slots, ncols & 1, round0 + (unsigned)ncols, nv, tv, err,
-                                  spin, sx))
+                                  spin, sred, sx, false))
             return;
         hnext = wsqrt(tv[0]);
         if (PVS)
