@@ -371,7 +371,8 @@ def bench_ours(args):
     kernel_names = {"ortho": ("CGSR passes (k_cgs_rows x2 + k_cgs_passb_reg + "
                               "k_reduce_cols x2)" if prec == "mixed"
                               else "CGSR passes (k_cgs_rows x3 + k_reduce_cols x2)")
-                    if ortho == "cgsr" else "MGS step (k_mgs_persist, cooperative)",
+                    if ortho == "cgsr" else ("MGS step (cooperative: k_mgs_staged where its "
+                                             "shared-memory ring fits, else k_mgs_persist)"),
                     "block": "single-block solver (k_block_solve)",
                     "spmv": "SpMV (k_spmv_step)", "residual": "binary64 residual (k_residual)"}
     out = {
