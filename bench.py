@@ -69,6 +69,8 @@ def parse():
                    help="batched workload: orthogonalisation of the timed solves")
     p.add_argument("--spmv-lanes", type=int, default=0,
                    help="lanes per CSR row (0: autotuned)")
+    p.add_argument("--spmv-format", choices=["auto", "csr", "sliced"], default="auto",
+                   help="storage of A for the Krylov step's product (auto: the autotuner's)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     return p.parse_args()
@@ -219,6 +221,9 @@ def bench_ours(args):
         solver.set_opts(spmv_lanes=args.spmv_lanes)
     else:
         lanes32, lanes64 = G.gmres_autotune(solver.h)
+    if args.spmv_format != "auto":
+        solver.set_opts(spmv_format={"csr": G.SPMV_CSR, "sliced": G.SPMV_SLICED}[args.spmv_format])
+    fmt32, fmt64 = G.gmres_spmv_format(solver.h)
     solver.set_opts(profile=1, cgs_kernel=args.cgs_kernel)
     if args.l2_prefetch is not None:
         solver.set_opts(l2_prefetch=args.l2_prefetch)
@@ -374,7 +379,11 @@ def bench_ours(args):
                     if ortho == "cgsr" else ("MGS step (cooperative: k_mgs_staged where its "
                                              "shared-memory ring fits, else k_mgs_persist)"),
                     "block": "single-block solver (k_block_solve)",
-                    "spmv": "SpMV (k_spmv_step)", "residual": "binary64 residual (k_residual)"}
+                    "spmv": ("SpMV (k_spmv_step_sell, sliced storage)"
+                             if prec != "mixed_limited"
+                             and (fmt64 if prec == "fp64" else fmt32) == G.SPMV_SLICED
+                             else "SpMV (k_spmv_step)"),
+                    "residual": "binary64 residual (k_residual)"}
     out = {
         "metric": "time-to-1e-10 residual and HBM GB/s: mixed vs FP64 GMRES(m), one GB300",
         "value": round(ms_step, 3),
@@ -400,6 +409,8 @@ def bench_ours(args):
                   else "inputs L2-resident (no flush; small-system workload)",
             "parallelism": "replicas" if world > 1 else "single GPU",
             "spmv_lanes": {"f32": lanes32, "f64": lanes64},
+            "spmv_format": {"f32": "sliced" if fmt32 == G.SPMV_SLICED else "csr",
+                            "f64": "sliced" if fmt64 == G.SPMV_SLICED else "csr"},
             "cgs_kernel": {0: "register-streaming rows, pass B slice in registers",
                            2: "register-streaming rows, per-row-group update"}[args.cgs_kernel],
             "l2_prefetch": int(G.gmres_get_opts(solver.h).l2_prefetch),

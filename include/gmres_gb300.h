@@ -193,7 +193,23 @@ typedef struct gmres_opts {
                              precision study; GMRES_FP64 on the grid path only
                              (not with split storage), else gmres_solve
                              returns GMRES_ERR_ARG                            */
+    int32_t spmv_format;  /* storage of A for w = A v_j on the grid path and
+                             for gmres_spmv: GMRES_SPMV_AUTO (default: the
+                             format gmres_autotune chose per precision, CSR
+                             before it runs), GMRES_SPMV_CSR, or
+                             GMRES_SPMV_SLICED (slices of 32 rows stored
+                             column-major, built when these options are set;
+                             gmres_set_opts returns GMRES_ERR_ARG with split
+                             storage or a row longer than 65535 entries).  The
+                             sliced product sums each row exactly as CSR at
+                             one lane per row; the limited, split and
+                             binary32-A per-variable forms read CSR         */
 } gmres_opts;
+
+/* Values of gmres_opts.spmv_format. */
+#define GMRES_SPMV_AUTO 0
+#define GMRES_SPMV_CSR 1
+#define GMRES_SPMV_SLICED 2
 
 /* Kernel classes reported in gmres_info (index into kernel_ms / kernel_bytes). */
 enum {
@@ -267,7 +283,8 @@ gmres_status gmres_solve(gmres_t h, const double *b, double *x, int32_t m, doubl
                          gmres_info *info);
 
 /* y = A x with the precision's copy of A (Alg. 1, "w <- A v_j"): for
- * GMRES_FP64 x and y are binary64 device vectors, otherwise binary32. */
+ * GMRES_FP64 x and y are binary64 device vectors, otherwise binary32.  A is
+ * read in the storage gmres_spmv_format reports for the precision. */
 gmres_status gmres_spmv(gmres_t h, const void *x, void *y, gmres_precision prec);
 
 /* z = b - A x in binary64 (Alg. 1, first step of every restart) with
@@ -310,10 +327,19 @@ gmres_status gmres_arnoldi(gmres_t h, const double *r0, int32_t m, int32_t kmax,
 gmres_status gmres_arnoldi_step(gmres_t h, const double *V, int32_t ncols, gmres_ortho ortho,
                                 gmres_precision prec, double *hcol, double *vnext);
 
-/* Time every SpMV variant (lanes per row 1..32) on this matrix in binary32
- * and binary64 and keep the fastest for later solves (the tile autotuner).
- * lanes32 / lanes64 (may be NULL) receive the choices. */
+/* Time every SpMV variant (lanes per CSR row 1..32, and the sliced storage
+ * of A where it can be built) on this matrix in binary32 and binary64 and keep
+ * the fastest for later solves (the tile autotuner).  lanes32 / lanes64 (may
+ * be NULL) receive the CSR choices; gmres_spmv_format reports the storage.
+ * The sliced copy is kept only when it won in one of the precisions.
+ * Synchronizes the handle's stream. */
 gmres_status gmres_autotune(gmres_t h, int32_t *lanes32, int32_t *lanes64);
+
+/* Storage of A the grid path's w = A v_j and gmres_spmv read under the current
+ * options, per precision: GMRES_SPMV_CSR or GMRES_SPMV_SLICED (for the
+ * mixed precisions fmt32, for GMRES_FP64 fmt64; either may be NULL).  The
+ * limited and split forms always read CSR. */
+gmres_status gmres_spmv_format(gmres_t h, int32_t *fmt32, int32_t *fmt64);
 
 /* ---------------------------------------------------------------------------
  * Learned sparse-approximate-inverse right preconditioner (the paper has no
@@ -462,9 +488,10 @@ gmres_status gmres_solve_noalloc(int32_t n, const int32_t *rowptr, const int32_t
                                  int32_t maxiter, void *stream, gmres_info *info);
 
 /* Device bytes the handle holds for the matrix (both value copies, shared
- * indices) and, for a solve with restart length m in precision prec, the
- * workspace (basis, vectors, Hessenberg).  Matches the paper's storage model
- * (Sec. 4) without the ILU factors. */
+ * indices, and the sliced copy of A when one is built) and, for a solve with
+ * restart length m in precision prec, the workspace (basis, vectors,
+ * Hessenberg).  Matches the paper's storage model (Sec. 4) without the ILU
+ * factors. */
 gmres_status gmres_memory_bytes(gmres_t h, int32_t m, gmres_precision prec, int64_t *matrix_bytes,
                                 int64_t *workspace_bytes);
 

@@ -28,6 +28,7 @@
 #include "ilu.hpp"
 #include "handle.hpp"
 #include "host_util.hpp"
+#include "sell.hpp"
 
 using namespace gmres;
 using namespace gmres_host;
@@ -176,6 +177,22 @@ gmres_status ensure_workspace(gmres_handle *h, int m, gmres_precision prec) {
     return GMRES_OK;
 }
 
+// Storage the product with A reads: 1 / 2 = the sliced copy (16-bit / 32-bit
+// columns), 0 = CSR.  `step`: for the Krylov step of a running solve, where
+// the limited form and the per-variable binary32 A read CSR.
+template <class T>
+int sell_fmt_for(const gmres_handle *h, bool step) {
+    if (!h->sell_fmt || h->split || h->opts.spmv_format == GMRES_SPMV_CSR)
+        return 0;
+    if (h->opts.spmv_format == GMRES_SPMV_AUTO &&
+        !(std::is_same<T, double>::value ? h->sell64 : h->sell32))
+        return 0;
+    if (step && (h->limited || (std::is_same<T, double>::value &&
+                                (h->opts.pv_mask & GMRES_PV_A_KRYLOV))))
+        return 0;
+    return h->sell_fmt;
+}
+
 template <class T, class VT>
 GridCtx<T, VT> make_ctx(gmres_handle *h, int m) {
     GridCtx<T, VT> c;
@@ -241,6 +258,14 @@ GridCtx<T, VT> make_ctx(gmres_handle *h, int m) {
         if (h->limited || (c.pv & PV_M))
             c.pvals_lim = h->pvals32.as<float>();
     }
+    c.sfmt = c.aform == 0 ? sell_fmt_for<T>(h, true) : 0;
+    if (c.sfmt) {
+        c.sptr = h->sptr.as<int>();
+        c.slen = h->slen.as<unsigned short>();
+        c.scol = h->scol.p;
+        c.sval = std::is_same<T, double>::value ? reinterpret_cast<const T *>(h->sval64.p)
+                                                : reinterpret_cast<const T *>(h->sval32.p);
+    }
     return c;
 }
 
@@ -263,6 +288,14 @@ GridCtx<T, VT> stream_ctx(const gmres_handle *h, const GridCtx<T, VT> &c, int *g
 template <class T, class VT, class XT>
 cudaError_t launch_spmv_step(gmres_handle *h, const GridCtx<T, VT> &c, const XT *x, T *y, int L) {
     dim3 g(spmv_grid(h)), b(kThreads);
+    if (c.sfmt == 1) {
+        k_spmv_step_sell<T, VT, XT, SellCol16><<<g, b, 0, h->stream>>>(c, x, y);
+        return cudaGetLastError();
+    }
+    if (c.sfmt == 2) {
+        k_spmv_step_sell<T, VT, XT, SellCol32><<<g, b, 0, h->stream>>>(c, x, y);
+        return cudaGetLastError();
+    }
     switch (L) {
     case 1: k_spmv_step<T, VT, XT, 1><<<g, b, 0, h->stream>>>(c, x, y); break;
     case 2: k_spmv_step<T, VT, XT, 2><<<g, b, 0, h->stream>>>(c, x, y); break;
@@ -591,6 +624,7 @@ gmres_status enqueue_step_core(gmres_handle *h, GridCtx<T, VT> &c, int col, gmre
         cp.a = c.pvals;
         cp.a_lim = c.pvals_lim;
         cp.aform = c.pvals_lim ? 1 : 0;
+        cp.sfmt = 0;  // M is on CSR
         CK((launch_spmv_step<T, VT, VT>(h, cp, vj, c.t, L)));
         acct.launches[GMRES_K_PRECOND]++;
         h->timer.end(GMRES_K_PRECOND, e);
@@ -733,9 +767,15 @@ void account_cycle(gmres_handle *h, int j, gmres_ortho ortho, Acct &acct) {
     // row pointers, diagonal positions) plus its vectors and ready flags
     const double sL = (sizeof(T) == 8 && !h->limited && !h->opts.ilu_binary32) ? 8.0 : 4.0;
     const double ilu_bytes = nnz * (sL + 4) + 2.0 * (n + 1) * 4 + n * 4 + 4.0 * n * sT + 8.0 * n;
+    // A's bytes per product: CSR values, column indices and row pointers, or
+    // the sliced copy's values, indices, row lengths and slice offsets
+    const int sf = sell_fmt_for<T>(h, true);
+    const double nsl = (double)((h->n + SELL_C - 1) / SELL_C);
+    const double a_bytes = sf ? nnz * (sA + (sf == 1 ? 2 : 4)) + nsl * SELL_C * 2 + (nsl + 1) * 4
+                              : nnz * (sA + 4) + (n + 1) * 4;
     for (int it = 0; it < j; ++it) {
         const double c = it + 1;
-        acct.bytes[GMRES_K_SPMV] += nnz * (sA + 4) + (n + 1) * 4 + n * (pre ? sT : sV) + n * sT;
+        acct.bytes[GMRES_K_SPMV] += a_bytes + n * (pre ? sT : sV) + n * sT;
         if (pre)
             acct.bytes[GMRES_K_PRECOND] += nnz * (sA + 4) + (n + 1) * 4 + n * sV + n * sT;
         if (ilu)
@@ -1103,7 +1143,8 @@ gmres_status validate_opts(const gmres_opts *o) {
         (o->orth_norm != GMRES_ORTH_OFF && !(o->orth_threshold > 0)) ||
         o->repeat_first < -1 || o->repeat_first > 1 || o->precond < 0 || o->precond > 2 ||
         o->ilu_binary32 < 0 || o->ilu_binary32 > 1 || o->trsv_kernel < 0 || o->trsv_kernel > 3 ||
-        o->pv_mask < 0 || o->pv_mask > (int32_t)PV_ALL)
+        o->pv_mask < 0 || o->pv_mask > (int32_t)PV_ALL || o->spmv_format < GMRES_SPMV_AUTO ||
+        o->spmv_format > GMRES_SPMV_SLICED)
         return GMRES_ERR_ARG;
     return GMRES_OK;
 }
@@ -1295,7 +1336,8 @@ void gmres_destroy(gmres_t h) {
                       &h->pvals32, &h->spai_feat, &h->spai_rowv, &h->tvals32, &h->spai_params,
                       &h->spai_m, &h->spai_gm, &h->spai_H, &h->spai_vec, &h->spai_part,
                       &h->spai_Z, &h->spai_grad, &h->mgs_seq, &h->mon, &h->ilu64, &h->ilu32,
-                      &h->ilu_dpos, &h->ilu_flags, &h->t2, &h->ilu_order})
+                      &h->ilu_dpos, &h->ilu_flags, &h->t2, &h->ilu_order, &h->ilu_lptr,
+                      &h->sptr, &h->slen, &h->scol, &h->sval32, &h->sval64})
         b->release();
     if (h->hctl)
         cudaFreeHost(h->hctl);
@@ -1339,7 +1381,7 @@ gmres_status gmres_set_values(gmres_t h, const double *vals) {
     h->spai_feat_ok = 0;
     h->has_precond = 0;
     h->ilu_ok = 0;
-    return GMRES_OK;
+    return sell_refill(h);  // the sliced copy takes the new values
 }
 
 gmres_status gmres_set_stream(gmres_t h, void *stream) {
@@ -1356,7 +1398,22 @@ gmres_status gmres_set_opts(gmres_t h, const gmres_opts *o) {
     gmres_status st = validate_opts(o);
     if (st != GMRES_OK)
         return st;
+    if (o->spmv_format == GMRES_SPMV_SLICED) {
+        st = sell_build(h);  // the sliced copy must exist before a solve reads it
+        if (st != GMRES_OK)
+            return st;
+    }
     h->opts = *o;
+    return GMRES_OK;
+}
+
+gmres_status gmres_spmv_format(gmres_t h, int32_t *fmt32, int32_t *fmt64) {
+    if (!h)
+        return GMRES_ERR_ARG;
+    if (fmt32)
+        *fmt32 = sell_fmt_for<float>(h, false) ? GMRES_SPMV_SLICED : GMRES_SPMV_CSR;
+    if (fmt64)
+        *fmt64 = sell_fmt_for<double>(h, false) ? GMRES_SPMV_SLICED : GMRES_SPMV_CSR;
     return GMRES_OK;
 }
 
@@ -1442,7 +1499,11 @@ gmres_status gmres_solve(gmres_t h, const double *b, double *x, int32_t m, doubl
 gmres_status gmres_spmv(gmres_t h, const void *x, void *y, gmres_precision prec) {
     if (!h || !x || !y || prec < GMRES_FP64 || prec > GMRES_MIXED_FP16)
         return GMRES_ERR_ARG;
-    if (prec == GMRES_FP64)
+    if (prec == GMRES_FP64 && sell_fmt_for<double>(h, false))
+        CK(sell_spmv_plain<double>(h, (const double *)x, (double *)y));
+    else if (prec != GMRES_FP64 && sell_fmt_for<float>(h, false))
+        CK(sell_spmv_plain<float>(h, (const float *)x, (float *)y));
+    else if (prec == GMRES_FP64)
         CK(launch_spmv_any<double>(h, h->opts.spmv_lanes ? h->opts.spmv_lanes : h->lanes64,
                                    (const double *)x, (double *)y));
     else
@@ -1789,6 +1850,42 @@ gmres_status gmres_autotune(gmres_t h, int32_t *lanes32, int32_t *lanes64) {
             }
         }
     }
+    // the sliced copy of A, where it can be built: kept when it beats the
+    // best CSR variant in either precision
+    bool s32 = false, s64 = false;
+    const bool had = h->sell_fmt != 0;
+    if (!h->split && sell_build(h) == GMRES_OK) {
+        for (int prec = 0; prec < 2; ++prec) {
+            for (int rep = 0; rep < 2; ++rep) {  // warm-up
+                if (prec)
+                    CK(sell_spmv_plain<float>(h, x32, y32));
+                else
+                    CK(sell_spmv_plain<double>(h, x64, y64));
+            }
+            CK(cudaEventRecord(a, h->stream));
+            const int reps = 5;
+            for (int rep = 0; rep < reps; ++rep) {
+                if (prec)
+                    CK(sell_spmv_plain<float>(h, x32, y32));
+                else
+                    CK(sell_spmv_plain<double>(h, x64, y64));
+            }
+            CK(cudaEventRecord(b, h->stream));
+            CK(cudaEventSynchronize(b));
+            float ms = 0;
+            CK(cudaEventElapsedTime(&ms, a, b));
+            if (prec)
+                s32 = ms < best32;
+            else
+                s64 = ms < best64;
+        }
+        // an explicitly requested copy stays; an unused one is released
+        if (!s32 && !s64 && !(had && h->opts.spmv_format == GMRES_SPMV_SLICED))
+            sell_free(h);
+    }
+    cudaGetLastError();  // a copy that did not fit is not an error here
+    h->sell32 = s32;
+    h->sell64 = s64;
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     h->lanes32 = L32;
@@ -1807,7 +1904,8 @@ gmres_status gmres_memory_bytes(gmres_t h, int32_t m, gmres_precision prec, int6
     const int64_t n = h->n, nnz = h->nnz;
     // indices shared by both copies; binary64 + binary32 values (Sec. 4)
     if (matrix_bytes)
-        *matrix_bytes = 4 * (n + 1) + 4 * nnz + 8 * nnz + (h->split ? 0 : 4 * nnz);
+        *matrix_bytes =
+            4 * (n + 1) + 4 * nnz + 8 * nnz + (h->split ? 0 : 4 * nnz) + sell_bytes(h);
     if (workspace_bytes) {
         const int64_t sT = (prec == GMRES_FP64 || prec == GMRES_MIXED_LIMITED) ? 8 : 4;
         *workspace_bytes = h->ldv * (m + 1) * elem_bytes(prec)  // basis

@@ -14,6 +14,7 @@
 #include <type_traits>
 
 #include "common.cuh"
+#include "sell.cuh"
 
 namespace gmres {
 
@@ -89,6 +90,13 @@ struct GridCtx {
     // the residual under PV_A_RESID
     unsigned pv;
     const float *a_res32;
+    // A in sliced storage (sell.cuh) for the Krylov step, read when sfmt is
+    // 1 (16-bit column offsets) or 2 (32-bit columns); 0 = the CSR arrays
+    int sfmt;
+    const int *sptr;
+    const unsigned short *slen;
+    const void *scol;
+    const T *sval;
 };
 
 // 4 consecutive basis entries starting at p (16-byte aligned for fp32 /
@@ -313,6 +321,26 @@ __global__ void __launch_bounds__(256) k_spmv_step(GridCtx<T, VT> c, const XT *x
         int row = (int)(base + gi);
         T v = step_row<T, VT, XT, L>(c, x, row, gl);
         if (row < c.n && gl == 0)
+            y[row] = v;
+    }
+}
+
+// The same product with A in sliced storage: one warp per slice of 32 rows,
+// the rows' sums bit for bit those of k_spmv_step at one lane per row.
+template <class T, class VT, class XT, class CV>
+__global__ void __launch_bounds__(256) k_spmv_step_sell(GridCtx<T, VT> c, const XT *x, T *y) {
+    if (!c.ctl->active)
+        return;
+    const int lane = threadIdx.x & 31;
+    const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
+    const int nsl = (c.n + SELL_C - 1) / SELL_C;
+    const CV col = sell_cols<CV>(c.scol);
+    for (int s = warp; s < nsl; s += nwarps) {
+        const int row = s * SELL_C + lane;
+        const T v = sell_row<T>(c.sptr, c.slen, col, ValPlain<T>{c.sval}, XPlain<T, XT>{x, c.vinv},
+                                s, lane, row, c.n);
+        if (row < c.n)
             y[row] = v;
     }
 }

@@ -104,6 +104,13 @@ struct gmres_handle {
     int64_t chunk = 0;     // rows per block
     // matrix
     DevBuf rowptr, colind, vals64, vals32;
+    // A in sliced storage (sell.cuh): slice offsets, row lengths, columns
+    // (16-bit offsets from the row or 32-bit), binary32 and binary64 values;
+    // built by gmres_autotune or on request (gmres_opts.spmv_format)
+    DevBuf sptr, slen, scol, sval32, sval64;
+    int sell_fmt = 0;             // 0: not built, 1: 16-bit offsets, 2: 32-bit columns
+    int64_t sell_entries = 0;     // entries stored, padding included
+    bool sell32 = false, sell64 = false;  // the autotuner chose it (binary32 / binary64)
     DevBuf trowptr, tcolind, tvals64;  // A^T (optional)
     // workspace
     DevBuf V, w, r, t, z, xb, bb;

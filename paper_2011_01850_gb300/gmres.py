@@ -29,6 +29,8 @@ ORTH_OFF, ORTH_SPECTRAL, ORTH_FROBENIUS = 0, 1, 2
 # per-variable precision switches (gmres_opts.pv_mask)
 PV_A_KRYLOV, PV_M, PV_V, PV_W, PV_H, PV_GIVENS, PV_Z = 1, 2, 4, 8, 16, 32, 64
 PV_A_RESID, PV_B, PV_X, PV_AX = 128, 256, 512, 1024
+# storage of A for the Krylov step's product (gmres_opts.spmv_format)
+SPMV_AUTO, SPMV_CSR, SPMV_SLICED = 0, 1, 2
 K_RESIDUAL, K_SPMV, K_ORTHO, K_NORMALIZE, K_UPDATE, K_PRECOND, K_BLOCK = range(7)
 K_COUNT = 8
 KERNEL_CLASS_NAMES = ["residual", "spmv", "ortho", "normalize", "update", "precond", "block"]
@@ -67,6 +69,7 @@ class Opts(ctypes.Structure):
         ("orth_iters", ctypes.c_int32),
         ("trsv_kernel", ctypes.c_int32),
         ("pv_mask", ctypes.c_int32),
+        ("spmv_format", ctypes.c_int32),
     ]
 
 
@@ -118,6 +121,7 @@ SIGNATURES = {
                       + [ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
     "gmres_arnoldi_step": (_st, [_vp, _vp, _i32, _i32, _i32, _vp, _vp]),
     "gmres_autotune": (_st, [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
+    "gmres_spmv_format": (_st, [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
     "gmres_memory_bytes": (_st, [_vp, _i32, _i32, ctypes.POINTER(ctypes.c_int64),
                                  ctypes.POINTER(ctypes.c_int64)]),
     "gmres_orth_norms": (_st, [_vp, _vp, _i32]),
@@ -301,6 +305,15 @@ def gmres_autotune(h):
     a = ctypes.c_int32()
     b = ctypes.c_int32()
     _check(lib().gmres_autotune(h, ctypes.byref(a), ctypes.byref(b)), "gmres_autotune")
+    return a.value, b.value
+
+
+def gmres_spmv_format(h):
+    """(binary32, binary64) storage of A the product reads: SPMV_CSR or
+    SPMV_SLICED."""
+    a = ctypes.c_int32()
+    b = ctypes.c_int32()
+    _check(lib().gmres_spmv_format(h, ctypes.byref(a), ctypes.byref(b)), "gmres_spmv_format")
     return a.value, b.value
 
 
