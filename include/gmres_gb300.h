@@ -69,7 +69,10 @@ typedef enum {
     GMRES_ERR_NONFINITE = -3, /* NaN or Inf in an input or produced by a step  */
     GMRES_ERR_BREAKDOWN = -4, /* no progress possible (singular projected LS)  */
     GMRES_ERR_TIMEOUT = -5,   /* a bounded device wait ran out                 */
-    GMRES_ERR_OOM = -6        /* device allocation failed                      */
+    GMRES_ERR_OOM = -6,       /* device allocation failed                      */
+    GMRES_ERR_INDEX = -7      /* checked build only: a column index outside its
+                                 system reached a kernel (see
+                                 gmres_checks_enabled)                         */
 } gmres_status;
 
 /* gmres_create flags. */
@@ -334,6 +337,23 @@ gmres_status gmres_arnoldi_step(gmres_t h, const double *V, int32_t ncols, gmres
  * The sliced copy is kept only when it won in one of the precisions.
  * Synchronizes the handle's stream. */
 gmres_status gmres_autotune(gmres_t h, int32_t *lanes32, int32_t *lanes64);
+
+/* 1 when this library is the checked build (compiled with -DGMRES_CHECKS, the
+ * library's stand-in for a memory sanitizer), else 0.  In the checked build
+ * every kernel that gathers x through a column index (the CSR and sliced
+ * products, the binary64 residuals, the block and batched solvers) first
+ * tests the index against its system's columns; an index outside is counted
+ * in a device word and replaced by column 0, so the load stays inside x.
+ * gmres_solve, gmres_spmv, gmres_batch_solve and gmres_solve_noalloc then
+ * return GMRES_ERR_INDEX (their other outputs are meaningless).  Matrices
+ * that pass through gmres_create or gmres_batch_create are validated on the
+ * host and never trigger it; gmres_solve_noalloc checks only rowptr's ends,
+ * so it is the entry point the checked build guards.  Row pointers, ILU(0)
+ * factors and the learned preconditioner's kernels are not checked.  The
+ * checked build is the same source with the flag
+ * (paper_2011_01850_gb300.build.build(checked=True)); it costs one compare
+ * per gathered entry. */
+int32_t gmres_checks_enabled(void);
 
 /* Storage of A the grid path's w = A v_j and gmres_spmv read under the current
  * options, per precision: GMRES_SPMV_CSR or GMRES_SPMV_SLICED (for the

@@ -21,6 +21,10 @@ INCLUDE = os.path.join(ROOT, "include")
 LIB_NAME = "libgmres_gb300.so"
 LIB_PATH = os.path.join(HERE, LIB_NAME)
 BUILD_DIR = os.path.join(ROOT, "_build")
+# the checked build: the same sources with -DGMRES_CHECKS (column indices
+# tested in every gather kernel; include/gmres_gb300.h, gmres_checks_enabled)
+LIB_CHECKED_PATH = os.path.join(HERE, "libgmres_gb300_checked.so")
+BUILD_DIR_CHECKED = os.path.join(ROOT, "_build", "checked")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC",
@@ -44,23 +48,29 @@ def _deps():
     return files
 
 
-def stale() -> bool:
-    if not os.path.exists(LIB_PATH):
+def stale(checked: bool = False) -> bool:
+    path = LIB_CHECKED_PATH if checked else LIB_PATH
+    if not os.path.exists(path):
         return True
-    t = os.path.getmtime(LIB_PATH)
+    t = os.path.getmtime(path)
     return any(os.path.getmtime(f) > t for f in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, extra=()) -> str:
-    """Compile every .cu under csrc/ and link libgmres_gb300.so (if stale)."""
-    if not force and not stale():
-        return LIB_PATH
-    os.makedirs(BUILD_DIR, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra=(), checked: bool = False) -> str:
+    """Compile every .cu under csrc/ and link libgmres_gb300.so (if stale);
+    with checked=True the checked build libgmres_gb300_checked.so instead."""
+    lib_path = LIB_CHECKED_PATH if checked else LIB_PATH
+    build_dir = BUILD_DIR_CHECKED if checked else BUILD_DIR
+    if checked:
+        extra = (*extra, "-DGMRES_CHECKS")
+    if not force and not stale(checked):
+        return lib_path
+    os.makedirs(build_dir, exist_ok=True)
     nv = nvcc()
     units = _units()
 
     def compile_one(src):
-        obj = os.path.join(BUILD_DIR, os.path.basename(src) + ".o")
+        obj = os.path.join(build_dir, os.path.basename(src) + ".o")
         cmd = [nv, *ARCH, *NVCC_FLAGS, *extra, "-I", INCLUDE, "-c", src, "-o", obj]
         if verbose:
             print(" ".join(cmd), flush=True)
@@ -73,14 +83,24 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
 
     with cf.ThreadPoolExecutor(max_workers=max(1, min(len(units), os.cpu_count() or 4))) as ex:
         objs = list(ex.map(compile_one, units))
-    tmp = LIB_PATH + ".tmp%d" % os.getpid()
+    tmp = lib_path + ".tmp%d" % os.getpid()
     cmd = [nv, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s%s" % (r.stdout, r.stderr))
-    os.replace(tmp, LIB_PATH)
-    return LIB_PATH
+    os.replace(tmp, lib_path)
+    return lib_path
+
+
+def build_all(force: bool = False, verbose: bool = False):
+    """Both libraries, the normal and the checked build, compiled side by side
+    (their units share one machine's cores); returns the two paths."""
+    with cf.ThreadPoolExecutor(max_workers=2) as ex:
+        normal = ex.submit(build, force, verbose)
+        checked = ex.submit(build, force, verbose, (), True)
+        return normal.result(), checked.result()
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv,
+                checked="--checked" in sys.argv))

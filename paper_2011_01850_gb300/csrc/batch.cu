@@ -488,6 +488,10 @@ gmres_status gmres_batch_solve(gmres_batch_t B, const double *rhs, double *x, in
         CK(cudaMemcpyAsync(x, dx, sizeof(double) * B->nrows, cudaMemcpyDeviceToHost, B->stream));
         CK(cudaStreamSynchronize(B->stream));
     }
+#ifdef GMRES_CHECKS
+    if (st != GMRES_ERR_CUDA && check_word_take(B->stream) != 0)
+        st = GMRES_ERR_INDEX;
+#endif
     if (info)
         info->time_ms =
             std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0)

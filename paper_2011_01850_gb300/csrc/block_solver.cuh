@@ -126,12 +126,12 @@ struct BlockParams {
     int stall_w = 1;
 };
 
-// w[row] = A x for the system's rows, L lanes per row.
+// w[row] = A x for the system's rows rb..n-1 (of ncol), L lanes per row.
 template <class T, class XT, int L>
 __device__ __forceinline__ void block_spmv(const int *__restrict__ rowptr,
                                            const int *__restrict__ colind,
                                            const T *__restrict__ a, const XT *x, float xinv, T *y,
-                                           int rb, int n) {
+                                           int rb, int n, int ncol) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int nw = blockDim.x >> 5;
     const int G = 32 / L, gl = lane % L, gi = lane / L;
@@ -141,7 +141,7 @@ __device__ __forceinline__ void block_spmv(const int *__restrict__ rowptr,
         if (row < n) {
             int beg = rowptr[row], end = rowptr[row + 1];
             for (int k = beg + gl; k < end; k += L)
-                acc += a[k] * (T)Basis<XT>::ld(x + colind[k], xinv);
+                acc += a[k] * (T)Basis<XT>::ld(x + chk_col(colind[k], ncol), xinv);
         }
 #pragma unroll
         for (int off = L / 2; off > 0; off >>= 1)
@@ -220,7 +220,7 @@ __device__ void team_solve_one(const BlockSys<T, VT> &S, const BlockParams &P, B
                 if (row < re) {
                     int beg = S.rowptr[row], end = S.rowptr[row + 1];
                     for (int k = beg + gl; k < end; k += L)
-                        acc += S.a64[k] * S.x[S.colind[k]];
+                        acc += S.a64[k] * S.x[chk_col(S.colind[k], S.n)];
                 }
 #pragma unroll
                 for (int off = L / 2; off > 0; off >>= 1)
@@ -274,7 +274,7 @@ __device__ void team_solve_one(const BlockSys<T, VT> &S, const BlockParams &P, B
         for (;;) {
             const int c = j;
             const VT *vj = S.V + (size_t)c * S.ldv;
-            block_spmv<T, VT, L>(S.rowptr, S.colind, S.a, vj, S.vinv, S.w, rb, re);
+            block_spmv<T, VT, L>(S.rowptr, S.colind, S.a, vj, S.vinv, S.w, rb, re, S.n);
             __syncthreads();
             // ||A v_j|| (breakdown reference)
             T w0 = 0;

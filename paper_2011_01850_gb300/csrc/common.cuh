@@ -104,6 +104,44 @@ __device__ __forceinline__ float wsqrt(float v) { return sqrtf(v); }
 __device__ __forceinline__ bool finite_d(double v) { return isfinite(v); }
 
 // ---------------------------------------------------------------------------
+// The checked build (compiled with -DGMRES_CHECKS, in place of a memory
+// sanitizer): every column index a gather kernel reads x with is tested
+// against the system's columns [0, ncol) before the load.  A column outside
+// is counted in this translation unit's check word and replaced by column 0,
+// so the load stays inside x.  The entry points that launch these kernels
+// read and clear the word after their last synchronize and return
+// GMRES_ERR_INDEX when it was set.  Without the flag the check is the
+// identity and costs nothing.
+// ---------------------------------------------------------------------------
+#ifdef GMRES_CHECKS
+static __device__ unsigned gmres_check_word;
+
+__device__ __forceinline__ int chk_col(int c, int ncol) {
+    if ((unsigned)c >= (unsigned)ncol) {
+        atomicAdd(&gmres_check_word, 1u);
+        return 0;
+    }
+    return c;
+}
+
+// Host side: the number of bad columns this translation unit's kernels met
+// since the last call, then cleared (synchronizes st).
+static inline unsigned check_word_take(cudaStream_t st) {
+    unsigned v = 0;
+    const unsigned z = 0;
+    if (cudaMemcpyFromSymbolAsync(&v, gmres_check_word, sizeof(v), 0, cudaMemcpyDeviceToHost,
+                                  st) != cudaSuccess ||
+        cudaMemcpyToSymbolAsync(gmres_check_word, &z, sizeof(z), 0, cudaMemcpyHostToDevice, st) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return ~0u;  // the check itself failed: report it as a violation
+    return v;
+}
+#else
+__device__ __forceinline__ int chk_col(int c, int) { return c; }
+#endif
+
+// ---------------------------------------------------------------------------
 // Deterministic reductions.  The xor-butterfly gives the same association
 // order on every run, so repeated solves are bitwise reproducible.
 // ---------------------------------------------------------------------------

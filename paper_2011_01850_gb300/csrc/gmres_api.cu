@@ -1184,6 +1184,7 @@ const char *gmres_status_str(gmres_status s) {
     case GMRES_ERR_BREAKDOWN: return "breakdown without progress";
     case GMRES_ERR_TIMEOUT: return "device wait timed out";
     case GMRES_ERR_OOM: return "out of device memory";
+    case GMRES_ERR_INDEX: return "column index outside its system (checked build)";
     }
     return "unknown status";
 }
@@ -1491,6 +1492,10 @@ gmres_status gmres_solve(gmres_t h, const double *b, double *x, int32_t m, doubl
     }
     CK(cudaStreamSynchronize(h->stream));
     h->timer.on = false;
+#ifdef GMRES_CHECKS
+    if (check_word_take(h->stream) != 0)
+        st = GMRES_ERR_INDEX;
+#endif
     info->time_ms =
         std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     return st;
@@ -1510,7 +1515,19 @@ gmres_status gmres_spmv(gmres_t h, const void *x, void *y, gmres_precision prec)
         CK(launch_spmv_any<float>(h, h->opts.spmv_lanes ? h->opts.spmv_lanes : h->lanes32,
                                   (const float *)x, (float *)y));
     CK(cudaStreamSynchronize(h->stream));
+#ifdef GMRES_CHECKS
+    if (check_word_take(h->stream) + sell_check_take(h->stream) != 0)
+        return GMRES_ERR_INDEX;
+#endif
     return GMRES_OK;
+}
+
+int32_t gmres_checks_enabled(void) {
+#ifdef GMRES_CHECKS
+    return 1;
+#else
+    return 0;
+#endif
 }
 
 gmres_status gmres_residual(gmres_t h, const double *b, const double *x, double *z,

@@ -237,10 +237,10 @@ __device__ __forceinline__ T csr_row_g(const int *__restrict__ rowptr,
         // sequential order of k
         for (; k < end; k += 4 * L) {
             const bool p1 = k + L < end, p2 = k + 2 * L < end, p3 = k + 3 * L < end;
-            const int c0 = __ldg(colind + k);
-            const int c1 = p1 ? __ldg(colind + k + L) : c0;
-            const int c2 = p2 ? __ldg(colind + k + 2 * L) : c0;
-            const int c3 = p3 ? __ldg(colind + k + 3 * L) : c0;
+            const int c0 = chk_col(__ldg(colind + k), n);
+            const int c1 = p1 ? chk_col(__ldg(colind + k + L), n) : c0;
+            const int c2 = p2 ? chk_col(__ldg(colind + k + 2 * L), n) : c0;
+            const int c3 = p3 ? chk_col(__ldg(colind + k + 3 * L), n) : c0;
             const T a0 = (T)a(k);
             const T a1 = p1 ? (T)a(k + L) : T(0);
             const T a2 = p2 ? (T)a(k + 2 * L) : T(0);

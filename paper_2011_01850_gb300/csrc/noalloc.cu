@@ -232,6 +232,10 @@ extern "C" gmres_status gmres_solve_noalloc(int32_t n, const int32_t *rowptr,
                                 s, info);
         break;
     }
+#ifdef GMRES_CHECKS
+    if (st != GMRES_ERR_CUDA && check_word_take(s) != 0)
+        st = GMRES_ERR_INDEX;
+#endif
     if (info)
         info->time_ms =
             std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0)

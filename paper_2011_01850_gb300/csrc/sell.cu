@@ -202,6 +202,10 @@ cudaError_t sell_spmv_plain(gmres_handle *h, const T *x, T *y) {
     return cudaGetLastError();
 }
 
+#ifdef GMRES_CHECKS
+unsigned sell_check_take(cudaStream_t st) { return check_word_take(st); }
+#endif
+
 template cudaError_t sell_spmv_plain<float>(gmres_handle *, const float *, float *);
 template cudaError_t sell_spmv_plain<double>(gmres_handle *, const double *, double *);
 

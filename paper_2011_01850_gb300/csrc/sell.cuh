@@ -71,7 +71,7 @@ __device__ __forceinline__ T sell_row(const int *__restrict__ sptr,
 #pragma unroll
         for (int g = 0; g < SELL_G; ++g) {
             const bool p = k + g < len;
-            c[g] = p ? col(i + g * SELL_C, row) : row;
+            c[g] = p ? chk_col(col(i + g * SELL_C, row), n) : row;
             av[g] = p ? (T)a(i + g * SELL_C) : T(0);
         }
 #pragma unroll

@@ -28,3 +28,9 @@ cudaError_t sell_spmv_plain(gmres_handle *h, const T *x, T *y);
 
 // Device bytes the sliced copy holds (0 when there is none).
 int64_t sell_bytes(const gmres_handle *h);
+
+#ifdef GMRES_CHECKS
+// Checked build: bad columns met by this file's kernels since the last call
+// (then cleared; synchronizes st).
+unsigned sell_check_take(cudaStream_t st);
+#endif

@@ -15,13 +15,17 @@ import numpy as np
 
 from . import build as _build
 
-LIB_PATH = _build.LIB_PATH
+# GMRES_GB300_CHECKS=1 in the environment loads the checked build instead
+# (column indices tested in the kernels; gmres_checks_enabled)
+CHECKED = os.environ.get("GMRES_GB300_CHECKS") == "1"
+LIB_PATH = _build.LIB_CHECKED_PATH if CHECKED else _build.LIB_PATH
 
 # enums (include/gmres_gb300.h)
 ORTHO_MGS, ORTHO_CGSR = 0, 1
 FP64, MIXED, MIXED_BF16, MIXED_FP16, MIXED_LIMITED = 0, 1, 2, 3, 4
 OK, MAXITER, ERR_ARG, ERR_CUDA, ERR_NONFINITE, ERR_BREAKDOWN, ERR_TIMEOUT, ERR_OOM = (
     0, 1, -1, -2, -3, -4, -5, -6)
+ERR_INDEX = -7
 CREATE_DEVICE_PTRS, CREATE_TRANSPOSE, CREATE_SPLIT = 1, 2, 4
 PATH_AUTO, PATH_GRID, PATH_BLOCK = 0, 1, 2
 PRECOND_NONE, PRECOND_SPAI, PRECOND_ILU0 = 0, 1, 2
@@ -122,6 +126,7 @@ SIGNATURES = {
     "gmres_arnoldi_step": (_st, [_vp, _vp, _i32, _i32, _i32, _vp, _vp]),
     "gmres_autotune": (_st, [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
     "gmres_spmv_format": (_st, [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
+    "gmres_checks_enabled": (_i32, []),
     "gmres_memory_bytes": (_st, [_vp, _i32, _i32, ctypes.POINTER(ctypes.c_int64),
                                  ctypes.POINTER(ctypes.c_int64)]),
     "gmres_orth_norms": (_st, [_vp, _vp, _i32]),
@@ -160,8 +165,9 @@ def lib():
     global _lib
     if _lib is None:
         if not os.path.exists(LIB_PATH):
-            raise RuntimeError("libgmres_gb300.so is missing: run paper_2011_01850_gb300.build "
-                               "(or __graft_entry__.build()) first; there is no fallback")
+            raise RuntimeError("%s is missing: run paper_2011_01850_gb300.build "
+                               "(or __graft_entry__.build()) first; there is no fallback"
+                               % os.path.basename(LIB_PATH))
         L = ctypes.CDLL(LIB_PATH)
         for name, (res, args) in SIGNATURES.items():
             fn = getattr(L, name)
@@ -306,6 +312,11 @@ def gmres_autotune(h):
     b = ctypes.c_int32()
     _check(lib().gmres_autotune(h, ctypes.byref(a), ctypes.byref(b)), "gmres_autotune")
     return a.value, b.value
+
+
+def gmres_checks_enabled():
+    """1 when the loaded library is the checked build (GMRES_GB300_CHECKS=1)."""
+    return int(lib().gmres_checks_enabled())
 
 
 def gmres_spmv_format(h):

@@ -52,11 +52,24 @@ def test_binding_covers_header():
     assert set(G.SIGNATURES) == declared_functions()
 
 
+def test_checked_build_exports_and_reports(so):
+    """The checked build (-DGMRES_CHECKS) exports the same entry points and
+    says it is the checked build; the normal build says it is not."""
+    L = ctypes.CDLL(B.build(checked=True))
+    missing = [n for n in sorted(declared_functions()) if not hasattr(L, n)]
+    assert not missing, missing
+    for lib_, want in ((L, 1), (so, 0)):
+        lib_.gmres_checks_enabled.restype = ctypes.c_int32
+        lib_.gmres_checks_enabled.argtypes = []
+        assert lib_.gmres_checks_enabled() == want
+
+
 def test_host_only_calls(so):
     # calls that touch no device: status strings, version, default options
     G._lib = None
     assert G.gmres_status_str(G.OK) == "converged"
     assert G.gmres_status_str(G.ERR_ARG) == "invalid argument"
+    assert "checked build" in G.gmres_status_str(G.ERR_INDEX)
     assert "sm_103a" in G.gmres_version()
     o = G.gmres_default_opts()
     assert o.tau < 0 and o.inner_factor == 0.5 and o.repeat_first == -1
