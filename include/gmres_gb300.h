@@ -260,8 +260,10 @@ gmres_status gmres_create(gmres_t *out, int32_t n, const int32_t *rowptr, const 
 void gmres_destroy(gmres_t h);
 
 /* Replace A's values (same pattern; nnz binary64 values, host or device).
- * Drops the learned preconditioner and cached derived data of the old values.
- * Errors: GMRES_ERR_ARG, GMRES_ERR_NONFINITE (host values), GMRES_ERR_CUDA. */
+ * Drops the learned preconditioner and cached derived data of the old values
+ * (A^T, the ILU(0) factors); A's sliced copy, when one is built, takes the
+ * new values.  Synchronizes the handle's stream.  Errors: GMRES_ERR_ARG,
+ * GMRES_ERR_NONFINITE (host values), GMRES_ERR_CUDA. */
 gmres_status gmres_set_values(gmres_t h, const double *vals);
 
 /* Change the stream used by later calls. */
@@ -515,7 +517,6 @@ gmres_status gmres_solve_noalloc(int32_t n, const int32_t *rowptr, const int32_t
 gmres_status gmres_memory_bytes(gmres_t h, int32_t m, gmres_precision prec, int64_t *matrix_bytes,
                                 int64_t *workspace_bytes);
 
-/* Static text for a status code. */
 /* ILU(0) of the handle's A, the paper's preconditioner (Sec. 4): L (unit
  * lower) and U on A's sparsity pattern, factored on the GPU one level of the
  * row-dependency graph per launch (the levels come from a host analysis of
@@ -554,6 +555,7 @@ gmres_status gmres_ilu_apply(gmres_t h, const void *z, void *out, gmres_precisio
  * separate interface for them. */
 gmres_status gmres_orth_norms(gmres_t h, double *out, int32_t count);
 
+/* Static text for a status code. */
 const char *gmres_status_str(gmres_status s);
 
 /* Library version string. */
